@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Frame benchmark of the GB300 ray tracer.
+
+One step = one frame of the medium workload (64 instances of 4 procedural
+meshes, 158,964 unique triangles, 1920x1080, 4 point lights, max depth 4):
+seeded per-instance motion, a full TLAS rebuild (float64 instance inverses,
+Arvo boxes, Morton codes, radix sort, Karras hierarchy, refit), then the
+Whitted render (ray generation, closest-hit traversal, shading and queue
+compaction, any-hit shadow traversal with accumulation) into an RGBA32F
+image.  The four BLAS are built once per scene (their build time is reported
+in config.blas_build_ms).
+
+value  = traced rays (closest-hit + shadow) per second over all ranks, inputs
+         resident in HBM, L2 flushed (256 MiB write) before every timed frame.
+e2e    = the same frames with the instance transforms copied host->device from
+         pinned memory and the image copied back to pinned memory, inside the
+         timed region.
+--impl reference runs the float64 CPU oracle on the same frames.
+
+Multi-GPU (torchrun): replicas, each rank renders its own frames; value is
+the sum of all ranks' rays over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenegen as g  # noqa: E402
+
+METRIC = "Mrays/s closest-hit at 1 GB300 vs plain path & oracle; p50/p99 frame latency"
+WORKLOAD = ("medium: 64 instances of 4 procedural meshes (UV sphere 80x40, icosphere s5, cube, 256^2 heightfield; "
+            "158,964 unique tris) with seeded affine transforms in a 100^3 box, materials diffuse/mirror/glass "
+            "60/20/20%, 4 point lights, 1920x1080, max_depth 4; per frame seeded motion + full TLAS rebuild + render")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU baseline budget (wall seconds)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------- clocks
+
+REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="rg_clocks_", suffix=".csv")
+        os.close(fd)
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.send_signal(signal.SIGTERM)
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, v in zip(REASONS, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def traffic_record():
+    """Per-ray DRAM bytes of the closest-hit traversal from the committed ncu
+    summary, valid only while the traversal source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "trace_closest_medium.md")
+    src = os.path.join(ROOT, "paper_2001_09792_gb300", "csrc", "trace.cu")
+    try:
+        txt = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        m = re.search(r"dram_bytes_per_closest_ray:\s*([0-9.]+)", txt)
+        s = re.search(r"trace_cu_sha256_16:\s*([0-9a-f]+)", txt)
+        if m and s and s.group(1) == sha:
+            return float(m.group(1))
+    except OSError:
+        pass
+    return None
+
+
+def frame_motions(scene, n):
+    return [g.motion(scene.M, k) for k in range(n)]
+
+
+# ---------------------------------------------------------------- native arm
+
+def run_native(args, world, rank, local):
+    import torch
+    import paper_2001_09792_gb300 as rg
+    from paper_2001_09792_gb300 import _build
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+
+    s = g.medium_scene()
+    W, H, D = s.width, s.height, s.max_depth
+    n_frames = args.warmup + args.steps
+    motions = frame_motions(s, n_frames)
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gs = rg.GpuScene(s, flags=rg.RG_SCENE_TIMING)
+    torch.cuda.synchronize()
+    blas_build_ms = (time.perf_counter() - t0) * 1e3  # four BLAS + first TLAS, host-timed incl. uploads
+    blas_ids = [gs.blas[m] for m in s.mesh_id]
+    inst_host = [rg.pack_instances(M, blas_ids, s.material_id) for M in motions]
+    inst_dev = [torch.from_numpy(x).cuda() for x in inst_host]
+    img = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > 129 MB L2
+    cam = rg.make_camera(s.camera)
+    stream = torch.cuda.current_stream()
+
+    def frame(k):
+        rg.rg_tlas_build(gs.h, inst_dev[k])
+        rg.rg_render(gs.h, cam, W, H, D, out=img)
+
+    for k in range(args.warmup):
+        frame(k)
+    torch.cuda.synchronize()
+
+    # algorithmic work per closest-hit ray: one counting frame on a second scene
+    with rg.GpuScene(s, flags=rg.RG_SCENE_COUNT) as gc:
+        rg.rg_tlas_build(gc.h, torch.from_numpy(inst_host[args.warmup]).cuda())
+        rg.rg_reset_stats(gc.h)
+        rg.rg_render(gc.h, cam, W, H, D)
+        cst = rg.rg_get_stats(gc.h)
+
+    rg.rg_sync(gs.h)
+    rg.rg_reset_stats(gs.h)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(gpu_index(local))
+    clocks.start()
+    times = []
+    for k in range(args.warmup, n_frames):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        frame(k)
+        e1.record(stream)
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in times]
+    st = rg.rg_get_stats(gs.h)
+    rg.rg_sync(gs.h)
+    rays = st["closest_rays"] + st["shadow_rays"]
+    total_s = sum(ms) / 1e3
+
+    # e2e: host instance transforms in, host image out, through the same calls
+    e2e = None
+    if not args.no_e2e:
+        pin_in = [torch.from_numpy(x).pin_memory() for x in inst_host]
+        pin_out = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
+        dev_in = torch.empty_like(inst_dev[0])
+        rg.rg_reset_stats(gs.h)
+        torch.cuda.synchronize()
+        ev = []
+        for k in range(args.warmup, n_frames):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dev_in.copy_(pin_in[k], non_blocking=True)
+            rg.rg_tlas_build(gs.h, dev_in)
+            rg.rg_render(gs.h, cam, W, H, D, out=img)
+            pin_out.copy_(img, non_blocking=True)
+            e1.record(stream)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        e2e_ms = [a.elapsed_time(b) for a, b in ev]
+        st2 = rg.rg_get_stats(gs.h)
+        e2e_rays = st2["closest_rays"] + st2["shadow_rays"]
+        e2e = (e2e_rays, sum(e2e_ms) / 1e3, inst_host[0].nbytes, W * H * 16)
+
+    # aggregate over ranks
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_s, float(rays)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        total_s_all, rays_all = float(tmax[0]), float(t[1])
+        if e2e:
+            e = torch.tensor([e2e[1], float(e2e[0])], dtype=torch.float64, device="cuda")
+            dist.all_reduce(e[:1], op=dist.ReduceOp.MAX)
+            dist.all_reduce(e[1:], op=dist.ReduceOp.SUM)
+            e2e = (float(e[1]), float(e[0]), e2e[2], e2e[3])
+    else:
+        total_s_all, rays_all = total_s, float(rays)
+
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        cr = max(cst["closest_rays"], 1)
+        bytes_per_ray = 32 + 16 + 64 * cst["node_visits"] / cr + 48 * cst["tri_tests"] / cr + 80 * cst["inst_entries"] / cr
+        launch_ms = st["trace_ms"] / max(st["trace_launches"], 1)
+        rays_per_launch = st["closest_rays"] / max(st["trace_launches"], 1)
+        achieved = bytes_per_ray * rays_per_launch / (launch_ms / 1e3) / 1e9
+        tr = traffic_record()
+        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": None if tr is None else round(tr * rays_per_launch),
+                    "kernel": "k_trace closest-hit (render)", "peak_kind": peak_kind,
+                    "algorithmic_bytes_per_ray": round(bytes_per_ray, 1),
+                    "nodes_per_ray": round(cst["node_visits"] / cr, 2), "tris_per_ray": round(cst["tri_tests"] / cr, 2),
+                    "inst_per_ray": round(cst["inst_entries"] / cr, 3), "avg_launch_ms": round(launch_ms, 4),
+                    "trace_share_of_frame": round(st["trace_ms"] / sum(ms), 3)}
+        ms_sorted = sorted(ms)
+        out = {
+            "metric": METRIC,
+            "value": round(rays_all / total_s_all / 1e6, 2),
+            "unit": "Mrays/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(total_s_all * 1e3 / args.steps, 3),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic (seeded procedural scene, random-free shading)",
+            "config": {"workload": WORKLOAD, "width": W, "height": H, "max_depth": D, "lights": 4,
+                       "instances": s.n_instances, "instanced_tris": s.instanced_tris(),
+                       "rays_per_step": round(rays / args.steps), "closest_rays_per_step": round(st["closest_rays"] / args.steps),
+                       "shadow_rays_per_step": round(st["shadow_rays"] / args.steps),
+                       "closest_mrays_s": round(st["closest_rays"] / total_s / 1e6, 2),
+                       "p50_ms": round(ms_sorted[len(ms) // 2], 3),
+                       "p99_ms": round(ms_sorted[min(len(ms) - 1, math.ceil(0.99 * len(ms)) - 1)], 3),
+                       "blas_build_ms": round(blas_build_ms, 2), "l2": "flushed before each step (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "gpu_launches": int(st["kernel_launches"]),
+        }
+        if clk:
+            out["clocks"] = clk
+        if e2e:
+            out["e2e"] = {"value": round(e2e[0] / e2e[1] / 1e6, 2), "unit": "Mrays/s",
+                          "h2d_bytes_per_step": int(e2e[2]), "d2h_bytes_per_step": int(e2e[3])}
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(s, motions[args.warmup:], args.cpu_seconds)
+        print(json.dumps(out), flush=True)
+    gs.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def gpu_index(local):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        parts = [p.strip() for p in vis.split(",")]
+        if local < len(parts) and parts[local].isdigit():
+            return int(parts[local])
+    return local
+
+
+# ---------------------------------------------------------------- oracle arms
+
+def oracle_frames(scene, motions, budget_s, min_frames=1):
+    """Render whole frames with the float64 oracle until the budget is spent."""
+    import oracle
+    O = oracle.OracleScene(scene)
+    rays = 0
+    frames = 0
+    t0 = time.perf_counter()
+    per_frame = []
+    for M in motions:
+        f0 = time.perf_counter()
+        O.set_instances(M, scene.mesh_id, scene.material_id)
+        r = O.render(scene.camera, scene.width, scene.height, scene.max_depth)
+        per_frame.append(time.perf_counter() - f0)
+        rays += r["closest_rays"] + r["shadow_rays"]
+        frames += 1
+        if frames >= min_frames and time.perf_counter() - t0 >= budget_s:
+            break
+    return rays, time.perf_counter() - t0, frames, per_frame
+
+
+def cpu_baseline(scene, motions, budget_s):
+    cores = len(os.sched_getaffinity(0))
+    rays, secs, frames, _ = oracle_frames(scene, motions, budget_s)
+    return {"value": round(rays / secs / 1e6, 3), "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+            "sample": f"{frames} whole frame(s) of the same workload (float64, {cores} threads), {secs:.1f} s"}
+
+
+def run_reference(args, world, rank, local):
+    if rank != 0:
+        return
+    s = g.medium_scene()
+    n_frames = args.warmup + args.steps
+    motions = frame_motions(s, n_frames)
+    # bounded sample per step: a seeded subset of the frame's pixels
+    import oracle
+    O = oracle.OracleScene(s)
+    n_pix = s.width * s.height
+    sample = max(1, n_pix // 8)
+    rng = np.random.default_rng(7)
+    times, rays = [], 0
+    for k in range(n_frames):
+        pix = np.sort(rng.choice(n_pix, sample, replace=False)).astype(np.uint32)
+        t0 = time.perf_counter()
+        O.set_instances(motions[k], s.mesh_id, s.material_id)
+        r = O.render(s.camera, s.width, s.height, s.max_depth, pixels=pix)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            rays += r["closest_rays"] + r["shadow_rays"]
+    total = sum(times)
+    cores = len(os.sched_getaffinity(0))
+    value = round(rays / total / 1e6, 3)
+    ts = sorted(times)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total * 1e3 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded procedural scene)",
+        "config": {"workload": WORKLOAD, "width": s.width, "height": s.height, "max_depth": s.max_depth,
+                   "sample_pixels_per_step": sample, "p50_ms": round(ts[len(ts) // 2] * 1e3, 3),
+                   "p99_ms": round(ts[-1] * 1e3, 3), "parallelism": "host threads"},
+        "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": "Mrays/s",
+                         "sample": f"{sample} seeded pixels of each 1920x1080 frame, float64, {cores} threads"},
+        "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank, local)
+    else:
+        run_native(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

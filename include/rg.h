@@ -1,0 +1,217 @@
+/*
+ * rg.h -- C ABI of the GB300 ray tracer (librg.so).
+ *
+ * The method is the two-step ray tracing model of "Running on Raygun"
+ * (Hirsch & Thoman, Sec. 1): first a two-layered acceleration structure is
+ * built from the models' vertices and their transformation matrices (here:
+ * one bottom-level BVH per mesh, rg_blas_build, and a top-level BVH over
+ * transformed instances, rg_tlas_build / rg_tlas_refit); then rays are
+ * dispatched, and per ray a closest-hit, any-hit or miss result is produced
+ * (rg_trace_rays).  rg_render runs the paper's Whitted-style renderer on top
+ * (Sec. 2.1: multiple objects, shadow casting, reflection and refraction;
+ * Sec. 1: recursion to a fixed depth, per-ray payload).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns rg_status (RG_OK = 0).  On failure the call leaves
+ *    its outputs unspecified and rg_last_error() returns a message for the
+ *    calling thread.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Device work is asynchronous on it.  Errors detected by a
+ *    kernel (stack overflow, iteration cap, singular transform) are recorded
+ *    in the scene and returned by the next rg_sync() on that scene.
+ *  - Pointers named d_* are device pointers, h_* are host pointers.  The
+ *    caller owns every buffer it passes; the library never frees them and
+ *    keeps no pointer to them after the call returns (rg_blas_build copies
+ *    the geometry it needs).  The library owns the acceleration structures,
+ *    ray queues and counters it allocates; rg_scene_destroy frees them.
+ *  - All device geometry is float32.  float64 is used on the device only to
+ *    invert instance transforms.
+ *  - Calls on one scene must not run concurrently from several host threads.
+ */
+#ifndef RG_H
+#define RG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t rg_status;
+enum {
+    RG_OK = 0,
+    RG_ERR_INVALID_ARG = 1, /* bad pointer, size, id or flag */
+    RG_ERR_OOM = 2,         /* device allocation failed */
+    RG_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    RG_ERR_NOT_BUILT = 4,   /* trace/render/refit before rg_tlas_build */
+    RG_ERR_STACK = 5,       /* traversal stack overflow (ray abandoned as a miss) */
+    RG_ERR_TIMEOUT = 6,     /* a device loop hit its iteration cap */
+    RG_ERR_SINGULAR = 7     /* an instance transform is not invertible */
+};
+
+typedef struct rg_scene rg_scene;
+
+/* A ray: origin, parametric interval [tmin, tmax] (closed), direction.  The
+ * direction need not be unit length; t is measured in units of |d|.  32 B. */
+typedef struct { float o[3]; float tmin; float d[3]; float tmax; } rg_ray;
+
+/* A hit record, 20 B.  instance = index into the array given to
+ * rg_tlas_build; prim = triangle index within that instance's mesh; t the
+ * ray parameter; u, v the barycentric weights of the triangle's second and
+ * third vertex (the first has 1-u-v).  Miss: instance = prim = 0xFFFFFFFF,
+ * t = +inf, u = v = 0. */
+typedef struct { uint32_t instance, prim; float t, u, v; } rg_hit;
+
+/* An instance: row-major 3x4 object-to-world matrix [A | t] applied as
+ * world = A * object + t; the mesh (BLAS id) it places; its material; mask is
+ * reserved (ignored). 64 B. */
+typedef struct { float m[3][4]; uint32_t blas_id, material_id, mask, pad; } rg_instance;
+
+/* Pinhole camera: vertical field of view in degrees, aspect = w/h. */
+typedef struct { float eye[3], target[3], up[3], vfov_deg; } rg_camera;
+
+enum { RG_MAT_DIFFUSE = 0, RG_MAT_MIRROR = 1, RG_MAT_GLASS = 2 };
+/* Material: diffuse albedo / mirror tint; glass uses ior (tint ignored). */
+typedef struct { uint32_t type; float albedo[3]; float ior; float pad[3]; } rg_material;
+
+/* Point light: position and RGB intensity (no distance falloff). */
+typedef struct { float pos[3]; float intensity[3]; } rg_light;
+
+/* Scene-wide shading constants.  flags: RG_SCENE_TIMING records CUDA events
+ * around every traversal launch; RG_SCENE_COUNT makes rg_render's traversals
+ * count node visits, triangle tests and instance entries (slower; see
+ * rg_get_stats). */
+enum { RG_SCENE_TIMING = 1u, RG_SCENE_COUNT = 2u };
+typedef struct { float background[3]; float ambient; uint32_t flags; } rg_scene_desc;
+
+/* Counters since the last rg_reset_stats. */
+typedef struct {
+    uint64_t closest_rays;    /* rays traced by closest-hit traversal */
+    uint64_t shadow_rays;     /* rays traced by any-hit traversal */
+    uint64_t trace_launches;  /* timed closest-hit traversal launches */
+    double trace_ms;          /* summed device time of those launches (RG_SCENE_TIMING) */
+    uint64_t any_launches;    /* timed any-hit traversal launches */
+    double any_ms;            /* summed device time of those launches */
+    uint64_t node_visits;     /* counting traversals only (RG_TRACE_STATS, RG_SCENE_COUNT), */
+    uint64_t tri_tests;       /*   closest-hit: BVH nodes fetched, triangles tested, */
+    uint64_t inst_entries;    /*   instance (BLAS) entries */
+    uint64_t any_node_visits; /*   the same for any-hit traversals */
+    uint64_t any_tri_tests;
+    uint64_t any_inst_entries;
+    uint64_t kernel_launches; /* kernels launched by the library (all scenes of the process) */
+} rg_stats;
+
+/* ---- scene lifetime ---------------------------------------------------- */
+
+/* Create an empty scene on the current CUDA device.  desc may be NULL
+ * (background (0.2,0.3,0.5), ambient 0.1, no flags). */
+rg_status rg_scene_create(rg_scene** out, const rg_scene_desc* desc);
+/* Free every device allocation of the scene (synchronises the device). */
+rg_status rg_scene_destroy(rg_scene* scene);
+
+/* ---- step 1 of the paper's model: the two-layered structure (Sec. 1) ---- */
+
+enum { RG_MORTON30 = 0u, RG_MORTON63 = 1u };
+/* Bottom-level BVH of one triangle mesh (LBVH: Morton codes of triangle
+ * centroids, radix sort, Karras hierarchy, atomic bottom-up box refit).
+ * d_vtx: nv x float3 (12 B each); d_idx: nt x uint3 vertex indices (CCW =
+ * outward).  flags: RG_MORTON30 (10 bits/axis, u32 keys) or RG_MORTON63 (21
+ * bits/axis, u64 keys).  Writes the new BLAS id to *blas_id.  nt >= 1;
+ * indices must be < nv (checked on the device: RG_ERR_INVALID_ARG at
+ * rg_sync).  The mesh is copied; d_vtx/d_idx may be freed after the call
+ * once the stream has passed it. */
+rg_status rg_blas_build(rg_scene* scene, const float* d_vtx, uint32_t nv, const uint32_t* d_idx, uint32_t nt,
+                        uint32_t flags, uint32_t* blas_id, void* stream);
+
+/* Top-level BVH over n instances (device array of rg_instance).  Inverts
+ * every transform in float64 (RG_ERR_SINGULAR at rg_sync if |det| is 0),
+ * bounds each instance with Arvo's method in outward-rounded float32, and
+ * builds an LBVH over the instance boxes (30-bit Morton). */
+rg_status rg_tlas_build(rg_scene* scene, const rg_instance* d_inst, uint32_t n, void* stream);
+
+/* Update the instance transforms of the last rg_tlas_build (the
+ * "update" mode of an acceleration structure): same n (checked on the host,
+ * RG_ERR_INVALID_ARG) and the same blas_id per instance (checked on the
+ * device, RG_ERR_INVALID_ARG at rg_sync).  Recomputes the instance inverses
+ * and boxes and the node boxes; the topology is unchanged. */
+rg_status rg_tlas_refit(rg_scene* scene, const rg_instance* d_inst, uint32_t n, void* stream);
+
+/* Materials (host array, copied) and point lights (host array, copied). */
+rg_status rg_scene_set_materials(rg_scene* scene, const rg_material* h_mat, uint32_t n);
+rg_status rg_scene_set_lights(rg_scene* scene, const rg_light* h_lights, uint32_t n);
+
+/* ---- step 2: dispatch rays (Sec. 1) ------------------------------------ */
+
+enum {
+    RG_CLOSEST = 0u,       /* nearest hit in [tmin, tmax]; ties: smaller instance, then smaller prim */
+    RG_ANY = 1u,           /* any hit in [tmin, tmax] (shadow query); record of some hit or a miss */
+    RG_TRACE_BRUTE = 2u,   /* test every triangle of every instance (no BVH); for validation */
+    RG_TRACE_STATS = 4u    /* count node visits / triangle tests into rg_stats (slower) */
+};
+/* Trace n rays (device array d_rays) and write n hit records to d_hits.
+ * n may be 0. */
+rg_status rg_trace_rays(rg_scene* scene, const rg_ray* d_rays, uint32_t n, uint32_t flags, rg_hit* d_hits,
+                        void* stream);
+
+/* Whitted render into d_rgba (w*h*4 float32, row 0 = top, RGB linear
+ * radiance, A = 1 where the primary ray hit).  Primary rays through pixel
+ * centres; diffuse: ambient + unshadowed Lambert per light; mirror: tinted
+ * reflection; glass: Schlick-weighted reflection + refraction (total internal
+ * reflection beyond the critical angle); misses: background.  Reflection and
+ * refraction rays are spawned while the ray depth (primary = 1) is below
+ * max_depth.  Synchronises the stream once per depth level to size queues. */
+rg_status rg_render(rg_scene* scene, const rg_camera* h_cam, uint32_t w, uint32_t h, uint32_t max_depth,
+                    float* d_rgba, void* stream);
+
+/* Wait for the scene's stream work and return the first device-side error
+ * recorded since the last rg_sync (then clear it). */
+rg_status rg_sync(rg_scene* scene);
+rg_status rg_get_stats(rg_scene* scene, rg_stats* out);
+rg_status rg_reset_stats(rg_scene* scene);
+/* Message of the last failed call on this thread ("" if none). */
+const char* rg_last_error(void);
+
+/* ---- the build steps, exposed one by one (for validation) -------------- */
+
+/* Per-triangle box: d_lohi[6*i] = {lo.xyz, hi.xyz}, exact float32 min/max of
+ * the triangle's vertices. */
+rg_status rg_tri_bounds(const float* d_vtx, uint32_t nv, const uint32_t* d_idx, uint32_t nt, float* d_lohi,
+                        void* stream);
+/* Morton code of each box centroid c = (lo+hi)*0.5: per axis s = 2^b/(cmax-cmin)
+ * (q = 0 on an axis with cmax == cmin), q = clamp(floor((c-cmin)*s), 0, 2^b-1),
+ * bits interleaved x (most significant), y, z.  bits = 10 writes uint32 codes,
+ * bits = 21 uint64 codes.  d_cbounds (6 floats, may be NULL) receives the
+ * centroid bounds {cmin.xyz, cmax.xyz}. */
+rg_status rg_morton_codes(const float* d_lohi, uint32_t n, uint32_t bits, void* d_codes, float* d_cbounds,
+                          void* stream);
+/* Stable LSD radix sort (8-bit digits) of (key, value) pairs; key_bits = 32
+ * (uint32 keys, 4 passes) or 64 (uint64 keys, 8 passes).  Inputs are not
+ * modified.  Allocates temporary device memory on the stream. */
+rg_status rg_radix_sort_pairs(const void* d_keys, const uint32_t* d_vals, uint32_t n, uint32_t key_bits,
+                              void* d_keys_out, uint32_t* d_vals_out, void* stream);
+/* Binary radix tree over n >= 2 sorted keys (Karras 2012, Sec. 4): for internal
+ * node i (root 0) writes d_children[2i] / [2i+1]; a child with bit 31 set is
+ * leaf (child & 0x7FFFFFFF), else internal node `child`.  d_parents (2n-1,
+ * may be NULL): parent of internal node i at [i], of leaf j at [n-1+j]; the
+ * root's parent is 0xFFFFFFFF. */
+rg_status rg_karras(const void* d_sorted_keys, uint32_t n, uint32_t key_bits, uint32_t* d_children,
+                    uint32_t* d_parents, void* stream);
+
+/* Copy a built BLAS to host memory: h_nodes (nt-1) x 64 B nodes (float
+ * lo0[3], hi0[3], lo1[3], hi1[3], uint32 child0, child1, 2 x pad), h_tris
+ * nt x 48 B triangles in leaf order (v0.xyz, uint32 prim; v1.xyz, pad;
+ * v2.xyz, pad), *h_root the root reference (leaf refs have bit 31 set).
+ * Any output may be NULL.  Synchronises the device. */
+rg_status rg_blas_export(rg_scene* scene, uint32_t blas_id, void* h_nodes, void* h_tris, uint32_t* h_root);
+/* Copy the TLAS: h_nodes (n-1) x 64 B, h_wbox n x 6 floats (world box of
+ * instance i, in input order), h_inv n x 12 floats (float32 world-to-object
+ * 3x4 of instance i, input order), h_order n uint32 (input index of TLAS
+ * leaf j), *h_root.  Any output may be NULL.  Synchronises the device. */
+rg_status rg_tlas_export(rg_scene* scene, void* h_nodes, float* h_wbox, float* h_inv, uint32_t* h_order,
+                         uint32_t* h_root);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RG_H */

@@ -194,6 +194,7 @@ struct Scene {
 };
 
 constexpr double EPS32 = 5.9604644775390625e-08;  // 2^-24, float32 unit roundoff
+constexpr double kGrazeInv = 256.0;                // |cos| below 1/256 counts as grazing
 
 inline V3 xform_point(const double* m, V3 p) {
     return {m[0] * p.x + m[1] * p.y + m[2] * p.z + m[3], m[4] * p.x + m[5] * p.y + m[6] * p.z + m[7],
@@ -264,10 +265,12 @@ WT watertight(const RayPre& p, V3 o, V3 v0, V3 v1, V3 v2) {
 // point with an absolute position error of at most eta (object-space units):
 //   eta = kappa * 2^-24 * (|Minv||o| + |m| + t |Minv||d| + max|v|),
 // i.e. a few roundings of the largest magnitudes that enter the transformed
-// ray and the sheared vertices.  A triangle is
+// ray and the sheared vertices.  Moving the ray by eta moves its plane point
+// by up to eta_p = eta / |cos| (cos between the ray and the triangle normal;
+// capped at |cos| = 1/256, below which the hit counts as grazing).  A triangle is
 //   strict : the exact test accepts it (b_i >= 0, det != 0, t in range);
-//   outer  : the point lies within eta of the triangle (b_i h_i >= -eta);
-//   inner  : strict and at least eta inside every edge (b_i h_i >= eta).
+//   outer  : the point lies within eta_p of the triangle (b_i h_i >= -eta_p);
+//   inner  : strict, not grazing, and at least eta_p inside every edge.
 // A closest-hit ray is ambiguous when the float32 answer may differ from the
 // exact one: the exact winner is not inner, another outer candidate lies
 // within the distance tolerance of the winner, or there is no winner but an
@@ -320,14 +323,20 @@ struct Query {
             double eta = kappa * EPS32 * (E0 + std::fabs(t) * E1 + m.vmax);
             double e0 = b0 / m.inv_h[3 * prim], e1 = b1 / m.inv_h[3 * prim + 1], e2 = b2 / m.inv_h[3 * prim + 2];
             double cosv = std::fabs(dot(m.ng[prim], dd)) / dn;
-            double tau = rel_t * std::fabs(t) + (cosv > 0 ? eta / (cosv * dn) : INFINITY);
-            bool outer = e0 >= -eta && e1 >= -eta && e2 >= -eta;
+            // an offset eta of the ray moves its plane point by up to eta/|cos|
+            // within the plane (along the ray by eta/(|cos| |d|) in t); below
+            // |cos| = 1/kGrazeInv the band stops growing and the hit is never
+            // "inner" (so a grazing winner is always ambiguous)
+            bool grazing = cosv * kGrazeInv < 1.0;
+            double eta_p = eta * (grazing ? kGrazeInv : 1.0 / cosv);
+            double tau = rel_t * std::fabs(t) + eta_p / dn;
+            bool outer = e0 >= -eta_p && e1 >= -eta_p && e2 >= -eta_p;
             if (!outer) return;
             bool inside = (w.U >= 0 && w.V >= 0 && w.W >= 0) || (w.U <= 0 && w.V <= 0 && w.W <= 0);
             bool strict = inside && t >= t0 && t <= t1_cull;  // caller re-checks against tmax
-            bool inner = inside && e0 >= eta && e1 >= eta && e2 >= eta;
+            bool inner = inside && !grazing && e0 >= eta_p && e1 >= eta_p && e2 >= eta_p;
             double hmin_inv = std::max(m.inv_h[3 * prim], std::max(m.inv_h[3 * prim + 1], m.inv_h[3 * prim + 2]));
-            on_tri(Cand{t, k, prim, strict, inner, b1, b2, tau, eta * hmin_inv}, eta);
+            on_tri(Cand{t, k, prim, strict, inner, b1, b2, tau, eta_p * hmin_inv}, eta);
         };
         if (brute) {
             uint32_t nt = (uint32_t)(m.idx.size() / 3);
@@ -342,7 +351,8 @@ struct Query {
             V3 ext{m.box.hi[0] - c.x, m.box.hi[1] - c.y, m.box.hi[2] - c.z};
             tup = (norm(oo - c) + norm(ext)) / dn;
         }
-        double pad = kappa * EPS32 * (E0 + tup * E1 + m.vmax) * 2 + 1e-12 * (1 + m.vmax);
+        // a candidate's plane point lies within eta * kGrazeInv of its triangle
+        double pad = kGrazeInv * kappa * EPS32 * (E0 + tup * E1 + m.vmax) * 2 + 1e-12 * (1 + m.vmax);
         double tlo = t0 - 1e-3 * (amax(o) + 1.0);
         int stack[256];
         int sp = 0;
@@ -376,7 +386,7 @@ struct Query {
             }
             return;
         }
-        double pad = 1e-4 * (amax(o) + 1.0);
+        double pad = 1e-3 * (amax(o) + 1.0);
         double tlo = t0 - 1e-3 * (amax(o) + 1.0);
         int stack[256];
         int sp = 0;
@@ -386,7 +396,7 @@ struct Query {
             const Bvh::Node& nd = S.tlas.nodes[ni];
             double ext = 0;
             for (int a = 0; a < 3; ++a) ext = std::max(ext, nd.box.hi[a] - nd.box.lo[a]);
-            if (box_hit(nd.box, pad + 1e-4 * ext, o, d, tlo, cull) == INFINITY) continue;
+            if (box_hit(nd.box, pad + 1e-3 * ext, o, d, tlo, cull) == INFINITY) continue;
             if (nd.left < 0) {
                 for (int i = nd.first; i < nd.first + nd.count; ++i) {
                     visit_instance(S.tlas.items[i], o, d, t0, t1, false, on_tri);

@@ -1,0 +1,383 @@
+"""Python binding of librg, the GB300 ray tracer (see include/rg.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+kernels of librg.so.  PyTorch provides device memory and streams.  There is
+no CPU fallback: if librg.so is missing or the device is not a CUDA GPU the
+calls raise.
+
+Functions carry the C names (rg_scene_create, rg_blas_build, rg_tlas_build,
+rg_tlas_refit, rg_trace_rays, rg_render, ...).  Device buffers are torch
+tensors on the current CUDA device; uint32 data travels in int32 tensors and
+uint64 keys in int64 tensors (bit patterns unchanged).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librg.so")
+
+RG_OK = 0
+RG_ERR_INVALID_ARG, RG_ERR_OOM, RG_ERR_CUDA, RG_ERR_NOT_BUILT, RG_ERR_STACK, RG_ERR_TIMEOUT, RG_ERR_SINGULAR = range(1, 8)
+RG_MORTON30, RG_MORTON63 = 0, 1
+RG_CLOSEST, RG_ANY, RG_TRACE_BRUTE, RG_TRACE_STATS = 0, 1, 2, 4
+RG_SCENE_TIMING = 1
+RG_SCENE_COUNT = 2
+RG_MAT_DIFFUSE, RG_MAT_MIRROR, RG_MAT_GLASS = 0, 1, 2
+MISS = 0xFFFFFFFF
+
+# exported symbols, in include/rg.h order
+SYMBOLS = ["rg_scene_create", "rg_scene_destroy", "rg_blas_build", "rg_tlas_build", "rg_tlas_refit",
+           "rg_scene_set_materials", "rg_scene_set_lights", "rg_trace_rays", "rg_render", "rg_sync", "rg_get_stats",
+           "rg_reset_stats", "rg_last_error", "rg_tri_bounds", "rg_morton_codes", "rg_radix_sort_pairs", "rg_karras",
+           "rg_blas_export", "rg_tlas_export"]
+
+f32x3 = ctypes.c_float * 3
+
+
+class rg_camera(ctypes.Structure):
+    _fields_ = [("eye", f32x3), ("target", f32x3), ("up", f32x3), ("vfov_deg", ctypes.c_float)]
+
+
+class rg_material(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_uint32), ("albedo", f32x3), ("ior", ctypes.c_float), ("pad", f32x3)]
+
+
+class rg_light(ctypes.Structure):
+    _fields_ = [("pos", f32x3), ("intensity", f32x3)]
+
+
+class rg_scene_desc(ctypes.Structure):
+    _fields_ = [("background", f32x3), ("ambient", ctypes.c_float), ("flags", ctypes.c_uint32)]
+
+
+class rg_stats(ctypes.Structure):
+    _fields_ = [("closest_rays", ctypes.c_uint64), ("shadow_rays", ctypes.c_uint64),
+                ("trace_launches", ctypes.c_uint64), ("trace_ms", ctypes.c_double),
+                ("any_launches", ctypes.c_uint64), ("any_ms", ctypes.c_double),
+                ("node_visits", ctypes.c_uint64), ("tri_tests", ctypes.c_uint64), ("inst_entries", ctypes.c_uint64),
+                ("any_node_visits", ctypes.c_uint64), ("any_tri_tests", ctypes.c_uint64),
+                ("any_inst_entries", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
+
+
+class RgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"rg status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load librg.so (build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build(); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        P, u32, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32
+        sig = {
+            "rg_scene_create": [ctypes.POINTER(P), P],
+            "rg_scene_destroy": [P],
+            "rg_blas_build": [P, P, u32, P, u32, u32, ctypes.POINTER(u32), P],
+            "rg_tlas_build": [P, P, u32, P],
+            "rg_tlas_refit": [P, P, u32, P],
+            "rg_scene_set_materials": [P, P, u32],
+            "rg_scene_set_lights": [P, P, u32],
+            "rg_trace_rays": [P, P, u32, u32, P, P],
+            "rg_render": [P, P, u32, u32, u32, P, P],
+            "rg_sync": [P],
+            "rg_get_stats": [P, P],
+            "rg_reset_stats": [P],
+            "rg_tri_bounds": [P, u32, P, u32, P, P],
+            "rg_morton_codes": [P, u32, u32, P, P, P],
+            "rg_radix_sort_pairs": [P, P, u32, u32, P, P, P],
+            "rg_karras": [P, u32, u32, P, P, P],
+            "rg_blas_export": [P, u32, P, P, ctypes.POINTER(u32)],
+            "rg_tlas_export": [P, P, P, P, P, ctypes.POINTER(u32)],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = i32
+        L.rg_last_error.argtypes = []
+        L.rg_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != RG_OK:
+        raise RgError(status, lib().rg_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dev(t, dtype, shape_tail=None, name="tensor"):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape_tail is not None and tuple(t.shape[1:]) != tuple(shape_tail):
+        raise ValueError(f"{name} must have shape (n, {', '.join(map(str, shape_tail))})")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- scene
+
+def rg_scene_create(background=(0.2, 0.3, 0.5), ambient=0.1, flags=0):
+    d = rg_scene_desc(f32x3(*background), float(ambient), int(flags))
+    h = ctypes.c_void_p()
+    _check(lib().rg_scene_create(ctypes.byref(h), ctypes.byref(d)))
+    return h
+
+
+def rg_scene_destroy(scene):
+    _check(lib().rg_scene_destroy(scene))
+
+
+def rg_blas_build(scene, vtx, idx, flags=RG_MORTON30, stream=None):
+    """vtx: (nv,3) float32, idx: (nt,3) int32 (uint32 indices); returns the BLAS id."""
+    torch = _torch()
+    pv = _dev(vtx, torch.float32, (3,), "vtx")
+    pi = _dev(idx, torch.int32, (3,), "idx")
+    out = ctypes.c_uint32()
+    _check(lib().rg_blas_build(scene, pv, vtx.shape[0], pi, idx.shape[0], flags, ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def pack_instances(M, blas_ids, material_ids=None):
+    """rg_instance array as a (n,16) float32 numpy array (ids as uint32 bit patterns)."""
+    M = np.ascontiguousarray(M, np.float32).reshape(-1, 12)
+    n = M.shape[0]
+    out = np.zeros((n, 16), np.float32)
+    out[:, :12] = M
+    ids = out.view(np.uint32)
+    ids[:, 12] = np.asarray(blas_ids, np.uint32)
+    ids[:, 13] = 0 if material_ids is None else np.asarray(material_ids, np.uint32)
+    ids[:, 14] = 0xFF
+    return out
+
+
+def rg_tlas_build(scene, inst, stream=None):
+    """inst: (n,16) float32 CUDA tensor of rg_instance records (see pack_instances)."""
+    torch = _torch()
+    _check(lib().rg_tlas_build(scene, _dev(inst, torch.float32, (16,), "inst"), inst.shape[0], _stream(stream)))
+
+
+def rg_tlas_refit(scene, inst, stream=None):
+    torch = _torch()
+    _check(lib().rg_tlas_refit(scene, _dev(inst, torch.float32, (16,), "inst"), inst.shape[0], _stream(stream)))
+
+
+def rg_scene_set_materials(scene, types, albedo, ior):
+    types = np.asarray(types, np.uint32)
+    albedo = np.asarray(albedo, np.float32).reshape(-1, 3)
+    ior = np.asarray(ior, np.float32)
+    arr = (rg_material * len(types))()
+    for k in range(len(types)):
+        arr[k] = rg_material(int(types[k]), f32x3(*albedo[k]), float(ior[k]), f32x3(0, 0, 0))
+    _check(lib().rg_scene_set_materials(scene, arr, len(types)))
+
+
+def rg_scene_set_lights(scene, pos, intensity):
+    pos = np.asarray(pos, np.float32).reshape(-1, 3)
+    intensity = np.asarray(intensity, np.float32).reshape(-1, 3)
+    arr = (rg_light * max(len(pos), 1))()
+    for k in range(len(pos)):
+        arr[k] = rg_light(f32x3(*pos[k]), f32x3(*intensity[k]))
+    _check(lib().rg_scene_set_lights(scene, arr, len(pos)))
+
+
+# ---------------------------------------------------------------- dispatch
+
+def rg_trace_rays(scene, rays, flags=RG_CLOSEST, hits=None, stream=None):
+    """rays: (n,8) float32 CUDA tensor {o, tmin, d, tmax}; returns hits (n,5) int32
+    {instance, prim, t, u, v} (t/u/v as float32 bit patterns; see split_hits)."""
+    torch = _torch()
+    pr = _dev(rays, torch.float32, (8,), "rays")
+    n = rays.shape[0]
+    if hits is None:
+        hits = torch.empty((n, 5), dtype=torch.int32, device=rays.device)
+    ph = _dev(hits, torch.int32, (5,), "hits")
+    if hits.shape[0] < n:
+        raise ValueError("hits buffer too small")
+    _check(lib().rg_trace_rays(scene, pr, n, flags, ph, _stream(stream)))
+    return hits
+
+
+def split_hits(hits):
+    """Host view of a hit tensor: dict of numpy arrays instance/prim (uint32), t/u/v (float32)."""
+    h = hits.cpu().numpy() if hasattr(hits, "cpu") else np.asarray(hits)
+    h = np.ascontiguousarray(h)
+    return dict(inst=h[:, 0].view(np.uint32), prim=h[:, 1].view(np.uint32), t=h[:, 2].view(np.float32),
+                u=h[:, 3].view(np.float32), v=h[:, 4].view(np.float32))
+
+
+def make_camera(camera):
+    return rg_camera(f32x3(*camera["eye"]), f32x3(*camera["target"]), f32x3(*camera.get("up", (0, 1, 0))),
+                     float(camera["vfov"]))
+
+
+def rg_render(scene, camera, width, height, max_depth, out=None, stream=None):
+    """Render into a (h, w, 4) float32 CUDA tensor (allocated if out is None)."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty((height, width, 4), dtype=torch.float32, device="cuda")
+    if out.numel() != width * height * 4 or out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float32 CUDA tensor of w*h*4 elements")
+    cam = camera if isinstance(camera, rg_camera) else make_camera(camera)
+    _check(lib().rg_render(scene, ctypes.byref(cam), width, height, max_depth, ctypes.c_void_p(out.data_ptr()),
+                           _stream(stream)))
+    return out
+
+
+def rg_sync(scene):
+    _check(lib().rg_sync(scene))
+
+
+def rg_get_stats(scene):
+    st = rg_stats()
+    _check(lib().rg_get_stats(scene, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in rg_stats._fields_}
+
+
+def rg_reset_stats(scene):
+    _check(lib().rg_reset_stats(scene))
+
+
+# ---------------------------------------------------------------- build steps
+
+def rg_tri_bounds(vtx, idx, stream=None):
+    torch = _torch()
+    out = torch.empty((idx.shape[0], 6), dtype=torch.float32, device=vtx.device)
+    _check(lib().rg_tri_bounds(_dev(vtx, torch.float32, (3,), "vtx"), vtx.shape[0], _dev(idx, torch.int32, (3,), "idx"),
+                               idx.shape[0], ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def rg_morton_codes(lohi, bits, stream=None):
+    """Morton codes (int32 for bits=10, int64 for bits=21) and centroid bounds."""
+    torch = _torch()
+    n = lohi.shape[0]
+    codes = torch.empty(n, dtype=torch.int32 if bits == 10 else torch.int64, device=lohi.device)
+    cb = torch.empty(6, dtype=torch.float32, device=lohi.device)
+    _check(lib().rg_morton_codes(_dev(lohi, torch.float32, (6,), "lohi"), n, bits, ctypes.c_void_p(codes.data_ptr()),
+                                 ctypes.c_void_p(cb.data_ptr()), _stream(stream)))
+    return codes, cb
+
+
+def rg_radix_sort_pairs(keys, vals, stream=None):
+    """Stable sort of (keys int32/int64 as unsigned, vals int32); returns (keys, vals)."""
+    torch = _torch()
+    key_bits = 64 if keys.dtype == torch.int64 else 32
+    ko = torch.empty_like(keys)
+    vo = torch.empty_like(vals)
+    _check(lib().rg_radix_sort_pairs(_dev(keys, keys.dtype, None, "keys"), _dev(vals, torch.int32, None, "vals"),
+                                     keys.shape[0], key_bits, ctypes.c_void_p(ko.data_ptr()),
+                                     ctypes.c_void_p(vo.data_ptr()), _stream(stream)))
+    return ko, vo
+
+
+def rg_karras(sorted_keys, stream=None):
+    """(children (n-1,2) int32, parents (2n-1,) int32) of the radix tree."""
+    torch = _torch()
+    n = sorted_keys.shape[0]
+    key_bits = 64 if sorted_keys.dtype == torch.int64 else 32
+    ch = torch.empty((max(n - 1, 1), 2), dtype=torch.int32, device=sorted_keys.device)
+    par = torch.empty(max(2 * n - 1, 1), dtype=torch.int32, device=sorted_keys.device)
+    _check(lib().rg_karras(_dev(sorted_keys, sorted_keys.dtype, None, "keys"), n, key_bits,
+                           ctypes.c_void_p(ch.data_ptr()), ctypes.c_void_p(par.data_ptr()), _stream(stream)))
+    return ch, par
+
+
+def rg_blas_export(scene, blas_id, nt):
+    nodes = np.zeros((max(nt - 1, 1), 16), np.float32)
+    tris = np.zeros((nt, 12), np.float32)
+    root = ctypes.c_uint32()
+    _check(lib().rg_blas_export(scene, blas_id, nodes.ctypes.data_as(ctypes.c_void_p),
+                                tris.ctypes.data_as(ctypes.c_void_p), ctypes.byref(root)))
+    return dict(nodes=nodes[: max(nt - 1, 0)], tris=tris, root=root.value)
+
+
+def rg_tlas_export(scene, n):
+    nodes = np.zeros((max(n - 1, 1), 16), np.float32)
+    wbox = np.zeros((n, 6), np.float32)
+    inv = np.zeros((n, 12), np.float32)
+    order = np.zeros(n, np.uint32)
+    root = ctypes.c_uint32()
+    v = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(lib().rg_tlas_export(scene, v(nodes), v(wbox), v(inv), v(order), ctypes.byref(root)))
+    return dict(nodes=nodes[: max(n - 1, 0)], wbox=wbox, inv=inv.reshape(n, 3, 4), order=order, root=root.value)
+
+
+# ---------------------------------------------------------------- convenience
+
+class GpuScene:
+    """Owns one rg_scene built from a scenegen-style scene description
+    (meshes, instance transforms, materials, lights)."""
+
+    def __init__(self, scene, flags=0, morton_flags=RG_MORTON30, stream=None):
+        torch = _torch()
+        self.h = rg_scene_create(scene.background, scene.ambient, flags)
+        self.n_inst = scene.n_instances
+        self.nts = []
+        try:
+            self.blas = []
+            for v, i in scene.meshes:
+                tv = torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda()
+                ti = torch.from_numpy(np.ascontiguousarray(i, np.uint32).view(np.int32)).cuda()
+                self.blas.append(rg_blas_build(self.h, tv, ti, morton_flags, stream))
+                self.nts.append(int(i.shape[0]))
+            self.inst_host = pack_instances(scene.M, [self.blas[m] for m in scene.mesh_id], scene.material_id)
+            self.inst = torch.from_numpy(self.inst_host).cuda()
+            rg_tlas_build(self.h, self.inst, stream)
+            rg_scene_set_materials(self.h, scene.mat_type, scene.mat_albedo, scene.mat_ior)
+            rg_scene_set_lights(self.h, scene.light_pos, scene.light_I)
+            rg_sync(self.h)
+        except Exception:
+            self.close()
+            raise
+
+    def refit(self, M, stream=None):
+        torch = _torch()
+        host = self.inst_host.copy()
+        host[:, :12] = np.ascontiguousarray(M, np.float32).reshape(-1, 12)
+        self.inst = torch.from_numpy(host).cuda()
+        rg_tlas_refit(self.h, self.inst, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            rg_scene_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

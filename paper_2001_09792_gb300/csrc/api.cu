@@ -1,0 +1,772 @@
+// The extern "C" boundary of librg: argument checks, ownership of the
+// acceleration structures and ray queues, and the launch sequences of the
+// build, trace and render calls.  See include/rg.h for the contract.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstddef>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rg_internal.cuh"
+
+using namespace rg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+rg_status fail(rg_status code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+rg_status cuda_fail(cudaError_t e, const char* what) {
+    cudaGetLastError();  // clear a sticky launch error
+    return fail(e == cudaErrorMemoryAllocation ? RG_ERR_OOM : RG_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define RG_CK(call)                                          \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+    } while (0)
+
+// Host-side fault injection for tests: RG_FAULT=alloc:N fails the N-th
+// device allocation (1-based) made by the library with RG_ERR_OOM.
+long g_alloc_count = 0;
+long fault_alloc_index() {
+    static long idx = -2;
+    if (idx == -2) {
+        idx = -1;
+        const char* f = std::getenv("RG_FAULT");
+        if (f && std::strncmp(f, "alloc:", 6) == 0) idx = std::atol(f + 6);
+    }
+    return idx;
+}
+
+rg_status dev_alloc(void** p, size_t bytes, const char* what) {
+    *p = nullptr;
+    long k = ++g_alloc_count;
+    if (fault_alloc_index() == k) return fail(RG_ERR_OOM, std::string("injected allocation failure: ") + what);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, what);
+    }
+    return RG_OK;
+}
+
+struct TempAlloc {
+    // stream-ordered temporaries, freed on the stream when the call ends
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit TempAlloc(cudaStream_t st) : s(st) {}
+    ~TempAlloc() {
+        for (void* p : ptrs) cudaFreeAsync(p, s);
+    }
+    rg_status get(void** p, size_t bytes, const char* what) {
+        *p = nullptr;
+        long k = ++g_alloc_count;
+        if (fault_alloc_index() == k) return fail(RG_ERR_OOM, std::string("injected allocation failure: ") + what);
+        cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, s);
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            return cuda_fail(e, what);
+        }
+        ptrs.push_back(*p);
+        return RG_OK;
+    }
+};
+
+template <class T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t cap = 0;  // elements
+    rg_status ensure(size_t n, const char* what) {
+        if (n <= cap && p) return RG_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = n < 16 ? 16 : n;
+        rg_status st = dev_alloc(reinterpret_cast<void**>(&p), want * sizeof(T), what);
+        if (st == RG_OK) cap = want;
+        return st;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+struct BlasHost {
+    float4* nodes = nullptr;
+    float4* tris = nullptr;
+    uint32_t nt = 0;
+    uint32_t root = 0;
+};
+
+struct EventPair {
+    cudaEvent_t a, b;
+    int kind;  // 0 closest, 1 any
+};
+
+}  // namespace
+
+struct rg_scene {
+    int device = 0;
+    rg_scene_desc desc{};
+    DevStatus* st = nullptr;
+    // BLAS
+    std::vector<BlasHost> blas;
+    DevBuf<BlasDev> d_blas;
+    uint32_t max_nt = 0;
+    // TLAS
+    bool tlas_built = false;
+    uint32_t n_inst = 0;
+    uint32_t tlas_root = 0;
+    DevBuf<float4> tlas_nodes;
+    DevBuf<InstDev> inst, inst_tmp;
+    DevBuf<float> wbox;
+    DevBuf<uint32_t> perm, parents, flags;
+    // shading
+    DevBuf<rg_material> mats;
+    uint32_t n_mats = 0;
+    DevBuf<rg_light> lights;
+    uint32_t n_lights = 0;
+    // queues
+    DevBuf<float4> q_rays[2], s_rays;
+    DevBuf<Payload> q_pay[2], s_pay;
+    DevBuf<HitDev> hits;
+    DevBuf<uint32_t> counters;     // [0] closest work, [1] next count, [2] shadow count, [3] shadow work
+    uint32_t* h_counts = nullptr;  // pinned, 4 entries
+    // statistics and timing
+    uint64_t closest_rays = 0, shadow_rays_host = 0;
+    std::vector<EventPair> events, free_events;
+    double trace_ms = 0, any_ms = 0;
+    uint64_t trace_launches = 0, any_launches = 0;
+    unsigned long long launch_base = 0;
+};
+
+namespace {
+
+rg_status check_scene(rg_scene* s) {
+    if (!s) return fail(RG_ERR_INVALID_ARG, "scene is NULL");
+    return RG_OK;
+}
+
+rg_status set_device(rg_scene* s) {
+    int cur = -1;
+    RG_CK(cudaGetDevice(&cur));
+    if (cur != s->device) RG_CK(cudaSetDevice(s->device));
+    return RG_OK;
+}
+
+rg_status event_begin(rg_scene* s, int kind, cudaStream_t st, EventPair** out) {
+    *out = nullptr;
+    if (!(s->desc.flags & RG_SCENE_TIMING)) return RG_OK;
+    EventPair ep;
+    if (!s->free_events.empty()) {
+        ep = s->free_events.back();
+        s->free_events.pop_back();
+    } else {
+        RG_CK(cudaEventCreate(&ep.a));
+        RG_CK(cudaEventCreate(&ep.b));
+    }
+    ep.kind = kind;
+    RG_CK(cudaEventRecord(ep.a, st));
+    s->events.push_back(ep);
+    *out = &s->events.back();
+    return RG_OK;
+}
+
+rg_status event_end(rg_scene* s, cudaStream_t st) {
+    if (!(s->desc.flags & RG_SCENE_TIMING) || s->events.empty()) return RG_OK;
+    RG_CK(cudaEventRecord(s->events.back().b, st));
+    return RG_OK;
+}
+
+rg_status collect_events(rg_scene* s) {
+    for (EventPair& ep : s->events) {
+        RG_CK(cudaEventSynchronize(ep.b));
+        float ms = 0;
+        RG_CK(cudaEventElapsedTime(&ms, ep.a, ep.b));
+        if (ep.kind == 0) {
+            s->trace_ms += ms;
+            s->trace_launches++;
+        } else {
+            s->any_ms += ms;
+            s->any_launches++;
+        }
+        s->free_events.push_back(ep);
+    }
+    s->events.clear();
+    return RG_OK;
+}
+
+uint32_t iter_cap_for(const rg_scene* s, bool brute) {
+    // brute force: every node and triangle of every instance once, with pops;
+    // a BVH traversal visits a tiny fraction of that, and 2^22 steps per ray
+    // bound it far above any valid traversal of the supported scene sizes
+    uint64_t per_inst = 4ull * (uint64_t)s->max_nt + 16;
+    uint64_t cap = 4ull * (uint64_t)s->n_inst + (uint64_t)s->n_inst * per_inst + 64;
+    if (!brute && cap > (1ull << 22)) cap = 1ull << 22;
+    return cap > 0xFFFFFFF0ull ? 0xFFFFFFF0u : (uint32_t)cap;
+}
+
+TraceArgs base_trace_args(rg_scene* s) {
+    TraceArgs a{};
+    a.tlas_nodes = s->tlas_nodes.p;
+    a.tlas_root = s->tlas_root;
+    a.inst = s->inst.p;
+    a.n_inst = s->n_inst;
+    a.st = s->st;
+    a.iter_cap = iter_cap_for(s, false);
+    return a;
+}
+
+// Shared LBVH steps: lohi + centroid bounds already computed into cb_ord.
+// Sorts the Morton codes of `lohi` and emits the topology into `nodes`.
+rg_status lbvh_topology(TempAlloc& tmp, const float* lohi, uint32_t n, const int* cb_ord, int bits, float4* nodes,
+                        uint32_t* perm, uint32_t* parents, cudaStream_t s) {
+    const int key_bits = bits == 21 ? 64 : 32;
+    const size_t kb = key_bits / 8;
+    void *codes, *sorted, *vals, *scratch;
+    rg_status r;
+    if ((r = tmp.get(&codes, n * kb, "morton codes"))) return r;
+    if ((r = tmp.get(&sorted, n * kb, "sorted codes"))) return r;
+    if ((r = tmp.get(&vals, n * 4ull, "sort values"))) return r;
+    if ((r = tmp.get(&scratch, radix_sort_scratch_bytes(n, key_bits), "sort scratch"))) return r;
+    RG_CK(launch_morton(lohi, n, cb_ord, bits, codes, static_cast<uint32_t*>(vals), nullptr, s));
+    RG_CK(radix_sort_pairs(codes, static_cast<uint32_t*>(vals), n, key_bits, sorted, perm, scratch, s));
+    RG_CK(launch_karras(sorted, n, key_bits, reinterpret_cast<uint32_t*>(nodes) + 12, 16, parents, s));
+    return RG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rg_last_error(void) { return g_last_error.c_str(); }
+
+rg_status rg_scene_create(rg_scene** out, const rg_scene_desc* desc) {
+    if (!out) return fail(RG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    rg_scene* s = new rg_scene();
+    RG_CK(cudaGetDevice(&s->device));
+    if (desc) {
+        s->desc = *desc;
+    } else {
+        s->desc.background[0] = 0.2f;
+        s->desc.background[1] = 0.3f;
+        s->desc.background[2] = 0.5f;
+        s->desc.ambient = 0.1f;
+        s->desc.flags = 0;
+    }
+    rg_status r = dev_alloc(reinterpret_cast<void**>(&s->st), sizeof(DevStatus), "status");
+    if (r) {
+        delete s;
+        return r;
+    }
+    if ((r = s->counters.ensure(16, "counters"))) {
+        cudaFree(s->st);
+        delete s;
+        return r;
+    }
+    cudaError_t e = cudaMemset(s->st, 0, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&s->h_counts), 16 * sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        cudaFree(s->st);
+        s->counters.release();
+        delete s;
+        return cuda_fail(e, "scene setup");
+    }
+    *out = s;
+    return RG_OK;
+}
+
+rg_status rg_scene_destroy(rg_scene* s) {
+    if (!s) return RG_OK;
+    set_device(s);
+    cudaDeviceSynchronize();
+    for (BlasHost& b : s->blas) {
+        cudaFree(b.nodes);
+        cudaFree(b.tris);
+    }
+    s->d_blas.release();
+    s->tlas_nodes.release();
+    s->inst.release();
+    s->inst_tmp.release();
+    s->wbox.release();
+    s->perm.release();
+    s->parents.release();
+    s->flags.release();
+    s->mats.release();
+    s->lights.release();
+    for (int k = 0; k < 2; ++k) {
+        s->q_rays[k].release();
+        s->q_pay[k].release();
+    }
+    s->s_rays.release();
+    s->s_pay.release();
+    s->hits.release();
+    s->counters.release();
+    if (s->st) cudaFree(s->st);
+    if (s->h_counts) cudaFreeHost(s->h_counts);
+    for (EventPair& ep : s->events) {
+        cudaEventDestroy(ep.a);
+        cudaEventDestroy(ep.b);
+    }
+    for (EventPair& ep : s->free_events) {
+        cudaEventDestroy(ep.a);
+        cudaEventDestroy(ep.b);
+    }
+    delete s;
+    return RG_OK;
+}
+
+rg_status rg_blas_build(rg_scene* s, const float* d_vtx, uint32_t nv, const uint32_t* d_idx, uint32_t nt,
+                        uint32_t flags, uint32_t* blas_id, void* stream) {
+    rg_status r;
+    if ((r = check_scene(s))) return r;
+    if (!d_vtx || !d_idx || !blas_id) return fail(RG_ERR_INVALID_ARG, "NULL geometry or id pointer");
+    if (nt == 0 || nv == 0) return fail(RG_ERR_INVALID_ARG, "empty mesh");
+    if (flags & ~RG_MORTON63) return fail(RG_ERR_INVALID_ARG, "unknown BLAS flags");
+    if (nt > (1u << 30)) return fail(RG_ERR_INVALID_ARG, "too many triangles");
+    if ((r = set_device(s))) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int bits = (flags & RG_MORTON63) ? 21 : 10;
+
+    BlasHost b;
+    b.nt = nt;
+    b.root = nt == 1 ? kLeaf : 0u;
+    if ((r = dev_alloc(reinterpret_cast<void**>(&b.nodes), (size_t)(nt > 1 ? nt - 1 : 1) * 64, "BLAS nodes"))) return r;
+    if ((r = dev_alloc(reinterpret_cast<void**>(&b.tris), (size_t)nt * 48, "BLAS triangles"))) {
+        cudaFree(b.nodes);
+        return r;
+    }
+    uint32_t id = (uint32_t)s->blas.size();
+    if ((r = [&]() -> rg_status {
+             // grow the descriptor array, keeping the old entries
+             if (id + 1 > s->d_blas.cap) {
+                 size_t ncap = (id + 1) * 2;
+                 BlasDev* np = nullptr;
+                 rg_status rr = dev_alloc(reinterpret_cast<void**>(&np), ncap * sizeof(BlasDev), "BLAS table");
+                 if (rr) return rr;
+                 if (s->d_blas.p && id) RG_CK(cudaMemcpyAsync(np, s->d_blas.p, id * sizeof(BlasDev), cudaMemcpyDeviceToDevice, st));
+                 if (s->d_blas.p) {
+                     RG_CK(cudaStreamSynchronize(st));
+                     cudaFree(s->d_blas.p);
+                 }
+                 s->d_blas.p = np;
+                 s->d_blas.cap = ncap;
+             }
+             BlasDev hd{};
+             hd.nodes = b.nodes;
+             hd.tris = b.tris;
+             hd.root = b.root;
+             hd.nt = nt;
+             RG_CK(cudaMemcpyAsync(s->d_blas.p + id, &hd, sizeof hd, cudaMemcpyHostToDevice, st));
+             RG_CK(cudaStreamSynchronize(st));  // hd lives on this stack frame
+
+             TempAlloc tmp(st);
+             void *lohi, *cb, *perm, *parents, *fl;
+             rg_status q;
+             if ((q = tmp.get(&lohi, (size_t)nt * 24, "triangle boxes"))) return q;
+             if ((q = tmp.get(&cb, 64, "centroid bounds"))) return q;
+             if ((q = tmp.get(&perm, (size_t)nt * 4, "permutation"))) return q;
+             if ((q = tmp.get(&parents, (size_t)(2 * (size_t)nt - 1) * 4, "parents"))) return q;
+             if ((q = tmp.get(&fl, (size_t)(nt > 1 ? nt - 1 : 1) * 4, "refit flags"))) return q;
+             RG_CK(launch_init_bounds(static_cast<int*>(cb), st));
+             RG_CK(launch_tri_bounds(d_vtx, nv, d_idx, nt, static_cast<float*>(lohi), static_cast<int*>(cb), s->st, st));
+             if (nt > 1) {
+                 if ((q = lbvh_topology(tmp, static_cast<float*>(lohi), nt, static_cast<int*>(cb), bits, b.nodes,
+                                        static_cast<uint32_t*>(perm), static_cast<uint32_t*>(parents), st)))
+                     return q;
+                 RG_CK(cudaMemsetAsync(fl, 0, (size_t)(nt - 1) * 4, st));
+             } else {
+                 RG_CK(cudaMemsetAsync(perm, 0, 4, st));
+             }
+             RG_CK(launch_blas_leaves_refit(d_vtx, d_idx, static_cast<uint32_t*>(perm), static_cast<float*>(lohi), nt,
+                                            static_cast<uint32_t*>(parents), b.nodes, static_cast<uint32_t*>(fl), b.tris,
+                                            s->d_blas.p + id, s->st, st));
+             return RG_OK;
+         }())) {
+        cudaStreamSynchronize(st);
+        cudaFree(b.nodes);
+        cudaFree(b.tris);
+        return r;
+    }
+    s->blas.push_back(b);
+    if (nt > s->max_nt) s->max_nt = nt;
+    *blas_id = id;
+    return RG_OK;
+}
+
+static rg_status tlas_common(rg_scene* s, const rg_instance* d_inst, uint32_t n, cudaStream_t st, bool refit) {
+    rg_status r;
+    TempAlloc tmp(st);
+    void* cb;
+    if ((r = tmp.get(&cb, 64, "centroid bounds"))) return r;
+    if (!refit) RG_CK(launch_init_bounds(static_cast<int*>(cb), st));
+    RG_CK(launch_instance_prep(d_inst, n, s->d_blas.p, (uint32_t)s->blas.size(), s->inst_tmp.p, s->wbox.p,
+                               refit ? nullptr : static_cast<int*>(cb), refit, s->st, st));
+    if (!refit) {
+        if (n > 1) {
+            if ((r = lbvh_topology(tmp, s->wbox.p, n, static_cast<int*>(cb), 10, s->tlas_nodes.p, s->perm.p,
+                                   s->parents.p, st)))
+                return r;
+        } else {
+            RG_CK(cudaMemsetAsync(s->perm.p, 0, 4, st));
+        }
+    }
+    if (n > 1) RG_CK(cudaMemsetAsync(s->flags.p, 0, (size_t)(n - 1) * 4, st));
+    RG_CK(launch_tlas_leaves_refit(s->inst_tmp.p, s->wbox.p, s->perm.p, n, s->parents.p, s->tlas_nodes.p, s->flags.p,
+                                   s->inst.p, s->st, st));
+    return RG_OK;
+}
+
+rg_status rg_tlas_build(rg_scene* s, const rg_instance* d_inst, uint32_t n, void* stream) {
+    rg_status r;
+    if ((r = check_scene(s))) return r;
+    if (!d_inst || n == 0) return fail(RG_ERR_INVALID_ARG, "no instances");
+    if (n > (1u << 28)) return fail(RG_ERR_INVALID_ARG, "too many instances");
+    if (s->blas.empty()) return fail(RG_ERR_NOT_BUILT, "no BLAS built");
+    if ((r = set_device(s))) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    s->tlas_built = false;
+    if ((r = s->tlas_nodes.ensure((size_t)(n > 1 ? n - 1 : 1) * 4, "TLAS nodes"))) return r;
+    if ((r = s->inst.ensure(n, "instances"))) return r;
+    if ((r = s->inst_tmp.ensure(n, "instance staging"))) return r;
+    if ((r = s->wbox.ensure((size_t)n * 6, "instance boxes"))) return r;
+    if ((r = s->perm.ensure(n, "TLAS order"))) return r;
+    if ((r = s->parents.ensure(2 * (size_t)n, "TLAS parents"))) return r;
+    if ((r = s->flags.ensure(n, "TLAS flags"))) return r;
+    if ((r = tlas_common(s, d_inst, n, st, false))) return r;
+    s->n_inst = n;
+    s->tlas_root = n == 1 ? kLeaf : 0u;
+    s->tlas_built = true;
+    return RG_OK;
+}
+
+rg_status rg_tlas_refit(rg_scene* s, const rg_instance* d_inst, uint32_t n, void* stream) {
+    rg_status r;
+    if ((r = check_scene(s))) return r;
+    if (!s->tlas_built) return fail(RG_ERR_NOT_BUILT, "refit before rg_tlas_build");
+    if (!d_inst || n != s->n_inst) return fail(RG_ERR_INVALID_ARG, "refit needs the instance count of the build");
+    if ((r = set_device(s))) return r;
+    return tlas_common(s, d_inst, n, static_cast<cudaStream_t>(stream), true);
+}
+
+rg_status rg_scene_set_materials(rg_scene* s, const rg_material* h, uint32_t n) {
+    rg_status r;
+    if ((r = check_scene(s))) return r;
+    if (!h || n == 0) return fail(RG_ERR_INVALID_ARG, "no materials");
+    for (uint32_t i = 0; i < n; ++i)
+        if (h[i].type > RG_MAT_GLASS || (h[i].type == RG_MAT_GLASS && !(h[i].ior > 0.0f)))
+            return fail(RG_ERR_INVALID_ARG, "bad material type or ior");
+    if ((r = set_device(s))) return r;
+    if ((r = s->mats.ensure(n, "materials"))) return r;
+    RG_CK(cudaMemcpy(s->mats.p, h, n * sizeof(rg_material), cudaMemcpyHostToDevice));
+    s->n_mats = n;
+    return RG_OK;
+}
+
+rg_status rg_scene_set_lights(rg_scene* s, const rg_light* h, uint32_t n) {
+    rg_status r;
+    if ((r = check_scene(s))) return r;
+    if (n && !h) return fail(RG_ERR_INVALID_ARG, "NULL lights");
+    if ((r = set_device(s))) return r;
+    if ((r = s->lights.ensure(n ? n : 1, "lights"))) return r;
+    if (n) RG_CK(cudaMemcpy(s->lights.p, h, n * sizeof(rg_light), cudaMemcpyHostToDevice));
+    s->n_lights = n;
+    return RG_OK;
+}
+
+rg_status rg_trace_rays(rg_scene* s, const rg_ray* d_rays, uint32_t n, uint32_t flags, rg_hit* d_hits, void* stream) {
+    rg_status r;
+    if ((r = check_scene(s))) return r;
+    if (!s->tlas_built) return fail(RG_ERR_NOT_BUILT, "trace before rg_tlas_build");
+    if (flags & ~(RG_ANY | RG_TRACE_BRUTE | RG_TRACE_STATS)) return fail(RG_ERR_INVALID_ARG, "unknown trace flags");
+    if ((flags & RG_TRACE_BRUTE) && (flags & RG_TRACE_STATS))
+        return fail(RG_ERR_INVALID_ARG, "brute force and statistics are exclusive");
+    if (n == 0) return RG_OK;
+    if (!d_rays || !d_hits) return fail(RG_ERR_INVALID_ARG, "NULL ray or hit buffer");
+    if ((r = set_device(s))) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    TraceArgs a = base_trace_args(s);
+    a.rays = reinterpret_cast<const float4*>(d_rays);
+    a.n = n;
+    a.hits_abi = d_hits;
+    a.work_counter = s->counters.p;
+    a.iter_cap = iter_cap_for(s, flags & RG_TRACE_BRUTE);
+    RG_CK(cudaMemsetAsync(s->counters.p, 0, 4, st));
+    const bool any = flags & RG_ANY;
+    EventPair* ev;
+    if ((r = event_begin(s, any ? 1 : 0, st, &ev))) return r;
+    RG_CK(launch_trace(any ? kModeAnyAbi : kModeClosestAbi, flags & RG_TRACE_BRUTE, flags & RG_TRACE_STATS, a, st));
+    if ((r = event_end(s, st))) return r;
+    if (any)
+        s->shadow_rays_host += n;
+    else
+        s->closest_rays += n;
+    return RG_OK;
+}
+
+rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, uint32_t max_depth, float* d_rgba,
+                    void* stream) {
+    rg_status r;
+    if ((r = check_scene(s))) return r;
+    if (!s->tlas_built) return fail(RG_ERR_NOT_BUILT, "render before rg_tlas_build");
+    if (!cam || !d_rgba || w == 0 || h == 0 || max_depth == 0) return fail(RG_ERR_INVALID_ARG, "bad render arguments");
+    if ((uint64_t)w * h > (1ull << 28)) return fail(RG_ERR_INVALID_ARG, "image too large");
+    if (s->n_mats == 0) return fail(RG_ERR_NOT_BUILT, "no materials set");
+    if ((r = set_device(s))) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const uint32_t N = w * h;
+    const uint32_t L = s->n_lights;
+    if ((r = s->q_rays[0].ensure(2 * (size_t)N, "ray queue"))) return r;
+    if ((r = s->q_pay[0].ensure(N, "payload queue"))) return r;
+    RG_CK(cudaMemsetAsync(d_rgba, 0, (size_t)N * 16, st));
+    CameraDev cd;
+    std::memcpy(&cd, cam, sizeof cd);
+    RG_CK(launch_raygen(cd, w, h, s->q_rays[0].p, s->q_pay[0].p, st));
+    uint32_t n = N;
+    int cur = 0;
+    for (uint32_t depth = 1; depth <= max_depth && n > 0; ++depth) {
+        const bool last = depth == max_depth;
+        if ((r = s->hits.ensure(n, "hit queue"))) return r;
+        if (L && (r = s->s_rays.ensure(2 * (size_t)n * L, "shadow queue"))) return r;
+        if (L && (r = s->s_pay.ensure((size_t)n * L, "shadow payload"))) return r;
+        if (!last) {
+            if ((r = s->q_rays[1 - cur].ensure(4 * (size_t)n, "ray queue"))) return r;
+            if ((r = s->q_pay[1 - cur].ensure(2 * (size_t)n, "payload queue"))) return r;
+        }
+        RG_CK(cudaMemsetAsync(s->counters.p, 0, 4 * sizeof(uint32_t), st));
+        TraceArgs a = base_trace_args(s);
+        a.rays = s->q_rays[cur].p;
+        a.n = n;
+        a.hits_render = s->hits.p;
+        a.work_counter = s->counters.p + 0;
+        EventPair* ev;
+        if ((r = event_begin(s, 0, st, &ev))) return r;
+        RG_CK(launch_trace(kModeClosestRender, false, s->desc.flags & RG_SCENE_COUNT, a, st));
+        if ((r = event_end(s, st))) return r;
+        s->closest_rays += n;
+
+        ShadeArgs sa{};
+        sa.rays = s->q_rays[cur].p;
+        sa.payload = s->q_pay[cur].p;
+        sa.hits = s->hits.p;
+        sa.inst = s->inst.p;
+        sa.mats = s->mats.p;
+        sa.n_mats = s->n_mats;
+        sa.lights = s->lights.p;
+        sa.n_lights = L;
+        sa.bg[0] = s->desc.background[0];
+        sa.bg[1] = s->desc.background[1];
+        sa.bg[2] = s->desc.background[2];
+        sa.ambient = s->desc.ambient;
+        sa.depth = depth;
+        sa.max_depth = max_depth;
+        sa.image = d_rgba;
+        sa.next_rays = last ? nullptr : s->q_rays[1 - cur].p;
+        sa.next_payload = last ? nullptr : s->q_pay[1 - cur].p;
+        sa.next_count = s->counters.p + 1;
+        sa.shadow_rays = s->s_rays.p;
+        sa.shadow_payload = s->s_pay.p;
+        sa.shadow_count = s->counters.p + 2;
+        sa.st = s->st;
+        RG_CK(launch_shade(sa, n, st));
+
+        if (L) {
+            TraceArgs b = base_trace_args(s);
+            b.rays = s->s_rays.p;
+            b.d_count = s->counters.p + 2;
+            b.payload = s->s_pay.p;
+            b.image = d_rgba;
+            b.work_counter = s->counters.p + 3;
+            if ((r = event_begin(s, 1, st, &ev))) return r;
+            RG_CK(launch_trace(kModeShadowRender, false, s->desc.flags & RG_SCENE_COUNT, b, st));
+            if ((r = event_end(s, st))) return r;
+        }
+        if (last) break;
+        RG_CK(cudaMemcpyAsync(s->h_counts, s->counters.p + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        RG_CK(cudaStreamSynchronize(st));
+        n = s->h_counts[0];
+        cur = 1 - cur;
+    }
+    return RG_OK;
+}
+
+rg_status rg_sync(rg_scene* s) {
+    rg_status r;
+    if ((r = check_scene(s))) return r;
+    if ((r = set_device(s))) return r;
+    RG_CK(cudaDeviceSynchronize());
+    int err = 0;
+    RG_CK(cudaMemcpy(&err, &s->st->error, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        RG_CK(cudaMemset(&s->st->error, 0, sizeof(int)));
+        const char* what = err == RG_ERR_STACK       ? "traversal stack overflow"
+                           : err == RG_ERR_TIMEOUT   ? "device loop iteration cap reached"
+                           : err == RG_ERR_SINGULAR  ? "singular instance transform"
+                           : err == RG_ERR_INVALID_ARG ? "invalid index or id found on the device"
+                                                       : "device error";
+        return fail(err, what);
+    }
+    return RG_OK;
+}
+
+rg_status rg_get_stats(rg_scene* s, rg_stats* out) {
+    rg_status r;
+    if ((r = check_scene(s))) return r;
+    if (!out) return fail(RG_ERR_INVALID_ARG, "out is NULL");
+    if ((r = set_device(s))) return r;
+    RG_CK(cudaDeviceSynchronize());
+    if ((r = collect_events(s))) return r;
+    DevStatus d;
+    RG_CK(cudaMemcpy(&d, s->st, sizeof d, cudaMemcpyDeviceToHost));
+    out->closest_rays = s->closest_rays;
+    out->shadow_rays = s->shadow_rays_host + d.shadow_rays;
+    out->trace_launches = s->trace_launches;
+    out->trace_ms = s->trace_ms;
+    out->any_launches = s->any_launches;
+    out->any_ms = s->any_ms;
+    out->node_visits = d.count[0][0];
+    out->tri_tests = d.count[0][1];
+    out->inst_entries = d.count[0][2];
+    out->any_node_visits = d.count[1][0];
+    out->any_tri_tests = d.count[1][1];
+    out->any_inst_entries = d.count[1][2];
+    out->kernel_launches = launches_so_far() - s->launch_base;
+    return RG_OK;
+}
+
+rg_status rg_reset_stats(rg_scene* s) {
+    rg_status r;
+    if ((r = check_scene(s))) return r;
+    if ((r = set_device(s))) return r;
+    RG_CK(cudaDeviceSynchronize());
+    if ((r = collect_events(s))) return r;
+    s->closest_rays = s->shadow_rays_host = 0;
+    s->trace_ms = s->any_ms = 0;
+    s->trace_launches = s->any_launches = 0;
+    s->launch_base = launches_so_far();
+    RG_CK(cudaMemset(reinterpret_cast<char*>(s->st) + offsetof(DevStatus, closest_rays), 0,
+                     sizeof(DevStatus) - offsetof(DevStatus, closest_rays)));
+    return RG_OK;
+}
+
+rg_status rg_tri_bounds(const float* d_vtx, uint32_t nv, const uint32_t* d_idx, uint32_t nt, float* d_lohi,
+                        void* stream) {
+    if (nt == 0) return RG_OK;
+    if (!d_vtx || !d_idx || !d_lohi || nv == 0) return fail(RG_ERR_INVALID_ARG, "bad arguments");
+    RG_CK(launch_tri_bounds(d_vtx, nv, d_idx, nt, d_lohi, nullptr, nullptr, static_cast<cudaStream_t>(stream)));
+    return RG_OK;
+}
+
+rg_status rg_morton_codes(const float* d_lohi, uint32_t n, uint32_t bits, void* d_codes, float* d_cbounds,
+                          void* stream) {
+    if (bits != 10 && bits != 21) return fail(RG_ERR_INVALID_ARG, "bits must be 10 or 21");
+    if (n == 0) return RG_OK;
+    if (!d_lohi || !d_codes) return fail(RG_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    TempAlloc tmp(st);
+    void* cb;
+    rg_status r;
+    if ((r = tmp.get(&cb, 64, "centroid bounds"))) return r;
+    RG_CK(launch_init_bounds(static_cast<int*>(cb), st));
+    RG_CK(launch_centroid_bounds(d_lohi, n, static_cast<int*>(cb), st));
+    RG_CK(launch_morton(d_lohi, n, static_cast<int*>(cb), (int)bits, d_codes, nullptr, d_cbounds, st));
+    return RG_OK;
+}
+
+rg_status rg_radix_sort_pairs(const void* d_keys, const uint32_t* d_vals, uint32_t n, uint32_t key_bits,
+                              void* d_keys_out, uint32_t* d_vals_out, void* stream) {
+    if (key_bits != 32 && key_bits != 64) return fail(RG_ERR_INVALID_ARG, "key_bits must be 32 or 64");
+    if (n == 0) return RG_OK;
+    if (!d_keys || !d_vals || !d_keys_out || !d_vals_out) return fail(RG_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    TempAlloc tmp(st);
+    void* scratch;
+    rg_status r;
+    if ((r = tmp.get(&scratch, radix_sort_scratch_bytes(n, (int)key_bits), "sort scratch"))) return r;
+    RG_CK(radix_sort_pairs(d_keys, d_vals, n, (int)key_bits, d_keys_out, d_vals_out, scratch, st));
+    return RG_OK;
+}
+
+rg_status rg_karras(const void* d_sorted_keys, uint32_t n, uint32_t key_bits, uint32_t* d_children,
+                    uint32_t* d_parents, void* stream) {
+    if (key_bits != 32 && key_bits != 64) return fail(RG_ERR_INVALID_ARG, "key_bits must be 32 or 64");
+    if (n < 2 || !d_sorted_keys || !d_children) return fail(RG_ERR_INVALID_ARG, "bad arguments");
+    RG_CK(launch_karras(d_sorted_keys, n, (int)key_bits, d_children, 2, d_parents, static_cast<cudaStream_t>(stream)));
+    return RG_OK;
+}
+
+rg_status rg_blas_export(rg_scene* s, uint32_t blas_id, void* h_nodes, void* h_tris, uint32_t* h_root) {
+    rg_status r;
+    if ((r = check_scene(s))) return r;
+    if (blas_id >= s->blas.size()) return fail(RG_ERR_INVALID_ARG, "no such BLAS");
+    if ((r = set_device(s))) return r;
+    RG_CK(cudaDeviceSynchronize());
+    const BlasHost& b = s->blas[blas_id];
+    if (h_nodes && b.nt > 1) RG_CK(cudaMemcpy(h_nodes, b.nodes, (size_t)(b.nt - 1) * 64, cudaMemcpyDeviceToHost));
+    if (h_tris) RG_CK(cudaMemcpy(h_tris, b.tris, (size_t)b.nt * 48, cudaMemcpyDeviceToHost));
+    if (h_root) *h_root = b.root;
+    return RG_OK;
+}
+
+rg_status rg_tlas_export(rg_scene* s, void* h_nodes, float* h_wbox, float* h_inv, uint32_t* h_order,
+                         uint32_t* h_root) {
+    rg_status r;
+    if ((r = check_scene(s))) return r;
+    if (!s->tlas_built) return fail(RG_ERR_NOT_BUILT, "no TLAS");
+    if ((r = set_device(s))) return r;
+    RG_CK(cudaDeviceSynchronize());
+    const uint32_t n = s->n_inst;
+    if (h_nodes && n > 1) RG_CK(cudaMemcpy(h_nodes, s->tlas_nodes.p, (size_t)(n - 1) * 64, cudaMemcpyDeviceToHost));
+    if (h_wbox) RG_CK(cudaMemcpy(h_wbox, s->wbox.p, (size_t)n * 24, cudaMemcpyDeviceToHost));
+    if (h_order) RG_CK(cudaMemcpy(h_order, s->perm.p, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    if (h_inv) {
+        std::vector<InstDev> v(n);
+        RG_CK(cudaMemcpy(v.data(), s->inst.p, (size_t)n * sizeof(InstDev), cudaMemcpyDeviceToHost));
+        for (uint32_t j = 0; j < n; ++j) {
+            uint32_t k = v[j].id;
+            if (k >= n) return fail(RG_ERR_CUDA, "corrupt instance table");
+            for (int row = 0; row < 3; ++row) {
+                h_inv[12 * (size_t)k + 4 * row + 0] = v[j].inv[row].x;
+                h_inv[12 * (size_t)k + 4 * row + 1] = v[j].inv[row].y;
+                h_inv[12 * (size_t)k + 4 * row + 2] = v[j].inv[row].z;
+                h_inv[12 * (size_t)k + 4 * row + 3] = v[j].inv[row].w;
+            }
+        }
+    }
+    if (h_root) *h_root = s->tlas_root;
+    return RG_OK;
+}
+
+}  // extern "C"
+
+namespace rg {
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+int device_sm_count() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+}  // namespace rg

@@ -1,0 +1,170 @@
+// Internal layout and launcher declarations of librg (not part of the ABI).
+//
+// Device data layout (all arrays 16-byte aligned, read with 16-byte vector
+// loads on the traversal path):
+//
+//   BVH node, 64 B (BLAS and TLAS alike), binary, both child boxes inline:
+//     float4 n0 = {lo0.x, lo0.y, lo0.z, hi0.x}
+//     float4 n1 = {hi0.y, hi0.z, lo1.x, lo1.y}
+//     float4 n2 = {lo1.z, hi1.x, hi1.y, hi1.z}
+//     uint4  n3 = {child0, child1, 0, 0}      bit 31 set = leaf index, else node index
+//   Internal node i is Karras's node i; the root is node 0 (a one-leaf tree has
+//   no nodes and its root reference is the leaf itself).
+//
+//   Triangle, 48 B, stored in BLAS leaf order (sorted by Morton code):
+//     float4 {v0.xyz, prim (uint32 bits)}  float4 {v1.xyz, 0}  float4 {v2.xyz, 0}
+//
+//   Instance, 128 B, stored in TLAS leaf order (InstDev below): float32
+//   world-to-object rows, BLAS pointers, ids, object-to-world rows.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rg.h"
+
+namespace rg {
+
+constexpr uint32_t kLeaf = 0x80000000u;
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kMiss = 0xFFFFFFFFu;
+
+struct __align__(16) InstDev {
+    float4 inv[3];          // world -> object rows (float32 of the float64 inverse)
+    const float4* nodes;    // BLAS nodes
+    const float4* tris;     // BLAS triangles
+    uint32_t root;          // BLAS root reference
+    uint32_t id;            // index in the caller's instance array
+    uint32_t material;
+    uint32_t blas;
+    float4 m[3];            // object -> world rows (as given)
+};
+static_assert(sizeof(InstDev) == 128, "instance record is 128 B");
+
+struct __align__(16) BlasDev {
+    const float4* nodes;
+    const float4* tris;
+    uint32_t root;
+    uint32_t nt;
+    float lo[3];
+    float hi[3];
+};
+static_assert(sizeof(BlasDev) == 48, "BLAS descriptor is 48 B");
+
+// Per-ray payload of the wavefront renderer, 16 B: pixel index and the RGB
+// weight (throughput for path rays, unshadowed contribution for shadow rays).
+struct __align__(16) Payload {
+    uint32_t pixel;
+    float r, g, b;
+};
+
+// Internal closest-hit record of the renderer, 16 B: TLAS leaf of the
+// instance, BLAS leaf of the triangle, t.
+struct __align__(16) HitDev {
+    uint32_t inst_leaf;
+    uint32_t tri_leaf;
+    float t;
+    uint32_t pad;
+};
+
+// Device-side status word and statistics of one scene.
+struct DevStatus {
+    int error;                 // first rg_status recorded by a kernel
+    int pad;
+    unsigned long long closest_rays;
+    unsigned long long shadow_rays;
+    unsigned long long count[2][3];  // [closest, any][node visits, triangle tests, instance entries]
+};
+
+// Kernels launched by the library since process start (host counter).
+void count_launches(unsigned n);
+unsigned long long launches_so_far();
+
+__device__ __forceinline__ void record_error(DevStatus* st, int code) {
+    if (st) atomicCAS(&st->error, 0, code);
+}
+
+// Monotone map of float32 to int32 (for atomicMin/atomicMax on floats).
+__device__ __forceinline__ int f2ord(float f) {
+    int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float ord2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
+
+// ---------------------------------------------------------------- launchers
+// build.cu
+cudaError_t launch_tri_bounds(const float* vtx, uint32_t nv, const uint32_t* idx, uint32_t nt, float* lohi,
+                              int* cb_ord, DevStatus* st, cudaStream_t s);
+cudaError_t launch_init_bounds(int* cb_ord, cudaStream_t s);
+cudaError_t launch_centroid_bounds(const float* lohi, uint32_t n, int* cb_ord, cudaStream_t s);
+cudaError_t launch_morton(const float* lohi, uint32_t n, const int* cb_ord, int bits, void* codes, uint32_t* vals,
+                          float* cb_out, cudaStream_t s);
+// Radix sort; scratch must hold radix_sort_scratch_bytes(n, key_bits) bytes.
+size_t radix_sort_scratch_bytes(uint32_t n, int key_bits);
+cudaError_t radix_sort_pairs(const void* keys_in, const uint32_t* vals_in, uint32_t n, int key_bits, void* keys_out,
+                             uint32_t* vals_out, void* scratch, cudaStream_t s);
+cudaError_t launch_karras(const void* keys, uint32_t n, int key_bits, uint32_t* child_base, int child_stride_words,
+                          uint32_t* parents, cudaStream_t s);
+cudaError_t launch_blas_leaves_refit(const float* vtx, const uint32_t* idx, const uint32_t* perm, const float* lohi,
+                                     uint32_t n, const uint32_t* parents, float4* nodes, uint32_t* flags,
+                                     float4* tris, BlasDev* blas_out, DevStatus* st, cudaStream_t s);
+cudaError_t launch_instance_prep(const rg_instance* in, uint32_t n, const BlasDev* blas, uint32_t nblas,
+                                 InstDev* tmp, float* wbox, int* cb_ord, bool check_blas, DevStatus* st,
+                                 cudaStream_t s);
+cudaError_t launch_tlas_leaves_refit(const InstDev* tmp, const float* wbox, const uint32_t* perm, uint32_t n,
+                                     const uint32_t* parents, float4* nodes, uint32_t* flags, InstDev* inst_out,
+                                     DevStatus* st, cudaStream_t s);
+
+// trace.cu
+enum TraceMode { kModeClosestAbi = 0, kModeAnyAbi = 1, kModeClosestRender = 2, kModeShadowRender = 3 };
+struct TraceArgs {
+    const float4* rays;          // n x 2 float4 {o, tmin}, {d, tmax}
+    uint32_t n;                  // ray count, or
+    const uint32_t* d_count;     // device ray count (if not null)
+    const float4* tlas_nodes;
+    uint32_t tlas_root;
+    const InstDev* inst;
+    uint32_t n_inst;
+    rg_hit* hits_abi;            // kModeClosestAbi / kModeAnyAbi
+    HitDev* hits_render;         // kModeClosestRender
+    const Payload* payload;      // kModeShadowRender
+    float* image;                // kModeShadowRender: RGBA32F accumulation
+    uint32_t* work_counter;      // persistent-thread work queue head (zeroed before launch)
+    DevStatus* st;
+    uint32_t iter_cap;           // bound on the loop steps of one ray (a valid traversal needs fewer)
+};
+cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a, cudaStream_t s);
+
+// render.cu
+struct CameraDev {
+    float eye[3], target[3], up[3], vfov_deg;
+};
+struct ShadeArgs {
+    const float4* rays;
+    const Payload* payload;
+    const HitDev* hits;
+    const uint32_t* d_count;     // rays in this wavefront
+    const InstDev* inst;
+    const rg_material* mats;
+    uint32_t n_mats;
+    const rg_light* lights;
+    uint32_t n_lights;
+    float bg[3];
+    float ambient;
+    uint32_t depth, max_depth;
+    float* image;
+    float4* next_rays;
+    Payload* next_payload;
+    uint32_t* next_count;
+    float4* shadow_rays;
+    Payload* shadow_payload;
+    uint32_t* shadow_count;
+    DevStatus* st;
+};
+cudaError_t launch_raygen(const CameraDev& cam, uint32_t w, uint32_t h, float4* rays, Payload* payload,
+                          cudaStream_t s);
+cudaError_t launch_shade(const ShadeArgs& a, uint32_t n_max, cudaStream_t s);
+
+int device_sm_count();
+
+}  // namespace rg

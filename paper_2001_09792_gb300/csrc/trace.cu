@@ -1,0 +1,370 @@
+// Ray traversal of the two-level BVH: closest-hit, any-hit and miss (paper
+// Sec. 1: per ray, the closest-hit or any-hit shader runs when the ray meets a
+// triangle, the miss shader when it meets none).
+//
+// Persistent warps pull 32-ray batches from a global counter.  Each thread
+// runs a stack traversal: TLAS nodes in world space; at an instance leaf the
+// ray is moved to object space with the instance's float32 inverse (t is
+// shared, the direction is not renormalised), a marker is pushed, and the
+// BLAS is traversed; popping the marker restores the world ray.  Nodes are
+// 64 B (two child boxes), read with four 16 B loads; triangles are 48 B, read
+// with three 16 B loads.
+//
+// Triangle test: the watertight test of Woop, Benthin & Wald (JCGT 2013) in
+// float32, with every product and difference of the edge functions rounded
+// separately (no FMA), so that a shared edge evaluates to exactly opposite
+// values in its two triangles and no ray leaks through it.  Box test: slabs
+// with the far distance scaled by 1 + 2*gamma_3 (Ize, "Robust BVH Ray
+// Traversal", JCGT 2013), and a relative slack of 2^-12 on the culling
+// distance, so that a box is never culled while a triangle inside it can
+// still win.  Ties in t are broken by (instance, prim), which makes the
+// result independent of the visit order (BVH == brute force).
+#include "rg_internal.cuh"
+
+namespace rg {
+
+namespace {
+
+constexpr int kStack = 64;
+constexpr uint32_t kMarker = 0xFFFFFFFEu;
+constexpr int kTraceBlock = 128;
+// 1 + 2 * gamma_3, gamma_3 = 3u / (1 - 3u), u = 2^-24
+constexpr float kIze = 1.0f + 2.0f * (3.0f * 5.9604644775390625e-08f) / (1.0f - 3.0f * 5.9604644775390625e-08f);
+constexpr float kCullSlack = 1.0f + 1.0f / 4096.0f;
+
+// 1/d with IEEE semantics: a zero component gives +-inf.
+__device__ __forceinline__ float safe_rcp(float d) { return __fdiv_rn(1.0f, d); }
+
+struct SpaceRay {
+    float ox, oy, oz;
+    float ix, iy, iz;
+};
+
+// Per-axis slab interval.  For a zero direction component the distances are
+// +-inf, or NaN (0 * inf) when the origin lies on the slab plane.  The PTX
+// min.NaN / max.NaN forms return NaN if either operand is NaN, and the
+// fminf/fmaxf that combine the axes drop NaN, so an axis whose origin lies in
+// the (closed) slab with d == 0 leaves the interval unconstrained, and one
+// outside it makes the interval empty.
+__device__ __forceinline__ float nan_min(float a, float b) {
+    float r;
+    asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float nan_max(float a, float b) {
+    float r;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ bool slab(float lx, float ly, float lz, float hx, float hy, float hz, const SpaceRay& r,
+                                     float tmin, float tlim, float& tnear) {
+    float t0x = __fmul_rn(__fsub_rn(lx, r.ox), r.ix), t1x = __fmul_rn(__fsub_rn(hx, r.ox), r.ix);
+    float t0y = __fmul_rn(__fsub_rn(ly, r.oy), r.iy), t1y = __fmul_rn(__fsub_rn(hy, r.oy), r.iy);
+    float t0z = __fmul_rn(__fsub_rn(lz, r.oz), r.iz), t1z = __fmul_rn(__fsub_rn(hz, r.oz), r.iz);
+    float tn = fmaxf(fmaxf(nan_min(t0x, t1x), nan_min(t0y, t1y)), fmaxf(nan_min(t0z, t1z), tmin));
+    float tf = fminf(fminf(nan_max(t0x, t1x), nan_max(t0y, t1y)), nan_max(t0z, t1z));
+    tf = fminf(__fmul_rn(tf, kIze), tlim);
+    tnear = tn;
+    return tn <= tf;
+}
+
+__device__ __forceinline__ float sel(float4 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+// Watertight-test state of the object-space ray.
+struct Shear {
+    float ox, oy, oz;  // origin permuted to (kx, ky, kz)
+    float Sx, Sy, Sz;
+    int kx, ky, kz;
+};
+
+__device__ __forceinline__ Shear make_shear(float ox, float oy, float oz, float dx, float dy, float dz) {
+    Shear s;
+    float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
+    int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    float dkz = kz == 0 ? dx : (kz == 1 ? dy : dz);
+    if (dkz < 0.0f) {
+        int t = kx;
+        kx = ky;
+        ky = t;
+    }
+    float dkx = kx == 0 ? dx : (kx == 1 ? dy : dz);
+    float dky = ky == 0 ? dx : (ky == 1 ? dy : dz);
+    s.Sx = __fdiv_rn(dkx, dkz);
+    s.Sy = __fdiv_rn(dky, dkz);
+    s.Sz = __fdiv_rn(1.0f, dkz);
+    s.kx = kx;
+    s.ky = ky;
+    s.kz = kz;
+    s.ox = kx == 0 ? ox : (kx == 1 ? oy : oz);
+    s.oy = ky == 0 ? ox : (ky == 1 ? oy : oz);
+    s.oz = kz == 0 ? ox : (kz == 1 ? oy : oz);
+    return s;
+}
+
+struct TriResult {
+    bool hit;
+    float t, V, W, det;
+};
+
+// Woop-Benthin-Wald watertight test; returns the hit if t in [tmin, tmax_incl].
+__device__ __forceinline__ TriResult tri_test(const Shear& s, float4 v0, float4 v1, float4 v2, float tmin,
+                                              float tmax_incl) {
+    TriResult r;
+    r.hit = false;
+    float az = __fsub_rn(sel(v0, s.kz), s.oz), bz = __fsub_rn(sel(v1, s.kz), s.oz), cz = __fsub_rn(sel(v2, s.kz), s.oz);
+    float Ax = __fsub_rn(__fsub_rn(sel(v0, s.kx), s.ox), __fmul_rn(s.Sx, az));
+    float Ay = __fsub_rn(__fsub_rn(sel(v0, s.ky), s.oy), __fmul_rn(s.Sy, az));
+    float Bx = __fsub_rn(__fsub_rn(sel(v1, s.kx), s.ox), __fmul_rn(s.Sx, bz));
+    float By = __fsub_rn(__fsub_rn(sel(v1, s.ky), s.oy), __fmul_rn(s.Sy, bz));
+    float Cx = __fsub_rn(__fsub_rn(sel(v2, s.kx), s.ox), __fmul_rn(s.Sx, cz));
+    float Cy = __fsub_rn(__fsub_rn(sel(v2, s.ky), s.oy), __fmul_rn(s.Sy, cz));
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return r;
+    float det = __fadd_rn(__fadd_rn(U, V), W);
+    if (det == 0.0f) return r;
+    float T = __fadd_rn(__fadd_rn(__fmul_rn(U, __fmul_rn(s.Sz, az)), __fmul_rn(V, __fmul_rn(s.Sz, bz))),
+                        __fmul_rn(W, __fmul_rn(s.Sz, cz)));
+    float t = __fdiv_rn(T, det);
+    if (!(t >= tmin && t <= tmax_incl)) return r;
+    r.hit = true;
+    r.t = t;
+    r.V = V;
+    r.W = W;
+    r.det = det;
+    return r;
+}
+
+template <int MODE, bool BRUTE, bool STATS>
+__global__ void __launch_bounds__(kTraceBlock) k_trace(TraceArgs a) {
+    const uint32_t iter_cap = a.iter_cap;
+    constexpr bool kAny = (MODE == kModeAnyAbi || MODE == kModeShadowRender);
+    const uint32_t n = a.d_count ? *a.d_count : a.n;
+    const int lane = threadIdx.x & 31;
+    unsigned long long c_nodes = 0, c_tris = 0, c_inst = 0;
+    for (;;) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(a.work_counter, 32u);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (base >= n) break;
+        const uint32_t i = base + lane;
+        if (i >= n) continue;
+
+        const float4 r0 = __ldg(a.rays + 2 * (size_t)i), r1 = __ldg(a.rays + 2 * (size_t)i + 1);
+        const float tmin = r0.w, tmax = r1.w;
+        SpaceRay wr;
+        wr.ox = r0.x; wr.oy = r0.y; wr.oz = r0.z;
+        wr.ix = safe_rcp(r1.x); wr.iy = safe_rcp(r1.y); wr.iz = safe_rcp(r1.z);
+        SpaceRay cr = wr;  // ray of the current space
+        Shear sh;
+
+        float best_t = tmax;
+        uint32_t best_id = kMiss, best_prim = kMiss;
+        uint32_t best_il = kMiss, best_tl = kMiss;
+        float best_V = 0.f, best_W = 0.f, best_det = 1.f;
+        bool found = false;
+
+        uint32_t stack[kStack];
+        int sp = 0;
+        uint32_t ref = a.tlas_root;
+        bool in_blas = false;
+        const float4* nodes = a.tlas_nodes;
+        const float4* tris = nullptr;
+        uint32_t cur_id = 0, cur_leaf = 0;
+        bool ok = true;
+
+        for (uint32_t iter = 0;; ++iter) {
+            if (iter >= iter_cap) {
+                record_error(a.st, RG_ERR_TIMEOUT);
+                ok = false;
+                break;
+            }
+            if (ref == kNone) {
+                if (sp == 0) break;
+                ref = stack[--sp];
+                if (ref == kMarker) {
+                    in_blas = false;
+                    nodes = a.tlas_nodes;
+                    cr = wr;
+                    ref = kNone;
+                }
+                continue;
+            }
+            if (!(ref & kLeaf)) {
+                const float4* nd = nodes + 4 * (size_t)ref;
+                const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2);
+                const uint4 n3 = __ldg(reinterpret_cast<const uint4*>(nd + 3));
+                if (STATS) ++c_nodes;
+                const float tlim = kAny ? __fmul_rn(tmax, kCullSlack) : __fmul_rn(best_t, kCullSlack);
+                float tn0, tn1;
+                bool h0 = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, cr, tmin, tlim, tn0);
+                bool h1 = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, cr, tmin, tlim, tn1);
+                if (BRUTE) h0 = h1 = true;
+                if (h0 && h1) {
+                    uint32_t nearc = tn0 <= tn1 ? n3.x : n3.y;
+                    uint32_t farc = tn0 <= tn1 ? n3.y : n3.x;
+                    if (sp >= kStack) {
+                        record_error(a.st, RG_ERR_STACK);
+                        ok = false;
+                        break;
+                    }
+                    stack[sp++] = farc;
+                    ref = nearc;
+                } else if (h0) {
+                    ref = n3.x;
+                } else if (h1) {
+                    ref = n3.y;
+                } else {
+                    ref = kNone;
+                }
+                continue;
+            }
+            const uint32_t leaf = ref & ~kLeaf;
+            if (!in_blas) {
+                const InstDev* I = a.inst + leaf;
+                const float4 m0 = __ldg(&I->inv[0]), m1 = __ldg(&I->inv[1]), m2 = __ldg(&I->inv[2]);
+                const float4 meta0 = __ldg(reinterpret_cast<const float4*>(&I->nodes));        // nodes, tris
+                const uint4 meta1 = __ldg(reinterpret_cast<const uint4*>(&I->root));           // root, id, mat, blas
+                if (STATS) ++c_inst;
+                const float dx = r1.x, dy = r1.y, dz = r1.z;
+                float ox = fmaf(m0.x, wr.ox, fmaf(m0.y, wr.oy, fmaf(m0.z, wr.oz, m0.w)));
+                float oy = fmaf(m1.x, wr.ox, fmaf(m1.y, wr.oy, fmaf(m1.z, wr.oz, m1.w)));
+                float oz = fmaf(m2.x, wr.ox, fmaf(m2.y, wr.oy, fmaf(m2.z, wr.oz, m2.w)));
+                float ddx = fmaf(m0.x, dx, fmaf(m0.y, dy, __fmul_rn(m0.z, dz)));
+                float ddy = fmaf(m1.x, dx, fmaf(m1.y, dy, __fmul_rn(m1.z, dz)));
+                float ddz = fmaf(m2.x, dx, fmaf(m2.y, dy, __fmul_rn(m2.z, dz)));
+                cr.ox = ox; cr.oy = oy; cr.oz = oz;
+                cr.ix = safe_rcp(ddx); cr.iy = safe_rcp(ddy); cr.iz = safe_rcp(ddz);
+                sh = make_shear(ox, oy, oz, ddx, ddy, ddz);
+                const unsigned long long pn = ((unsigned long long)__float_as_uint(meta0.y) << 32) | __float_as_uint(meta0.x);
+                const unsigned long long pt = ((unsigned long long)__float_as_uint(meta0.w) << 32) | __float_as_uint(meta0.z);
+                nodes = reinterpret_cast<const float4*>(pn);
+                tris = reinterpret_cast<const float4*>(pt);
+                cur_id = meta1.y;
+                cur_leaf = leaf;
+                in_blas = true;
+                if (sp >= kStack) {
+                    record_error(a.st, RG_ERR_STACK);
+                    ok = false;
+                    break;
+                }
+                stack[sp++] = kMarker;
+                ref = meta1.x;
+                continue;
+            }
+            // triangle leaf
+            {
+                const float4* tp = tris + 3 * (size_t)leaf;
+                const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+                if (STATS) ++c_tris;
+                TriResult h = tri_test(sh, v0, v1, v2, tmin, kAny ? tmax : best_t);
+                ref = kNone;
+                if (h.hit) {
+                    const uint32_t prim = __float_as_uint(v0.w);
+                    if (kAny) {
+                        best_t = h.t; best_id = cur_id; best_prim = prim;
+                        best_V = h.V; best_W = h.W; best_det = h.det;
+                        found = true;
+                        break;
+                    }
+                    bool better = h.t < best_t || cur_id < best_id || (cur_id == best_id && prim < best_prim);
+                    if (better) {
+                        best_t = h.t; best_id = cur_id; best_prim = prim;
+                        best_il = cur_leaf; best_tl = leaf;
+                        best_V = h.V; best_W = h.W; best_det = h.det;
+                        found = true;
+                    }
+                }
+            }
+        }
+        if (!ok) found = false;
+
+        if (MODE == kModeClosestAbi || MODE == kModeAnyAbi) {
+            rg_hit out;
+            if (found) {
+                out.instance = best_id;
+                out.prim = best_prim;
+                out.t = best_t;
+                out.u = __fdiv_rn(best_V, best_det);
+                out.v = __fdiv_rn(best_W, best_det);
+            } else {
+                out.instance = kMiss;
+                out.prim = kMiss;
+                out.t = __int_as_float(0x7F800000);
+                out.u = 0.f;
+                out.v = 0.f;
+            }
+            a.hits_abi[i] = out;
+        } else if (MODE == kModeClosestRender) {
+            HitDev hd;
+            hd.inst_leaf = found ? best_il : kMiss;
+            hd.tri_leaf = found ? best_tl : kMiss;
+            hd.t = found ? best_t : __int_as_float(0x7F800000);
+            hd.pad = 0;
+            *reinterpret_cast<uint4*>(a.hits_render + i) = *reinterpret_cast<const uint4*>(&hd);
+        } else {  // shadow: accumulate the unshadowed contribution
+            if (!found && ok) {
+                const Payload p = a.payload[i];
+                float* px = a.image + 4 * (size_t)p.pixel;
+                atomicAdd(px + 0, p.r);
+                atomicAdd(px + 1, p.g);
+                atomicAdd(px + 2, p.b);
+            }
+        }
+    }
+    if (STATS) {
+        // warp-reduce, one set of atomics per warp
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            c_nodes += __shfl_xor_sync(0xFFFFFFFFu, c_nodes, off);
+            c_tris += __shfl_xor_sync(0xFFFFFFFFu, c_tris, off);
+            c_inst += __shfl_xor_sync(0xFFFFFFFFu, c_inst, off);
+        }
+        if (lane == 0) {
+            unsigned long long* c = a.st->count[kAny ? 1 : 0];
+            atomicAdd(c + 0, c_nodes);
+            atomicAdd(c + 1, c_tris);
+            atomicAdd(c + 2, c_inst);
+        }
+    }
+}
+
+template <int MODE, bool BRUTE, bool STATS>
+cudaError_t launch_mode(const TraceArgs& a, cudaStream_t s) {
+    static int blocks = 0;
+    if (blocks == 0) {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<MODE, BRUTE, STATS>, kTraceBlock, 0);
+        if (e != cudaSuccess) return e;
+        blocks = device_sm_count() * (per_sm > 0 ? per_sm : 1);
+    }
+    k_trace<MODE, BRUTE, STATS><<<blocks, kTraceBlock, 0, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a, cudaStream_t s) {
+    switch (mode) {
+        case kModeClosestAbi:
+            if (brute) return launch_mode<kModeClosestAbi, true, false>(a, s);
+            return stats ? launch_mode<kModeClosestAbi, false, true>(a, s) : launch_mode<kModeClosestAbi, false, false>(a, s);
+        case kModeAnyAbi:
+            if (brute) return launch_mode<kModeAnyAbi, true, false>(a, s);
+            return stats ? launch_mode<kModeAnyAbi, false, true>(a, s) : launch_mode<kModeAnyAbi, false, false>(a, s);
+        case kModeClosestRender:
+            return stats ? launch_mode<kModeClosestRender, false, true>(a, s)
+                         : launch_mode<kModeClosestRender, false, false>(a, s);
+        case kModeShadowRender:
+            return stats ? launch_mode<kModeShadowRender, false, true>(a, s)
+                         : launch_mode<kModeShadowRender, false, false>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace rg
