@@ -210,6 +210,28 @@ rg_status rg_blas_export(rg_scene* scene, uint32_t blas_id, void* h_nodes, void*
 rg_status rg_tlas_export(rg_scene* scene, void* h_nodes, float* h_wbox, float* h_inv, uint32_t* h_order,
                          uint32_t* h_root);
 
+/* ---- sorting without allocation ---------------------------------------- */
+
+/* The paper has no counterpart to this call; it is a service of the library.
+ * Same result as rg_radix_sort_pairs (same arguments and order), but the call
+ * makes no device allocation: its temporaries live in one fixed array inside
+ * librg.so, sized for RG_NOALLOC_SORT_MAX_PAIRS pairs of 64-bit keys (about
+ * 3.2 MB, held on every GPU that loads the library until the process exits).
+ * It is meant for callers that cannot allocate device memory: code that runs
+ * while a stream is captured into a CUDA graph (cudaMalloc is refused during
+ * capture), code whose device memory is owned by a caching allocator that
+ * holds what the GPU has free, and frame loops that must not stall on an
+ * allocation.  The caller still provides inputs and outputs.
+ *  - n > RG_NOALLOC_SORT_MAX_PAIRS returns RG_ERR_INVALID_ARG.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - All calls share the array and it keeps the last call's contents (every
+ *    byte a call reads there it wrote first): calls whose GPU work overlaps
+ *    (other streams, other host threads) race and must be serialised. */
+#define RG_NOALLOC_SORT_MAX_PAIRS 262144u
+rg_status rg_radix_sort_pairs_noalloc(const void* d_keys, const uint32_t* d_vals, uint32_t n, uint32_t key_bits,
+                                      void* d_keys_out, uint32_t* d_vals_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,8 @@ MISS = 0xFFFFFFFF
 SYMBOLS = ["rg_scene_create", "rg_scene_destroy", "rg_blas_build", "rg_tlas_build", "rg_tlas_refit",
            "rg_scene_set_materials", "rg_scene_set_lights", "rg_trace_rays", "rg_render", "rg_sync", "rg_get_stats",
            "rg_reset_stats", "rg_last_error", "rg_tri_bounds", "rg_morton_codes", "rg_radix_sort_pairs", "rg_karras",
-           "rg_blas_export", "rg_tlas_export"]
+           "rg_blas_export", "rg_tlas_export", "rg_radix_sort_pairs_noalloc"]
+RG_NOALLOC_SORT_MAX_PAIRS = 262144
 
 f32x3 = ctypes.c_float * 3
 
@@ -99,6 +100,7 @@ def lib():
             "rg_karras": [P, u32, u32, P, P, P],
             "rg_blas_export": [P, u32, P, P, ctypes.POINTER(u32)],
             "rg_tlas_export": [P, P, P, P, P, ctypes.POINTER(u32)],
+            "rg_radix_sort_pairs_noalloc": [P, P, u32, u32, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -295,6 +297,21 @@ def rg_radix_sort_pairs(keys, vals, stream=None):
     _check(lib().rg_radix_sort_pairs(_dev(keys, keys.dtype, None, "keys"), _dev(vals, torch.int32, None, "vals"),
                                      keys.shape[0], key_bits, ctypes.c_void_p(ko.data_ptr()),
                                      ctypes.c_void_p(vo.data_ptr()), _stream(stream)))
+    return ko, vo
+
+
+def rg_radix_sort_pairs_noalloc(keys, vals, keys_out=None, vals_out=None, stream=None):
+    """rg_radix_sort_pairs through the entry point that allocates nothing on
+    the device (its temporaries live in a fixed array inside librg.so; at
+    most RG_NOALLOC_SORT_MAX_PAIRS pairs).  Outputs are caller buffers; they
+    are allocated here only when not given."""
+    torch = _torch()
+    key_bits = 64 if keys.dtype == torch.int64 else 32
+    ko = torch.empty_like(keys) if keys_out is None else keys_out
+    vo = torch.empty_like(vals) if vals_out is None else vals_out
+    _check(lib().rg_radix_sort_pairs_noalloc(_dev(keys, keys.dtype, None, "keys"), _dev(vals, torch.int32, None, "vals"),
+                                             keys.shape[0], key_bits, _dev(ko, keys.dtype, None, "keys_out"),
+                                             _dev(vo, torch.int32, None, "vals_out"), _stream(stream)))
     return ko, vo
 
 

@@ -755,6 +755,8 @@ rg_status rg_tlas_export(rg_scene* s, void* h_nodes, float* h_wbox, float* h_inv
 }  // extern "C"
 
 namespace rg {
+rg_status report_error(rg_status code, const char* msg) { return fail(code, msg); }
+
 static std::atomic<unsigned long long> g_launches{0};
 void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }

@@ -167,4 +167,7 @@ cudaError_t launch_shade(const ShadeArgs& a, uint32_t n_max, cudaStream_t s);
 
 int device_sm_count();
 
+// Record `msg` as this thread's rg_last_error() and return `code`.
+rg_status report_error(rg_status code, const char* msg);
+
 }  // namespace rg
