@@ -51,7 +51,7 @@ WORKLOAD = ("medium: 64 instances of 4 procedural meshes (UV sphere 80x40, icosp
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU baseline budget (wall seconds)")
@@ -73,7 +73,7 @@ REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_powe
 
 
 class ClockSampler:
-    """nvidia-smi samples every 200 ms during the timed region."""
+    """nvidia-smi samples every 50 ms during the timed region."""
 
     def __init__(self, gpu_index):
         self.gpu_index = gpu_index
@@ -88,7 +88,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -251,21 +251,11 @@ def run_native(args, world, rank, local):
         e2e_rays = st2["closest_rays"] + st2["shadow_rays"]
         e2e = (e2e_rays, sum(e2e_ms) / 1e3, inst_host[0].nbytes, W * H * 16)
 
-    # aggregate over ranks
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_s, float(rays)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_s_all, rays_all = float(tmax[0]), float(t[1])
-        if e2e:
-            e = torch.tensor([e2e[1], float(e2e[0])], dtype=torch.float64, device="cuda")
-            dist.all_reduce(e[:1], op=dist.ReduceOp.MAX)
-            dist.all_reduce(e[1:], op=dist.ReduceOp.SUM)
-            e2e = (float(e[1]), float(e[0]), e2e[2], e2e[3])
-    else:
-        total_s_all, rays_all = total_s, float(rays)
+    # aggregate over ranks: the slowest rank's time, every rank's rays
+    (total_s_all, e2e_s_all), (rays_all, e2e_rays_all) = reduce_over_ranks(
+        [total_s, e2e[1] if e2e else 0.0], [float(rays), float(e2e[0]) if e2e else 0.0], "cuda")
+    if e2e:
+        e2e = (e2e_rays_all, e2e_s_all, e2e[2], e2e[3])
 
     if rank == 0:
         peak, peak_kind = measured_peaks()
@@ -320,6 +310,20 @@ def run_native(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def reduce_over_ranks(max_vals, sum_vals, device):
+    """MAX-reduce `max_vals` and SUM-reduce `sum_vals` over the ranks of the
+    default process group (identity when there is none or one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(max_vals), list(sum_vals)
+    t_max = torch.tensor(list(max_vals), dtype=torch.float64, device=device)
+    t_sum = torch.tensor(list(sum_vals), dtype=torch.float64, device=device)
+    dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t_sum, op=dist.ReduceOp.SUM)
+    return t_max.tolist(), t_sum.tolist()
 
 
 def gpu_index(local):
