@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU baseline budget (wall seconds)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--plain", action="store_true",
+                   help="trace with the float32 binary BVH (default: the compressed 8-wide BVH)")
     p.add_argument("--workload", default="medium", choices=["medium", "large"],
                    help="medium: the render frame (default); large: incoherent closest/any-hit queries")
     return p.parse_args()
@@ -151,6 +153,20 @@ def traffic_record():
     return None
 
 
+def path_flag(args):
+    import paper_2001_09792_gb300 as rg
+    return 0 if args.plain else rg.RG_SCENE_COMPRESSED
+
+
+def node_bytes(args):
+    return 64 if args.plain else 80
+
+
+def kernel_name(args, where):
+    return (f"k_trace closest-hit, binary float32 BVH ({where})" if args.plain
+            else f"k_trace8 closest-hit, compressed 8-wide BVH ({where})")
+
+
 def frame_motions(scene, n):
     return [g.motion(scene.M, k) for k in range(n)]
 
@@ -175,7 +191,7 @@ def run_native(args, world, rank, local):
 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    gs = rg.GpuScene(s, flags=rg.RG_SCENE_TIMING)
+    gs = rg.GpuScene(s, flags=rg.RG_SCENE_TIMING | path_flag(args))
     torch.cuda.synchronize()
     blas_build_ms = (time.perf_counter() - t0) * 1e3  # four BLAS + first TLAS, host-timed incl. uploads
     blas_ids = [gs.blas[m] for m in s.mesh_id]
@@ -195,7 +211,7 @@ def run_native(args, world, rank, local):
     torch.cuda.synchronize()
 
     # algorithmic work per closest-hit ray: one counting frame on a second scene
-    with rg.GpuScene(s, flags=rg.RG_SCENE_COUNT) as gc:
+    with rg.GpuScene(s, flags=rg.RG_SCENE_COUNT | path_flag(args)) as gc:
         rg.rg_tlas_build(gc.h, torch.from_numpy(inst_host[args.warmup]).cuda())
         rg.rg_reset_stats(gc.h)
         rg.rg_render(gc.h, cam, W, H, D)
@@ -262,14 +278,14 @@ def run_native(args, world, rank, local):
     if rank == 0:
         peak, peak_kind = measured_peaks()
         cr = max(cst["closest_rays"], 1)
-        bytes_per_ray = 32 + 16 + 64 * cst["node_visits"] / cr + 48 * cst["tri_tests"] / cr + 80 * cst["inst_entries"] / cr
+        bytes_per_ray = 32 + 16 + node_bytes(args) * cst["node_visits"] / cr + 48 * cst["tri_tests"] / cr + 80 * cst["inst_entries"] / cr
         launch_ms = st["trace_ms"] / max(st["trace_launches"], 1)
         rays_per_launch = st["closest_rays"] / max(st["trace_launches"], 1)
         achieved = bytes_per_ray * rays_per_launch / (launch_ms / 1e3) / 1e9
-        tr = traffic_record()
+        tr = traffic_record() if args.plain else None
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(achieved / peak, 4), "traffic": None if tr is None else round(tr * rays_per_launch),
-                    "kernel": "k_trace closest-hit (render)", "peak_kind": peak_kind,
+                    "kernel": kernel_name(args, "render"), "peak_kind": peak_kind,
                     "algorithmic_bytes_per_ray": round(bytes_per_ray, 1),
                     "nodes_per_ray": round(cst["node_visits"] / cr, 2), "tris_per_ray": round(cst["tri_tests"] / cr, 2),
                     "inst_per_ray": round(cst["inst_entries"] / cr, 3), "avg_launch_ms": round(launch_ms, 4),
@@ -296,7 +312,7 @@ def run_native(args, world, rank, local):
                        "p50_ms": round(ms_sorted[len(ms) // 2], 3),
                        "p99_ms": round(ms_sorted[min(len(ms) - 1, math.ceil(0.99 * len(ms)) - 1)], 3),
                        "blas_build_ms": round(blas_build_ms, 2), "l2": "flushed before each step (256 MiB write)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "bvh": "binary float32" if args.plain else "compressed 8-wide"},
             "roofline": roofline,
             "gpu_launches": int(st["kernel_launches"]),
         }
@@ -428,7 +444,7 @@ def run_native_large(args, world, rank, local):
     n = 1 << 24
     closest, anyhit = g.large_rays(s, n)
     n_frames = args.warmup + args.steps
-    gs = rg.GpuScene(s, flags=rg.RG_SCENE_TIMING)
+    gs = rg.GpuScene(s, flags=rg.RG_SCENE_TIMING | path_flag(args))
     blas_ids = [gs.blas[m] for m in s.mesh_id]
     inst_dev = [torch.from_numpy(rg.pack_instances(g.motion(s.M, k), blas_ids, s.material_id)).cuda()
                 for k in range(min(n_frames, 8))]
@@ -445,7 +461,7 @@ def run_native_large(args, world, rank, local):
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize()
-    with rg.GpuScene(s, flags=rg.RG_SCENE_COUNT) as gc:
+    with rg.GpuScene(s, flags=rg.RG_SCENE_COUNT | path_flag(args)) as gc:
         rg.rg_tlas_build(gc.h, torch.from_numpy(rg.pack_instances(g.motion(s.M, 0), [gc.blas[m] for m in s.mesh_id],
                                                                   s.material_id)).cuda())
         rg.rg_reset_stats(gc.h)
@@ -478,7 +494,7 @@ def run_native_large(args, world, rank, local):
     if rank == 0:
         peak, peak_kind = measured_peaks()
         cr = max(cst["closest_rays"], 1)
-        bpr = 32 + 20 + 64 * cst["node_visits"] / cr + 48 * cst["tri_tests"] / cr + 80 * cst["inst_entries"] / cr
+        bpr = 32 + 20 + node_bytes(args) * cst["node_visits"] / cr + 48 * cst["tri_tests"] / cr + 80 * cst["inst_entries"] / cr
         launch_ms = st["trace_ms"] / max(st["trace_launches"], 1)
         achieved = bpr * (st["closest_rays"] / max(st["trace_launches"], 1)) / (launch_ms / 1e3) / 1e9
         ms_sorted = sorted(ms)
@@ -491,10 +507,10 @@ def run_native_large(args, world, rank, local):
                           "closest_ms": round(launch_ms, 3), "any_ms": round(st["any_ms"] / max(st["any_launches"], 1), 3),
                           "p50_ms": round(ms_sorted[len(ms) // 2], 3), "p99_ms": round(ms_sorted[-1], 3),
                           "l2": "inputs larger than L2 (2 x 512 MiB of rays, ~220 MB of BVH)",
-                          "parallelism": f"replicas x{world}"},
+                          "parallelism": f"replicas x{world}", "bvh": "binary float32" if args.plain else "compressed 8-wide"},
                "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                             "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
-                            "kernel": "k_trace closest-hit (rg_trace_rays)", "algorithmic_bytes_per_ray": round(bpr, 1),
+                            "kernel": kernel_name(args, "rg_trace_rays"), "algorithmic_bytes_per_ray": round(bpr, 1),
                             "nodes_per_ray": round(cst["node_visits"] / cr, 2),
                             "tris_per_ray": round(cst["tri_tests"] / cr, 2),
                             "inst_per_ray": round(cst["inst_entries"] / cr, 3)},

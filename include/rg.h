@@ -80,8 +80,12 @@ typedef struct { float pos[3]; float intensity[3]; } rg_light;
 /* Scene-wide shading constants.  flags: RG_SCENE_TIMING records CUDA events
  * around every traversal launch; RG_SCENE_COUNT makes rg_render's traversals
  * count node visits, triangle tests and instance entries (slower; see
- * rg_get_stats). */
-enum { RG_SCENE_TIMING = 1u, RG_SCENE_COUNT = 2u };
+ * rg_get_stats); RG_SCENE_COMPRESSED builds, next to every binary BVH, a
+ * compressed 8-wide BVH whose child boxes are 8-bit integers against a
+ * float32 parent origin and per-axis power-of-two scale, rounded outward (80 B
+ * per 8 children instead of 64 B per 2), and traces and renders with it; hit
+ * records are bit-identical to the binary float32 path. */
+enum { RG_SCENE_TIMING = 1u, RG_SCENE_COUNT = 2u, RG_SCENE_COMPRESSED = 4u };
 typedef struct { float background[3]; float ambient; uint32_t flags; } rg_scene_desc;
 
 /* Counters since the last rg_reset_stats. */
@@ -111,12 +115,18 @@ rg_status rg_scene_destroy(rg_scene* scene);
 
 /* ---- step 1 of the paper's model: the two-layered structure (Sec. 1) ---- */
 
-enum { RG_MORTON30 = 0u, RG_MORTON63 = 1u };
+enum { RG_MORTON30 = 0u, RG_MORTON63 = 1u, RG_COMPRESSED = 2u };
+/* Largest number of triangles in one leaf slot of the wide BLAS (1..3;
+ * default 2), as a flag of rg_blas_build.  (TLAS leaf slots hold one
+ * instance each.) */
+#define RG_WIDE_LEAF(n) ((uint32_t)(n) << 8)
 /* Bottom-level BVH of one triangle mesh (LBVH: Morton codes of triangle
  * centroids, radix sort, Karras hierarchy, atomic bottom-up box refit).
  * d_vtx: nv x float3 (12 B each); d_idx: nt x uint3 vertex indices (CCW =
  * outward).  flags: RG_MORTON30 (10 bits/axis, u32 keys) or RG_MORTON63 (21
- * bits/axis, u64 keys).  Writes the new BLAS id to *blas_id.  nt >= 1;
+ * bits/axis, u64 keys), plus RG_COMPRESSED to also build the compressed
+ * 8-wide BVH (always built in an RG_SCENE_COMPRESSED scene).  Writes the new
+ * BLAS id to *blas_id.  nt >= 1;
  * indices must be < nv (checked on the device: RG_ERR_INVALID_ARG at
  * rg_sync).  The mesh is copied; d_vtx/d_idx may be freed after the call
  * once the stream has passed it. */
@@ -146,7 +156,8 @@ enum {
     RG_CLOSEST = 0u,       /* nearest hit in [tmin, tmax]; ties: smaller instance, then smaller prim */
     RG_ANY = 1u,           /* any hit in [tmin, tmax] (shadow query); record of some hit or a miss */
     RG_TRACE_BRUTE = 2u,   /* test every triangle of every instance (no BVH); for validation */
-    RG_TRACE_STATS = 4u    /* count node visits / triangle tests into rg_stats (slower) */
+    RG_TRACE_STATS = 4u,   /* count node visits / triangle tests into rg_stats (slower) */
+    RG_TRACE_PLAIN = 8u    /* in an RG_SCENE_COMPRESSED scene: use the binary float32 BVH */
 };
 /* Trace n rays (device array d_rays) and write n hit records to d_hits.
  * n may be 0. */
@@ -209,6 +220,17 @@ rg_status rg_blas_export(rg_scene* scene, uint32_t blas_id, void* h_nodes, void*
  * leaf j), *h_root.  Any output may be NULL.  Synchronises the device. */
 rg_status rg_tlas_export(rg_scene* scene, void* h_nodes, float* h_wbox, float* h_inv, uint32_t* h_order,
                          uint32_t* h_root);
+
+/* Copy a compressed 8-wide BVH to host memory (blas_id, or RG_TLAS_ID for the
+ * TLAS): h_counts[0] = nodes, [1] = items; h_nodes 80 B per node (layout in
+ * csrc/rg_internal.cuh); h_src 8 uint32 per node, the binary-BVH reference of
+ * each child slot (0xFFFFFFFF if empty; bit 31 = binary leaf); h_item_src one
+ * uint32 per item, the binary leaf it copies.  Buffers must hold max(n-1,1)
+ * nodes and n items for an n-leaf tree.  Any output may be NULL.
+ * Synchronises the device.  RG_ERR_NOT_BUILT if that BVH has no wide form. */
+#define RG_TLAS_ID 0xFFFFFFFFu
+rg_status rg_wide_export(rg_scene* scene, uint32_t blas_id, void* h_nodes, uint32_t* h_src, uint32_t* h_item_src,
+                         uint32_t* h_counts);
 
 /* ---- sorting without allocation ---------------------------------------- */
 

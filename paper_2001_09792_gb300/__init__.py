@@ -23,9 +23,12 @@ LIB_PATH = os.path.join(_PKG, "librg.so")
 RG_OK = 0
 RG_ERR_INVALID_ARG, RG_ERR_OOM, RG_ERR_CUDA, RG_ERR_NOT_BUILT, RG_ERR_STACK, RG_ERR_TIMEOUT, RG_ERR_SINGULAR = range(1, 8)
 RG_MORTON30, RG_MORTON63 = 0, 1
-RG_CLOSEST, RG_ANY, RG_TRACE_BRUTE, RG_TRACE_STATS = 0, 1, 2, 4
+RG_CLOSEST, RG_ANY, RG_TRACE_BRUTE, RG_TRACE_STATS, RG_TRACE_PLAIN = 0, 1, 2, 4, 8
 RG_SCENE_TIMING = 1
 RG_SCENE_COUNT = 2
+RG_SCENE_COMPRESSED = 4
+RG_COMPRESSED = 2
+RG_TLAS_ID = 0xFFFFFFFF
 RG_MAT_DIFFUSE, RG_MAT_MIRROR, RG_MAT_GLASS = 0, 1, 2
 MISS = 0xFFFFFFFF
 
@@ -33,7 +36,7 @@ MISS = 0xFFFFFFFF
 SYMBOLS = ["rg_scene_create", "rg_scene_destroy", "rg_blas_build", "rg_tlas_build", "rg_tlas_refit",
            "rg_scene_set_materials", "rg_scene_set_lights", "rg_trace_rays", "rg_render", "rg_sync", "rg_get_stats",
            "rg_reset_stats", "rg_last_error", "rg_tri_bounds", "rg_morton_codes", "rg_radix_sort_pairs", "rg_karras",
-           "rg_blas_export", "rg_tlas_export", "rg_radix_sort_pairs_noalloc"]
+           "rg_blas_export", "rg_tlas_export", "rg_wide_export", "rg_radix_sort_pairs_noalloc"]
 RG_NOALLOC_SORT_MAX_PAIRS = 262144
 
 f32x3 = ctypes.c_float * 3
@@ -101,6 +104,7 @@ def lib():
             "rg_blas_export": [P, u32, P, P, ctypes.POINTER(u32)],
             "rg_tlas_export": [P, P, P, P, P, ctypes.POINTER(u32)],
             "rg_radix_sort_pairs_noalloc": [P, P, u32, u32, P, P, P],
+            "rg_wide_export": [P, u32, P, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -334,6 +338,30 @@ def rg_blas_export(scene, blas_id, nt):
     _check(lib().rg_blas_export(scene, blas_id, nodes.ctypes.data_as(ctypes.c_void_p),
                                 tris.ctypes.data_as(ctypes.c_void_p), ctypes.byref(root)))
     return dict(nodes=nodes[: max(nt - 1, 0)], tris=tris, root=root.value)
+
+
+def rg_wide_export(scene, blas_id, n_leaves):
+    """Compressed 8-wide BVH of a BLAS (or RG_TLAS_ID): dict with the decoded
+    nodes (p, e, imask, child_base, item_base, meta, qlo, qhi), slot sources
+    and item sources (numpy arrays)."""
+    cap = max(n_leaves - 1, 1)
+    raw = np.zeros((cap, 20), np.uint32)
+    src = np.zeros((cap, 8), np.uint32)
+    item_src = np.zeros(max(n_leaves, 1), np.uint32)
+    counts = np.zeros(2, np.uint32)
+    v = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(lib().rg_wide_export(scene, blas_id, v(raw), src.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                item_src.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                counts.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))))
+    nn, ni = int(counts[0]), int(counts[1])
+    raw = raw[:nn]
+    b = raw.view(np.uint8).reshape(nn, 80)
+    bits = raw[:, 3]
+    e = np.stack([(bits >> (8 * k)) & 0xFF for k in range(3)], 1).astype(np.uint8).view(np.int8).astype(np.int32)
+    return dict(p=raw[:, 0:3].view(np.float32), e=e, imask=(bits >> 24).astype(np.uint32), child_base=raw[:, 4],
+                item_base=raw[:, 5], meta=b[:, 24:32], qlo=np.stack([b[:, 32:40], b[:, 40:48], b[:, 48:56]], 2),
+                qhi=np.stack([b[:, 56:64], b[:, 64:72], b[:, 72:80]], 2), src=src[:nn], item_src=item_src[:ni],
+                n_nodes=nn, n_items=ni)
 
 
 def rg_tlas_export(scene, n):

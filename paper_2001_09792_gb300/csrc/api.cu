@@ -110,7 +110,24 @@ struct BlasHost {
     float4* tris = nullptr;
     uint32_t nt = 0;
     uint32_t root = 0;
+    // compressed 8-wide form (null if not built)
+    float4* nodes8 = nullptr;
+    float4* tris8 = nullptr;
+    uint32_t* src8 = nullptr;
+    uint32_t* item_src8 = nullptr;
+    uint32_t* counts8 = nullptr;
 };
+
+void free_blas(BlasHost& b) {
+    cudaFree(b.nodes);
+    cudaFree(b.tris);
+    if (b.nodes8) cudaFree(b.nodes8);
+    if (b.tris8) cudaFree(b.tris8);
+    if (b.src8) cudaFree(b.src8);
+    if (b.item_src8) cudaFree(b.item_src8);
+    if (b.counts8) cudaFree(b.counts8);
+    b = BlasHost();
+}
 
 struct EventPair {
     cudaEvent_t a, b;
@@ -135,6 +152,12 @@ struct rg_scene {
     DevBuf<InstDev> inst, inst_tmp;
     DevBuf<float> wbox;
     DevBuf<uint32_t> perm, parents, flags;
+    // compressed 8-wide TLAS
+    bool wide = false;
+    DevBuf<float4> tlas8;
+    DevBuf<InstDev> inst8;
+    DevBuf<uint32_t> src8, item_src8, counts8;
+    DevBuf<uint2> tasks8;
     // shading
     DevBuf<rg_material> mats;
     uint32_t n_mats = 0;
@@ -220,7 +243,7 @@ uint32_t iter_cap_for(const rg_scene* s, bool brute) {
     return cap > 0xFFFFFFF0ull ? 0xFFFFFFF0u : (uint32_t)cap;
 }
 
-TraceArgs base_trace_args(rg_scene* s) {
+TraceArgs base_trace_args(rg_scene* s, bool wide) {
     TraceArgs a{};
     a.tlas_nodes = s->tlas_nodes.p;
     a.tlas_root = s->tlas_root;
@@ -228,13 +251,17 @@ TraceArgs base_trace_args(rg_scene* s) {
     a.n_inst = s->n_inst;
     a.st = s->st;
     a.iter_cap = iter_cap_for(s, false);
+    if (wide && s->wide) {
+        a.tlas_nodes8 = s->tlas8.p;
+        a.inst8 = s->inst8.p;
+    }
     return a;
 }
 
 // Shared LBVH steps: lohi + centroid bounds already computed into cb_ord.
 // Sorts the Morton codes of `lohi` and emits the topology into `nodes`.
 rg_status lbvh_topology(TempAlloc& tmp, const float* lohi, uint32_t n, const int* cb_ord, int bits, float4* nodes,
-                        uint32_t* perm, uint32_t* parents, cudaStream_t s) {
+                        uint32_t* perm, uint32_t* parents, cudaStream_t s, uint32_t* ranges = nullptr) {
     const int key_bits = bits == 21 ? 64 : 32;
     const size_t kb = key_bits / 8;
     void *codes, *sorted, *vals, *scratch;
@@ -245,7 +272,7 @@ rg_status lbvh_topology(TempAlloc& tmp, const float* lohi, uint32_t n, const int
     if ((r = tmp.get(&scratch, radix_sort_scratch_bytes(n, key_bits), "sort scratch"))) return r;
     RG_CK(launch_morton(lohi, n, cb_ord, bits, codes, static_cast<uint32_t*>(vals), nullptr, s));
     RG_CK(radix_sort_pairs(codes, static_cast<uint32_t*>(vals), n, key_bits, sorted, perm, scratch, s));
-    RG_CK(launch_karras(sorted, n, key_bits, reinterpret_cast<uint32_t*>(nodes) + 12, 16, parents, s));
+    RG_CK(launch_karras(sorted, n, key_bits, reinterpret_cast<uint32_t*>(nodes) + 12, 16, parents, s, ranges));
     return RG_OK;
 }
 
@@ -295,11 +322,14 @@ rg_status rg_scene_destroy(rg_scene* s) {
     if (!s) return RG_OK;
     set_device(s);
     cudaDeviceSynchronize();
-    for (BlasHost& b : s->blas) {
-        cudaFree(b.nodes);
-        cudaFree(b.tris);
-    }
+    for (BlasHost& b : s->blas) free_blas(b);
     s->d_blas.release();
+    s->tlas8.release();
+    s->inst8.release();
+    s->src8.release();
+    s->item_src8.release();
+    s->counts8.release();
+    s->tasks8.release();
     s->tlas_nodes.release();
     s->inst.release();
     s->inst_tmp.release();
@@ -337,19 +367,32 @@ rg_status rg_blas_build(rg_scene* s, const float* d_vtx, uint32_t nv, const uint
     if ((r = check_scene(s))) return r;
     if (!d_vtx || !d_idx || !blas_id) return fail(RG_ERR_INVALID_ARG, "NULL geometry or id pointer");
     if (nt == 0 || nv == 0) return fail(RG_ERR_INVALID_ARG, "empty mesh");
-    if (flags & ~RG_MORTON63) return fail(RG_ERR_INVALID_ARG, "unknown BLAS flags");
+    if (flags & ~(RG_MORTON63 | RG_COMPRESSED | RG_WIDE_LEAF(3))) return fail(RG_ERR_INVALID_ARG, "unknown BLAS flags");
+    const uint32_t leaf_max = ((flags >> 8) & 3u) ? ((flags >> 8) & 3u) : 2u;
     if (nt > (1u << 30)) return fail(RG_ERR_INVALID_ARG, "too many triangles");
     if ((r = set_device(s))) return r;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int bits = (flags & RG_MORTON63) ? 21 : 10;
+    const bool wide = (flags & RG_COMPRESSED) || (s->desc.flags & RG_SCENE_COMPRESSED);
+    const size_t n_int = nt > 1 ? nt - 1 : 1;
 
     BlasHost b;
     b.nt = nt;
     b.root = nt == 1 ? kLeaf : 0u;
-    if ((r = dev_alloc(reinterpret_cast<void**>(&b.nodes), (size_t)(nt > 1 ? nt - 1 : 1) * 64, "BLAS nodes"))) return r;
+    if ((r = dev_alloc(reinterpret_cast<void**>(&b.nodes), n_int * 64, "BLAS nodes"))) return r;
     if ((r = dev_alloc(reinterpret_cast<void**>(&b.tris), (size_t)nt * 48, "BLAS triangles"))) {
-        cudaFree(b.nodes);
+        free_blas(b);
         return r;
+    }
+    if (wide) {
+        if ((r = dev_alloc(reinterpret_cast<void**>(&b.nodes8), n_int * 80, "wide BLAS nodes")) ||
+            (r = dev_alloc(reinterpret_cast<void**>(&b.tris8), (size_t)nt * 48, "wide BLAS triangles")) ||
+            (r = dev_alloc(reinterpret_cast<void**>(&b.src8), n_int * 32, "wide BLAS slot sources")) ||
+            (r = dev_alloc(reinterpret_cast<void**>(&b.item_src8), (size_t)nt * 4, "wide BLAS item sources")) ||
+            (r = dev_alloc(reinterpret_cast<void**>(&b.counts8), 16, "wide BLAS counts"))) {
+            free_blas(b);
+            return r;
+        }
     }
     uint32_t id = (uint32_t)s->blas.size();
     if ((r = [&]() -> rg_status {
@@ -372,12 +415,18 @@ rg_status rg_blas_build(rg_scene* s, const float* d_vtx, uint32_t nv, const uint
              hd.tris = b.tris;
              hd.root = b.root;
              hd.nt = nt;
+             hd.nodes8 = b.nodes8;
+             hd.tris8 = b.tris8;
              RG_CK(cudaMemcpyAsync(s->d_blas.p + id, &hd, sizeof hd, cudaMemcpyHostToDevice, st));
              RG_CK(cudaStreamSynchronize(st));  // hd lives on this stack frame
 
              TempAlloc tmp(st);
-             void *lohi, *cb, *perm, *parents, *fl;
+             void *lohi, *cb, *perm, *parents, *fl, *ranges = nullptr, *tasks = nullptr;
              rg_status q;
+             if (wide) {
+                 if ((q = tmp.get(&ranges, n_int * 8, "ranges"))) return q;
+                 if ((q = tmp.get(&tasks, (size_t)nt * 16, "collapse tasks"))) return q;
+             }
              if ((q = tmp.get(&lohi, (size_t)nt * 24, "triangle boxes"))) return q;
              if ((q = tmp.get(&cb, 64, "centroid bounds"))) return q;
              if ((q = tmp.get(&perm, (size_t)nt * 4, "permutation"))) return q;
@@ -387,7 +436,8 @@ rg_status rg_blas_build(rg_scene* s, const float* d_vtx, uint32_t nv, const uint
              RG_CK(launch_tri_bounds(d_vtx, nv, d_idx, nt, static_cast<float*>(lohi), static_cast<int*>(cb), s->st, st));
              if (nt > 1) {
                  if ((q = lbvh_topology(tmp, static_cast<float*>(lohi), nt, static_cast<int*>(cb), bits, b.nodes,
-                                        static_cast<uint32_t*>(perm), static_cast<uint32_t*>(parents), st)))
+                                        static_cast<uint32_t*>(perm), static_cast<uint32_t*>(parents), st,
+                                        static_cast<uint32_t*>(ranges))))
                      return q;
                  RG_CK(cudaMemsetAsync(fl, 0, (size_t)(nt - 1) * 4, st));
              } else {
@@ -396,11 +446,17 @@ rg_status rg_blas_build(rg_scene* s, const float* d_vtx, uint32_t nv, const uint
              RG_CK(launch_blas_leaves_refit(d_vtx, d_idx, static_cast<uint32_t*>(perm), static_cast<float*>(lohi), nt,
                                             static_cast<uint32_t*>(parents), b.nodes, static_cast<uint32_t*>(fl), b.tris,
                                             s->d_blas.p + id, s->st, st));
+             if (wide) {
+                 WideOut out{b.nodes8, b.src8, b.item_src8, b.counts8, static_cast<uint2*>(tasks)};
+                 const float* leaf_box = reinterpret_cast<const float*>(reinterpret_cast<const char*>(s->d_blas.p + id) +
+                                                                        offsetof(BlasDev, lo));
+                 RG_CK(launch_collapse(b.nodes, static_cast<uint32_t*>(ranges), nt, leaf_box, b.tris, b.tris8, nullptr,
+                                       nullptr, s->d_blas.p, out, s->st, st, leaf_max));
+             }
              return RG_OK;
          }())) {
         cudaStreamSynchronize(st);
-        cudaFree(b.nodes);
-        cudaFree(b.tris);
+        free_blas(b);
         return r;
     }
     s->blas.push_back(b);
@@ -417,10 +473,12 @@ static rg_status tlas_common(rg_scene* s, const rg_instance* d_inst, uint32_t n,
     if (!refit) RG_CK(launch_init_bounds(static_cast<int*>(cb), st));
     RG_CK(launch_instance_prep(d_inst, n, s->d_blas.p, (uint32_t)s->blas.size(), s->inst_tmp.p, s->wbox.p,
                                refit ? nullptr : static_cast<int*>(cb), refit, s->st, st));
+    void* ranges = nullptr;
     if (!refit) {
         if (n > 1) {
+            if (s->wide && (r = tmp.get(&ranges, (size_t)(n - 1) * 8, "ranges"))) return r;
             if ((r = lbvh_topology(tmp, s->wbox.p, n, static_cast<int*>(cb), 10, s->tlas_nodes.p, s->perm.p,
-                                   s->parents.p, st)))
+                                   s->parents.p, st, static_cast<uint32_t*>(ranges))))
                 return r;
         } else {
             RG_CK(cudaMemsetAsync(s->perm.p, 0, 4, st));
@@ -429,6 +487,15 @@ static rg_status tlas_common(rg_scene* s, const rg_instance* d_inst, uint32_t n,
     if (n > 1) RG_CK(cudaMemsetAsync(s->flags.p, 0, (size_t)(n - 1) * 4, st));
     RG_CK(launch_tlas_leaves_refit(s->inst_tmp.p, s->wbox.p, s->perm.p, n, s->parents.p, s->tlas_nodes.p, s->flags.p,
                                    s->inst.p, s->st, st));
+    if (s->wide) {
+        WideOut out{s->tlas8.p, s->src8.p, s->item_src8.p, s->counts8.p, s->tasks8.p};
+        if (refit)
+            RG_CK(launch_wide_refit(s->tlas_nodes.p, s->wbox.p, s->perm.p, n, s->inst.p, s->inst8.p, s->d_blas.p, out,
+                                    s->st, st));
+        else
+            RG_CK(launch_collapse(s->tlas_nodes.p, static_cast<uint32_t*>(ranges), n, s->wbox.p, nullptr, nullptr,
+                                  s->inst.p, s->inst8.p, s->d_blas.p, out, s->st, st, 1u));
+    }
     return RG_OK;
 }
 
@@ -448,6 +515,19 @@ rg_status rg_tlas_build(rg_scene* s, const rg_instance* d_inst, uint32_t n, void
     if ((r = s->perm.ensure(n, "TLAS order"))) return r;
     if ((r = s->parents.ensure(2 * (size_t)n, "TLAS parents"))) return r;
     if ((r = s->flags.ensure(n, "TLAS flags"))) return r;
+    s->wide = false;
+    if (s->desc.flags & RG_SCENE_COMPRESSED) {
+        for (const BlasHost& b : s->blas)
+            if (!b.nodes8) return fail(RG_ERR_NOT_BUILT, "a BLAS of this compressed scene has no wide form");
+        const size_t n_int = n > 1 ? n - 1 : 1;
+        if ((r = s->tlas8.ensure(n_int * 5, "wide TLAS nodes"))) return r;
+        if ((r = s->inst8.ensure(n, "wide TLAS instances"))) return r;
+        if ((r = s->src8.ensure(n_int * 8, "wide TLAS slot sources"))) return r;
+        if ((r = s->item_src8.ensure(n, "wide TLAS item sources"))) return r;
+        if ((r = s->counts8.ensure(4, "wide TLAS counts"))) return r;
+        if ((r = s->tasks8.ensure(2 * (size_t)n, "collapse tasks"))) return r;
+        s->wide = true;
+    }
     if ((r = tlas_common(s, d_inst, n, st, false))) return r;
     s->n_inst = n;
     s->tlas_root = n == 1 ? kLeaf : 0u;
@@ -493,14 +573,15 @@ rg_status rg_trace_rays(rg_scene* s, const rg_ray* d_rays, uint32_t n, uint32_t 
     rg_status r;
     if ((r = check_scene(s))) return r;
     if (!s->tlas_built) return fail(RG_ERR_NOT_BUILT, "trace before rg_tlas_build");
-    if (flags & ~(RG_ANY | RG_TRACE_BRUTE | RG_TRACE_STATS)) return fail(RG_ERR_INVALID_ARG, "unknown trace flags");
+    if (flags & ~(RG_ANY | RG_TRACE_BRUTE | RG_TRACE_STATS | RG_TRACE_PLAIN))
+        return fail(RG_ERR_INVALID_ARG, "unknown trace flags");
     if ((flags & RG_TRACE_BRUTE) && (flags & RG_TRACE_STATS))
         return fail(RG_ERR_INVALID_ARG, "brute force and statistics are exclusive");
     if (n == 0) return RG_OK;
     if (!d_rays || !d_hits) return fail(RG_ERR_INVALID_ARG, "NULL ray or hit buffer");
     if ((r = set_device(s))) return r;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    TraceArgs a = base_trace_args(s);
+    TraceArgs a = base_trace_args(s, !(flags & RG_TRACE_PLAIN));
     a.rays = reinterpret_cast<const float4*>(d_rays);
     a.n = n;
     a.hits_abi = d_hits;
@@ -549,7 +630,7 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
             if ((r = s->q_pay[1 - cur].ensure(2 * (size_t)n, "payload queue"))) return r;
         }
         RG_CK(cudaMemsetAsync(s->counters.p, 0, 4 * sizeof(uint32_t), st));
-        TraceArgs a = base_trace_args(s);
+        TraceArgs a = base_trace_args(s, true);
         a.rays = s->q_rays[cur].p;
         a.n = n;
         a.hits_render = s->hits.p;
@@ -564,7 +645,7 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
         sa.rays = s->q_rays[cur].p;
         sa.payload = s->q_pay[cur].p;
         sa.hits = s->hits.p;
-        sa.inst = s->inst.p;
+        sa.inst = s->wide ? s->inst8.p : s->inst.p;
         sa.mats = s->mats.p;
         sa.n_mats = s->n_mats;
         sa.lights = s->lights.p;
@@ -586,7 +667,7 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
         RG_CK(launch_shade(sa, n, st));
 
         if (L) {
-            TraceArgs b = base_trace_args(s);
+            TraceArgs b = base_trace_args(s, true);
             b.rays = s->s_rays.p;
             b.d_count = s->counters.p + 2;
             b.payload = s->s_pay.p;
@@ -720,6 +801,41 @@ rg_status rg_blas_export(rg_scene* s, uint32_t blas_id, void* h_nodes, void* h_t
     if (h_nodes && b.nt > 1) RG_CK(cudaMemcpy(h_nodes, b.nodes, (size_t)(b.nt - 1) * 64, cudaMemcpyDeviceToHost));
     if (h_tris) RG_CK(cudaMemcpy(h_tris, b.tris, (size_t)b.nt * 48, cudaMemcpyDeviceToHost));
     if (h_root) *h_root = b.root;
+    return RG_OK;
+}
+
+rg_status rg_wide_export(rg_scene* s, uint32_t blas_id, void* h_nodes, uint32_t* h_src, uint32_t* h_item_src,
+                         uint32_t* h_counts) {
+    rg_status r;
+    if ((r = check_scene(s))) return r;
+    if ((r = set_device(s))) return r;
+    const float4* nodes;
+    const uint32_t *src, *item_src, *counts;
+    if (blas_id == RG_TLAS_ID) {
+        if (!s->tlas_built || !s->wide) return fail(RG_ERR_NOT_BUILT, "no wide TLAS");
+        nodes = s->tlas8.p;
+        src = s->src8.p;
+        item_src = s->item_src8.p;
+        counts = s->counts8.p;
+    } else {
+        if (blas_id >= s->blas.size()) return fail(RG_ERR_INVALID_ARG, "no such BLAS");
+        const BlasHost& b = s->blas[blas_id];
+        if (!b.nodes8) return fail(RG_ERR_NOT_BUILT, "this BLAS has no wide form");
+        nodes = b.nodes8;
+        src = b.src8;
+        item_src = b.item_src8;
+        counts = b.counts8;
+    }
+    RG_CK(cudaDeviceSynchronize());
+    uint32_t c[2];
+    RG_CK(cudaMemcpy(c, counts, sizeof c, cudaMemcpyDeviceToHost));
+    if (h_counts) {
+        h_counts[0] = c[0];
+        h_counts[1] = c[1];
+    }
+    if (h_nodes) RG_CK(cudaMemcpy(h_nodes, nodes, (size_t)c[0] * 80, cudaMemcpyDeviceToHost));
+    if (h_src) RG_CK(cudaMemcpy(h_src, src, (size_t)c[0] * 32, cudaMemcpyDeviceToHost));
+    if (h_item_src) RG_CK(cudaMemcpy(h_item_src, item_src, (size_t)c[1] * 4, cudaMemcpyDeviceToHost));
     return RG_OK;
 }
 

@@ -283,7 +283,7 @@ __device__ __forceinline__ int delta(const K* __restrict__ k, int64_t n, int64_t
 
 template <class K>
 __global__ void k_karras(const K* __restrict__ keys, uint32_t n, uint32_t* __restrict__ child_base, int stride,
-                         uint32_t* __restrict__ parents) {
+                         uint32_t* __restrict__ parents, uint32_t* __restrict__ ranges) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)n - 1) return;
     const int64_t N = n;
@@ -309,6 +309,10 @@ __global__ void k_karras(const K* __restrict__ keys, uint32_t n, uint32_t* __res
     uint32_t right = (hi == gamma + 1) ? (kLeaf | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
     child_base[(size_t)i * stride] = left;
     child_base[(size_t)i * stride + 1] = right;
+    if (ranges) {
+        ranges[2 * (size_t)i] = (uint32_t)lo;
+        ranges[2 * (size_t)i + 1] = (uint32_t)hi;
+    }
     if (parents) {
         parents[(left & kLeaf) ? (size_t)(n - 1) + (left & ~kLeaf) : left] = (uint32_t)i;
         parents[(right & kLeaf) ? (size_t)(n - 1) + (right & ~kLeaf) : right] = (uint32_t)i;
@@ -571,14 +575,14 @@ cudaError_t radix_sort_pairs(const void* keys_in, const uint32_t* vals_in, uint3
 }
 
 cudaError_t launch_karras(const void* keys, uint32_t n, int key_bits, uint32_t* child_base, int stride,
-                          uint32_t* parents, cudaStream_t s) {
+                          uint32_t* parents, cudaStream_t s, uint32_t* ranges) {
     if (n < 2) return cudaSuccess;
     if (key_bits == 64)
         k_karras<uint64_t><<<grid_for(n - 1), kBlock, 0, s>>>(static_cast<const uint64_t*>(keys), n, child_base, stride,
-                                                              parents);
+                                                              parents, ranges);
     else
         k_karras<uint32_t><<<grid_for(n - 1), kBlock, 0, s>>>(static_cast<const uint32_t*>(keys), n, child_base, stride,
-                                                              parents);
+                                                              parents, ranges);
     count_launches(1);
     return cudaGetLastError();
 }

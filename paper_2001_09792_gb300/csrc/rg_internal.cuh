@@ -48,8 +48,35 @@ struct __align__(16) BlasDev {
     uint32_t nt;
     float lo[3];
     float hi[3];
+    const float4* nodes8;   // compressed 8-wide BVH (null if not built)
+    const float4* tris8;    // its triangles, in wide-leaf order
 };
-static_assert(sizeof(BlasDev) == 48, "BLAS descriptor is 48 B");
+static_assert(sizeof(BlasDev) == 64, "BLAS descriptor is 64 B");
+
+// ---------------------------------------------------------------- wide BVH
+// Compressed 8-wide node, 80 B (five 16 B words):
+//   w0 = {p.x, p.y, p.z, bits(ex | ey << 8 | ez << 16 | imask << 24)}
+//   w1 = {child_base, item_base, meta[0..3], meta[4..7]}
+//   w2 = {qlo.x[0..3], qlo.x[4..7], qlo.y[0..3], qlo.y[4..7]}
+//   w3 = {qlo.z[0..3], qlo.z[4..7], qhi.x[0..3], qhi.x[4..7]}
+//   w4 = {qhi.y[0..3], qhi.y[4..7], qhi.z[0..3], qhi.z[4..7]}
+// Child box of slot s along axis a: [p_a + qlo_a[s] * 2^e_a, p_a + qhi_a[s] * 2^e_a]
+// (e_a a signed byte), rounded outward at build time so that it contains the
+// exact float32 box.  imask bit s = slot s is an internal child; internal
+// children are stored consecutively from child_base in slot order.  A leaf slot
+// has meta = count << 5 | offset: items item_base + offset .. + count - 1; an
+// empty slot has meta = 0 and no imask bit.  Slot s holds a child lying toward
+// octant s of the node (bit a of s set: the negative side of axis a), so a ray
+// visits children in the order of (s ^ its direction-sign bits), highest first.
+constexpr int kWideLeafMax = 3;  // largest number of items a leaf slot may hold (count is 2 bits)
+
+struct WideOut {
+    float4* nodes;      // 5 float4 per node
+    uint32_t* src;      // 8 per node: binary-tree reference of each slot (kNone if empty)
+    uint32_t* item_src; // per item: binary leaf index it was copied from
+    uint32_t* counts;   // [0] nodes, [1] items (written at the end)
+    uint2* tasks;       // scratch: 2 x n task entries
+};
 
 // Per-ray payload of the wavefront renderer, 16 B: pixel index and the RGB
 // weight (throughput for path rays, unshadowed contribution for shadow rays).
@@ -103,8 +130,9 @@ cudaError_t launch_morton(const float* lohi, uint32_t n, const int* cb_ord, int 
 size_t radix_sort_scratch_bytes(uint32_t n, int key_bits);
 cudaError_t radix_sort_pairs(const void* keys_in, const uint32_t* vals_in, uint32_t n, int key_bits, void* keys_out,
                              uint32_t* vals_out, void* scratch, cudaStream_t s);
+// ranges (optional, 2 per internal node): first and last leaf of node i.
 cudaError_t launch_karras(const void* keys, uint32_t n, int key_bits, uint32_t* child_base, int child_stride_words,
-                          uint32_t* parents, cudaStream_t s);
+                          uint32_t* parents, cudaStream_t s, uint32_t* ranges = nullptr);
 cudaError_t launch_blas_leaves_refit(const float* vtx, const uint32_t* idx, const uint32_t* perm, const float* lohi,
                                      uint32_t n, const uint32_t* parents, float4* nodes, uint32_t* flags,
                                      float4* tris, BlasDev* blas_out, DevStatus* st, cudaStream_t s);
@@ -114,6 +142,20 @@ cudaError_t launch_instance_prep(const rg_instance* in, uint32_t n, const BlasDe
 cudaError_t launch_tlas_leaves_refit(const InstDev* tmp, const float* wbox, const uint32_t* perm, uint32_t n,
                                      const uint32_t* parents, float4* nodes, uint32_t* flags, InstDev* inst_out,
                                      DevStatus* st, cudaStream_t s);
+
+// wide.cu
+// Collapse a binary LBVH (n leaves) into a compressed 8-wide BVH in one
+// single-block launch.  Items are triangles (tris2 -> tris8) or instances
+// (inst2 -> inst8, whose BLAS pointers are switched to the wide ones).
+// leaf_max (1..kWideLeafMax): a subtree with at most that many items becomes a leaf slot.
+cudaError_t launch_collapse(const float4* nodes2, const uint32_t* ranges, uint32_t n, const float* leaf_box,
+                            const float4* tris2, float4* tris8, const InstDev* inst2, InstDev* inst8,
+                            const BlasDev* blas, const WideOut& out, DevStatus* st, cudaStream_t s,
+                            uint32_t leaf_max);
+// Re-quantize the wide TLAS after a binary refit and refresh its instance copies.
+cudaError_t launch_wide_refit(const float4* nodes2, const float* wbox, const uint32_t* perm, uint32_t n,
+                              const InstDev* inst2, InstDev* inst8, const BlasDev* blas, const WideOut& out,
+                              DevStatus* st, cudaStream_t s);
 
 // trace.cu
 enum TraceMode { kModeClosestAbi = 0, kModeAnyAbi = 1, kModeClosestRender = 2, kModeShadowRender = 3 };
@@ -132,6 +174,8 @@ struct TraceArgs {
     uint32_t* work_counter;      // persistent-thread work queue head (zeroed before launch)
     DevStatus* st;
     uint32_t iter_cap;           // bound on the loop steps of one ray (a valid traversal needs fewer)
+    const float4* tlas_nodes8;   // compressed 8-wide TLAS (null: binary path)
+    const InstDev* inst8;        // its instances, in wide-leaf order (BLAS pointers to wide BLAS)
 };
 cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a, cudaStream_t s);
 

@@ -78,7 +78,39 @@ struct Shear {
     int kx, ky, kz;
 };
 
-__device__ __forceinline__ Shear make_shear(float ox, float oy, float oz, float dx, float dy, float dz) {
+// Shear for the wide traversal.  ix, iy, iz: the correctly rounded reciprocals
+// of dx, dy, dz (already needed by the box test); Sz = 1/d_kz is taken from
+// them and Sx, Sy are products, so an instance entry costs no division beyond
+// the reciprocals.  Any fixed shear keeps the test watertight for the ray.
+__device__ __forceinline__ Shear make_shear(float ox, float oy, float oz, float dx, float dy, float dz, float ix,
+                                            float iy, float iz) {
+    Shear s;
+    float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
+    int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    float dkz = kz == 0 ? dx : (kz == 1 ? dy : dz);
+    if (dkz < 0.0f) {
+        int t = kx;
+        kx = ky;
+        ky = t;
+    }
+    float dkx = kx == 0 ? dx : (kx == 1 ? dy : dz);
+    float dky = ky == 0 ? dx : (ky == 1 ? dy : dz);
+    s.Sz = kz == 0 ? ix : (kz == 1 ? iy : iz);
+    s.Sx = __fmul_rn(dkx, s.Sz);
+    s.Sy = __fmul_rn(dky, s.Sz);
+    s.kx = kx;
+    s.ky = ky;
+    s.kz = kz;
+    s.ox = kx == 0 ? ox : (kx == 1 ? oy : oz);
+    s.oy = ky == 0 ? ox : (ky == 1 ? oy : oz);
+    s.oz = kz == 0 ? ox : (kz == 1 ? oy : oz);
+    return s;
+}
+
+// Shear of the watertight test with IEEE divisions (binary traversal).
+__device__ __forceinline__ Shear make_shear_div(float ox, float oy, float oz, float dx, float dy, float dz) {
     Shear s;
     float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
     int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
@@ -137,6 +169,65 @@ __device__ __forceinline__ TriResult tri_test(const Shear& s, float4 v0, float4 
     r.W = W;
     r.det = det;
     return r;
+}
+
+// Write one ray's result: an ABI hit record, a render hit, or (shadow rays)
+// the unshadowed contribution added to the image.
+template <int MODE>
+__device__ __forceinline__ void emit(const TraceArgs& a, uint32_t i, bool found, bool ok, float best_t, uint32_t best_id,
+                                     uint32_t best_prim, uint32_t best_il, uint32_t best_tl, float best_V,
+                                     float best_W, float best_det) {
+    if (MODE == kModeClosestAbi || MODE == kModeAnyAbi) {
+        rg_hit out;
+        if (found) {
+            out.instance = best_id;
+            out.prim = best_prim;
+            out.t = best_t;
+            out.u = __fdiv_rn(best_V, best_det);
+            out.v = __fdiv_rn(best_W, best_det);
+        } else {
+            out.instance = kMiss;
+            out.prim = kMiss;
+            out.t = __int_as_float(0x7F800000);
+            out.u = 0.f;
+            out.v = 0.f;
+        }
+        a.hits_abi[i] = out;
+    } else if (MODE == kModeClosestRender) {
+        HitDev hd;
+        hd.inst_leaf = found ? best_il : kMiss;
+        hd.tri_leaf = found ? best_tl : kMiss;
+        hd.t = found ? best_t : __int_as_float(0x7F800000);
+        hd.pad = 0;
+        *reinterpret_cast<uint4*>(a.hits_render + i) = *reinterpret_cast<const uint4*>(&hd);
+    } else {  // shadow: accumulate the unshadowed contribution
+        if (!found && ok) {
+            const Payload p = a.payload[i];
+            float* px = a.image + 4 * (size_t)p.pixel;
+            atomicAdd(px + 0, p.r);
+            atomicAdd(px + 1, p.g);
+            atomicAdd(px + 2, p.b);
+        }
+    }
+}
+
+template <bool ANY, bool STATS>
+__device__ __forceinline__ void flush_counts(const TraceArgs& a, unsigned long long c_nodes, unsigned long long c_tris,
+                                             unsigned long long c_inst) {
+    if constexpr (STATS) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            c_nodes += __shfl_xor_sync(0xFFFFFFFFu, c_nodes, off);
+            c_tris += __shfl_xor_sync(0xFFFFFFFFu, c_tris, off);
+            c_inst += __shfl_xor_sync(0xFFFFFFFFu, c_inst, off);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            unsigned long long* c = a.st->count[ANY ? 1 : 0];
+            atomicAdd(c + 0, c_nodes);
+            atomicAdd(c + 1, c_tris);
+            atomicAdd(c + 2, c_inst);
+        }
+    }
 }
 
 template <int MODE, bool BRUTE, bool STATS>
@@ -239,7 +330,7 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace(TraceArgs a) {
                 float ddz = fmaf(m2.x, dx, fmaf(m2.y, dy, __fmul_rn(m2.z, dz)));
                 cr.ox = ox; cr.oy = oy; cr.oz = oz;
                 cr.ix = safe_rcp(ddx); cr.iy = safe_rcp(ddy); cr.iz = safe_rcp(ddz);
-                sh = make_shear(ox, oy, oz, ddx, ddy, ddz);
+                sh = make_shear_div(ox, oy, oz, ddx, ddy, ddz);
                 const unsigned long long pn = ((unsigned long long)__float_as_uint(meta0.y) << 32) | __float_as_uint(meta0.x);
                 const unsigned long long pt = ((unsigned long long)__float_as_uint(meta0.w) << 32) | __float_as_uint(meta0.z);
                 nodes = reinterpret_cast<const float4*>(pn);
@@ -282,55 +373,279 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace(TraceArgs a) {
             }
         }
         if (!ok) found = false;
+        emit<MODE>(a, i, found, ok, best_t, best_id, best_prim, best_il, best_tl, best_V, best_W, best_det);
+    }
+    flush_counts<kAny, STATS>(a, c_nodes, c_tris, c_inst);
+}
 
-        if (MODE == kModeClosestAbi || MODE == kModeAnyAbi) {
-            rg_hit out;
-            if (found) {
-                out.instance = best_id;
-                out.prim = best_prim;
-                out.t = best_t;
-                out.u = __fdiv_rn(best_V, best_det);
-                out.v = __fdiv_rn(best_W, best_det);
+// ---------------------------------------------------------------- wide BVH
+// Traversal of the compressed 8-wide BVH (layout in rg_internal.cuh).  The
+// state is a node group (children of one node still to visit: base index,
+// hit bits in visiting order, the node's internal-slot mask) and an item
+// group (triangles or instances of the leaf slots hit at the last node: base
+// index, one bit per item).  Items are handled before the next node is
+// fetched; unfinished groups and the BLAS marker go on a short stack of
+// 8-byte entries.  Child boxes are tested with one FMA per plane,
+// t = q * (2^e / d) + (p - o) / d, which differs from the exact slab
+// distance by at most kQuantErr * (255 |2^e / d| + |(p - o) / d|) (a few
+// roundings of those magnitudes); widening every child interval of the node
+// by that bound E keeps the test conservative, so the wide path finds the same
+// hits as the binary one.
+constexpr int kStack8 = 48;
+constexpr uint32_t kKindNode = 0u, kKindItem = 1u << 30, kKindMarker = 2u << 30;
+constexpr float kQuantErr = 8.0f * 5.9604644775390625e-08f;
+
+__device__ __forceinline__ uint32_t oct_of(const SpaceRay& r) {
+    return (__float_as_uint(r.ix) >> 31) | ((__float_as_uint(r.iy) >> 31) << 1) | ((__float_as_uint(r.iz) >> 31) << 2);
+}
+
+// Byte k of w as a float: one byte permute builds the bit pattern of 2^23 + q
+// (exponent byte 0x4B above the byte), then an exact subtraction of 2^23.
+__device__ __forceinline__ float byte_f(uint32_t w, int k) {
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, (uint32_t)k | 0x7440u)) - 8388608.0f;
+}
+
+template <int MODE, bool STATS>
+__global__ void __launch_bounds__(kTraceBlock) k_trace8(TraceArgs a) {
+    const uint32_t iter_cap = a.iter_cap;
+    constexpr bool kAny = (MODE == kModeAnyAbi || MODE == kModeShadowRender);
+    const uint32_t n = a.d_count ? *a.d_count : a.n;
+    const int lane = threadIdx.x & 31;
+    unsigned long long c_nodes = 0, c_tris = 0, c_inst = 0;
+    for (;;) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(a.work_counter, 32u);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (base >= n) break;
+        const uint32_t i = base + lane;
+        if (i >= n) continue;
+
+        const float4 r0 = __ldg(a.rays + 2 * (size_t)i), r1 = __ldg(a.rays + 2 * (size_t)i + 1);
+        const float tmin = r0.w, tmax = r1.w;
+        SpaceRay wr;
+        wr.ox = r0.x; wr.oy = r0.y; wr.oz = r0.z;
+        wr.ix = safe_rcp(r1.x); wr.iy = safe_rcp(r1.y); wr.iz = safe_rcp(r1.z);
+        const uint32_t oct_w = oct_of(wr);
+        SpaceRay cr = wr;
+        uint32_t oct = oct_w;
+        Shear sh;
+
+        float best_t = tmax;
+        uint32_t best_id = kMiss, best_prim = kMiss, best_il = kMiss, best_tl = kMiss;
+        float best_V = 0.f, best_W = 0.f, best_det = 1.f;
+        bool found = false, ok = true, in_blas = false;
+
+        uint2 stack[kStack8];
+        int sp = 0;
+        const float4* nodes = a.tlas_nodes8;
+        const float4* tris = nullptr;
+        uint32_t cur_id = 0, cur_leaf = 0;
+        // node group: the root as the only internal child (slot 0) of a virtual node
+        uint32_t g_base = 0, g_hits = 1u << oct, g_imask = 1u;
+        uint32_t i_base = 0, i_bits = 0;
+
+        // Phases keep the lanes of a warp on the same kind of work: all lanes
+        // fetch nodes until each has items pending (or is done with nodes),
+        // then all process items; only then does a lane pop its stack.
+        bool done = false;
+        uint32_t iter = 0;
+        while (!done) {
+            while (g_hits && !i_bits) {
+                if (++iter > iter_cap) {
+                    record_error(a.st, RG_ERR_TIMEOUT);
+                    ok = false;
+                    done = true;
+                    break;
+                }
+                    const uint32_t b = 31 - __clz(g_hits);
+                    g_hits &= ~(1u << b);
+                    const uint32_t s = b ^ oct;
+                    const uint32_t node = g_base + __popc(g_imask & ((1u << s) - 1u));
+                    if (g_hits) {
+                        if (sp >= kStack8) {
+                            record_error(a.st, RG_ERR_STACK);
+                            ok = false;
+                            done = true;
+                            break;
+                        }
+                        stack[sp++] = make_uint2(g_base, g_hits | (g_imask << 8) | kKindNode);
+                    }
+                    const float4* nd = nodes + 5 * (size_t)node;
+                    const float4 w0 = __ldg(nd);
+                    const uint4 w1 = __ldg(reinterpret_cast<const uint4*>(nd + 1));
+                    const uint4 w2 = __ldg(reinterpret_cast<const uint4*>(nd + 2));
+                    const uint4 w3 = __ldg(reinterpret_cast<const uint4*>(nd + 3));
+                    const uint4 w4 = __ldg(reinterpret_cast<const uint4*>(nd + 4));
+                    if (STATS) ++c_nodes;
+                    const uint32_t bits = __float_as_uint(w0.w);
+                    const uint32_t imask = bits >> 24;
+                    const float sx = __int_as_float((((int)(int8_t)(bits & 0xFF)) + 127) << 23);
+                    const float sy = __int_as_float((((int)(int8_t)((bits >> 8) & 0xFF)) + 127) << 23);
+                    const float sz = __int_as_float((((int)(int8_t)((bits >> 16) & 0xFF)) + 127) << 23);
+                    const float Sx = sx * cr.ix, Sy = sy * cr.iy, Sz = sz * cr.iz;  // exact: powers of two
+                    const float Bx = __fmul_rn(__fsub_rn(w0.x, cr.ox), cr.ix);
+                    const float By = __fmul_rn(__fsub_rn(w0.y, cr.oy), cr.iy);
+                    const float Bz = __fmul_rn(__fsub_rn(w0.z, cr.oz), cr.iz);
+                    const float E = kQuantErr * fmaxf(fmaxf(fmaf(255.0f, fabsf(Sx), fabsf(Bx)), fmaf(255.0f, fabsf(Sy), fabsf(By))),
+                                                      fmaf(255.0f, fabsf(Sz), fabsf(Bz)));
+                    // near planes shifted down by E, far planes up by E
+                    const float Bxn = Bx - E, Byn = By - E, Bzn = Bz - E;
+                    const float Bxf = Bx + E, Byf = By + E, Bzf = Bz + E;
+                    // near/far planes per axis from the direction signs
+                    const bool nx = oct & 1, ny = oct & 2, nz = oct & 4;
+                    const uint32_t nx0 = nx ? w3.z : w2.x, nx1 = nx ? w3.w : w2.y, fx0 = nx ? w2.x : w3.z, fx1 = nx ? w2.y : w3.w;
+                    const uint32_t ny0 = ny ? w4.x : w2.z, ny1 = ny ? w4.y : w2.w, fy0 = ny ? w2.z : w4.x, fy1 = ny ? w2.w : w4.y;
+                    const uint32_t nz0 = nz ? w4.z : w3.x, nz1 = nz ? w4.w : w3.y, fz0 = nz ? w3.x : w4.z, fz1 = nz ? w3.y : w4.w;
+                    const float tlim = kAny ? __fmul_rn(tmax, kCullSlack) : __fmul_rn(best_t, kCullSlack);
+                    const uint32_t meta_lo = w1.z, meta_hi = w1.w;
+                    uint32_t hitmask = 0;
+    #pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const int k = c & 3;
+                        const float tnx = fmaf(byte_f(c < 4 ? nx0 : nx1, k), Sx, Bxn);
+                        const float tfx = fmaf(byte_f(c < 4 ? fx0 : fx1, k), Sx, Bxf);
+                        const float tny = fmaf(byte_f(c < 4 ? ny0 : ny1, k), Sy, Byn);
+                        const float tfy = fmaf(byte_f(c < 4 ? fy0 : fy1, k), Sy, Byf);
+                        const float tnz = fmaf(byte_f(c < 4 ? nz0 : nz1, k), Sz, Bzn);
+                        const float tfz = fmaf(byte_f(c < 4 ? fz0 : fz1, k), Sz, Bzf);
+                        const float tn = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, tmin));
+                        const float tf = fminf(fminf(tfx, tfy), fminf(tfz, tlim));
+                        if (tn <= tf) hitmask |= 1u << c;
+                    }
+                    // keep occupied slots only: internal ones and leaves (meta != 0)
+                    const uint32_t occ_lo = __vcmpne4(meta_lo, 0u) & 0x08040201u;
+                    const uint32_t occ_hi = __vcmpne4(meta_hi, 0u) & 0x80402010u;
+                    uint32_t occ = occ_lo | occ_hi;
+                    occ = (occ | (occ >> 8) | (occ >> 16) | (occ >> 24)) & 0xFFu;
+                    hitmask &= occ | imask;
+                    // internal hits, bit positions permuted to visiting order (slot ^ oct)
+                    uint32_t hits = hitmask & imask;
+                    if (oct & 1u) hits = ((hits & 0x55u) << 1) | ((hits >> 1) & 0x55u);
+                    if (oct & 2u) hits = ((hits & 0x33u) << 2) | ((hits >> 2) & 0x33u);
+                    if (oct & 4u) hits = ((hits & 0x0Fu) << 4) | ((hits >> 4) & 0x0Fu);
+                    uint32_t items = 0;
+                    for (uint32_t lm = hitmask & ~imask; lm; lm &= lm - 1) {
+                        const int c = __ffs(lm) - 1;
+                        const uint32_t meta = ((c < 4 ? meta_lo : meta_hi) >> (8 * (c & 3))) & 0xFFu;
+                        items |= ((1u << (meta >> 5)) - 1u) << (meta & 31u);
+                    }
+                    g_base = w1.x;
+                    g_hits = hits;
+                    g_imask = imask;
+                    i_base = w1.y;
+                    i_bits = items;
+            }
+            if (done) break;
+            while (i_bits) {
+                if (++iter > iter_cap) {
+                    record_error(a.st, RG_ERR_TIMEOUT);
+                    ok = false;
+                    done = true;
+                    break;
+                }
+                    const uint32_t k = __ffs(i_bits) - 1;
+                    i_bits &= i_bits - 1;
+                    const uint32_t item = i_base + k;
+                    if (!in_blas) {
+                        // instance: save the TLAS groups, enter its BLAS
+                        if (sp + 3 > kStack8) {
+                            record_error(a.st, RG_ERR_STACK);
+                            ok = false;
+                            done = true;
+                            break;
+                        }
+                        if (g_hits) stack[sp++] = make_uint2(g_base, g_hits | (g_imask << 8) | kKindNode);
+                        if (i_bits) stack[sp++] = make_uint2(i_base, i_bits | kKindItem);
+                        stack[sp++] = make_uint2(0u, kKindMarker);
+                        const InstDev* I = a.inst8 + item;
+                        const float4 m0 = __ldg(&I->inv[0]), m1 = __ldg(&I->inv[1]), m2 = __ldg(&I->inv[2]);
+                        const float4 meta0 = __ldg(reinterpret_cast<const float4*>(&I->nodes));
+                        const uint4 meta1 = __ldg(reinterpret_cast<const uint4*>(&I->root));
+                        if (STATS) ++c_inst;
+                        const float dx = r1.x, dy = r1.y, dz = r1.z;
+                        float ox = fmaf(m0.x, wr.ox, fmaf(m0.y, wr.oy, fmaf(m0.z, wr.oz, m0.w)));
+                        float oy = fmaf(m1.x, wr.ox, fmaf(m1.y, wr.oy, fmaf(m1.z, wr.oz, m1.w)));
+                        float oz = fmaf(m2.x, wr.ox, fmaf(m2.y, wr.oy, fmaf(m2.z, wr.oz, m2.w)));
+                        float ddx = fmaf(m0.x, dx, fmaf(m0.y, dy, __fmul_rn(m0.z, dz)));
+                        float ddy = fmaf(m1.x, dx, fmaf(m1.y, dy, __fmul_rn(m1.z, dz)));
+                        float ddz = fmaf(m2.x, dx, fmaf(m2.y, dy, __fmul_rn(m2.z, dz)));
+                        cr.ox = ox; cr.oy = oy; cr.oz = oz;
+                        cr.ix = safe_rcp(ddx); cr.iy = safe_rcp(ddy); cr.iz = safe_rcp(ddz);
+                        oct = oct_of(cr);
+                        sh = make_shear(ox, oy, oz, ddx, ddy, ddz, cr.ix, cr.iy, cr.iz);
+                        const unsigned long long pn =
+                            ((unsigned long long)__float_as_uint(meta0.y) << 32) | __float_as_uint(meta0.x);
+                        const unsigned long long pt =
+                            ((unsigned long long)__float_as_uint(meta0.w) << 32) | __float_as_uint(meta0.z);
+                        nodes = reinterpret_cast<const float4*>(pn);
+                        tris = reinterpret_cast<const float4*>(pt);
+                        cur_id = meta1.y;
+                        cur_leaf = item;
+                        in_blas = true;
+                        g_base = 0;
+                        g_hits = 1u << oct;
+                        g_imask = 1u;
+                        i_bits = 0;
+                        continue;
+                    }
+                    const float4* tp = tris + 3 * (size_t)item;
+                    const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+                    if (STATS) ++c_tris;
+                    TriResult h = tri_test(sh, v0, v1, v2, tmin, kAny ? tmax : best_t);
+                    if (h.hit) {
+                        const uint32_t prim = __float_as_uint(v0.w);
+                        if (kAny) {
+                            best_t = h.t; best_id = cur_id; best_prim = prim;
+                            best_V = h.V; best_W = h.W; best_det = h.det;
+                            found = true;
+                            done = true;
+                            break;
+                        }
+                        if (h.t < best_t || cur_id < best_id || (cur_id == best_id && prim < best_prim)) {
+                            best_t = h.t; best_id = cur_id; best_prim = prim;
+                            best_il = cur_leaf; best_tl = item;
+                            best_V = h.V; best_W = h.W; best_det = h.det;
+                            found = true;
+                        }
+                    }
+            }
+            if (done) break;
+            if (g_hits) continue;
+            if (sp == 0) break;
+            const uint2 e = stack[--sp];
+            const uint32_t kind = e.y & (3u << 30);
+            if (kind == kKindMarker) {
+                in_blas = false;
+                nodes = a.tlas_nodes8;
+                cr = wr;
+                oct = oct_w;
+            } else if (kind == kKindItem) {
+                i_base = e.x;
+                i_bits = e.y & 0xFFFFFFu;
             } else {
-                out.instance = kMiss;
-                out.prim = kMiss;
-                out.t = __int_as_float(0x7F800000);
-                out.u = 0.f;
-                out.v = 0.f;
-            }
-            a.hits_abi[i] = out;
-        } else if (MODE == kModeClosestRender) {
-            HitDev hd;
-            hd.inst_leaf = found ? best_il : kMiss;
-            hd.tri_leaf = found ? best_tl : kMiss;
-            hd.t = found ? best_t : __int_as_float(0x7F800000);
-            hd.pad = 0;
-            *reinterpret_cast<uint4*>(a.hits_render + i) = *reinterpret_cast<const uint4*>(&hd);
-        } else {  // shadow: accumulate the unshadowed contribution
-            if (!found && ok) {
-                const Payload p = a.payload[i];
-                float* px = a.image + 4 * (size_t)p.pixel;
-                atomicAdd(px + 0, p.r);
-                atomicAdd(px + 1, p.g);
-                atomicAdd(px + 2, p.b);
+                g_base = e.x;
+                g_hits = e.y & 0xFFu;
+                g_imask = (e.y >> 8) & 0xFFu;
             }
         }
+        if (!ok) found = false;
+        emit<MODE>(a, i, found, ok, best_t, best_id, best_prim, best_il, best_tl, best_V, best_W, best_det);
     }
-    if (STATS) {
-        // warp-reduce, one set of atomics per warp
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            c_nodes += __shfl_xor_sync(0xFFFFFFFFu, c_nodes, off);
-            c_tris += __shfl_xor_sync(0xFFFFFFFFu, c_tris, off);
-            c_inst += __shfl_xor_sync(0xFFFFFFFFu, c_inst, off);
-        }
-        if (lane == 0) {
-            unsigned long long* c = a.st->count[kAny ? 1 : 0];
-            atomicAdd(c + 0, c_nodes);
-            atomicAdd(c + 1, c_tris);
-            atomicAdd(c + 2, c_inst);
-        }
+    flush_counts<kAny, STATS>(a, c_nodes, c_tris, c_inst);
+}
+
+template <int MODE, bool STATS>
+cudaError_t launch_mode8(const TraceArgs& a, cudaStream_t s) {
+    static int blocks = 0;
+    if (blocks == 0) {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace8<MODE, STATS>, kTraceBlock, 0);
+        if (e != cudaSuccess) return e;
+        blocks = device_sm_count() * (per_sm > 0 ? per_sm : 1);
     }
+    k_trace8<MODE, STATS><<<blocks, kTraceBlock, 0, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 template <int MODE, bool BRUTE, bool STATS>
@@ -350,6 +665,21 @@ cudaError_t launch_mode(const TraceArgs& a, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a, cudaStream_t s) {
+    if (a.tlas_nodes8 && !brute) {
+        switch (mode) {
+            case kModeClosestAbi:
+                return stats ? launch_mode8<kModeClosestAbi, true>(a, s) : launch_mode8<kModeClosestAbi, false>(a, s);
+            case kModeAnyAbi:
+                return stats ? launch_mode8<kModeAnyAbi, true>(a, s) : launch_mode8<kModeAnyAbi, false>(a, s);
+            case kModeClosestRender:
+                return stats ? launch_mode8<kModeClosestRender, true>(a, s)
+                             : launch_mode8<kModeClosestRender, false>(a, s);
+            case kModeShadowRender:
+                return stats ? launch_mode8<kModeShadowRender, true>(a, s)
+                             : launch_mode8<kModeShadowRender, false>(a, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (mode) {
         case kModeClosestAbi:
             if (brute) return launch_mode<kModeClosestAbi, true, false>(a, s);

@@ -24,3 +24,11 @@ def read_golden(name):
             if line:
                 rows.append(line.split())
     return rows
+
+
+
+@pytest.fixture(scope="session")
+def librg():
+    """Build librg.so (a no-op when it is up to date); GPU tests request it."""
+    from paper_2001_09792_gb300 import _build
+    return _build.build()

@@ -9,7 +9,7 @@ import oracle
 import paper_2001_09792_gb300 as rg
 import scenegen as g
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("librg")]
 LEAF = 0x80000000
 
 

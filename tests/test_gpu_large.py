@@ -11,7 +11,7 @@ import paper_2001_09792_gb300 as rg
 import scenegen as g
 from test_gpu_trace import KAPPA, MAX_EXEMPT, MISS, REL_T, compare_closest
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("librg")]
 N_RAYS = 1 << 24
 SAMPLE = 20_000
 

@@ -21,7 +21,7 @@ import oracle
 import paper_2001_09792_gb300 as rg
 import scenegen as g
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("librg")]
 MISS = 0xFFFFFFFF
 KAPPA = 16.0
 REL_T = 1e-5

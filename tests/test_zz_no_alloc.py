@@ -13,7 +13,7 @@ import torch
 
 import paper_2001_09792_gb300 as rg
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("librg")]
 
 
 def keys_for(n, key_bits, seed):
