@@ -57,8 +57,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU baseline budget (wall seconds)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--plain", action="store_true",
-                   help="trace with the float32 binary BVH (default: the compressed 8-wide BVH)")
+    p.add_argument("--compressed", action="store_true",
+                   help="trace with the compressed 8-wide BVH (default: the float32 binary BVH, faster here)")
     p.add_argument("--workload", default="medium", choices=["medium", "large"],
                    help="medium: the render frame (default); large: incoherent closest/any-hit queries")
     return p.parse_args()
@@ -155,16 +155,16 @@ def traffic_record():
 
 def path_flag(args):
     import paper_2001_09792_gb300 as rg
-    return 0 if args.plain else rg.RG_SCENE_COMPRESSED
+    return rg.RG_SCENE_COMPRESSED if args.compressed else 0
 
 
 def node_bytes(args):
-    return 64 if args.plain else 80
+    return 80 if args.compressed else 64
 
 
 def kernel_name(args, where):
-    return (f"k_trace closest-hit, binary float32 BVH ({where})" if args.plain
-            else f"k_trace8 closest-hit, compressed 8-wide BVH ({where})")
+    return (f"k_trace8 closest-hit, compressed 8-wide BVH ({where})" if args.compressed
+            else f"k_trace closest-hit, binary float32 BVH ({where})")
 
 
 def frame_motions(scene, n):
@@ -282,7 +282,7 @@ def run_native(args, world, rank, local):
         launch_ms = st["trace_ms"] / max(st["trace_launches"], 1)
         rays_per_launch = st["closest_rays"] / max(st["trace_launches"], 1)
         achieved = bytes_per_ray * rays_per_launch / (launch_ms / 1e3) / 1e9
-        tr = traffic_record() if args.plain else None
+        tr = None if args.compressed else traffic_record()
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(achieved / peak, 4), "traffic": None if tr is None else round(tr * rays_per_launch),
                     "kernel": kernel_name(args, "render"), "peak_kind": peak_kind,
@@ -312,7 +312,7 @@ def run_native(args, world, rank, local):
                        "p50_ms": round(ms_sorted[len(ms) // 2], 3),
                        "p99_ms": round(ms_sorted[min(len(ms) - 1, math.ceil(0.99 * len(ms)) - 1)], 3),
                        "blas_build_ms": round(blas_build_ms, 2), "l2": "flushed before each step (256 MiB write)",
-                       "parallelism": f"replicas x{world}", "bvh": "binary float32" if args.plain else "compressed 8-wide"},
+                       "parallelism": f"replicas x{world}", "bvh": "compressed 8-wide" if args.compressed else "binary float32"},
             "roofline": roofline,
             "gpu_launches": int(st["kernel_launches"]),
         }
@@ -507,7 +507,7 @@ def run_native_large(args, world, rank, local):
                           "closest_ms": round(launch_ms, 3), "any_ms": round(st["any_ms"] / max(st["any_launches"], 1), 3),
                           "p50_ms": round(ms_sorted[len(ms) // 2], 3), "p99_ms": round(ms_sorted[-1], 3),
                           "l2": "inputs larger than L2 (2 x 512 MiB of rays, ~220 MB of BVH)",
-                          "parallelism": f"replicas x{world}", "bvh": "binary float32" if args.plain else "compressed 8-wide"},
+                          "parallelism": f"replicas x{world}", "bvh": "compressed 8-wide" if args.compressed else "binary float32"},
                "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                             "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
                             "kernel": kernel_name(args, "rg_trace_rays"), "algorithmic_bytes_per_ray": round(bpr, 1),
