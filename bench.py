@@ -59,8 +59,11 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--compressed", action="store_true",
                    help="trace with the compressed 8-wide BVH (default: the float32 binary BVH, faster here)")
-    p.add_argument("--workload", default="medium", choices=["medium", "large"],
-                   help="medium: the render frame (default); large: incoherent closest/any-hit queries")
+    p.add_argument("--workload", default="medium", choices=["medium", "large", "serve"],
+                   help="medium: the render frame (default); large: incoherent closest/any-hit queries; "
+                        "serve: the continuous-batching render server alone")
+    p.add_argument("--requests", type=int, default=400, help="serving: requests in the Poisson stream")
+    p.add_argument("--no-serving", action="store_true", help="medium: skip the serving measurement")
     return p.parse_args()
 
 
@@ -321,6 +324,8 @@ def run_native(args, world, rank, local):
         if e2e:
             out["e2e"] = {"value": round(e2e[0] / e2e[1] / 1e6, 2), "unit": "Mrays/s",
                           "h2d_bytes_per_step": int(e2e[2]), "d2h_bytes_per_step": int(e2e[3])}
+        if world == 1 and not args.no_serving:
+            out["serving"] = run_serving(args.requests)
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(s, motions[args.warmup:], args.cpu_seconds)
         print(json.dumps(out), flush=True)
@@ -328,6 +333,111 @@ def run_native(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+SERVE_WORKLOAD = ("serve: Poisson arrivals at 200 req/s over 8 resident scenes (the tiny scene + 7 medium-style "
+                  "scenes), resolution uniform over 320x240 / 640x480 / 1280x720 / 1920x1080 / 3840x2160, max_depth "
+                  "uniform 1..8, seeded per-request instance motion (per-request TLAS refit)")
+
+
+def pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, max(0, math.ceil(q * len(xs)) - 1))]
+
+
+def run_serving(n_requests):
+    """The request stream through the continuous-batching server in real time,
+    then the same requests one at a time (rg_tlas_refit + rg_render each, FIFO
+    in arrival order; latencies from the measured service times).  Latency =
+    arrival to the step that completes the image on the device."""
+    import torch
+    import paper_2001_09792_gb300 as rg
+
+    scenes = g.serving_scenes()
+    reqs = g.serving_requests(n_requests)
+    gss = [rg.GpuScene(sc) for sc in scenes]
+    trans = [g.motion(scenes[q["scene"]].M, q["motion_seed"]) for q in reqs]
+    cams = [rg.make_camera(sc.camera) for sc in scenes]
+    srv = rg.rg_server_create()
+    try:
+        for gsc in gss:
+            rg.rg_server_add_scene(srv, gsc.h)
+        scratch = torch.empty((1080, 1920, 4), device="cuda")
+        cache = os.environ.get("RG_TUNE_CACHE", os.path.join(tempfile.gettempdir(), "rg_tuned_shapes.json"))
+        tuned = rg.rg_server_autotune(srv, 1, scenes[1].camera, 1920, 1080, 4, scratch, cache_path=cache)
+        del scratch
+        # warm-up: one request of each scene through the server (graph captures)
+        for k in range(len(scenes)):
+            img = torch.empty((240, 320, 4), device="cuda")
+            rg.rg_server_submit(srv, k, cams[k], 320, 240, 4, img)
+            rg.rg_server_drain(srv)
+        rg.rg_server_poll(srv, 64)
+        base = rg.rg_server_get_stats(srv)
+        torch.cuda.synchronize()
+        imgs, lat, busy = {}, [], 0.0
+        nxt = 0
+        t0 = time.perf_counter()
+        t_first = reqs[0]["arrival"]
+        while len(lat) < len(reqs):
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and reqs[nxt]["arrival"] <= now:
+                q = reqs[nxt]
+                imgs[nxt] = torch.empty((q["height"], q["width"], 4), device="cuda")
+                rg.rg_server_submit(srv, q["scene"], cams[q["scene"]], q["width"], q["height"], q["max_depth"],
+                                    imgs[nxt], trans[nxt], tag=nxt)
+                nxt += 1
+            st = rg.rg_server_get_stats(srv)
+            if st["active"] == 0 and st["pending"] == 0:
+                time.sleep(max(0.0, reqs[nxt]["arrival"] - (time.perf_counter() - t0)))
+                continue
+            a = time.perf_counter()
+            rg.rg_server_step(srv)
+            b = time.perf_counter()
+            busy += b - a
+            for c in rg.rg_server_poll(srv, 256):
+                lat.append(b - t0 - reqs[c["tag"]]["arrival"])
+                del imgs[c["tag"]]
+        t_end = time.perf_counter() - t0
+        st = rg.rg_server_get_stats(srv)
+        rays = (st["closest_rays"] - base["closest_rays"]) + (st["shadow_rays"] - base["shadow_rays"])
+        steps = st["steps"] - base["steps"]
+    finally:
+        rg.rg_server_destroy(srv)
+
+    # one request at a time through the plain path
+    for gsc in gss:
+        rg.rg_reset_stats(gsc.h)
+    service = []
+    for k, q in enumerate(reqs):
+        gsc = gss[q["scene"]]
+        out = torch.empty((q["height"], q["width"], 4), device="cuda")
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        gsc.refit(trans[k])
+        rg.rg_render(gsc.h, cams[q["scene"]], q["width"], q["height"], q["max_depth"], out=out)
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - a)
+    seq_rays = 0
+    for gsc in gss:
+        s2 = rg.rg_get_stats(gsc.h)
+        seq_rays += s2["closest_rays"] + s2["shadow_rays"]
+        gsc.close()
+    finish, seq_lat = 0.0, []
+    for q, sv in zip(reqs, service):
+        finish = max(finish, q["arrival"]) + sv
+        seq_lat.append(finish - q["arrival"])
+    return {
+        "workload": SERVE_WORKLOAD, "requests": len(reqs),
+        "offered_req_s": round(len(reqs) / (reqs[-1]["arrival"] - t_first + 1e-9), 1),
+        "p50_ms": round(pct(lat, 0.50) * 1e3, 2), "p99_ms": round(pct(lat, 0.99) * 1e3, 2),
+        "mrays_s": round(rays / (t_end - t_first) / 1e6, 2), "busy_mrays_s": round(rays / busy / 1e6, 2),
+        "rays": int(rays), "steps": int(steps), "ring_peak": int(st["ring_peak"]),
+        "shapes": tuned,
+        "one_at_a_time": {"p50_ms": round(pct(seq_lat, 0.50) * 1e3, 2), "p99_ms": round(pct(seq_lat, 0.99) * 1e3, 2),
+                          "busy_mrays_s": round(seq_rays / sum(service) / 1e6, 2),
+                          "mrays_s": round(seq_rays / (finish - t_first) / 1e6, 2), "rays": int(seq_rays)},
+        "latency": "arrival to completion of the image on the device (host clock)",
+    }
 
 
 def reduce_over_ranks(max_vals, sum_vals, device):
@@ -521,6 +631,23 @@ def run_native_large(args, world, rank, local):
     gs.close()
 
 
+def run_native_serve(args, world, rank, local):
+    import torch
+    from paper_2001_09792_gb300 import _build
+
+    torch.cuda.set_device(local)
+    _build.build()
+    if rank != 0:
+        return
+    r = run_serving(args.requests)
+    out = {"metric": "served Mrays/s and p50/p99 request latency (continuous batching) vs one request at a time",
+           "value": r["mrays_s"], "unit": "Mrays/s", "n_gpus": 1, "steps": r["steps"], "warmup": len(g.serving_scenes()),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded procedural scenes and request stream)", "config": {"workload": SERVE_WORKLOAD},
+           "serving": r}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -528,6 +655,8 @@ def main():
         run_reference(args, world, rank, local)
     elif args.workload == "large":
         run_native_large(args, world, rank, local)
+    elif args.workload == "serve":
+        run_native_serve(args, world, rank, local)
     else:
         run_native(args, world, rank, local)
 

@@ -254,6 +254,129 @@ rg_status rg_wide_export(rg_scene* scene, uint32_t blas_id, void* h_nodes, uint3
 rg_status rg_radix_sort_pairs_noalloc(const void* d_keys, const uint32_t* d_vals, uint32_t n, uint32_t key_bits,
                                       void* d_keys_out, uint32_t* d_vals_out, void* stream);
 
+/* ---- continuous-batching render server --------------------------------- */
+
+/* Serving many render requests at once over resident scenes.  The paper
+ * renders one frame per dispatch (Sec. 1: a scene is set up, then rays are
+ * dispatched and recursively traced); the server keeps that per-ray work and
+ * batches it: the path rays (primary, reflected, refracted) of every request
+ * in flight share one ring of rays; each rg_server_step traces and shades a
+ * batch of them (closest hit, then the shadow rays the shading spawned) and
+ * appends the rays it spawns, so requests of different scenes, resolutions
+ * and depths are traced in the same launches.  Requests join as earlier ones
+ * complete (continuous batching).  Each request carries its own instance
+ * transforms: on admission the server refits a private copy of the scene's
+ * TLAS with them (same topology, new boxes), so the images equal those of
+ * rg_tlas_refit + rg_render of the request alone, up to the order of the
+ * float additions into a pixel.
+ *
+ * Admission is by free ring memory: a request of w*h pixels is admitted, in
+ * arrival order, when a request slot is free (at most RG_SERVER_MAX_SLOTS in
+ * flight) and the rays in the ring plus its w*h primary rays fit in half the
+ * ring; the other half takes the rays steps spawn (at most two per traced
+ * ray).  A step traces up to min(batch_rays, shadow capacity / max lights)
+ * rays, oldest first, as many as the free ring takes in the worst case.  When
+ * that is under a quarter of a batch (glass doubling the rays of deep ray
+ * trees), steps take the newest rays instead (the deepest: the trees are then
+ * finished depth first, which bounds the live rays), a batch of at most
+ * free ring / (2 (RG_SERVER_MAX_DEPTH + 1)).  RG_ERR_OOM only if even that is
+ * zero.
+ *
+ * Every step's device work runs on the server's own stream, as one CUDA graph
+ * (captured on first use, re-captured when buffers or launch shapes change);
+ * rg_server_step returns when that work has finished.  Calls on one server
+ * must not run concurrently. */
+typedef struct rg_server rg_server;
+
+#define RG_SERVER_MAX_SLOTS 32u
+#define RG_SERVER_MAX_PIXELS (1u << 23)   /* w*h of one request */
+#define RG_SERVER_MAX_DEPTH 15u
+
+typedef struct {
+    uint32_t ring_log2;   /* the ray ring holds 2^ring_log2 rays (48 B each); 0 = 2^25; 16..30 */
+    uint32_t batch_rays;  /* rays traced per step at most; 0 = 2^23 */
+    uint32_t max_lights;  /* shadow queue = batch_rays * max_lights rays (48 B each); 0 = 4; scenes with
+                             more lights are refused */
+    uint32_t flags;       /* RG_SERVER_NO_GRAPH: launch each step's kernels directly, no CUDA graph */
+} rg_server_desc;
+#define RG_SERVER_NO_GRAPH 1u
+
+/* One render request.  h_transforms: n_inst 3x4 row-major object-to-world
+ * matrices (12 floats each) in the order of the scene's rg_tlas_build, or
+ * NULL for the scene's own; copied at submission.  d_rgba: caller-owned
+ * device image of w*h RGBA32F (row 0 at the top), written by the server from
+ * admission to completion; the caller keeps it alive until then. */
+typedef struct {
+    uint32_t scene;        /* id from rg_server_add_scene */
+    rg_camera camera;
+    uint32_t width, height; /* 1 <= w*h <= RG_SERVER_MAX_PIXELS, and w*h <= 2^(ring_log2-1) */
+    uint32_t max_depth;     /* 1..RG_SERVER_MAX_DEPTH */
+    const float* h_transforms;
+    float* d_rgba;
+    uint64_t tag;           /* returned with the completion */
+} rg_request;
+
+typedef struct {
+    uint64_t id;          /* from rg_server_submit */
+    uint64_t tag;
+    uint32_t admitted_step, completed_step; /* step numbers (1-based) */
+} rg_completion;
+
+typedef struct {
+    uint64_t steps, submitted, admitted, completed;
+    uint64_t closest_rays, shadow_rays;     /* traced so far */
+    uint32_t pending, active;               /* waiting for admission / in flight */
+    uint32_t ring_rays, ring_peak;          /* rays in the ring now / at most so far */
+    uint64_t graph_launches, graph_captures;
+    uint64_t kernel_launches;               /* kernels launched by the server's steps (graph kernels included) */
+    uint64_t newest_first_steps;            /* steps that took the newest rays (ring nearly full) */
+} rg_server_stats;
+
+/* Creates a server on the current device (desc NULL: defaults).  Allocates the
+ * ring, the hit and shadow queues and the per-slot buffers up front. */
+rg_status rg_server_create(rg_server** out, const rg_server_desc* desc);
+rg_status rg_server_destroy(rg_server* server);
+/* Makes a built scene (rg_tlas_build and rg_scene_set_materials done)
+ * available to requests; the scene must stay alive and must not be rebuilt
+ * (rg_blas_build, rg_tlas_build) or destroyed while the server exists.
+ * Returns RG_ERR_INVALID_ARG for a compressed-only or foreign-device scene or
+ * one with more lights than max_lights. */
+rg_status rg_server_add_scene(rg_server* server, rg_scene* scene, uint32_t* scene_id);
+/* Queues a request; validated here (RG_ERR_INVALID_ARG on a bad size, depth,
+ * scene id or pointer). */
+rg_status rg_server_submit(rg_server* server, const rg_request* req, uint64_t* request_id);
+/* One step: admits what fits, refits the admitted requests' TLAS copies,
+ * traces and shades one batch, and waits for it.  *n_completed (may be NULL)
+ * = requests completed by this step; their images are final.  With nothing
+ * queued or in flight the step does nothing.  Device errors (stack overflow,
+ * iteration cap, singular transform, bad material) are returned here. */
+rg_status rg_server_step(rg_server* server, uint32_t* n_completed);
+/* Steps until nothing is queued or in flight. */
+rg_status rg_server_drain(rg_server* server);
+/* Moves up to `max` completions (oldest first) to out; *n = how many. */
+rg_status rg_server_poll(rg_server* server, rg_completion* out, uint32_t max, uint32_t* n);
+rg_status rg_server_get_stats(rg_server* server, rg_server_stats* out);
+
+/* Launch shapes of the server's two traversals (which: 0 closest hit,
+ * 1 shadow): threads per block 64 / 128 / 256, resident blocks per SM
+ * (0 = as many as fit) and rays a warp takes per grab of the work counter
+ * (a multiple of 32, <= 1024). */
+typedef struct { uint32_t block, blocks_per_sm, grab; float ms; } rg_trace_shape;
+rg_status rg_server_set_shape(rg_server* server, uint32_t which, const rg_trace_shape* shape);
+rg_status rg_server_get_shape(rg_server* server, uint32_t which, rg_trace_shape* out);
+/* Autotuner: picks both shapes by timing every candidate (block x blocks per
+ * SM x grab) on the sample request's rays (its primary rays for the closest
+ * traversal, the shadow rays their shading spawns for the shadow traversal),
+ * sets them, and reports them in out[0..1] (ms = best time of that
+ * traversal).  cache_path (may be NULL): a JSON file; if it holds shapes for
+ * this device model they are taken without timing (unless flags has
+ * RG_TUNE_FORCE), else the tuned shapes are written there.  Runs only on an
+ * idle server (nothing queued or in flight: else RG_ERR_INVALID_ARG); the
+ * sample's image is overwritten. */
+#define RG_TUNE_FORCE 1u
+rg_status rg_server_autotune(rg_server* server, const rg_request* sample, const char* cache_path, uint32_t flags,
+                             rg_trace_shape out[2]);
+
 #ifdef __cplusplus
 }
 #endif

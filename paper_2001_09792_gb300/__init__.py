@@ -36,8 +36,16 @@ MISS = 0xFFFFFFFF
 SYMBOLS = ["rg_scene_create", "rg_scene_destroy", "rg_blas_build", "rg_tlas_build", "rg_tlas_refit",
            "rg_scene_set_materials", "rg_scene_set_lights", "rg_trace_rays", "rg_render", "rg_sync", "rg_get_stats",
            "rg_reset_stats", "rg_last_error", "rg_tri_bounds", "rg_morton_codes", "rg_radix_sort_pairs", "rg_karras",
-           "rg_blas_export", "rg_tlas_export", "rg_wide_export", "rg_radix_sort_pairs_noalloc"]
+           "rg_blas_export", "rg_tlas_export", "rg_wide_export", "rg_radix_sort_pairs_noalloc",
+           "rg_server_create", "rg_server_destroy", "rg_server_add_scene", "rg_server_submit", "rg_server_step",
+           "rg_server_drain", "rg_server_poll", "rg_server_get_stats", "rg_server_set_shape", "rg_server_get_shape",
+           "rg_server_autotune"]
 RG_NOALLOC_SORT_MAX_PAIRS = 262144
+RG_SERVER_MAX_SLOTS = 32
+RG_SERVER_MAX_PIXELS = 1 << 23
+RG_SERVER_MAX_DEPTH = 15
+RG_SERVER_NO_GRAPH = 1
+RG_TUNE_FORCE = 1
 
 f32x3 = ctypes.c_float * 3
 
@@ -65,6 +73,36 @@ class rg_stats(ctypes.Structure):
                 ("node_visits", ctypes.c_uint64), ("tri_tests", ctypes.c_uint64), ("inst_entries", ctypes.c_uint64),
                 ("any_node_visits", ctypes.c_uint64), ("any_tri_tests", ctypes.c_uint64),
                 ("any_inst_entries", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
+
+
+class rg_server_desc(ctypes.Structure):
+    _fields_ = [("ring_log2", ctypes.c_uint32), ("batch_rays", ctypes.c_uint32), ("max_lights", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32)]
+
+
+class rg_request(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_uint32), ("camera", rg_camera), ("width", ctypes.c_uint32),
+                ("height", ctypes.c_uint32), ("max_depth", ctypes.c_uint32), ("h_transforms", ctypes.c_void_p),
+                ("d_rgba", ctypes.c_void_p), ("tag", ctypes.c_uint64)]
+
+
+class rg_completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("admitted_step", ctypes.c_uint32),
+                ("completed_step", ctypes.c_uint32)]
+
+
+class rg_server_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint64), ("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("closest_rays", ctypes.c_uint64), ("shadow_rays", ctypes.c_uint64),
+                ("pending", ctypes.c_uint32), ("active", ctypes.c_uint32), ("ring_rays", ctypes.c_uint32),
+                ("ring_peak", ctypes.c_uint32), ("graph_launches", ctypes.c_uint64),
+                ("graph_captures", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
+                ("newest_first_steps", ctypes.c_uint64)]
+
+
+class rg_trace_shape(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32), ("grab", ctypes.c_uint32),
+                ("ms", ctypes.c_float)]
 
 
 class RgError(RuntimeError):
@@ -105,6 +143,17 @@ def lib():
             "rg_tlas_export": [P, P, P, P, P, ctypes.POINTER(u32)],
             "rg_radix_sort_pairs_noalloc": [P, P, u32, u32, P, P, P],
             "rg_wide_export": [P, u32, P, P, P, P],
+            "rg_server_create": [ctypes.POINTER(P), P],
+            "rg_server_destroy": [P],
+            "rg_server_add_scene": [P, P, ctypes.POINTER(u32)],
+            "rg_server_submit": [P, P, ctypes.POINTER(ctypes.c_uint64)],
+            "rg_server_step": [P, ctypes.POINTER(u32)],
+            "rg_server_drain": [P],
+            "rg_server_poll": [P, P, u32, ctypes.POINTER(u32)],
+            "rg_server_get_stats": [P, P],
+            "rg_server_set_shape": [P, u32, P],
+            "rg_server_get_shape": [P, u32, P],
+            "rg_server_autotune": [P, P, ctypes.c_char_p, u32, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -373,6 +422,93 @@ def rg_tlas_export(scene, n):
     v = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
     _check(lib().rg_tlas_export(scene, v(nodes), v(wbox), v(inv), v(order), ctypes.byref(root)))
     return dict(nodes=nodes[: max(n - 1, 0)], wbox=wbox, inv=inv.reshape(n, 3, 4), order=order, root=root.value)
+
+
+# ---------------------------------------------------------------- render server
+
+def rg_server_create(ring_log2=0, batch_rays=0, max_lights=0, flags=0):
+    d = rg_server_desc(int(ring_log2), int(batch_rays), int(max_lights), int(flags))
+    h = ctypes.c_void_p()
+    _check(lib().rg_server_create(ctypes.byref(h), ctypes.byref(d)))
+    return h
+
+
+def rg_server_destroy(server):
+    _check(lib().rg_server_destroy(server))
+
+
+def rg_server_add_scene(server, scene):
+    sid = ctypes.c_uint32()
+    _check(lib().rg_server_add_scene(server, scene, ctypes.byref(sid)))
+    return sid.value
+
+
+def make_request(scene_id, camera, width, height, max_depth, image, transforms=None, tag=0):
+    """An rg_request; `image` is a contiguous float32 CUDA tensor of w*h*4
+    elements, `transforms` None or (n_inst, 3, 4) float32 (kept alive by the
+    returned pair until submission copies it)."""
+    torch = _torch()
+    if image.numel() != width * height * 4 or image.dtype != torch.float32 or not image.is_cuda \
+            or not image.is_contiguous():
+        raise ValueError("image must be a contiguous float32 CUDA tensor of w*h*4 elements")
+    cam = camera if isinstance(camera, rg_camera) else make_camera(camera)
+    tr = None
+    if transforms is not None:
+        tr = np.ascontiguousarray(transforms, np.float32).reshape(-1, 12)
+    q = rg_request(int(scene_id), cam, int(width), int(height), int(max_depth),
+                   ctypes.c_void_p(tr.ctypes.data) if tr is not None else None, ctypes.c_void_p(image.data_ptr()),
+                   int(tag))
+    return q, tr
+
+
+def rg_server_submit(server, scene_id, camera, width, height, max_depth, image, transforms=None, tag=0):
+    q, _keep = make_request(scene_id, camera, width, height, max_depth, image, transforms, tag)
+    rid = ctypes.c_uint64()
+    _check(lib().rg_server_submit(server, ctypes.byref(q), ctypes.byref(rid)))
+    return rid.value
+
+
+def rg_server_step(server):
+    n = ctypes.c_uint32()
+    _check(lib().rg_server_step(server, ctypes.byref(n)))
+    return n.value
+
+
+def rg_server_drain(server):
+    _check(lib().rg_server_drain(server))
+
+
+def rg_server_poll(server, max_n=RG_SERVER_MAX_SLOTS * 4):
+    buf = (rg_completion * max_n)()
+    n = ctypes.c_uint32()
+    _check(lib().rg_server_poll(server, buf, max_n, ctypes.byref(n)))
+    return [dict(id=c.id, tag=c.tag, admitted_step=c.admitted_step, completed_step=c.completed_step)
+            for c in buf[: n.value]]
+
+
+def rg_server_get_stats(server):
+    st = rg_server_stats()
+    _check(lib().rg_server_get_stats(server, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in rg_server_stats._fields_}
+
+
+def rg_server_set_shape(server, which, block, blocks_per_sm, grab):
+    sh = rg_trace_shape(int(block), int(blocks_per_sm), int(grab), 0.0)
+    _check(lib().rg_server_set_shape(server, int(which), ctypes.byref(sh)))
+
+
+def rg_server_get_shape(server, which):
+    sh = rg_trace_shape()
+    _check(lib().rg_server_get_shape(server, int(which), ctypes.byref(sh)))
+    return dict(block=sh.block, blocks_per_sm=sh.blocks_per_sm, grab=sh.grab)
+
+
+def rg_server_autotune(server, scene_id, camera, width, height, max_depth, image, cache_path=None, force=False):
+    q, _keep = make_request(scene_id, camera, width, height, max_depth, image)
+    out = (rg_trace_shape * 2)()
+    path = cache_path.encode() if cache_path else None
+    _check(lib().rg_server_autotune(server, ctypes.byref(q), path, RG_TUNE_FORCE if force else 0, out))
+    return [dict(block=o.block, blocks_per_sm=o.blocks_per_sm, grab=o.grab, ms=o.ms) for o in out]
 
 
 # ---------------------------------------------------------------- convenience

@@ -871,10 +871,40 @@ rg_status rg_tlas_export(rg_scene* s, void* h_nodes, float* h_wbox, float* h_inv
 }  // extern "C"
 
 namespace rg {
+rg_status scene_view(rg_scene* s, SceneView* v) {
+    rg_status r;
+    if ((r = check_scene(s))) return r;
+    if (!s->tlas_built) return fail(RG_ERR_NOT_BUILT, "scene has no TLAS");
+    if (s->n_mats == 0) return fail(RG_ERR_NOT_BUILT, "scene has no materials");
+    v->device = s->device;
+    v->d_blas = s->d_blas.p;
+    v->n_blas = (uint32_t)s->blas.size();
+    v->tlas_nodes = s->tlas_nodes.p;
+    v->perm = s->perm.p;
+    v->parents = s->parents.p;
+    v->inst = s->inst.p;
+    v->n_inst = s->n_inst;
+    v->tlas_root = s->tlas_root;
+    v->mats = s->mats.p;
+    v->n_mats = s->n_mats;
+    v->lights = s->lights.p;
+    v->n_lights = s->n_lights;
+    for (int k = 0; k < 3; ++k) v->bg[k] = s->desc.background[k];
+    v->ambient = s->desc.ambient;
+    v->iter_cap = iter_cap_for(s, false);
+    return RG_OK;
+}
+}  // namespace rg
+
+namespace rg {
 rg_status report_error(rg_status code, const char* msg) { return fail(code, msg); }
 
 static std::atomic<unsigned long long> g_launches{0};
-void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static thread_local bool g_capturing = false;
+void count_launches(unsigned n) {
+    if (!g_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+void set_capturing(bool on) { g_capturing = on; }
 unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 int device_sm_count() {

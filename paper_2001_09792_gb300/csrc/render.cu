@@ -39,11 +39,9 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
 }
 __device__ __forceinline__ float3 normalize3(float3 a) { return rsqrtf(dot3(a, a)) * a; }
 
-__global__ void k_raygen(CameraDev cam, uint32_t w, uint32_t h, float4* __restrict__ rays,
-                         Payload* __restrict__ payload) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= w * h) return;
-    uint32_t x = i % w, y = i / w;
+// Pinhole camera ray through the centre of pixel (x, y), row 0 at the top.
+__device__ __forceinline__ void camera_ray(const CameraDev& cam, uint32_t w, uint32_t h, uint32_t x, uint32_t y,
+                                           float4& o, float4& dir) {
     float3 eye = f3(cam.eye[0], cam.eye[1], cam.eye[2]);
     float3 F = normalize3(f3(cam.target[0], cam.target[1], cam.target[2]) - eye);
     float3 R = normalize3(cross3(F, f3(cam.up[0], cam.up[1], cam.up[2])));
@@ -53,8 +51,18 @@ __global__ void k_raygen(CameraDev cam, uint32_t w, uint32_t h, float4* __restri
     float px = (2.0f * ((float)x + 0.5f) / (float)w - 1.0f) * aspect * th;
     float py = (1.0f - 2.0f * ((float)y + 0.5f) / (float)h) * th;
     float3 d = normalize3(px * R + py * U + F);
-    rays[2 * (size_t)i] = make_float4(eye.x, eye.y, eye.z, 0.0f);
-    rays[2 * (size_t)i + 1] = make_float4(d.x, d.y, d.z, __int_as_float(0x7F800000));
+    o = make_float4(eye.x, eye.y, eye.z, 0.0f);
+    dir = make_float4(d.x, d.y, d.z, __int_as_float(0x7F800000));
+}
+
+__global__ void k_raygen(CameraDev cam, uint32_t w, uint32_t h, float4* __restrict__ rays,
+                         Payload* __restrict__ payload) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w * h) return;
+    float4 o, d;
+    camera_ray(cam, w, h, i % w, i / w, o, d);
+    rays[2 * (size_t)i] = o;
+    rays[2 * (size_t)i + 1] = d;
     Payload p;
     p.pixel = i;
     p.r = p.g = p.b = 1.0f;
@@ -87,31 +95,85 @@ struct Surf {
     bool entering;
 };
 
-__global__ void __launch_bounds__(kShadeBlock) k_shade(ShadeArgs a, uint32_t n) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = i < n;
+// What one ray's shading needs besides the ray: the tables of its scene or
+// request slot, its image, its depth and its pixel.
+struct RayCtx {
+    const InstDev* inst;
+    const rg_material* mats;
+    const rg_light* lights;
+    float* image;
+    uint32_t n_mats, n_lights, depth, max_depth, pixel, slot;
+    float bg[3];
+    float ambient;
+};
+
+template <bool BATCH>
+__device__ __forceinline__ RayCtx ray_ctx(const ShadeArgs& a, const SlotDev* slots, uint32_t pw) {
+    RayCtx c;
+    if (BATCH) {
+        const SlotDev* S = slots + slot_of_px(pw);
+        c.inst = S->inst;
+        c.mats = S->mats;
+        c.lights = S->lights;
+        c.image = S->image;
+        c.n_mats = S->n_mats;
+        c.n_lights = S->n_lights;
+        c.max_depth = S->max_depth;
+        c.bg[0] = S->bg[0];
+        c.bg[1] = S->bg[1];
+        c.bg[2] = S->bg[2];
+        c.ambient = S->ambient;
+        c.depth = depth_of(pw);
+        c.pixel = px_of(pw);
+        c.slot = slot_of_px(pw);
+    } else {
+        c.inst = a.inst;
+        c.mats = a.mats;
+        c.lights = a.lights;
+        c.image = a.image;
+        c.n_mats = a.n_mats;
+        c.n_lights = a.n_lights;
+        c.max_depth = a.max_depth;
+        c.bg[0] = a.bg[0];
+        c.bg[1] = a.bg[1];
+        c.bg[2] = a.bg[2];
+        c.ambient = a.ambient;
+        c.depth = a.depth;
+        c.pixel = pw;
+        c.slot = 0;
+    }
+    return c;
+}
+
+// Shade ray i (valid == false: take part in the warp's queue claims only).
+// live_delta (batched only): per-slot sums of (path rays spawned - 1) of this
+// block, in shared memory.
+template <bool BATCH>
+__device__ __forceinline__ void shade_one(const ShadeArgs& a, uint32_t head, uint32_t next_base, uint32_t i,
+                                          bool valid, int* live_delta) {
     uint32_t n_shadow = 0, n_next = 0;
     Surf s;
     uint32_t type = 0;
     float3 alb = f3(0, 0, 0), thr = f3(0, 0, 0);
     float ior = 1.0f;
-    uint32_t pixel = 0;
     bool hit = false;
+    RayCtx c;
     if (valid) {
-        const float4 r0 = a.rays[2 * (size_t)i], r1 = a.rays[2 * (size_t)i + 1];
-        const Payload pl = a.payload[i];
+        const uint32_t j = BATCH ? ((head + i) & a.ring_mask) : i;
+        const float4 r0 = a.rays[2 * (size_t)j], r1 = a.rays[2 * (size_t)j + 1];
+        const Payload pl = a.payload[j];
         const HitDev hd = a.hits[i];
-        pixel = pl.pixel;
+        c = ray_ctx<BATCH>(a, a.slots, pl.pixel);
         thr = f3(pl.r, pl.g, pl.b);
-        float* px = a.image + 4 * (size_t)pixel;
+        float* px = c.image + 4 * (size_t)c.pixel;
         if (hd.inst_leaf == kMiss) {
-            atomicAdd(px + 0, thr.x * a.bg[0]);
-            atomicAdd(px + 1, thr.y * a.bg[1]);
-            atomicAdd(px + 2, thr.z * a.bg[2]);
+            atomicAdd(px + 0, thr.x * c.bg[0]);
+            atomicAdd(px + 1, thr.y * c.bg[1]);
+            atomicAdd(px + 2, thr.z * c.bg[2]);
         } else {
             hit = true;
-            if (a.depth == 1) px[3] = 1.0f;
-            const InstDev* I = a.inst + hd.inst_leaf;
+            if (c.depth == 1) px[3] = 1.0f;
+            const InstDev* I = c.inst + hd.inst_leaf;
             const float4 i0 = I->inv[0], i1 = I->inv[1], i2 = I->inv[2];
             const float4* tp = I->tris + 3 * (size_t)hd.tri_leaf;
             const float4 v0 = tp[0], v1 = tp[1], v2 = tp[2];
@@ -127,25 +189,25 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ShadeArgs a, uint32_t n) 
             s.nf = s.entering ? nw : -1.0f * nw;
             s.eps = 1e-4f * fmaxf(1.0f, fmaxf(fabsf(s.p.x), fmaxf(fabsf(s.p.y), fabsf(s.p.z))));
             uint32_t mi = I->material;
-            if (mi >= a.n_mats) {
+            if (mi >= c.n_mats) {
                 record_error(a.st, RG_ERR_INVALID_ARG);
                 mi = 0;
             }
-            const rg_material M = a.mats[mi];
+            const rg_material M = c.mats[mi];
             type = M.type;
             alb = f3(M.albedo[0], M.albedo[1], M.albedo[2]);
             ior = M.ior;
             if (type == RG_MAT_DIFFUSE) {
-                atomicAdd(px + 0, thr.x * alb.x * a.ambient);
-                atomicAdd(px + 1, thr.y * alb.y * a.ambient);
-                atomicAdd(px + 2, thr.z * alb.z * a.ambient);
+                atomicAdd(px + 0, thr.x * alb.x * c.ambient);
+                atomicAdd(px + 1, thr.y * alb.y * c.ambient);
+                atomicAdd(px + 2, thr.z * alb.z * c.ambient);
                 float3 os = s.p + s.eps * s.nf;
-                for (uint32_t l = 0; l < a.n_lights; ++l) {
-                    const rg_light L = a.lights[l];
+                for (uint32_t l = 0; l < c.n_lights; ++l) {
+                    const rg_light L = c.lights[l];
                     float3 lv = f3(L.pos[0], L.pos[1], L.pos[2]) - os;
                     if (dot3(s.nf, lv) > 0.0f) ++n_shadow;
                 }
-            } else if (a.depth < a.max_depth) {
+            } else if (c.depth < c.max_depth) {
                 n_next = 1;
                 if (type == RG_MAT_GLASS) {
                     float eta = s.entering ? 1.0f / ior : ior;
@@ -159,25 +221,29 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ShadeArgs a, uint32_t n) 
     // claim queue slots (all lanes take part)
     uint32_t sbase = warp_claim(n_shadow, a.shadow_count, &a.st->shadow_rays);
     uint32_t nbase = warp_claim(n_next, a.next_count);
+    // live path rays of the slot: this ray leaves, its spawns join
+    if (BATCH && valid && n_next != 1) atomicAdd(live_delta + c.slot, (int)n_next - 1);
     if (!valid || !hit) return;
+    const uint32_t next_pw = BATCH ? pack_pixel(c.pixel, c.depth + 1, c.slot) : c.pixel;
+    const uint32_t shadow_pw = BATCH ? pack_pixel(c.pixel, c.depth, c.slot) : c.pixel;
     if (n_shadow) {
         float3 os = s.p + s.eps * s.nf;
         uint32_t k = 0;
-        for (uint32_t l = 0; l < a.n_lights; ++l) {
-            const rg_light L = a.lights[l];
+        for (uint32_t l = 0; l < c.n_lights; ++l) {
+            const rg_light L = c.lights[l];
             float3 lv = f3(L.pos[0], L.pos[1], L.pos[2]) - os;
             if (!(dot3(s.nf, lv) > 0.0f)) continue;
             float dist = sqrtf(dot3(lv, lv));
             float3 ld = (1.0f / dist) * lv;
-            float c = dot3(s.nf, ld);
+            float cl = dot3(s.nf, ld);
             uint32_t slot = sbase + k++;
             a.shadow_rays[2 * (size_t)slot] = make_float4(os.x, os.y, os.z, 0.0f);
             a.shadow_rays[2 * (size_t)slot + 1] = make_float4(ld.x, ld.y, ld.z, dist - s.eps);
             Payload sp;
-            sp.pixel = pixel;
-            sp.r = thr.x * alb.x * L.intensity[0] * c;
-            sp.g = thr.y * alb.y * L.intensity[1] * c;
-            sp.b = thr.z * alb.z * L.intensity[2] * c;
+            sp.pixel = shadow_pw;
+            sp.r = thr.x * alb.x * L.intensity[0] * cl;
+            sp.g = thr.y * alb.y * L.intensity[1] * cl;
+            sp.b = thr.z * alb.z * L.intensity[2] * cl;
             a.shadow_payload[slot] = sp;
         }
     }
@@ -196,29 +262,88 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ShadeArgs a, uint32_t n) 
             float3 T = normalize3(eta * s.d + (eta * ci - sk) * s.nf);
             float R0 = (1.0f - ior) / (1.0f + ior);
             R0 = R0 * R0;
-            float c = s.entering ? ci : sk;
-            float m = 1.0f - c;
+            float cc = s.entering ? ci : sk;
+            float m = 1.0f - cc;
             float R = R0 + (1.0f - R0) * (m * m * m * m * m);
             w_r = R * thr;
             float3 to = s.p - s.eps * s.nf;
-            uint32_t slot = nbase + 1;
+            uint32_t slot = BATCH ? ((next_base + nbase + 1) & a.ring_mask) : nbase + 1;
             a.next_rays[2 * (size_t)slot] = make_float4(to.x, to.y, to.z, 0.0f);
             a.next_rays[2 * (size_t)slot + 1] = make_float4(T.x, T.y, T.z, __int_as_float(0x7F800000));
             Payload tp;
-            tp.pixel = pixel;
+            tp.pixel = next_pw;
             tp.r = (1.0f - R) * thr.x;
             tp.g = (1.0f - R) * thr.y;
             tp.b = (1.0f - R) * thr.z;
             a.next_payload[slot] = tp;
         }
-        a.next_rays[2 * (size_t)nbase] = make_float4(ro.x, ro.y, ro.z, 0.0f);
-        a.next_rays[2 * (size_t)nbase + 1] = make_float4(r.x, r.y, r.z, __int_as_float(0x7F800000));
+        const uint32_t rslot = BATCH ? ((next_base + nbase) & a.ring_mask) : nbase;
+        a.next_rays[2 * (size_t)rslot] = make_float4(ro.x, ro.y, ro.z, 0.0f);
+        a.next_rays[2 * (size_t)rslot + 1] = make_float4(r.x, r.y, r.z, __int_as_float(0x7F800000));
         Payload rp;
-        rp.pixel = pixel;
+        rp.pixel = next_pw;
         rp.r = w_r.x;
         rp.g = w_r.y;
         rp.b = w_r.z;
-        a.next_payload[nbase] = rp;
+        a.next_payload[rslot] = rp;
+    }
+}
+
+__global__ void __launch_bounds__(kShadeBlock) k_shade(ShadeArgs a, uint32_t n) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    shade_one<false>(a, 0u, 0u, i, i < n, nullptr);
+}
+
+// Mixed queue: the count is read on the device; whole blocks step together so
+// that every lane takes part in the warp claims.
+__global__ void __launch_bounds__(kShadeBlock) k_shade_batch(ShadeArgs a) {
+    __shared__ int live_delta[kMaxSlots];
+    static_assert(kShadeBlock >= kMaxSlots, "one thread per slot flushes the block's sums");
+    if (threadIdx.x < kMaxSlots) live_delta[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t n = *a.d_count;
+    const uint32_t head = *a.ring_head, next_base = *a.next_base;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        shade_one<true>(a, head, next_base, i, i < n, live_delta);
+    }
+    __syncthreads();
+    if (threadIdx.x < kMaxSlots && live_delta[threadIdx.x] != 0)
+        atomicAdd(a.slot_live + threadIdx.x, live_delta[threadIdx.x]);
+}
+
+// Primary rays of the requests admitted in this step; ray r belongs to the
+// request whose [offset, offset + w h) range holds it (offsets ascending).
+__global__ void k_raygen_batch(const RaygenReq* __restrict__ reqs, const uint32_t* __restrict__ n_reqs_p,
+                               const uint32_t* __restrict__ n_rays_p, const uint32_t* __restrict__ gen_base_p,
+                               uint32_t ring_mask, float4* __restrict__ rays, Payload* __restrict__ payload) {
+    __shared__ RaygenReq sr[kMaxSlots];
+    const uint32_t n_reqs = min(*n_reqs_p, kMaxSlots);
+    const uint32_t n_rays = *n_rays_p, gen_base = *gen_base_p;
+    for (uint32_t k = threadIdx.x; k < n_reqs; k += blockDim.x) sr[k] = reqs[k];
+    __syncthreads();
+    if (n_reqs == 0) return;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rays; r += gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = n_reqs - 1;  // last request with offset <= r
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (sr[mid].offset <= r) lo = mid; else hi = mid - 1;
+        }
+        const RaygenReq& q = sr[lo];
+        const uint32_t i = r - q.offset;
+        const uint32_t w = q.w, h = q.h;
+        if (i >= w * h) continue;  // not a ray of any request (host offsets are dense)
+        const uint32_t x = i % w, y = i / w;
+        float4 o, d;
+        camera_ray(q.cam, w, h, x, y, o, d);
+        const uint32_t e = (gen_base + r) & ring_mask;
+        rays[2 * (size_t)e] = o;
+        rays[2 * (size_t)e + 1] = d;
+        Payload p;
+        p.pixel = pack_pixel(i, 1u, q.slot);
+        p.r = p.g = p.b = 1.0f;
+        payload[e] = p;
+        reinterpret_cast<float4*>(q.image)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -235,6 +360,21 @@ cudaError_t launch_raygen(const CameraDev& cam, uint32_t w, uint32_t h, float4* 
 cudaError_t launch_shade(const ShadeArgs& a, uint32_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_shade<<<(n + kShadeBlock - 1) / kShadeBlock, kShadeBlock, 0, s>>>(a, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_raygen_batch(const RaygenReq* reqs, const uint32_t* n_reqs, uint32_t max_rays,
+                                const uint32_t* n_rays, const uint32_t* gen_base, uint32_t ring_mask, float4* rays,
+                                Payload* payload, cudaStream_t s) {
+    const uint32_t blocks = (uint32_t)min((max_rays + 255u) / 256u, (uint32_t)device_sm_count() * 8u);
+    k_raygen_batch<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(reqs, n_reqs, n_rays, gen_base, ring_mask, rays, payload);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shade_batch(const ShadeArgs& a, cudaStream_t s) {
+    k_shade_batch<<<device_sm_count() * 8, kShadeBlock, 0, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }

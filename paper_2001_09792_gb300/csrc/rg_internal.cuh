@@ -85,6 +85,35 @@ struct __align__(16) Payload {
     float r, g, b;
 };
 
+// Batched wavefront (serving): rays of several requests share the queues; the
+// payload's pixel word packs the request slot, the ray depth and the pixel.
+constexpr uint32_t kPixelBits = 23, kDepthBits = 4, kSlotBits = 5;
+constexpr uint32_t kMaxSlots = 1u << kSlotBits;
+constexpr uint32_t kMaxBatchDepth = (1u << kDepthBits) - 1;
+__host__ __device__ __forceinline__ uint32_t pack_pixel(uint32_t pixel, uint32_t depth, uint32_t slot) {
+    return pixel | (depth << kPixelBits) | (slot << (kPixelBits + kDepthBits));
+}
+__host__ __device__ __forceinline__ uint32_t px_of(uint32_t w) { return w & ((1u << kPixelBits) - 1u); }
+__host__ __device__ __forceinline__ uint32_t depth_of(uint32_t w) { return (w >> kPixelBits) & ((1u << kDepthBits) - 1u); }
+__host__ __device__ __forceinline__ uint32_t slot_of_px(uint32_t w) { return w >> (kPixelBits + kDepthBits); }
+
+// One request slot of the batched wavefront: its TLAS (a per-request copy
+// refit with the request's transforms), its scene's shading tables, and its
+// image.
+struct __align__(16) SlotDev {
+    const float4* tlas_nodes;
+    const InstDev* inst;
+    const rg_material* mats;
+    const rg_light* lights;
+    float* image;
+    uint32_t tlas_root;
+    uint32_t n_mats;
+    uint32_t n_lights;
+    uint32_t max_depth;
+    float bg[3];
+    float ambient;
+};
+
 // Internal closest-hit record of the renderer, 16 B: TLAS leaf of the
 // instance, BLAS leaf of the triangle, t.
 struct __align__(16) HitDev {
@@ -105,6 +134,9 @@ struct DevStatus {
 
 // Kernels launched by the library since process start (host counter).
 void count_launches(unsigned n);
+// While set (per host thread), count_launches ignores launches: they are
+// being captured into a CUDA graph, whose replays are counted instead.
+void set_capturing(bool on);
 unsigned long long launches_so_far();
 
 __device__ __forceinline__ void record_error(DevStatus* st, int code) {
@@ -158,7 +190,22 @@ cudaError_t launch_wide_refit(const float4* nodes2, const float* wbox, const uin
                               DevStatus* st, cudaStream_t s);
 
 // trace.cu
-enum TraceMode { kModeClosestAbi = 0, kModeAnyAbi = 1, kModeClosestRender = 2, kModeShadowRender = 3 };
+enum TraceMode {
+    kModeClosestAbi = 0,
+    kModeAnyAbi = 1,
+    kModeClosestRender = 2,
+    kModeShadowRender = 3,
+    kModeClosestBatch = 4,  // like kModeClosestRender, TLAS chosen per ray by the payload's slot
+    kModeShadowBatch = 5    // like kModeShadowRender, image chosen per ray by the payload's slot
+};
+// Launch shape of a traversal (picked by the autotuner): threads per block
+// (64, 128 or 256), resident blocks per SM (0: as many as fit), and rays a
+// warp takes per grab of the work counter (a multiple of 32).
+struct TraceShape {
+    int block = 128;
+    int blocks_per_sm = 0;
+    int grab = 32;
+};
 struct TraceArgs {
     const float4* rays;          // n x 2 float4 {o, tmin}, {d, tmax}
     uint32_t n;                  // ray count, or
@@ -176,8 +223,13 @@ struct TraceArgs {
     uint32_t iter_cap;           // bound on the loop steps of one ray (a valid traversal needs fewer)
     const float4* tlas_nodes8;   // compressed 8-wide TLAS (null: binary path)
     const InstDev* inst8;        // its instances, in wide-leaf order (BLAS pointers to wide BLAS)
+    const SlotDev* slots;        // batched modes: request slots
+    uint32_t grab;               // rays per warp grab (multiple of 32)
+    const uint32_t* ring_head;   // kModeClosestBatch: ray i is ring entry (*ring_head + i) & ring_mask
+    uint32_t ring_mask;
 };
-cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a, cudaStream_t s);
+cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a, cudaStream_t s,
+                         const TraceShape& shape = TraceShape());
 
 // render.cu
 struct CameraDev {
@@ -204,14 +256,56 @@ struct ShadeArgs {
     Payload* shadow_payload;
     uint32_t* shadow_count;
     DevStatus* st;
+    // batched wavefront only: ray i is ring entry (*ring_head + i) & ring_mask,
+    // spawned path rays go to ring entries from *next_base, and each ray adds
+    // (path rays spawned - 1) to the live count of its slot
+    const SlotDev* slots;
+    int* slot_live;
+    const uint32_t* ring_head;
+    const uint32_t* next_base;
+    uint32_t ring_mask;
 };
 cudaError_t launch_raygen(const CameraDev& cam, uint32_t w, uint32_t h, float4* rays, Payload* payload,
                           cudaStream_t s);
 cudaError_t launch_shade(const ShadeArgs& a, uint32_t n_max, cudaStream_t s);
+// Batched wavefront: primary rays of newly admitted requests, written to ring
+// entries (*gen_base + req[k].offset + pixel) & ring_mask for request k; each
+// pixel of the request's image is cleared on the way.
+struct RaygenReq {
+    CameraDev cam;
+    uint32_t w, h, slot, offset;
+    float* image;
+};
+cudaError_t launch_raygen_batch(const RaygenReq* reqs, const uint32_t* n_reqs, uint32_t max_rays,
+                                const uint32_t* n_rays, const uint32_t* gen_base, uint32_t ring_mask, float4* rays,
+                                Payload* payload, cudaStream_t s);
+// Shading of a mixed queue: count read on the device (*a.d_count), per-ray
+// slot, depth and pixel from the payload, per-slot tables from a.slots.
+cudaError_t launch_shade_batch(const ShadeArgs& a, cudaStream_t s);
 
 int device_sm_count();
 
 // Record `msg` as this thread's rg_last_error() and return `code`.
 rg_status report_error(rg_status code, const char* msg);
+
+// Read-only view of a built scene (api.cu), for the serving loop.
+struct SceneView {
+    int device;
+    const BlasDev* d_blas;
+    uint32_t n_blas;
+    const float4* tlas_nodes;   // binary TLAS (n_inst - 1 nodes)
+    const uint32_t* perm;       // TLAS leaf -> instance index
+    const uint32_t* parents;
+    const InstDev* inst;        // instances in TLAS leaf order
+    uint32_t n_inst, tlas_root;
+    const rg_material* mats;
+    uint32_t n_mats;
+    const rg_light* lights;
+    uint32_t n_lights;
+    float bg[3];
+    float ambient;
+    uint32_t iter_cap;
+};
+rg_status scene_view(rg_scene* s, SceneView* v);
 
 }  // namespace rg

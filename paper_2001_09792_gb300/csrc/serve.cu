@@ -1,0 +1,964 @@
+// Continuous-batching render server (include/rg.h, "continuous-batching
+// render server").  The per-ray work is the renderer's (Sec. 1 and 2.1 of
+// "Running on Raygun": closest hit, shadow rays, reflection and refraction to
+// a fixed depth); what this file adds is the batching around it:
+//
+//  * one ring of 2^k path rays (ray 32 B + payload 16 B) shared by every
+//    request in flight; the payload's pixel word carries the request slot and
+//    the ray depth, so one launch traces rays of many requests;
+//  * a step traces the m oldest rays of the ring (closest hit), shades them
+//    (shadow rays into a dense queue, reflected / refracted rays appended to
+//    the ring), traces the shadow rays, and advances the ring head;
+//  * per-slot live counts (path rays still in the ring) tell the host which
+//    requests finished;
+//  * per-request TLAS: on admission, a slot's private copy of the scene's TLAS
+//    is refit with the request's instance transforms;
+//  * the step's launches and copies are one CUDA graph; each slot's refit
+//    sequence per scene is another.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <string>
+#include <vector>
+
+#include "rg_internal.cuh"
+
+using namespace rg;
+
+namespace {
+
+// Ring positions are free-running 32-bit counters; entry = position & mask.
+// A step consumes m rays, the oldest (from head) or, when the ring is nearly
+// full, the newest (from the tail: the deepest rays, so the work proceeds
+// depth first and the live rays stay bounded); spawned rays are appended.
+struct RingState {
+    uint32_t head, tail;        // oldest live ray, one past the newest
+    uint32_t gen_base;          // where this step's primary rays start
+    uint32_t next_base;         // where this step's spawned rays start (the tail after ray generation)
+    uint32_t cons;              // first ray consumed by this step
+    uint32_t work_closest, next_count, shadow_count, work_shadow;
+    uint32_t pad[3];
+    int slot_live[kMaxSlots];   // path rays of each slot in the ring
+};
+
+// Host -> device once per step.
+struct __align__(16) StepHdr {
+    uint32_t n_reqs;            // requests admitted this step
+    uint32_t n_new_rays;        // their primary rays (sum of w h)
+    uint32_t m;                 // rays traced this step
+    uint32_t new_mask;          // slots (re)started this step
+    uint32_t newest_first;      // consume the m newest rays instead of the m oldest
+    uint32_t pad[3];
+    int live_init[kMaxSlots];
+    RaygenReq reqs[kMaxSlots];  // offsets ascending
+    SlotDev slots[kMaxSlots];
+};
+
+// Device -> host once per step.
+struct __align__(16) StepOut {
+    uint32_t head, tail, next_count, shadow_count;
+    int error, pad[3];
+    int slot_live[kMaxSlots];
+};
+
+constexpr unsigned kStepKernels = 7;   // begin, raygen, closest, shade, shadow, close gap, end
+constexpr unsigned kRefitKernels = 2;  // instance prep, TLAS leaf refit
+
+__global__ void k_step_begin(const StepHdr* __restrict__ hdr, RingState* __restrict__ rs) {
+    const uint32_t l = threadIdx.x;
+    if (l < kMaxSlots && ((hdr->new_mask >> l) & 1u)) rs->slot_live[l] = hdr->live_init[l];
+    if (l == 0) {
+        const uint32_t t = rs->tail;
+        const uint32_t T = t + hdr->n_new_rays;
+        rs->gen_base = t;
+        rs->tail = T;
+        rs->next_base = T;
+        rs->cons = hdr->newest_first ? T - hdr->m : rs->head;
+        rs->work_closest = 0;
+        rs->next_count = 0;
+        rs->shadow_count = 0;
+        rs->work_shadow = 0;
+    }
+}
+
+// Newest-first steps leave the consumed rays [T - m, T) as a gap below the
+// spawned ones [T, T + next): the last min(m, next) spawned rays move into it
+// (order in the ring does not matter; source and target do not overlap).
+__global__ void k_close_gap(const StepHdr* __restrict__ hdr, const RingState* __restrict__ rs, uint32_t mask,
+                            float4* __restrict__ rays, Payload* __restrict__ payload) {
+    if (!hdr->newest_first) return;
+    const uint32_t m = hdr->m, T = rs->next_base, next = rs->next_count;
+    const uint32_t k = min(m, next);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+        const uint32_t src = (T + next - k + i) & mask, dst = (T - m + i) & mask;
+        rays[2 * (size_t)dst] = rays[2 * (size_t)src];
+        rays[2 * (size_t)dst + 1] = rays[2 * (size_t)src + 1];
+        payload[dst] = payload[src];
+    }
+}
+
+__global__ void k_step_end(const StepHdr* __restrict__ hdr, RingState* __restrict__ rs, StepOut* __restrict__ out,
+                           const DevStatus* __restrict__ st) {
+    const uint32_t l = threadIdx.x;
+    if (l < kMaxSlots) out->slot_live[l] = rs->slot_live[l];
+    if (l == 0) {
+        if (hdr->newest_first) {
+            rs->tail = rs->next_base - hdr->m + rs->next_count;
+        } else {
+            rs->head += hdr->m;
+            rs->tail = rs->next_base + rs->next_count;
+        }
+        out->head = rs->head;
+        out->tail = rs->tail;
+        out->next_count = rs->next_count;
+        out->shadow_count = rs->shadow_count;
+        out->error = st->error;
+    }
+}
+
+rg_status sfail(rg_status code, const std::string& msg) { return report_error(code, msg.c_str()); }
+
+rg_status scuda(cudaError_t e, const char* what) {
+    cudaGetLastError();
+    return sfail(e == cudaErrorMemoryAllocation ? RG_ERR_OOM : RG_ERR_CUDA,
+                 std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SV_CK(call)                                      \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return scuda(e_, #call);  \
+    } while (0)
+
+template <class T>
+rg_status salloc(T** p, size_t n, const char* what) {
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), (n ? n : 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return scuda(e, what);
+    }
+    return RG_OK;
+}
+
+struct SceneEntry {
+    rg_scene* scene;
+    SceneView v;
+    std::vector<rg_instance> base;  // build order
+};
+
+struct SlotBufs {
+    float4* tlas_nodes = nullptr;
+    InstDev* inst = nullptr;
+    InstDev* inst_tmp = nullptr;
+    float* wbox = nullptr;
+    uint32_t* flags = nullptr;
+    rg_instance* d_inst = nullptr;
+    rg_instance* h_inst = nullptr;            // pinned staging
+    std::vector<cudaGraphExec_t> refit_exec;  // per scene
+};
+
+struct Pending {
+    uint64_t id;
+    rg_request r;
+    std::vector<float> transforms;  // empty: the scene's own
+};
+
+struct Active {
+    bool on = false;
+    uint64_t id = 0, tag = 0;
+    uint32_t scene = 0, admitted_step = 0;
+};
+
+const char* device_error_text(int err) {
+    return err == RG_ERR_STACK      ? "traversal stack overflow"
+           : err == RG_ERR_TIMEOUT  ? "device loop iteration cap reached"
+           : err == RG_ERR_SINGULAR ? "singular instance transform"
+           : err == RG_ERR_INVALID_ARG ? "invalid instance BLAS id or material index"
+                                       : "device error";
+}
+
+}  // namespace
+
+struct rg_server {
+    int device = 0;
+    uint32_t ring_cap = 0, ring_mask = 0, batch = 0, max_lights = 0, flags = 0;
+    size_t shadow_cap = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done_ev = nullptr, t0 = nullptr, t1 = nullptr;
+    DevStatus* st = nullptr;
+    float4* ring_rays = nullptr;
+    Payload* ring_pay = nullptr;
+    HitDev* hits = nullptr;
+    float4* s_rays = nullptr;
+    Payload* s_pay = nullptr;
+    RingState* d_rs = nullptr;
+    StepHdr* d_hdr = nullptr;
+    StepOut* d_out = nullptr;
+    uint32_t* d_tune_count = nullptr;
+    StepHdr* h_hdr = nullptr;
+    StepOut* h_out = nullptr;
+    std::vector<SceneEntry> scenes;
+    uint32_t max_inst = 0, iter_cap = 64;
+    SlotBufs slots[kMaxSlots];
+    Active active[kMaxSlots];
+    std::deque<Pending> pending;
+    std::deque<rg_completion> done;
+    uint64_t next_id = 1;
+    uint32_t ring_rays_now = 0;  // tail - head after the last step
+    TraceShape shape[2];
+    cudaGraphExec_t step_exec = nullptr;
+    rg_server_stats stats{};
+};
+
+namespace {
+
+rg_status set_dev(rg_server* s) {
+    SV_CK(cudaSetDevice(s->device));
+    return RG_OK;
+}
+
+void free_slot_bufs(SlotBufs& b) {
+    cudaFree(b.tlas_nodes);
+    cudaFree(b.inst);
+    cudaFree(b.inst_tmp);
+    cudaFree(b.wbox);
+    cudaFree(b.flags);
+    cudaFree(b.d_inst);
+    if (b.h_inst) cudaFreeHost(b.h_inst);
+    for (cudaGraphExec_t g : b.refit_exec)
+        if (g) cudaGraphExecDestroy(g);
+    b = SlotBufs();
+}
+
+void drop_step_graph(rg_server* s) {
+    if (s->step_exec) cudaGraphExecDestroy(s->step_exec);
+    s->step_exec = nullptr;
+}
+
+rg_status alloc_slot_bufs(SlotBufs& b, uint32_t n, size_t n_scenes) {
+    rg_status r;
+    const size_t n_int = n > 1 ? n - 1 : 1;
+    if ((r = salloc(&b.tlas_nodes, n_int * 4, "slot TLAS nodes"))) return r;
+    if ((r = salloc(&b.inst, n, "slot instances"))) return r;
+    if ((r = salloc(&b.inst_tmp, n, "slot instance staging"))) return r;
+    if ((r = salloc(&b.wbox, (size_t)n * 6, "slot instance boxes"))) return r;
+    if ((r = salloc(&b.flags, n_int, "slot refit flags"))) return r;
+    if ((r = salloc(&b.d_inst, n, "slot instance records"))) return r;
+    SV_CK(cudaMallocHost(reinterpret_cast<void**>(&b.h_inst), (size_t)n * sizeof(rg_instance)));
+    b.refit_exec.assign(n_scenes, nullptr);
+    return RG_OK;
+}
+
+// The refit of slot k's TLAS copy for a request of scene e (transforms already
+// in the slot's pinned staging).
+rg_status enqueue_refit(rg_server* s, uint32_t k, uint32_t e) {
+    const SceneView& v = s->scenes[e].v;
+    SlotBufs& b = s->slots[k];
+    const uint32_t n = v.n_inst;
+    SV_CK(cudaMemcpyAsync(b.d_inst, b.h_inst, (size_t)n * sizeof(rg_instance), cudaMemcpyHostToDevice, s->stream));
+    SV_CK(launch_instance_prep(b.d_inst, n, v.d_blas, v.n_blas, b.inst_tmp, b.wbox, nullptr, false, s->st, s->stream));
+    if (n > 1) {
+        SV_CK(cudaMemcpyAsync(b.tlas_nodes, v.tlas_nodes, (size_t)(n - 1) * 64, cudaMemcpyDeviceToDevice, s->stream));
+        SV_CK(cudaMemsetAsync(b.flags, 0, (size_t)(n - 1) * 4, s->stream));
+    }
+    SV_CK(launch_tlas_leaves_refit(b.inst_tmp, b.wbox, v.perm, n, v.parents, b.tlas_nodes, b.flags, b.inst, s->st,
+                                   s->stream));
+    return RG_OK;
+}
+
+TraceArgs closest_args(rg_server* s, const uint32_t* d_count) {
+    TraceArgs a{};
+    a.rays = s->ring_rays;
+    a.d_count = d_count;
+    a.payload = s->ring_pay;
+    a.hits_render = s->hits;
+    a.work_counter = &s->d_rs->work_closest;
+    a.st = s->st;
+    a.iter_cap = s->iter_cap;
+    a.slots = s->d_hdr->slots;
+    a.ring_head = &s->d_rs->cons;
+    a.ring_mask = s->ring_mask;
+    return a;
+}
+
+TraceArgs shadow_args(rg_server* s) {
+    TraceArgs b{};
+    b.rays = s->s_rays;
+    b.d_count = &s->d_rs->shadow_count;
+    b.payload = s->s_pay;
+    b.work_counter = &s->d_rs->work_shadow;
+    b.st = s->st;
+    b.iter_cap = s->iter_cap;
+    b.slots = s->d_hdr->slots;
+    return b;
+}
+
+ShadeArgs shade_args(rg_server* s, const uint32_t* d_count) {
+    ShadeArgs a{};
+    a.rays = s->ring_rays;
+    a.payload = s->ring_pay;
+    a.hits = s->hits;
+    a.d_count = d_count;
+    a.next_rays = s->ring_rays;
+    a.next_payload = s->ring_pay;
+    a.next_count = &s->d_rs->next_count;
+    a.shadow_rays = s->s_rays;
+    a.shadow_payload = s->s_pay;
+    a.shadow_count = &s->d_rs->shadow_count;
+    a.st = s->st;
+    a.slots = s->d_hdr->slots;
+    a.slot_live = s->d_rs->slot_live;
+    a.ring_head = &s->d_rs->cons;
+    a.next_base = &s->d_rs->next_base;
+    a.ring_mask = s->ring_mask;
+    return a;
+}
+
+// Everything one step puts on the stream, graph-capturable (all counts are
+// read on the device).
+rg_status enqueue_step(rg_server* s) {
+    SV_CK(cudaMemcpyAsync(s->d_hdr, s->h_hdr, sizeof(StepHdr), cudaMemcpyHostToDevice, s->stream));
+    k_step_begin<<<1, 32, 0, s->stream>>>(s->d_hdr, s->d_rs);
+    count_launches(1);
+    SV_CK(cudaGetLastError());
+    SV_CK(launch_raygen_batch(s->d_hdr->reqs, &s->d_hdr->n_reqs, s->ring_cap / 2, &s->d_hdr->n_new_rays,
+                              &s->d_rs->gen_base, s->ring_mask, s->ring_rays, s->ring_pay, s->stream));
+    SV_CK(launch_trace(kModeClosestBatch, false, false, closest_args(s, &s->d_hdr->m), s->stream, s->shape[0]));
+    SV_CK(launch_shade_batch(shade_args(s, &s->d_hdr->m), s->stream));
+    SV_CK(launch_trace(kModeShadowBatch, false, false, shadow_args(s), s->stream, s->shape[1]));
+    k_close_gap<<<device_sm_count() * 4, 256, 0, s->stream>>>(s->d_hdr, s->d_rs, s->ring_mask, s->ring_rays,
+                                                              s->ring_pay);
+    count_launches(1);
+    SV_CK(cudaGetLastError());
+    k_step_end<<<1, 32, 0, s->stream>>>(s->d_hdr, s->d_rs, s->d_out, s->st);
+    count_launches(1);
+    SV_CK(cudaGetLastError());
+    SV_CK(cudaMemcpyAsync(s->h_out, s->d_out, sizeof(StepOut), cudaMemcpyDeviceToHost, s->stream));
+    return RG_OK;
+}
+
+// Captures `body` on the server's stream into an executable graph.
+template <class F>
+rg_status capture(rg_server* s, F body, cudaGraphExec_t* out) {
+    *out = nullptr;
+    SV_CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeRelaxed));
+    set_capturing(true);
+    rg_status r = body();
+    set_capturing(false);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+    if (r != RG_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+    }
+    if (e != cudaSuccess) return scuda(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        *out = nullptr;
+        return scuda(e, "cudaGraphInstantiate");
+    }
+    s->stats.graph_captures++;
+    return RG_OK;
+}
+
+rg_status run_step_work(rg_server* s) {
+    if (s->flags & RG_SERVER_NO_GRAPH) {
+        const unsigned long long before = launches_so_far();
+        rg_status r = enqueue_step(s);
+        s->stats.kernel_launches += launches_so_far() - before;
+        return r;
+    }
+    rg_status r;
+    if (!s->step_exec && (r = capture(s, [&] { return enqueue_step(s); }, &s->step_exec))) return r;
+    SV_CK(cudaGraphLaunch(s->step_exec, s->stream));
+    count_launches(kStepKernels);
+    s->stats.kernel_launches += kStepKernels;
+    s->stats.graph_launches++;
+    return RG_OK;
+}
+
+rg_status run_refit(rg_server* s, uint32_t k, uint32_t e) {
+    if (s->flags & RG_SERVER_NO_GRAPH) {
+        const unsigned long long before = launches_so_far();
+        rg_status r = enqueue_refit(s, k, e);
+        s->stats.kernel_launches += launches_so_far() - before;
+        return r;
+    }
+    rg_status r;
+    cudaGraphExec_t& g = s->slots[k].refit_exec[e];
+    if (!g && (r = capture(s, [&] { return enqueue_refit(s, k, e); }, &g))) return r;
+    SV_CK(cudaGraphLaunch(g, s->stream));
+    count_launches(kRefitKernels);
+    s->stats.kernel_launches += kRefitKernels;
+    s->stats.graph_launches++;
+    return RG_OK;
+}
+
+rg_status check_server(rg_server* s) {
+    if (!s) return sfail(RG_ERR_INVALID_ARG, "null server");
+    return RG_OK;
+}
+
+rg_status check_request(rg_server* s, const rg_request* q) {
+    if (!q) return sfail(RG_ERR_INVALID_ARG, "null request");
+    if (q->scene >= s->scenes.size()) return sfail(RG_ERR_INVALID_ARG, "unknown scene id");
+    const uint64_t px = (uint64_t)q->width * q->height;
+    if (q->width == 0 || q->height == 0 || px > RG_SERVER_MAX_PIXELS)
+        return sfail(RG_ERR_INVALID_ARG, "request size out of range");
+    if (px > s->ring_cap / 2) return sfail(RG_ERR_INVALID_ARG, "request larger than half the ray ring");
+    if (q->max_depth < 1 || q->max_depth > RG_SERVER_MAX_DEPTH)
+        return sfail(RG_ERR_INVALID_ARG, "max_depth out of range");
+    if (!q->d_rgba) return sfail(RG_ERR_INVALID_ARG, "null image");
+    if (reinterpret_cast<uintptr_t>(q->d_rgba) % 16) return sfail(RG_ERR_INVALID_ARG, "image not 16-byte aligned");
+    return RG_OK;
+}
+
+// Admission: in arrival order, while a slot is free and the ring keeps half
+// its capacity for spawned rays.  Returns the primary rays admitted.
+rg_status admit(rg_server* s, uint32_t* n_new) {
+    StepHdr& H = *s->h_hdr;
+    H.n_reqs = 0;
+    H.new_mask = 0;
+    uint32_t rays = 0;
+    while (!s->pending.empty()) {
+        Pending& p = s->pending.front();
+        const uint32_t px = p.r.width * p.r.height;
+        if ((uint64_t)s->ring_rays_now + rays + px > s->ring_cap / 2) break;
+        uint32_t k = 0;
+        while (k < kMaxSlots && s->active[k].on) ++k;
+        if (k == kMaxSlots) break;
+        const SceneEntry& E = s->scenes[p.r.scene];
+        const uint32_t n = E.v.n_inst;
+        rg_instance* hi = s->slots[k].h_inst;
+        std::memcpy(hi, E.base.data(), (size_t)n * sizeof(rg_instance));
+        if (!p.transforms.empty())
+            for (uint32_t i = 0; i < n; ++i) std::memcpy(hi[i].m, &p.transforms[12 * (size_t)i], 48);
+        rg_status r;
+        if ((r = run_refit(s, k, p.r.scene))) return r;
+        RaygenReq& q = H.reqs[H.n_reqs++];
+        std::memcpy(&q.cam, &p.r.camera, sizeof(CameraDev));
+        q.w = p.r.width;
+        q.h = p.r.height;
+        q.slot = k;
+        q.offset = rays;
+        q.image = p.r.d_rgba;
+        SlotDev& D = H.slots[k];
+        D.tlas_nodes = s->slots[k].tlas_nodes;
+        D.inst = s->slots[k].inst;
+        D.tlas_root = E.v.tlas_root;
+        D.mats = E.v.mats;
+        D.n_mats = E.v.n_mats;
+        D.lights = E.v.lights;
+        D.n_lights = E.v.n_lights;
+        D.image = p.r.d_rgba;
+        D.max_depth = p.r.max_depth;
+        for (int c = 0; c < 3; ++c) D.bg[c] = E.v.bg[c];
+        D.ambient = E.v.ambient;
+        H.live_init[k] = (int)px;
+        H.new_mask |= 1u << k;
+        Active& A = s->active[k];
+        A.on = true;
+        A.id = p.id;
+        A.tag = p.r.tag;
+        A.scene = p.r.scene;
+        A.admitted_step = (uint32_t)(s->stats.steps + 1);
+        rays += px;
+        s->stats.admitted++;
+        s->pending.pop_front();
+    }
+    H.n_new_rays = rays;
+    *n_new = rays;
+    return RG_OK;
+}
+
+// Rays one step traces with `avail` rays in the ring, and from which end.
+// Oldest first while the free ring F takes the worst case (two spawned rays
+// per traced ray) of at least a quarter of a full batch; else newest first
+// with m <= F / (2 (RG_SERVER_MAX_DEPTH + 1)): a newest-first descent grows
+// the ring by at most m per step until its rays reach their depth limit, so
+// it always finds room.  0: no room at all (F < 2 (RG_SERVER_MAX_DEPTH + 1)).
+uint32_t step_batch(const rg_server* s, uint32_t avail, bool* newest_first) {
+    uint64_t want = std::min<uint64_t>(avail, s->batch);
+    if (s->max_lights) want = std::min<uint64_t>(want, s->shadow_cap / s->max_lights);
+    const uint64_t F = s->ring_cap - (uint64_t)avail;
+    const uint64_t m_old = std::min<uint64_t>(want, F / 2);
+    *newest_first = false;
+    if (4 * m_old >= want) return (uint32_t)m_old;
+    *newest_first = true;
+    return (uint32_t)std::min<uint64_t>(want, F / (2 * (RG_SERVER_MAX_DEPTH + 1)));
+}
+
+rg_status finish_step(rg_server* s, uint32_t* n_completed) {
+    SV_CK(cudaEventRecord(s->done_ev, s->stream));
+    SV_CK(cudaEventSynchronize(s->done_ev));
+    const StepOut& O = *s->h_out;
+    s->stats.steps++;
+    s->stats.closest_rays += s->h_hdr->m;
+    s->stats.shadow_rays += O.shadow_count;
+    s->ring_rays_now = O.tail - O.head;
+    s->stats.ring_peak = std::max(s->stats.ring_peak, s->ring_rays_now);
+    int64_t live_sum = 0;
+    uint32_t completed = 0;
+    for (uint32_t k = 0; k < kMaxSlots; ++k) {
+        if (!s->active[k].on) {
+            if (O.slot_live[k] != 0) return sfail(RG_ERR_CUDA, "render server: rays of a free slot in the ring");
+            continue;
+        }
+        if (O.slot_live[k] < 0) return sfail(RG_ERR_CUDA, "render server: negative live ray count");
+        live_sum += O.slot_live[k];
+        if (O.slot_live[k] == 0) {
+            rg_completion c;
+            c.id = s->active[k].id;
+            c.tag = s->active[k].tag;
+            c.admitted_step = s->active[k].admitted_step;
+            c.completed_step = (uint32_t)s->stats.steps;
+            s->done.push_back(c);
+            s->active[k] = Active();
+            s->stats.completed++;
+            ++completed;
+        }
+    }
+    if (n_completed) *n_completed = completed;
+    if (O.error) {
+        // the step completed (a ray that failed counts as a miss); report it
+        SV_CK(cudaMemset(&s->st->error, 0, sizeof(int)));
+        return sfail(O.error, std::string("render server step: ") + device_error_text(O.error));
+    }
+    if (live_sum != (int64_t)s->ring_rays_now) return sfail(RG_ERR_CUDA, "render server: ring count mismatch");
+    return RG_OK;
+}
+
+uint32_t n_active(const rg_server* s) {
+    uint32_t c = 0;
+    for (const Active& a : s->active) c += a.on ? 1u : 0u;
+    return c;
+}
+
+// ---- autotuner cache: a JSON array, one object per line ---------------------
+std::string device_key(int dev, int* sms) {
+    cudaDeviceProp p{};
+    cudaGetDeviceProperties(&p, dev);
+    *sms = p.multiProcessorCount;
+    return std::string(p.name);
+}
+
+bool read_num(const std::string& line, const std::string& key, long* v) {
+    size_t p = line.find("\"" + key + "\"");
+    if (p == std::string::npos) return false;
+    p = line.find(':', p);
+    if (p == std::string::npos) return false;
+    *v = std::strtol(line.c_str() + p + 1, nullptr, 10);
+    return true;
+}
+
+bool parse_shape(const std::string& obj, TraceShape* sh) {
+    long b, bps, g;
+    if (!read_num(obj, "block", &b) || !read_num(obj, "blocks_per_sm", &bps) || !read_num(obj, "grab", &g)) return false;
+    if ((b != 64 && b != 128 && b != 256) || bps < 0 || bps > 64 || g < 32 || g > 1024 || g % 32) return false;
+    sh->block = (int)b;
+    sh->blocks_per_sm = (int)bps;
+    sh->grab = (int)g;
+    return true;
+}
+
+std::vector<std::string> read_lines(const char* path) {
+    std::vector<std::string> out;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return out;
+    char buf[4096];
+    std::string cur;
+    while (std::fgets(buf, sizeof buf, f)) {
+        cur += buf;
+        if (!cur.empty() && cur.back() == '\n') {
+            out.push_back(cur);
+            cur.clear();
+        }
+    }
+    if (!cur.empty()) out.push_back(cur);
+    std::fclose(f);
+    return out;
+}
+
+bool cache_lookup(const char* path, const std::string& dev, int sms, TraceShape sh[2]) {
+    for (const std::string& line : read_lines(path)) {
+        if (line.find("\"device\": \"" + dev + "\"") == std::string::npos) continue;
+        long n;
+        if (!read_num(line, "sms", &n) || n != sms) continue;
+        const size_t c = line.find("\"closest\""), d = line.find("\"shadow\"");
+        if (c == std::string::npos || d == std::string::npos || d < c) continue;
+        TraceShape a, b;
+        if (parse_shape(line.substr(c, d - c), &a) && parse_shape(line.substr(d), &b)) {
+            sh[0] = a;
+            sh[1] = b;
+            return true;
+        }
+    }
+    return false;
+}
+
+std::string shape_json(const TraceShape& t, float ms) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "{\"block\": %d, \"blocks_per_sm\": %d, \"grab\": %d, \"ms\": %.4f}", t.block,
+                  t.blocks_per_sm, t.grab, ms);
+    return buf;
+}
+
+rg_status cache_store(const char* path, const std::string& dev, int sms, const TraceShape sh[2], const float ms[2]) {
+    std::vector<std::string> keep;
+    for (const std::string& line : read_lines(path)) {
+        if (line.find("\"device\"") == std::string::npos) continue;
+        long n = -1;
+        read_num(line, "sms", &n);
+        if (line.find("\"device\": \"" + dev + "\"") != std::string::npos && n == sms) continue;
+        std::string l = line;
+        while (!l.empty() && (l.back() == '\n' || l.back() == ',' || l.back() == ' ' || l.back() == ']')) l.pop_back();
+        if (!l.empty() && l.front() == '[') l.erase(0, 1);
+        keep.push_back(l);
+    }
+    char head[256];
+    std::snprintf(head, sizeof head, "{\"device\": \"%s\", \"sms\": %d, ", dev.c_str(), sms);
+    keep.push_back(std::string(head) + "\"closest\": " + shape_json(sh[0], ms[0]) + ", \"shadow\": " +
+                   shape_json(sh[1], ms[1]) + "}");
+    FILE* f = std::fopen(path, "w");
+    if (!f) return sfail(RG_ERR_INVALID_ARG, std::string("cannot write ") + path);
+    std::fputs("[\n", f);
+    for (size_t i = 0; i < keep.size(); ++i) std::fprintf(f, "%s%s\n", keep[i].c_str(), i + 1 < keep.size() ? "," : "");
+    std::fputs("]\n", f);
+    std::fclose(f);
+    return RG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rg_status rg_server_create(rg_server** out, const rg_server_desc* desc) {
+    if (!out) return sfail(RG_ERR_INVALID_ARG, "null output");
+    *out = nullptr;
+    rg_server_desc d{};
+    if (desc) d = *desc;
+    const uint32_t lg = d.ring_log2 ? d.ring_log2 : 25u;
+    if (lg < 16 || lg > 30) return sfail(RG_ERR_INVALID_ARG, "ring_log2 must be in 16..30");
+    rg_server* s = new rg_server();
+    s->ring_cap = 1u << lg;
+    s->ring_mask = s->ring_cap - 1;
+    s->batch = d.batch_rays ? d.batch_rays : (1u << 23);
+    s->batch = std::min(s->batch, s->ring_cap / 2);
+    s->max_lights = d.max_lights ? d.max_lights : 4u;
+    if (s->max_lights > 64) {
+        delete s;
+        return sfail(RG_ERR_INVALID_ARG, "max_lights above 64");
+    }
+    s->shadow_cap = (size_t)s->batch * s->max_lights;
+    s->flags = d.flags;
+    rg_status r = RG_OK;
+    auto bail = [&](rg_status code) {
+        rg_server_destroy(s);
+        return code;
+    };
+    if (cudaGetDevice(&s->device) != cudaSuccess) return bail(scuda(cudaGetLastError(), "cudaGetDevice"));
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(sfail(RG_ERR_CUDA, "cudaStreamCreate failed"));
+    if (cudaEventCreateWithFlags(&s->done_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&s->t0) != cudaSuccess || cudaEventCreate(&s->t1) != cudaSuccess)
+        return bail(sfail(RG_ERR_CUDA, "cudaEventCreate failed"));
+    if ((r = salloc(&s->st, 1, "server status"))) return bail(r);
+    if ((r = salloc(&s->ring_rays, 2 * (size_t)s->ring_cap, "ray ring"))) return bail(r);
+    if ((r = salloc(&s->ring_pay, (size_t)s->ring_cap, "payload ring"))) return bail(r);
+    if ((r = salloc(&s->hits, (size_t)s->batch, "hit queue"))) return bail(r);
+    if ((r = salloc(&s->s_rays, 2 * s->shadow_cap, "shadow queue"))) return bail(r);
+    if ((r = salloc(&s->s_pay, s->shadow_cap, "shadow payload"))) return bail(r);
+    if ((r = salloc(&s->d_rs, 1, "ring state"))) return bail(r);
+    if ((r = salloc(&s->d_hdr, 1, "step header"))) return bail(r);
+    if ((r = salloc(&s->d_out, 1, "step result"))) return bail(r);
+    if ((r = salloc(&s->d_tune_count, 1, "tuning count"))) return bail(r);
+    if (cudaMallocHost(reinterpret_cast<void**>(&s->h_hdr), sizeof(StepHdr)) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&s->h_out), sizeof(StepOut)) != cudaSuccess)
+        return bail(sfail(RG_ERR_OOM, "pinned host buffers"));
+    std::memset(s->h_hdr, 0, sizeof(StepHdr));
+    std::memset(s->h_out, 0, sizeof(StepOut));
+    if (cudaMemset(s->st, 0, sizeof(DevStatus)) != cudaSuccess || cudaMemset(s->d_rs, 0, sizeof(RingState)) != cudaSuccess ||
+        cudaMemset(s->d_hdr, 0, sizeof(StepHdr)) != cudaSuccess)
+        return bail(scuda(cudaGetLastError(), "cudaMemset"));
+    *out = s;
+    return RG_OK;
+}
+
+rg_status rg_server_destroy(rg_server* s) {
+    if (!s) return RG_OK;
+    cudaSetDevice(s->device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    drop_step_graph(s);
+    for (SlotBufs& b : s->slots) free_slot_bufs(b);
+    cudaFree(s->st);
+    cudaFree(s->ring_rays);
+    cudaFree(s->ring_pay);
+    cudaFree(s->hits);
+    cudaFree(s->s_rays);
+    cudaFree(s->s_pay);
+    cudaFree(s->d_rs);
+    cudaFree(s->d_hdr);
+    cudaFree(s->d_out);
+    cudaFree(s->d_tune_count);
+    if (s->h_hdr) cudaFreeHost(s->h_hdr);
+    if (s->h_out) cudaFreeHost(s->h_out);
+    if (s->done_ev) cudaEventDestroy(s->done_ev);
+    if (s->t0) cudaEventDestroy(s->t0);
+    if (s->t1) cudaEventDestroy(s->t1);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+    return RG_OK;
+}
+
+rg_status rg_server_add_scene(rg_server* s, rg_scene* scene, uint32_t* scene_id) {
+    rg_status r;
+    if ((r = check_server(s))) return r;
+    if (!scene || !scene_id) return sfail(RG_ERR_INVALID_ARG, "null scene or id");
+    if (!s->pending.empty() || n_active(s)) return sfail(RG_ERR_INVALID_ARG, "add scenes while the server is idle");
+    SceneEntry E;
+    E.scene = scene;
+    if ((r = scene_view(scene, &E.v))) return r;
+    if (E.v.device != s->device) return sfail(RG_ERR_INVALID_ARG, "scene on another device");
+    if (E.v.n_lights > s->max_lights) return sfail(RG_ERR_INVALID_ARG, "scene has more lights than max_lights");
+    if ((r = set_dev(s))) return r;
+    // the scene's own instance records, back in build order
+    const uint32_t n = E.v.n_inst;
+    SV_CK(cudaDeviceSynchronize());  // the scene may have been built on any stream
+    std::vector<InstDev> leaf(n);
+    SV_CK(cudaMemcpy(leaf.data(), E.v.inst, (size_t)n * sizeof(InstDev), cudaMemcpyDeviceToHost));
+    E.base.assign(n, rg_instance{});
+    std::vector<char> seen(n, 0);
+    for (const InstDev& D : leaf) {
+        if (D.id >= n || seen[D.id]) return sfail(RG_ERR_INVALID_ARG, "scene TLAS is inconsistent");
+        seen[D.id] = 1;
+        rg_instance& I = E.base[D.id];
+        for (int row = 0; row < 3; ++row) {
+            I.m[row][0] = D.m[row].x;
+            I.m[row][1] = D.m[row].y;
+            I.m[row][2] = D.m[row].z;
+            I.m[row][3] = D.m[row].w;
+        }
+        I.blas_id = D.blas;
+        I.material_id = D.material;
+        I.mask = 0xFFu;
+    }
+    // slot buffers sized for the largest scene; every refit graph is per scene
+    const size_t n_scenes = s->scenes.size() + 1;
+    if (n > s->max_inst) {
+        for (SlotBufs& b : s->slots) free_slot_bufs(b);
+        for (SlotBufs& b : s->slots)
+            if ((r = alloc_slot_bufs(b, n, n_scenes))) return r;
+        s->max_inst = n;
+        drop_step_graph(s);
+    } else {
+        for (SlotBufs& b : s->slots) b.refit_exec.resize(n_scenes, nullptr);
+    }
+    s->iter_cap = std::max(s->iter_cap, E.v.iter_cap);
+    drop_step_graph(s);
+    s->scenes.push_back(std::move(E));
+    *scene_id = (uint32_t)(s->scenes.size() - 1);
+    return RG_OK;
+}
+
+rg_status rg_server_submit(rg_server* s, const rg_request* q, uint64_t* id) {
+    rg_status r;
+    if ((r = check_server(s))) return r;
+    if ((r = check_request(s, q))) return r;
+    Pending p;
+    p.id = s->next_id++;
+    p.r = *q;
+    if (q->h_transforms) {
+        const size_t n = 12 * (size_t)s->scenes[q->scene].v.n_inst;
+        p.transforms.assign(q->h_transforms, q->h_transforms + n);
+    }
+    p.r.h_transforms = nullptr;
+    s->pending.push_back(std::move(p));
+    s->stats.submitted++;
+    if (id) *id = s->pending.back().id;
+    return RG_OK;
+}
+
+rg_status rg_server_step(rg_server* s, uint32_t* n_completed) {
+    rg_status r;
+    if (n_completed) *n_completed = 0;
+    if ((r = check_server(s))) return r;
+    if ((r = set_dev(s))) return r;
+    uint32_t n_new = 0;
+    if ((r = admit(s, &n_new))) return r;
+    const uint32_t avail = s->ring_rays_now + n_new;
+    if (avail == 0) return RG_OK;
+    bool newest = false;
+    const uint32_t m = step_batch(s, avail, &newest);
+    if (m == 0) return sfail(RG_ERR_OOM, "ray ring full: no room for the rays a step spawns");
+    s->h_hdr->m = m;
+    s->h_hdr->newest_first = newest ? 1u : 0u;
+    if (newest) s->stats.newest_first_steps++;
+    if ((r = run_step_work(s))) return r;
+    return finish_step(s, n_completed);
+}
+
+rg_status rg_server_drain(rg_server* s) {
+    rg_status r;
+    if ((r = check_server(s))) return r;
+    while (!s->pending.empty() || n_active(s)) {
+        const uint64_t before = s->stats.steps;
+        if ((r = rg_server_step(s, nullptr))) return r;
+        if (s->stats.steps == before) return sfail(RG_ERR_INVALID_ARG, "render server cannot make progress");
+    }
+    return RG_OK;
+}
+
+rg_status rg_server_poll(rg_server* s, rg_completion* out, uint32_t max, uint32_t* n) {
+    rg_status r;
+    if ((r = check_server(s))) return r;
+    if (!n || (max && !out)) return sfail(RG_ERR_INVALID_ARG, "null output");
+    uint32_t k = 0;
+    while (k < max && !s->done.empty()) {
+        out[k++] = s->done.front();
+        s->done.pop_front();
+    }
+    *n = k;
+    return RG_OK;
+}
+
+rg_status rg_server_get_stats(rg_server* s, rg_server_stats* out) {
+    rg_status r;
+    if ((r = check_server(s))) return r;
+    if (!out) return sfail(RG_ERR_INVALID_ARG, "null output");
+    *out = s->stats;
+    out->pending = (uint32_t)s->pending.size();
+    out->active = n_active(s);
+    out->ring_rays = s->ring_rays_now;
+    return RG_OK;
+}
+
+rg_status rg_server_set_shape(rg_server* s, uint32_t which, const rg_trace_shape* sh) {
+    rg_status r;
+    if ((r = check_server(s))) return r;
+    if (which > 1 || !sh) return sfail(RG_ERR_INVALID_ARG, "bad shape selector");
+    if ((sh->block != 64 && sh->block != 128 && sh->block != 256) || sh->blocks_per_sm > 64 || sh->grab < 32 ||
+        sh->grab > 1024 || sh->grab % 32)
+        return sfail(RG_ERR_INVALID_ARG, "bad launch shape");
+    s->shape[which].block = (int)sh->block;
+    s->shape[which].blocks_per_sm = (int)sh->blocks_per_sm;
+    s->shape[which].grab = (int)sh->grab;
+    drop_step_graph(s);
+    return RG_OK;
+}
+
+rg_status rg_server_get_shape(rg_server* s, uint32_t which, rg_trace_shape* out) {
+    rg_status r;
+    if ((r = check_server(s))) return r;
+    if (which > 1 || !out) return sfail(RG_ERR_INVALID_ARG, "bad shape selector");
+    out->block = (uint32_t)s->shape[which].block;
+    out->blocks_per_sm = (uint32_t)s->shape[which].blocks_per_sm;
+    out->grab = (uint32_t)s->shape[which].grab;
+    out->ms = -1.0f;
+    return RG_OK;
+}
+
+rg_status rg_server_autotune(rg_server* s, const rg_request* sample, const char* cache_path, uint32_t flags,
+                             rg_trace_shape out[2]) {
+    rg_status r;
+    if ((r = check_server(s))) return r;
+    if ((r = check_request(s, sample))) return r;
+    if (!s->pending.empty() || n_active(s)) return sfail(RG_ERR_INVALID_ARG, "autotune needs an idle server");
+    if ((r = set_dev(s))) return r;
+    int sms = 0;
+    const std::string dev = device_key(s->device, &sms);
+    TraceShape best[2] = {s->shape[0], s->shape[1]};
+    float best_ms[2] = {-1.0f, -1.0f};
+    const bool cached = cache_path && !(flags & RG_TUNE_FORCE) && cache_lookup(cache_path, dev, sms, best);
+    if (!cached) {
+        // the sample's primary rays into the ring (a step that traces nothing)
+        const uint32_t px = sample->width * sample->height;
+        bool newest = false;
+        const uint32_t m = std::min(px, step_batch(s, px, &newest));
+        if ((r = rg_server_submit(s, sample, nullptr))) return r;
+        uint32_t n_new = 0;
+        if ((r = admit(s, &n_new))) return r;
+        s->h_hdr->m = 0;
+        s->h_hdr->newest_first = 0;
+        const uint32_t saved_flags = s->flags;
+        s->flags |= RG_SERVER_NO_GRAPH;
+        r = enqueue_step(s);
+        s->flags = saved_flags;
+        if (r) return r;
+        SV_CK(cudaMemcpyAsync(s->d_tune_count, &m, 4, cudaMemcpyHostToDevice, s->stream));
+        SV_CK(cudaStreamSynchronize(s->stream));
+        const int blocks[3] = {64, 128, 256}, bps[3] = {0, 4, 8}, grabs[4] = {32, 64, 128, 256};
+        auto time_one = [&](int which, const TraceShape& t, float* ms) -> rg_status {
+            float best_t = 1e30f;
+            for (int rep = 0; rep < 4; ++rep) {
+                uint32_t* wc = which == 0 ? &s->d_rs->work_closest : &s->d_rs->work_shadow;
+                SV_CK(cudaMemsetAsync(wc, 0, 4, s->stream));
+                SV_CK(cudaEventRecord(s->t0, s->stream));
+                if (which == 0)
+                    SV_CK(launch_trace(kModeClosestBatch, false, false, closest_args(s, s->d_tune_count), s->stream, t));
+                else
+                    SV_CK(launch_trace(kModeShadowBatch, false, false, shadow_args(s), s->stream, t));
+                SV_CK(cudaEventRecord(s->t1, s->stream));
+                SV_CK(cudaEventSynchronize(s->t1));
+                float e = 0;
+                SV_CK(cudaEventElapsedTime(&e, s->t0, s->t1));
+                if (rep > 0) best_t = std::min(best_t, e);
+            }
+            *ms = best_t;
+            return RG_OK;
+        };
+        for (int which = 0; which < 2; ++which) {
+            if (which == 1) {
+                // one shading pass makes the shadow rays (its spawned rays are discarded below)
+                SV_CK(cudaMemsetAsync(&s->d_rs->work_closest, 0, 4, s->stream));
+                SV_CK(launch_trace(kModeClosestBatch, false, false, closest_args(s, s->d_tune_count), s->stream,
+                                   best[0]));
+                SV_CK(launch_shade_batch(shade_args(s, s->d_tune_count), s->stream));
+            }
+            best_ms[which] = 1e30f;
+            for (int b : blocks)
+                for (int q : bps)
+                    for (int g : grabs) {
+                        TraceShape t;
+                        t.block = b;
+                        t.blocks_per_sm = q;
+                        t.grab = g;
+                        float ms;
+                        if ((r = time_one(which, t, &ms))) return r;
+                        if (ms < best_ms[which]) {
+                            best_ms[which] = ms;
+                            best[which] = t;
+                        }
+                    }
+        }
+        // back to an empty ring and a free slot
+        SV_CK(cudaStreamSynchronize(s->stream));
+        int err = 0;
+        SV_CK(cudaMemcpy(&err, &s->st->error, sizeof(int), cudaMemcpyDeviceToHost));
+        SV_CK(cudaMemset(s->d_rs, 0, sizeof(RingState)));
+        SV_CK(cudaMemset(&s->st->error, 0, sizeof(int)));
+        s->ring_rays_now = 0;
+        for (Active& a : s->active) a = Active();
+        s->stats.admitted--;
+        s->stats.submitted--;
+        if (err) return sfail(err, std::string("autotune: ") + device_error_text(err));
+        if (cache_path && (r = cache_store(cache_path, dev, sms, best, best_ms))) return r;
+    }
+    s->shape[0] = best[0];
+    s->shape[1] = best[1];
+    drop_step_graph(s);
+    if (out)
+        for (int w = 0; w < 2; ++w) {
+            out[w].block = (uint32_t)best[w].block;
+            out[w].blocks_per_sm = (uint32_t)best[w].blocks_per_sm;
+            out[w].grab = (uint32_t)best[w].grab;
+            out[w].ms = best_ms[w];
+        }
+    return RG_OK;
+}
+
+}  // extern "C"

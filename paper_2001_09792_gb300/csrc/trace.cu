@@ -78,38 +78,8 @@ struct Shear {
     int kx, ky, kz;
 };
 
-// Shear for the wide traversal.  ix, iy, iz: the correctly rounded reciprocals
-// of dx, dy, dz (already needed by the box test); Sz = 1/d_kz is taken from
-// them and Sx, Sy are products, so an instance entry costs no division beyond
-// the reciprocals.  Any fixed shear keeps the test watertight for the ray.
-__device__ __forceinline__ Shear make_shear(float ox, float oy, float oz, float dx, float dy, float dz, float ix,
-                                            float iy, float iz) {
-    Shear s;
-    float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
-    int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
-    int kx = kz == 2 ? 0 : kz + 1;
-    int ky = kx == 2 ? 0 : kx + 1;
-    float dkz = kz == 0 ? dx : (kz == 1 ? dy : dz);
-    if (dkz < 0.0f) {
-        int t = kx;
-        kx = ky;
-        ky = t;
-    }
-    float dkx = kx == 0 ? dx : (kx == 1 ? dy : dz);
-    float dky = ky == 0 ? dx : (ky == 1 ? dy : dz);
-    s.Sz = kz == 0 ? ix : (kz == 1 ? iy : iz);
-    s.Sx = __fmul_rn(dkx, s.Sz);
-    s.Sy = __fmul_rn(dky, s.Sz);
-    s.kx = kx;
-    s.ky = ky;
-    s.kz = kz;
-    s.ox = kx == 0 ? ox : (kx == 1 ? oy : oz);
-    s.oy = ky == 0 ? ox : (ky == 1 ? oy : oz);
-    s.oz = kz == 0 ? ox : (kz == 1 ? oy : oz);
-    return s;
-}
-
-// Shear of the watertight test with IEEE divisions (binary traversal).
+// Shear of the watertight test, with IEEE divisions (both traversals use it,
+// so their hit records are bit-identical).
 __device__ __forceinline__ Shear make_shear_div(float ox, float oy, float oz, float dx, float dy, float dz) {
     Shear s;
     float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
@@ -193,7 +163,7 @@ __device__ __forceinline__ void emit(const TraceArgs& a, uint32_t i, bool found,
             out.v = 0.f;
         }
         a.hits_abi[i] = out;
-    } else if (MODE == kModeClosestRender) {
+    } else if (MODE == kModeClosestRender || MODE == kModeClosestBatch) {
         HitDev hd;
         hd.inst_leaf = found ? best_il : kMiss;
         hd.tri_leaf = found ? best_tl : kMiss;
@@ -203,7 +173,8 @@ __device__ __forceinline__ void emit(const TraceArgs& a, uint32_t i, bool found,
     } else {  // shadow: accumulate the unshadowed contribution
         if (!found && ok) {
             const Payload p = a.payload[i];
-            float* px = a.image + 4 * (size_t)p.pixel;
+            float* px = (MODE == kModeShadowBatch ? a.slots[slot_of_px(p.pixel)].image : a.image) +
+                        4 * (size_t)px_of(p.pixel);
             atomicAdd(px + 0, p.r);
             atomicAdd(px + 1, p.g);
             atomicAdd(px + 2, p.b);
@@ -230,22 +201,40 @@ __device__ __forceinline__ void flush_counts(const TraceArgs& a, unsigned long l
     }
 }
 
-template <int MODE, bool BRUTE, bool STATS>
-__global__ void __launch_bounds__(kTraceBlock) k_trace(TraceArgs a) {
+template <int MODE, bool BRUTE, bool STATS, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_trace(TraceArgs a) {
     const uint32_t iter_cap = a.iter_cap;
-    constexpr bool kAny = (MODE == kModeAnyAbi || MODE == kModeShadowRender);
+    constexpr bool kAny = (MODE == kModeAnyAbi || MODE == kModeShadowRender || MODE == kModeShadowBatch);
+    constexpr bool kBatch = (MODE == kModeClosestBatch || MODE == kModeShadowBatch);
     const uint32_t n = a.d_count ? *a.d_count : a.n;
     const int lane = threadIdx.x & 31;
+    const uint32_t grab = a.grab;
+    // batched closest-hit rays sit in a ring of 2^k entries from *ring_head
+    const uint32_t head = MODE == kModeClosestBatch ? *a.ring_head : 0u;
     unsigned long long c_nodes = 0, c_tris = 0, c_inst = 0;
-    for (;;) {
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(a.work_counter, 32u);
-        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    for (uint32_t base = 0, sub = grab;; sub += 32u) {
+        if (sub >= grab) {  // take the next `grab` rays for this warp
+            if (lane == 0) base = atomicAdd(a.work_counter, grab);
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            sub = 0;
+        }
         if (base >= n) break;
-        const uint32_t i = base + lane;
+        const uint32_t i = base + sub + lane;
         if (i >= n) continue;
+        const uint32_t j = MODE == kModeClosestBatch ? ((head + i) & a.ring_mask) : i;
 
-        const float4 r0 = __ldg(a.rays + 2 * (size_t)i), r1 = __ldg(a.rays + 2 * (size_t)i + 1);
+        // the TLAS of this ray (per request slot in the batched modes)
+        const float4* tlas_nodes = a.tlas_nodes;
+        const InstDev* tlas_inst = a.inst;
+        uint32_t tlas_root = a.tlas_root;
+        if (kBatch) {
+            const SlotDev* S = a.slots + slot_of_px(a.payload[j].pixel);
+            tlas_nodes = S->tlas_nodes;
+            tlas_inst = S->inst;
+            tlas_root = S->tlas_root;
+        }
+
+        const float4 r0 = __ldg(a.rays + 2 * (size_t)j), r1 = __ldg(a.rays + 2 * (size_t)j + 1);
         const float tmin = r0.w, tmax = r1.w;
         SpaceRay wr;
         wr.ox = r0.x; wr.oy = r0.y; wr.oz = r0.z;
@@ -261,9 +250,9 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace(TraceArgs a) {
 
         uint32_t stack[kStack];
         int sp = 0;
-        uint32_t ref = a.tlas_root;
+        uint32_t ref = tlas_root;
         bool in_blas = false;
-        const float4* nodes = a.tlas_nodes;
+        const float4* nodes = tlas_nodes;
         const float4* tris = nullptr;
         uint32_t cur_id = 0, cur_leaf = 0;
         bool ok = true;
@@ -279,7 +268,7 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace(TraceArgs a) {
                 ref = stack[--sp];
                 if (ref == kMarker) {
                     in_blas = false;
-                    nodes = a.tlas_nodes;
+                    nodes = tlas_nodes;
                     cr = wr;
                     ref = kNone;
                 }
@@ -316,7 +305,7 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace(TraceArgs a) {
             }
             const uint32_t leaf = ref & ~kLeaf;
             if (!in_blas) {
-                const InstDev* I = a.inst + leaf;
+                const InstDev* I = tlas_inst + leaf;
                 const float4 m0 = __ldg(&I->inv[0]), m1 = __ldg(&I->inv[1]), m2 = __ldg(&I->inv[2]);
                 const float4 meta0 = __ldg(reinterpret_cast<const float4*>(&I->nodes));        // nodes, tris
                 const uint4 meta1 = __ldg(reinterpret_cast<const uint4*>(&I->root));           // root, id, mat, blas
@@ -572,7 +561,7 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace8(TraceArgs a) {
                         cr.ox = ox; cr.oy = oy; cr.oz = oz;
                         cr.ix = safe_rcp(ddx); cr.iy = safe_rcp(ddy); cr.iz = safe_rcp(ddz);
                         oct = oct_of(cr);
-                        sh = make_shear(ox, oy, oz, ddx, ddy, ddz, cr.ix, cr.iy, cr.iz);
+                        sh = make_shear_div(ox, oy, oz, ddx, ddy, ddz);
                         const unsigned long long pn =
                             ((unsigned long long)__float_as_uint(meta0.y) << 32) | __float_as_uint(meta0.x);
                         const unsigned long long pt =
@@ -648,23 +637,40 @@ cudaError_t launch_mode8(const TraceArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int MODE, bool BRUTE, bool STATS>
-cudaError_t launch_mode(const TraceArgs& a, cudaStream_t s) {
-    static int blocks = 0;
-    if (blocks == 0) {
-        int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<MODE, BRUTE, STATS>, kTraceBlock, 0);
+template <int MODE, bool BRUTE, bool STATS, int BLOCK>
+cudaError_t launch_block(const TraceArgs& a, int blocks_per_sm, cudaStream_t s) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<MODE, BRUTE, STATS, BLOCK>, BLOCK, 0);
         if (e != cudaSuccess) return e;
-        blocks = device_sm_count() * (per_sm > 0 ? per_sm : 1);
+        if (per_sm <= 0) per_sm = 1;
     }
-    k_trace<MODE, BRUTE, STATS><<<blocks, kTraceBlock, 0, s>>>(a);
+    const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
+    k_trace<MODE, BRUTE, STATS, BLOCK><<<device_sm_count() * b, BLOCK, 0, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
 
+// Shapes other than 128 threads are compiled for the render and batched modes
+// (the ones the autotuner sets); the rest run with 128.
+template <int MODE, bool BRUTE, bool STATS>
+cudaError_t launch_mode(const TraceArgs& a0, cudaStream_t s, const TraceShape& shape = TraceShape()) {
+    TraceArgs a = a0;
+    a.grab = (shape.grab >= 32 && shape.grab % 32 == 0) ? (uint32_t)shape.grab : 32u;
+    constexpr bool kTunable = !BRUTE && !STATS && MODE >= kModeClosestRender;
+    if constexpr (kTunable) {
+        if (shape.block == 64) return launch_block<MODE, BRUTE, STATS, 64>(a, shape.blocks_per_sm, s);
+        if (shape.block == 256) return launch_block<MODE, BRUTE, STATS, 256>(a, shape.blocks_per_sm, s);
+    }
+    return launch_block<MODE, BRUTE, STATS, 128>(a, shape.blocks_per_sm, s);
+}
+
 }  // namespace
 
-cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a, cudaStream_t s) {
+cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a0, cudaStream_t s,
+                         const TraceShape& shape) {
+    TraceArgs a = a0;
+    if (a.grab == 0) a.grab = 32;
     if (a.tlas_nodes8 && !brute) {
         switch (mode) {
             case kModeClosestAbi:
@@ -689,10 +695,14 @@ cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a, c
             return stats ? launch_mode<kModeAnyAbi, false, true>(a, s) : launch_mode<kModeAnyAbi, false, false>(a, s);
         case kModeClosestRender:
             return stats ? launch_mode<kModeClosestRender, false, true>(a, s)
-                         : launch_mode<kModeClosestRender, false, false>(a, s);
+                         : launch_mode<kModeClosestRender, false, false>(a, s, shape);
         case kModeShadowRender:
             return stats ? launch_mode<kModeShadowRender, false, true>(a, s)
-                         : launch_mode<kModeShadowRender, false, false>(a, s);
+                         : launch_mode<kModeShadowRender, false, false>(a, s, shape);
+        case kModeClosestBatch:
+            return launch_mode<kModeClosestBatch, false, false>(a, s, shape);
+        case kModeShadowBatch:
+            return launch_mode<kModeShadowBatch, false, false>(a, s, shape);
     }
     return cudaErrorInvalidValue;
 }

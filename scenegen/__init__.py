@@ -503,6 +503,13 @@ def large_rays(scene, n, seed=SEED_RAYS):
 SERVE_RESOLUTIONS = [(320, 240), (640, 480), (1280, 720), (1920, 1080), (3840, 2160)]
 
 
+def serving_scenes():
+    """The 8 resident scenes of the serving workload: the tiny scene and seven
+    medium-style scenes (seeds 11..17), each with its own meshes, layout,
+    materials and lights."""
+    return [tiny_scene()] + [medium_scene(seed=10 + k) for k in range(1, 8)]
+
+
 def serving_requests(n, rate=200.0, n_scenes=8, seed=SEED_SERVE):
     """Poisson arrival stream: (arrival_s, scene, width, height, max_depth, motion_seed)."""
     rng = np.random.default_rng(seed)

@@ -55,3 +55,36 @@ def test_null_scene_is_rejected_without_gpu():
     L = rg.lib()
     assert L.rg_sync(None) == rg.RG_ERR_INVALID_ARG
     assert b"NULL" in L.rg_last_error()
+
+
+STRUCTS = ["rg_camera", "rg_material", "rg_light", "rg_scene_desc", "rg_stats", "rg_server_desc", "rg_request",
+           "rg_completion", "rg_server_stats", "rg_trace_shape"]
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """Every ctypes mirror has the size and field offsets gcc gives the
+    header's struct."""
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rg.h"', "int main(void) {"]
+    for name in STRUCTS:
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in getattr(rg, name)._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n") if l)
+    for name in STRUCTS:
+        cls = getattr(rg, name)
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, f"{name}.{f}"
+
+
+def test_null_server_is_rejected_without_gpu():
+    L = rg.lib()
+    assert L.rg_server_step(None, None) == rg.RG_ERR_INVALID_ARG
+    assert L.rg_server_destroy(None) == rg.RG_OK
+    assert L.rg_server_create(None, None) == rg.RG_ERR_INVALID_ARG
