@@ -292,7 +292,9 @@ def run_native(args, world, rank, local):
                     "algorithmic_bytes_per_ray": round(bytes_per_ray, 1),
                     "nodes_per_ray": round(cst["node_visits"] / cr, 2), "tris_per_ray": round(cst["tri_tests"] / cr, 2),
                     "inst_per_ray": round(cst["inst_entries"] / cr, 3), "avg_launch_ms": round(launch_ms, 4),
-                    "trace_share_of_frame": round(st["trace_ms"] / sum(ms), 3)}
+                    "trace_share_of_frame": round(st["trace_ms"] / sum(ms), 3),
+                    "shadow_share_of_frame": round(st["any_ms"] / sum(ms), 3),
+                    "shadow_nodes_per_ray": round(cst["any_node_visits"] / max(cst["shadow_rays"], 1), 2)}
         ms_sorted = sorted(ms)
         out = {
             "metric": METRIC,

@@ -146,7 +146,8 @@ rg_status rg_tlas_build(rg_scene* scene, const rg_instance* d_inst, uint32_t n, 
  * and boxes and the node boxes; the topology is unchanged. */
 rg_status rg_tlas_refit(rg_scene* scene, const rg_instance* d_inst, uint32_t n, void* stream);
 
-/* Materials (host array, copied) and point lights (host array, copied). */
+/* Materials (host array, copied) and point lights (host array, copied; at
+ * most 64, else RG_ERR_INVALID_ARG). */
 rg_status rg_scene_set_materials(rg_scene* scene, const rg_material* h_mat, uint32_t n);
 rg_status rg_scene_set_lights(rg_scene* scene, const rg_light* h_lights, uint32_t n);
 
@@ -359,13 +360,14 @@ rg_status rg_server_get_stats(rg_server* server, rg_server_stats* out);
 
 /* Launch shapes of the server's two traversals (which: 0 closest hit,
  * 1 shadow): threads per block 64 / 128 / 256, resident blocks per SM
- * (0 = as many as fit) and rays a warp takes per grab of the work counter
- * (a multiple of 32, <= 1024). */
-typedef struct { uint32_t block, blocks_per_sm, grab; float ms; } rg_trace_shape;
+ * (0 = as many as fit) and how many of a warp's 32 lanes must have finished
+ * their rays before the warp fetches new ones (1..32; 32 = only when all
+ * have, a leaner loop; 0 = the default, 32). */
+typedef struct { uint32_t block, blocks_per_sm, refill; float ms; } rg_trace_shape;
 rg_status rg_server_set_shape(rg_server* server, uint32_t which, const rg_trace_shape* shape);
 rg_status rg_server_get_shape(rg_server* server, uint32_t which, rg_trace_shape* out);
 /* Autotuner: picks both shapes by timing every candidate (block x blocks per
- * SM x grab) on the sample request's rays (its primary rays for the closest
+ * SM x refill) on the sample request's rays (its primary rays for the closest
  * traversal, the shadow rays their shading spawns for the shadow traversal),
  * sets them, and reports them in out[0..1] (ms = best time of that
  * traversal).  cache_path (may be NULL): a JSON file; if it holds shapes for

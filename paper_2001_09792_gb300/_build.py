@@ -21,6 +21,12 @@ SOURCES = ["build.cu", "wide.cu", "trace.cu", "render.cu", "api.cu", "noalloc.cu
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", f"-I{INCLUDE}"]
+# The renderer's kernels (camera rays, shading, spawned rays) exist as a
+# single-request and a batched instantiation of the same source; without FMA
+# contraction both round every operation the same way, so a request renders
+# the same rays alone and in a batch.  (The traversal spells its roundings
+# out with intrinsics and needs no flag.)
+FILE_FLAGS = {"render.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -44,7 +50,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT, src.replace(".cu", ".o"))
-        cmd = [exe, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [exe, *ARCH, *NVCC_FLAGS, *FILE_FLAGS.get(src, []), *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{p.stdout}\n{p.stderr}")

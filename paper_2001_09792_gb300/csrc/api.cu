@@ -167,7 +167,8 @@ struct rg_scene {
     DevBuf<float4> q_rays[2], s_rays;
     DevBuf<Payload> q_pay[2], s_pay;
     DevBuf<HitDev> hits;
-    DevBuf<uint32_t> counters;     // [0] closest work, [1] next count, [2] shadow count, [3] shadow work
+    DevBuf<uint32_t> counters;     // [0] closest work, [1] next count, [2] shadow work, [3] unused,
+                                   // [4 + l] shadow rays toward light l
     uint32_t* h_counts = nullptr;  // pinned, 4 entries
     // statistics and timing
     uint64_t closest_rays = 0, shadow_rays_host = 0;
@@ -301,7 +302,7 @@ rg_status rg_scene_create(rg_scene** out, const rg_scene_desc* desc) {
         delete s;
         return r;
     }
-    if ((r = s->counters.ensure(16, "counters"))) {
+    if ((r = s->counters.ensure(4 + kMaxLights, "counters"))) {
         cudaFree(s->st);
         delete s;
         return r;
@@ -562,6 +563,7 @@ rg_status rg_scene_set_lights(rg_scene* s, const rg_light* h, uint32_t n) {
     rg_status r;
     if ((r = check_scene(s))) return r;
     if (n && !h) return fail(RG_ERR_INVALID_ARG, "NULL lights");
+    if (n > kMaxLights) return fail(RG_ERR_INVALID_ARG, "more than 64 lights");
     if ((r = set_device(s))) return r;
     if ((r = s->lights.ensure(n ? n : 1, "lights"))) return r;
     if (n) RG_CK(cudaMemcpy(s->lights.p, h, n * sizeof(rg_light), cudaMemcpyHostToDevice));
@@ -629,7 +631,7 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
             if ((r = s->q_rays[1 - cur].ensure(4 * (size_t)n, "ray queue"))) return r;
             if ((r = s->q_pay[1 - cur].ensure(2 * (size_t)n, "payload queue"))) return r;
         }
-        RG_CK(cudaMemsetAsync(s->counters.p, 0, 4 * sizeof(uint32_t), st));
+        RG_CK(cudaMemsetAsync(s->counters.p, 0, (4 + L) * sizeof(uint32_t), st));
         TraceArgs a = base_trace_args(s, true);
         a.rays = s->q_rays[cur].p;
         a.n = n;
@@ -662,17 +664,20 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
         sa.next_count = s->counters.p + 1;
         sa.shadow_rays = s->s_rays.p;
         sa.shadow_payload = s->s_pay.p;
-        sa.shadow_count = s->counters.p + 2;
+        sa.shadow_count = s->counters.p + 4;
+        sa.shadow_stride = n;
         sa.st = s->st;
         RG_CK(launch_shade(sa, n, st));
 
         if (L) {
             TraceArgs b = base_trace_args(s, true);
             b.rays = s->s_rays.p;
-            b.d_count = s->counters.p + 2;
+            b.sub_counts = s->counters.p + 4;
+            b.n_sub = L;
+            b.sub_stride = n;
             b.payload = s->s_pay.p;
             b.image = d_rgba;
-            b.work_counter = s->counters.p + 3;
+            b.work_counter = s->counters.p + 2;
             if ((r = event_begin(s, 1, st, &ev))) return r;
             RG_CK(launch_trace(kModeShadowRender, false, s->desc.flags & RG_SCENE_COUNT, b, st));
             if ((r = event_end(s, st))) return r;

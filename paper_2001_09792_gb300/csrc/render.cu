@@ -151,13 +151,14 @@ __device__ __forceinline__ RayCtx ray_ctx(const ShadeArgs& a, const SlotDev* slo
 template <bool BATCH>
 __device__ __forceinline__ void shade_one(const ShadeArgs& a, uint32_t head, uint32_t next_base, uint32_t i,
                                           bool valid, int* live_delta) {
-    uint32_t n_shadow = 0, n_next = 0;
+    uint32_t n_next = 0;
+    bool lit = false;  // a diffuse hit: ambient term and shadow rays
     Surf s;
     uint32_t type = 0;
     float3 alb = f3(0, 0, 0), thr = f3(0, 0, 0);
     float ior = 1.0f;
     bool hit = false;
-    RayCtx c;
+    RayCtx c{};
     if (valid) {
         const uint32_t j = BATCH ? ((head + i) & a.ring_mask) : i;
         const float4 r0 = a.rays[2 * (size_t)j], r1 = a.rays[2 * (size_t)j + 1];
@@ -201,12 +202,7 @@ __device__ __forceinline__ void shade_one(const ShadeArgs& a, uint32_t head, uin
                 atomicAdd(px + 0, thr.x * alb.x * c.ambient);
                 atomicAdd(px + 1, thr.y * alb.y * c.ambient);
                 atomicAdd(px + 2, thr.z * alb.z * c.ambient);
-                float3 os = s.p + s.eps * s.nf;
-                for (uint32_t l = 0; l < c.n_lights; ++l) {
-                    const rg_light L = c.lights[l];
-                    float3 lv = f3(L.pos[0], L.pos[1], L.pos[2]) - os;
-                    if (dot3(s.nf, lv) > 0.0f) ++n_shadow;
-                }
+                lit = true;
             } else if (c.depth < c.max_depth) {
                 n_next = 1;
                 if (type == RG_MAT_GLASS) {
@@ -218,27 +214,30 @@ __device__ __forceinline__ void shade_one(const ShadeArgs& a, uint32_t head, uin
             }
         }
     }
-    // claim queue slots (all lanes take part)
-    uint32_t sbase = warp_claim(n_shadow, a.shadow_count, &a.st->shadow_rays);
-    uint32_t nbase = warp_claim(n_next, a.next_count);
-    // live path rays of the slot: this ray leaves, its spawns join
-    if (BATCH && valid && n_next != 1) atomicAdd(live_delta + c.slot, (int)n_next - 1);
-    if (!valid || !hit) return;
-    const uint32_t next_pw = BATCH ? pack_pixel(c.pixel, c.depth + 1, c.slot) : c.pixel;
-    const uint32_t shadow_pw = BATCH ? pack_pixel(c.pixel, c.depth, c.slot) : c.pixel;
-    if (n_shadow) {
-        float3 os = s.p + s.eps * s.nf;
-        uint32_t k = 0;
-        for (uint32_t l = 0; l < c.n_lights; ++l) {
-            const rg_light L = c.lights[l];
-            float3 lv = f3(L.pos[0], L.pos[1], L.pos[2]) - os;
-            if (!(dot3(s.nf, lv) > 0.0f)) continue;
-            float dist = sqrtf(dot3(lv, lv));
-            float3 ld = (1.0f / dist) * lv;
-            float cl = dot3(s.nf, ld);
-            uint32_t slot = sbase + k++;
-            a.shadow_rays[2 * (size_t)slot] = make_float4(os.x, os.y, os.z, 0.0f);
-            a.shadow_rays[2 * (size_t)slot + 1] = make_float4(ld.x, ld.y, ld.z, dist - s.eps);
+    // shadow rays: one sub-queue per light, so that a warp of shadow rays
+    // holds neighbouring surface points seen toward the same light (all lanes
+    // take part in every claim)
+    {
+        const uint32_t shadow_pw = BATCH ? pack_pixel(c.pixel, c.depth, c.slot) : c.pixel;
+        const float3 os = lit ? s.p + s.eps * s.nf : f3(0.f, 0.f, 0.f);
+        const uint32_t n_loop = BATCH ? a.max_lights : a.n_lights;
+        for (uint32_t l = 0; l < n_loop; ++l) {
+            bool want = false;
+            rg_light L;
+            float3 lv = f3(0.f, 0.f, 0.f);
+            if (lit && l < c.n_lights) {
+                L = c.lights[l];
+                lv = f3(L.pos[0], L.pos[1], L.pos[2]) - os;
+                want = dot3(s.nf, lv) > 0.0f;
+            }
+            const uint32_t k = warp_claim(want ? 1u : 0u, a.shadow_count + l, &a.st->shadow_rays);
+            if (!want) continue;
+            const float dist = sqrtf(dot3(lv, lv));
+            const float3 ld = (1.0f / dist) * lv;
+            const float cl = dot3(s.nf, ld);
+            const size_t slot = (size_t)l * a.shadow_stride + k;
+            a.shadow_rays[2 * slot] = make_float4(os.x, os.y, os.z, 0.0f);
+            a.shadow_rays[2 * slot + 1] = make_float4(ld.x, ld.y, ld.z, dist - s.eps);
             Payload sp;
             sp.pixel = shadow_pw;
             sp.r = thr.x * alb.x * L.intensity[0] * cl;
@@ -247,6 +246,12 @@ __device__ __forceinline__ void shade_one(const ShadeArgs& a, uint32_t head, uin
             a.shadow_payload[slot] = sp;
         }
     }
+    // path rays (all lanes take part in the claim)
+    uint32_t nbase = warp_claim(n_next, a.next_count);
+    // live path rays of the slot: this ray leaves, its spawns join
+    if (BATCH && valid && n_next != 1) atomicAdd(live_delta + c.slot, (int)n_next - 1);
+    if (!valid || !hit) return;
+    const uint32_t next_pw = BATCH ? pack_pixel(c.pixel, c.depth + 1, c.slot) : c.pixel;
     if (n_next) {
         float dn = dot3(s.d, s.nf);
         float3 r = normalize3(s.d - (2.0f * dn) * s.nf);

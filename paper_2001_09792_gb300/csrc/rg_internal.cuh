@@ -199,12 +199,13 @@ enum TraceMode {
     kModeShadowBatch = 5    // like kModeShadowRender, image chosen per ray by the payload's slot
 };
 // Launch shape of a traversal (picked by the autotuner): threads per block
-// (64, 128 or 256), resident blocks per SM (0: as many as fit), and rays a
-// warp takes per grab of the work counter (a multiple of 32).
+// (64, 128 or 256), resident blocks per SM (0: as many as fit), and how many
+// lanes of a warp must be idle before the warp fetches new rays (1..32; 32:
+// the whole warp; 0: the traversal mode's default).
 struct TraceShape {
     int block = 128;
     int blocks_per_sm = 0;
-    int grab = 32;
+    int refill = 0;
 };
 struct TraceArgs {
     const float4* rays;          // n x 2 float4 {o, tmin}, {d, tmax}
@@ -224,10 +225,15 @@ struct TraceArgs {
     const float4* tlas_nodes8;   // compressed 8-wide TLAS (null: binary path)
     const InstDev* inst8;        // its instances, in wide-leaf order (BLAS pointers to wide BLAS)
     const SlotDev* slots;        // batched modes: request slots
-    uint32_t grab;               // rays per warp grab (multiple of 32)
+    uint32_t refill;             // binary traversal: idle lanes that make a warp fetch new rays (1..32)
     const uint32_t* ring_head;   // kModeClosestBatch: ray i is ring entry (*ring_head + i) & ring_mask
     uint32_t ring_mask;
+    // shadow modes: the rays sit in n_sub sub-queues (one per light) of
+    // sub_stride entries, sub_counts[l] rays in sub-queue l (then n, d_count unused)
+    const uint32_t* sub_counts;
+    uint32_t n_sub, sub_stride;
 };
+constexpr uint32_t kMaxLights = 64;  // lights per scene (one shadow sub-queue each)
 cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a, cudaStream_t s,
                          const TraceShape& shape = TraceShape());
 
@@ -252,9 +258,11 @@ struct ShadeArgs {
     float4* next_rays;
     Payload* next_payload;
     uint32_t* next_count;
-    float4* shadow_rays;
+    float4* shadow_rays;         // one sub-queue of shadow_stride rays per light
     Payload* shadow_payload;
-    uint32_t* shadow_count;
+    uint32_t* shadow_count;      // per light
+    uint32_t shadow_stride;
+    uint32_t max_lights;         // batched: lights of the scene with the most (loop bound)
     DevStatus* st;
     // batched wavefront only: ray i is ring entry (*ring_head + i) & ring_mask,
     // spawned path rays go to ring entries from *next_base, and each ray adds

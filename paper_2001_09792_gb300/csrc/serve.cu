@@ -39,9 +39,10 @@ struct RingState {
     uint32_t gen_base;          // where this step's primary rays start
     uint32_t next_base;         // where this step's spawned rays start (the tail after ray generation)
     uint32_t cons;              // first ray consumed by this step
-    uint32_t work_closest, next_count, shadow_count, work_shadow;
-    uint32_t pad[3];
+    uint32_t work_closest, next_count, work_shadow;
+    uint32_t pad[4];
     int slot_live[kMaxSlots];   // path rays of each slot in the ring
+    uint32_t shadow_count[kMaxLights];  // shadow rays toward each light (one sub-queue each)
 };
 
 // Host -> device once per step.
@@ -79,9 +80,9 @@ __global__ void k_step_begin(const StepHdr* __restrict__ hdr, RingState* __restr
         rs->cons = hdr->newest_first ? T - hdr->m : rs->head;
         rs->work_closest = 0;
         rs->next_count = 0;
-        rs->shadow_count = 0;
         rs->work_shadow = 0;
     }
+    for (uint32_t k = l; k < kMaxLights; k += blockDim.x) rs->shadow_count[k] = 0;
 }
 
 // Newest-first steps leave the consumed rays [T - m, T) as a gap below the
@@ -114,7 +115,9 @@ __global__ void k_step_end(const StepHdr* __restrict__ hdr, RingState* __restric
         out->head = rs->head;
         out->tail = rs->tail;
         out->next_count = rs->next_count;
-        out->shadow_count = rs->shadow_count;
+        uint32_t shadow = 0;
+        for (uint32_t k = 0; k < kMaxLights; ++k) shadow += rs->shadow_count[k];
+        out->shadow_count = shadow;
         out->error = st->error;
     }
 }
@@ -288,7 +291,9 @@ TraceArgs closest_args(rg_server* s, const uint32_t* d_count) {
 TraceArgs shadow_args(rg_server* s) {
     TraceArgs b{};
     b.rays = s->s_rays;
-    b.d_count = &s->d_rs->shadow_count;
+    b.sub_counts = s->d_rs->shadow_count;
+    b.n_sub = s->max_lights;
+    b.sub_stride = s->batch;
     b.payload = s->s_pay;
     b.work_counter = &s->d_rs->work_shadow;
     b.st = s->st;
@@ -308,7 +313,9 @@ ShadeArgs shade_args(rg_server* s, const uint32_t* d_count) {
     a.next_count = &s->d_rs->next_count;
     a.shadow_rays = s->s_rays;
     a.shadow_payload = s->s_pay;
-    a.shadow_count = &s->d_rs->shadow_count;
+    a.shadow_count = s->d_rs->shadow_count;
+    a.shadow_stride = s->batch;
+    a.max_lights = s->max_lights;
     a.st = s->st;
     a.slots = s->d_hdr->slots;
     a.slot_live = s->d_rs->slot_live;
@@ -558,11 +565,11 @@ bool read_num(const std::string& line, const std::string& key, long* v) {
 
 bool parse_shape(const std::string& obj, TraceShape* sh) {
     long b, bps, g;
-    if (!read_num(obj, "block", &b) || !read_num(obj, "blocks_per_sm", &bps) || !read_num(obj, "grab", &g)) return false;
-    if ((b != 64 && b != 128 && b != 256) || bps < 0 || bps > 64 || g < 32 || g > 1024 || g % 32) return false;
+    if (!read_num(obj, "block", &b) || !read_num(obj, "blocks_per_sm", &bps) || !read_num(obj, "refill", &g)) return false;
+    if ((b != 64 && b != 128 && b != 256) || bps < 0 || bps > 64 || g < 0 || g > 32) return false;
     sh->block = (int)b;
     sh->blocks_per_sm = (int)bps;
-    sh->grab = (int)g;
+    sh->refill = (int)g;
     return true;
 }
 
@@ -603,8 +610,8 @@ bool cache_lookup(const char* path, const std::string& dev, int sms, TraceShape 
 
 std::string shape_json(const TraceShape& t, float ms) {
     char buf[160];
-    std::snprintf(buf, sizeof buf, "{\"block\": %d, \"blocks_per_sm\": %d, \"grab\": %d, \"ms\": %.4f}", t.block,
-                  t.blocks_per_sm, t.grab, ms);
+    std::snprintf(buf, sizeof buf, "{\"block\": %d, \"blocks_per_sm\": %d, \"refill\": %d, \"ms\": %.4f}", t.block,
+                  t.blocks_per_sm, t.refill, ms);
     return buf;
 }
 
@@ -650,7 +657,7 @@ rg_status rg_server_create(rg_server** out, const rg_server_desc* desc) {
     s->batch = d.batch_rays ? d.batch_rays : (1u << 23);
     s->batch = std::min(s->batch, s->ring_cap / 2);
     s->max_lights = d.max_lights ? d.max_lights : 4u;
-    if (s->max_lights > 64) {
+    if (s->max_lights > kMaxLights) {
         delete s;
         return sfail(RG_ERR_INVALID_ARG, "max_lights above 64");
     }
@@ -841,12 +848,11 @@ rg_status rg_server_set_shape(rg_server* s, uint32_t which, const rg_trace_shape
     rg_status r;
     if ((r = check_server(s))) return r;
     if (which > 1 || !sh) return sfail(RG_ERR_INVALID_ARG, "bad shape selector");
-    if ((sh->block != 64 && sh->block != 128 && sh->block != 256) || sh->blocks_per_sm > 64 || sh->grab < 32 ||
-        sh->grab > 1024 || sh->grab % 32)
+    if ((sh->block != 64 && sh->block != 128 && sh->block != 256) || sh->blocks_per_sm > 64 || sh->refill > 32)
         return sfail(RG_ERR_INVALID_ARG, "bad launch shape");
     s->shape[which].block = (int)sh->block;
     s->shape[which].blocks_per_sm = (int)sh->blocks_per_sm;
-    s->shape[which].grab = (int)sh->grab;
+    s->shape[which].refill = (int)sh->refill;
     drop_step_graph(s);
     return RG_OK;
 }
@@ -857,7 +863,7 @@ rg_status rg_server_get_shape(rg_server* s, uint32_t which, rg_trace_shape* out)
     if (which > 1 || !out) return sfail(RG_ERR_INVALID_ARG, "bad shape selector");
     out->block = (uint32_t)s->shape[which].block;
     out->blocks_per_sm = (uint32_t)s->shape[which].blocks_per_sm;
-    out->grab = (uint32_t)s->shape[which].grab;
+    out->refill = (uint32_t)s->shape[which].refill;
     out->ms = -1.0f;
     return RG_OK;
 }
@@ -891,7 +897,7 @@ rg_status rg_server_autotune(rg_server* s, const rg_request* sample, const char*
         if (r) return r;
         SV_CK(cudaMemcpyAsync(s->d_tune_count, &m, 4, cudaMemcpyHostToDevice, s->stream));
         SV_CK(cudaStreamSynchronize(s->stream));
-        const int blocks[3] = {64, 128, 256}, bps[3] = {0, 4, 8}, grabs[4] = {32, 64, 128, 256};
+        const int blocks[3] = {64, 128, 256}, bps[3] = {0, 4, 8}, refills[4] = {8, 16, 24, 32};
         auto time_one = [&](int which, const TraceShape& t, float* ms) -> rg_status {
             float best_t = 1e30f;
             for (int rep = 0; rep < 4; ++rep) {
@@ -922,11 +928,11 @@ rg_status rg_server_autotune(rg_server* s, const rg_request* sample, const char*
             best_ms[which] = 1e30f;
             for (int b : blocks)
                 for (int q : bps)
-                    for (int g : grabs) {
+                    for (int g : refills) {
                         TraceShape t;
                         t.block = b;
                         t.blocks_per_sm = q;
-                        t.grab = g;
+                        t.refill = g;
                         float ms;
                         if ((r = time_one(which, t, &ms))) return r;
                         if (ms < best_ms[which]) {
@@ -955,7 +961,7 @@ rg_status rg_server_autotune(rg_server* s, const rg_request* sample, const char*
         for (int w = 0; w < 2; ++w) {
             out[w].block = (uint32_t)best[w].block;
             out[w].blocks_per_sm = (uint32_t)best[w].blocks_per_sm;
-            out[w].grab = (uint32_t)best[w].grab;
+            out[w].refill = (uint32_t)best[w].refill;
             out[w].ms = best_ms[w];
         }
     return RG_OK;

@@ -144,7 +144,7 @@ __device__ __forceinline__ TriResult tri_test(const Shear& s, float4 v0, float4 
 // Write one ray's result: an ABI hit record, a render hit, or (shadow rays)
 // the unshadowed contribution added to the image.
 template <int MODE>
-__device__ __forceinline__ void emit(const TraceArgs& a, uint32_t i, bool found, bool ok, float best_t, uint32_t best_id,
+__device__ __forceinline__ void emit(const TraceArgs& a, uint32_t i, uint32_t j, bool found, bool ok, float best_t, uint32_t best_id,
                                      uint32_t best_prim, uint32_t best_il, uint32_t best_tl, float best_V,
                                      float best_W, float best_det) {
     if (MODE == kModeClosestAbi || MODE == kModeAnyAbi) {
@@ -172,7 +172,7 @@ __device__ __forceinline__ void emit(const TraceArgs& a, uint32_t i, bool found,
         *reinterpret_cast<uint4*>(a.hits_render + i) = *reinterpret_cast<const uint4*>(&hd);
     } else {  // shadow: accumulate the unshadowed contribution
         if (!found && ok) {
-            const Payload p = a.payload[i];
+            const Payload p = a.payload[j];
             float* px = (MODE == kModeShadowBatch ? a.slots[slot_of_px(p.pixel)].image : a.image) +
                         4 * (size_t)px_of(p.pixel);
             atomicAdd(px + 0, p.r);
@@ -180,6 +180,31 @@ __device__ __forceinline__ void emit(const TraceArgs& a, uint32_t i, bool found,
             atomicAdd(px + 2, p.b);
         }
     }
+}
+
+// Shadow rays in per-light sub-queues: the block's prefix of the sub-queue
+// counts goes to shared memory (pre[l] = rays before sub-queue l, pre[n_sub]
+// = all); returns the number of rays.  Without sub-queues: *d_count or n.
+__device__ __forceinline__ uint32_t ray_count(const TraceArgs& a, uint32_t* pre) {
+    if (!a.sub_counts) return a.d_count ? *a.d_count : a.n;
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (uint32_t l = 0; l < a.n_sub; ++l) {
+            pre[l] = acc;
+            acc += a.sub_counts[l];
+        }
+        pre[a.n_sub] = acc;
+    }
+    __syncthreads();
+    return pre[a.n_sub];
+}
+
+// Queue entry of ray i: its place in its light's sub-queue.
+__device__ __forceinline__ uint32_t sub_entry(const TraceArgs& a, const uint32_t* pre, uint32_t i) {
+    if (!a.sub_counts) return i;
+    uint32_t l = 0;
+    while (l + 1 < a.n_sub && pre[l + 1] <= i) ++l;
+    return l * a.sub_stride + (i - pre[l]);
 }
 
 template <bool ANY, bool STATS>
@@ -201,27 +226,30 @@ __device__ __forceinline__ void flush_counts(const TraceArgs& a, unsigned long l
     }
 }
 
+// Binary traversal, whole-warp refill: a warp takes 32 rays from the work
+// counter, each lane runs its ray to completion (one loop iteration per node
+// visit, stack pop, instance entry or triangle test), and the warp takes the
+// next 32 when all its lanes are done.  Best when the rays of a warp take
+// similar work (camera and secondary rays).
 template <int MODE, bool BRUTE, bool STATS, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_trace(TraceArgs a) {
+__global__ void __launch_bounds__(BLOCK) k_trace_warp(TraceArgs a) {
     const uint32_t iter_cap = a.iter_cap;
     constexpr bool kAny = (MODE == kModeAnyAbi || MODE == kModeShadowRender || MODE == kModeShadowBatch);
     constexpr bool kBatch = (MODE == kModeClosestBatch || MODE == kModeShadowBatch);
-    const uint32_t n = a.d_count ? *a.d_count : a.n;
+    __shared__ uint32_t pre[kMaxLights + 1];
+    const uint32_t n = ray_count(a, pre);
     const int lane = threadIdx.x & 31;
-    const uint32_t grab = a.grab;
     // batched closest-hit rays sit in a ring of 2^k entries from *ring_head
     const uint32_t head = MODE == kModeClosestBatch ? *a.ring_head : 0u;
     unsigned long long c_nodes = 0, c_tris = 0, c_inst = 0;
-    for (uint32_t base = 0, sub = grab;; sub += 32u) {
-        if (sub >= grab) {  // take the next `grab` rays for this warp
-            if (lane == 0) base = atomicAdd(a.work_counter, grab);
-            base = __shfl_sync(0xFFFFFFFFu, base, 0);
-            sub = 0;
-        }
+    for (;;) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(a.work_counter, 32u);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
         if (base >= n) break;
-        const uint32_t i = base + sub + lane;
+        const uint32_t i = base + lane;
         if (i >= n) continue;
-        const uint32_t j = MODE == kModeClosestBatch ? ((head + i) & a.ring_mask) : i;
+        const uint32_t j = MODE == kModeClosestBatch ? ((head + i) & a.ring_mask) : sub_entry(a, pre, i);
 
         // the TLAS of this ray (per request slot in the batched modes)
         const float4* tlas_nodes = a.tlas_nodes;
@@ -362,7 +390,192 @@ __global__ void __launch_bounds__(BLOCK) k_trace(TraceArgs a) {
             }
         }
         if (!ok) found = false;
-        emit<MODE>(a, i, found, ok, best_t, best_id, best_prim, best_il, best_tl, best_V, best_W, best_det);
+        emit<MODE>(a, i, j, found, ok, best_t, best_id, best_prim, best_il, best_tl, best_V, best_W, best_det);
+    }
+    flush_counts<kAny, STATS>(a, c_nodes, c_tris, c_inst);
+}
+
+// Binary traversal, per-lane refill.  Each lane holds one ray and advances it
+// by one step per loop iteration (a node visit, an instance entry or a
+// triangle test, then the stack pops that step leaves for the next one).  A
+// warp refills its idle lanes from the work counter as soon as at least
+// `refill` of them are idle, so lanes do not wait for the slowest ray of the
+// warp; that pays when ray lengths vary widely (incoherent queries) and costs
+// a warp vote per step otherwise.
+template <int MODE, bool BRUTE, bool STATS, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
+    const uint32_t iter_cap = a.iter_cap;
+    constexpr bool kAny = (MODE == kModeAnyAbi || MODE == kModeShadowRender || MODE == kModeShadowBatch);
+    constexpr bool kBatch = (MODE == kModeClosestBatch || MODE == kModeShadowBatch);
+    __shared__ uint32_t pre[kMaxLights + 1];
+    const uint32_t n = ray_count(a, pre);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t refill = a.refill;
+    // batched closest-hit rays sit in a ring of 2^k entries from *ring_head
+    const uint32_t head = MODE == kModeClosestBatch ? *a.ring_head : 0u;
+    unsigned long long c_nodes = 0, c_tris = 0, c_inst = 0;
+
+    bool active = false, exhausted = false;
+    uint32_t i = 0, j = 0;  // ray index (dense) and queue entry
+    const float4* tlas_nodes = a.tlas_nodes;
+    const InstDev* tlas_inst = a.inst;
+    float tmin = 0.f, tmax = 0.f, dx = 0.f, dy = 0.f, dz = 0.f;
+    SpaceRay wr, cr;
+    Shear sh;
+    float best_t = 0.f, best_V = 0.f, best_W = 0.f, best_det = 1.f;
+    uint32_t best_id = kMiss, best_prim = kMiss, best_il = kMiss, best_tl = kMiss;
+    bool found = false, ok = true, in_blas = false;
+    uint32_t stack[kStack];
+    int sp = 0;
+    uint32_t ref = kNone, iter = 0, cur_id = 0, cur_leaf = 0;
+    const float4* nodes = nullptr;
+    const float4* tris = nullptr;
+
+    for (;;) {
+        // refill the idle lanes (all lanes take part: the ballot is warp-wide)
+        const uint32_t idle = __ballot_sync(0xFFFFFFFFu, !active);
+        if (!exhausted && idle != 0u && (__popc(idle) >= (int)refill || idle == 0xFFFFFFFFu)) {
+            const uint32_t k = (uint32_t)__popc(idle);
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(a.work_counter, k);
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            if (base + k >= n) exhausted = true;
+            if (!active) {
+                const uint32_t idx = base + (uint32_t)__popc(idle & ((1u << lane) - 1u));
+                if (idx < n) {
+                    i = idx;
+                    j = MODE == kModeClosestBatch ? ((head + i) & a.ring_mask) : sub_entry(a, pre, i);
+                    uint32_t tlas_root = a.tlas_root;
+                    if (kBatch) {  // the TLAS of this ray's request slot
+                        const SlotDev* S = a.slots + slot_of_px(a.payload[j].pixel);
+                        tlas_nodes = S->tlas_nodes;
+                        tlas_inst = S->inst;
+                        tlas_root = S->tlas_root;
+                    }
+                    const float4 r0 = __ldg(a.rays + 2 * (size_t)j), r1 = __ldg(a.rays + 2 * (size_t)j + 1);
+                    tmin = r0.w;
+                    tmax = r1.w;
+                    dx = r1.x;
+                    dy = r1.y;
+                    dz = r1.z;
+                    wr.ox = r0.x; wr.oy = r0.y; wr.oz = r0.z;
+                    wr.ix = safe_rcp(dx); wr.iy = safe_rcp(dy); wr.iz = safe_rcp(dz);
+                    cr = wr;
+                    best_t = tmax;
+                    best_id = best_prim = best_il = best_tl = kMiss;
+                    best_V = best_W = 0.f;
+                    best_det = 1.f;
+                    found = false;
+                    ok = true;
+                    in_blas = false;
+                    sp = 0;
+                    ref = tlas_root;
+                    nodes = tlas_nodes;
+                    iter = 0;
+                    active = true;
+                }
+            }
+        }
+        // every ray claimed above went to a lane, so a warp without one is done
+        if (__ballot_sync(0xFFFFFFFFu, active) == 0u) break;
+        if (!active) continue;
+
+        bool finished = false;
+        if (++iter > iter_cap) {
+            record_error(a.st, RG_ERR_TIMEOUT);
+            ok = false;
+            finished = true;
+        } else if (!(ref & kLeaf)) {
+            const float4* nd = nodes + 4 * (size_t)ref;
+            const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2);
+            const uint4 n3 = __ldg(reinterpret_cast<const uint4*>(nd + 3));
+            if (STATS) ++c_nodes;
+            const float tlim = kAny ? __fmul_rn(tmax, kCullSlack) : __fmul_rn(best_t, kCullSlack);
+            float tn0, tn1;
+            bool h0 = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, cr, tmin, tlim, tn0);
+            bool h1 = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, cr, tmin, tlim, tn1);
+            if (BRUTE) h0 = h1 = true;
+            if (h0 && h1) {
+                if (sp >= kStack) {
+                    record_error(a.st, RG_ERR_STACK);
+                    ok = false;
+                    finished = true;
+                } else {
+                    const bool first0 = tn0 <= tn1;
+                    stack[sp++] = first0 ? n3.y : n3.x;
+                    ref = first0 ? n3.x : n3.y;
+                }
+            } else {
+                ref = h0 ? n3.x : (h1 ? n3.y : kNone);
+            }
+        } else if (!in_blas) {
+            // instance: enter its BLAS with the object-space ray
+            const uint32_t leaf = ref & ~kLeaf;
+            const InstDev* I = tlas_inst + leaf;
+            const float4 m0 = __ldg(&I->inv[0]), m1 = __ldg(&I->inv[1]), m2 = __ldg(&I->inv[2]);
+            const float4 meta0 = __ldg(reinterpret_cast<const float4*>(&I->nodes));  // nodes, tris
+            const uint4 meta1 = __ldg(reinterpret_cast<const uint4*>(&I->root));     // root, id, mat, blas
+            if (STATS) ++c_inst;
+            const float ox = fmaf(m0.x, wr.ox, fmaf(m0.y, wr.oy, fmaf(m0.z, wr.oz, m0.w)));
+            const float oy = fmaf(m1.x, wr.ox, fmaf(m1.y, wr.oy, fmaf(m1.z, wr.oz, m1.w)));
+            const float oz = fmaf(m2.x, wr.ox, fmaf(m2.y, wr.oy, fmaf(m2.z, wr.oz, m2.w)));
+            const float ddx = fmaf(m0.x, dx, fmaf(m0.y, dy, __fmul_rn(m0.z, dz)));
+            const float ddy = fmaf(m1.x, dx, fmaf(m1.y, dy, __fmul_rn(m1.z, dz)));
+            const float ddz = fmaf(m2.x, dx, fmaf(m2.y, dy, __fmul_rn(m2.z, dz)));
+            if (sp >= kStack) {
+                record_error(a.st, RG_ERR_STACK);
+                ok = false;
+                finished = true;
+            } else {
+                cr.ox = ox; cr.oy = oy; cr.oz = oz;
+                cr.ix = safe_rcp(ddx); cr.iy = safe_rcp(ddy); cr.iz = safe_rcp(ddz);
+                sh = make_shear_div(ox, oy, oz, ddx, ddy, ddz);
+                nodes = reinterpret_cast<const float4*>(
+                    ((unsigned long long)__float_as_uint(meta0.y) << 32) | __float_as_uint(meta0.x));
+                tris = reinterpret_cast<const float4*>(
+                    ((unsigned long long)__float_as_uint(meta0.w) << 32) | __float_as_uint(meta0.z));
+                cur_id = meta1.y;
+                cur_leaf = leaf;
+                in_blas = true;
+                stack[sp++] = kMarker;
+                ref = meta1.x;
+            }
+        } else {
+            // triangle
+            const uint32_t leaf = ref & ~kLeaf;
+            const float4* tp = tris + 3 * (size_t)leaf;
+            const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+            if (STATS) ++c_tris;
+            const TriResult h = tri_test(sh, v0, v1, v2, tmin, kAny ? tmax : best_t);
+            ref = kNone;
+            if (h.hit) {
+                const uint32_t prim = __float_as_uint(v0.w);
+                if (kAny || h.t < best_t || cur_id < best_id || (cur_id == best_id && prim < best_prim)) {
+                    best_t = h.t; best_id = cur_id; best_prim = prim;
+                    best_il = cur_leaf; best_tl = leaf;
+                    best_V = h.V; best_W = h.W; best_det = h.det;
+                    found = true;
+                }
+                if (kAny) finished = true;
+            }
+        }
+        // pop what the step left (the BLAS marker brings back the world-space ray)
+        if (!finished && ref == kNone) {
+            if (sp > 0) {
+                ref = stack[--sp];
+                if (ref == kMarker) {
+                    in_blas = false;
+                    nodes = tlas_nodes;
+                    cr = wr;
+                    ref = sp > 0 ? stack[--sp] : kNone;
+                }
+            }
+            finished = ref == kNone;
+        }
+        if (finished) {
+            emit<MODE>(a, i, j, found && ok, ok, best_t, best_id, best_prim, best_il, best_tl, best_V, best_W, best_det);
+            active = false;
+        }
     }
     flush_counts<kAny, STATS>(a, c_nodes, c_tris, c_inst);
 }
@@ -398,7 +611,8 @@ template <int MODE, bool STATS>
 __global__ void __launch_bounds__(kTraceBlock) k_trace8(TraceArgs a) {
     const uint32_t iter_cap = a.iter_cap;
     constexpr bool kAny = (MODE == kModeAnyAbi || MODE == kModeShadowRender);
-    const uint32_t n = a.d_count ? *a.d_count : a.n;
+    __shared__ uint32_t pre[kMaxLights + 1];
+    const uint32_t n = ray_count(a, pre);
     const int lane = threadIdx.x & 31;
     unsigned long long c_nodes = 0, c_tris = 0, c_inst = 0;
     for (;;) {
@@ -408,8 +622,9 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace8(TraceArgs a) {
         if (base >= n) break;
         const uint32_t i = base + lane;
         if (i >= n) continue;
+        const uint32_t j = sub_entry(a, pre, i);
 
-        const float4 r0 = __ldg(a.rays + 2 * (size_t)i), r1 = __ldg(a.rays + 2 * (size_t)i + 1);
+        const float4 r0 = __ldg(a.rays + 2 * (size_t)j), r1 = __ldg(a.rays + 2 * (size_t)j + 1);
         const float tmin = r0.w, tmax = r1.w;
         SpaceRay wr;
         wr.ox = r0.x; wr.oy = r0.y; wr.oz = r0.z;
@@ -618,7 +833,7 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace8(TraceArgs a) {
             }
         }
         if (!ok) found = false;
-        emit<MODE>(a, i, found, ok, best_t, best_id, best_prim, best_il, best_tl, best_V, best_W, best_det);
+        emit<MODE>(a, i, j, found, ok, best_t, best_id, best_prim, best_il, best_tl, best_V, best_W, best_det);
     }
     flush_counts<kAny, STATS>(a, c_nodes, c_tris, c_inst);
 }
@@ -637,32 +852,56 @@ cudaError_t launch_mode8(const TraceArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int MODE, bool BRUTE, bool STATS, int BLOCK>
+template <int MODE, bool BRUTE, bool STATS, int BLOCK, bool LANE>
 cudaError_t launch_block(const TraceArgs& a, int blocks_per_sm, cudaStream_t s) {
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<MODE, BRUTE, STATS, BLOCK>, BLOCK, 0);
+        cudaError_t e = LANE ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_lane<MODE, BRUTE, STATS, BLOCK>,
+                                                                             BLOCK, 0)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_warp<MODE, BRUTE, STATS, BLOCK>,
+                                                                             BLOCK, 0);
         if (e != cudaSuccess) return e;
         if (per_sm <= 0) per_sm = 1;
     }
     const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
-    k_trace<MODE, BRUTE, STATS, BLOCK><<<device_sm_count() * b, BLOCK, 0, s>>>(a);
+    if (LANE)
+        k_trace_lane<MODE, BRUTE, STATS, BLOCK><<<device_sm_count() * b, BLOCK, 0, s>>>(a);
+    else
+        k_trace_warp<MODE, BRUTE, STATS, BLOCK><<<device_sm_count() * b, BLOCK, 0, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
 
+// Refill threshold when the shape leaves it open (0): per-lane refill (8 idle
+// lanes) for the closest-hit queries of rg_trace_rays, whose rays are often
+// incoherent; whole-warp refill elsewhere (faster on camera, secondary and
+// shadow rays and on incoherent any-hit queries, as measured on GB300).
+template <int MODE>
+constexpr int default_refill() {
+    return MODE == kModeClosestAbi ? 8 : 32;
+}
+
 // Shapes other than 128 threads are compiled for the render and batched modes
-// (the ones the autotuner sets); the rest run with 128.
+// (the ones the autotuner sets); the rest run with 128.  refill < 32 selects
+// the per-lane-refill kernel, 32 the whole-warp one.
 template <int MODE, bool BRUTE, bool STATS>
 cudaError_t launch_mode(const TraceArgs& a0, cudaStream_t s, const TraceShape& shape = TraceShape()) {
     TraceArgs a = a0;
-    a.grab = (shape.grab >= 32 && shape.grab % 32 == 0) ? (uint32_t)shape.grab : 32u;
+    const int refill = (shape.refill >= 1 && shape.refill <= 32) ? shape.refill : default_refill<MODE>();
+    a.refill = (uint32_t)refill;
     constexpr bool kTunable = !BRUTE && !STATS && MODE >= kModeClosestRender;
-    if constexpr (kTunable) {
-        if (shape.block == 64) return launch_block<MODE, BRUTE, STATS, 64>(a, shape.blocks_per_sm, s);
-        if (shape.block == 256) return launch_block<MODE, BRUTE, STATS, 256>(a, shape.blocks_per_sm, s);
+    if (refill < 32) {
+        if constexpr (kTunable) {
+            if (shape.block == 64) return launch_block<MODE, BRUTE, STATS, 64, true>(a, shape.blocks_per_sm, s);
+            if (shape.block == 256) return launch_block<MODE, BRUTE, STATS, 256, true>(a, shape.blocks_per_sm, s);
+        }
+        return launch_block<MODE, BRUTE, STATS, 128, true>(a, shape.blocks_per_sm, s);
     }
-    return launch_block<MODE, BRUTE, STATS, 128>(a, shape.blocks_per_sm, s);
+    if constexpr (kTunable) {
+        if (shape.block == 64) return launch_block<MODE, BRUTE, STATS, 64, false>(a, shape.blocks_per_sm, s);
+        if (shape.block == 256) return launch_block<MODE, BRUTE, STATS, 256, false>(a, shape.blocks_per_sm, s);
+    }
+    return launch_block<MODE, BRUTE, STATS, 128, false>(a, shape.blocks_per_sm, s);
 }
 
 }  // namespace
@@ -670,7 +909,6 @@ cudaError_t launch_mode(const TraceArgs& a0, cudaStream_t s, const TraceShape& s
 cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a0, cudaStream_t s,
                          const TraceShape& shape) {
     TraceArgs a = a0;
-    if (a.grab == 0) a.grab = 32;
     if (a.tlas_nodes8 && !brute) {
         switch (mode) {
             case kModeClosestAbi:

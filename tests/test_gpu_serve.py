@@ -177,8 +177,8 @@ def test_autotune_sets_valid_shapes_and_caches(scenes, tmp_path):
         sid = rg.rg_server_add_scene(srv, gss[1].h)
         out = rg.rg_server_autotune(srv, sid, s.camera, 480, 270, 4, scratch, cache_path=str(cache))
         for o in out:
-            assert o["block"] in (64, 128, 256) and o["grab"] % 32 == 0 and o["ms"] > 0
-        assert rg.rg_server_get_shape(srv, 0) == {k: out[0][k] for k in ("block", "blocks_per_sm", "grab")}
+            assert o["block"] in (64, 128, 256) and 1 <= o["refill"] <= 32 and o["ms"] > 0
+        assert rg.rg_server_get_shape(srv, 0) == {k: out[0][k] for k in ("block", "blocks_per_sm", "refill")}
         st = rg.rg_server_get_stats(srv)
         assert st["active"] == 0 and st["ring_rays"] == 0
         # the tuned server still renders correctly
@@ -197,8 +197,8 @@ def test_autotune_sets_valid_shapes_and_caches(scenes, tmp_path):
     try:
         sid = rg.rg_server_add_scene(srv, gss[1].h)
         again = rg.rg_server_autotune(srv, sid, s.camera, 480, 270, 4, scratch, cache_path=str(cache))
-        assert [{k: a[k] for k in ("block", "blocks_per_sm", "grab")} for a in again] == \
-               [{k: o[k] for k in ("block", "blocks_per_sm", "grab")} for o in out]
+        assert [{k: a[k] for k in ("block", "blocks_per_sm", "refill")} for a in again] == \
+               [{k: o[k] for k in ("block", "blocks_per_sm", "refill")} for o in out]
         assert again[0]["ms"] < 0
     finally:
         rg.rg_server_destroy(srv)
