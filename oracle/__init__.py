@@ -63,6 +63,7 @@ def lib():
             L.orc_render.argtypes = [P, P, u32, u32, u32, P, i64, f64, f64, i32, P, P, P]
             L.orc_reflect.argtypes = [P, P, P]
             L.orc_refract.argtypes = [P, P, i32, f64, P, P]
+            L.orc_fxaa.argtypes = [P, i32, i32, P, i32]
             _lib = L
     return _lib
 
@@ -246,3 +247,12 @@ def refract(d, nf, entering, ior):
     R = np.empty(1)
     ok = lib().orc_refract(_p(d), _p(nf), 1 if entering else 0, float(ior), _p(T), _p(R))
     return (T, float(R[0])) if ok else None
+
+
+def fxaa(rgba, threads=0):
+    """FXAA of an (h, w, 4) float32 image (the oracle's float32 restatement)."""
+    img = np.ascontiguousarray(rgba, np.float32)
+    h, w = img.shape[0], img.shape[1]
+    out = np.empty_like(img)
+    lib().orc_fxaa(_p(img), w, h, _p(out), int(threads))
+    return out

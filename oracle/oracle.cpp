@@ -30,6 +30,11 @@
 //    float32 error bound (see orc_trace).
 //  * Whitted shading with shadows, reflection and refraction (paper Sec. 2.1),
 //    recursive, per pixel, in float64.
+//  * FXAA on the rendered image (paper Sec. 2.1 names fast approximate
+//    anti-aliasing among its compute passes; the method is Lottes' FXAA,
+//    2009).  Every step is a threshold decision, so this one is float32 with
+//    the operation order written out (orc_fxaa), matching the product's
+//    decisions exactly.
 //
 // Compile with -O2 -ffp-contract=off -frounding-math (no fast-math).
 
@@ -940,6 +945,124 @@ int orc_refract(const double* d, const double* nf, int entering, double ior, dou
     if (!refract_dir(V3{d[0], d[1], d[2]}, V3{nf[0], nf[1], nf[2]}, entering != 0, ior, &t, R)) return 0;
     T[0] = t.x; T[1] = t.y; T[2] = t.z;
     return 1;
+}
+
+// ---------------------------------------------------------------- FXAA
+// Fast approximate anti-aliasing (Lottes 2009), float32, one pixel at a time,
+// clamp-to-edge addressing, pixel centres at integer coordinates:
+//  1. luma = sqrt(max(0.299 R + 0.587 G + 0.114 B, 0)) (a gamma-2 luma of the
+//     linear colour);
+//  2. skip the pixel (copy it) if the luma range of it and its 4 neighbours
+//     is below max(0.0312, 0.125 * the largest of them);
+//  3. edge orientation from second differences across the 3x3 block: the
+//     edge is horizontal if the vertical differences (weights 1,2,1) are at
+//     least the horizontal ones;
+//  4. the edge lies toward the neighbour (across the edge) with the larger
+//     luma step; the edge luma is the mean of that neighbour and the pixel;
+//  5. from half a pixel across (on the edge), step along it both ways (12
+//     steps of 1,1,1,1,1,1.5,2,2,2,2,4,8 pixels) until the bilinear luma
+//     differs from the edge luma by at least a quarter of the larger step;
+//  6. a pixel on the side whose luma change is opposite to the luma found at
+//     the nearer edge end moves by 0.5 - (distance to that end) / (edge
+//     length) across the edge; every pixel also gets the sub-pixel offset
+//     0.75 s^2 with s = smoothstep(|mean of the 3x3 (weights 2 on the 4
+//     neighbours, 1 on the corners) - luma| / range);
+//  7. the output colour is the bilinear sample at the larger of the two
+//     offsets, across the edge; alpha is kept.
+namespace fxaa {
+
+struct Img {
+    const float* p;
+    int w, h;
+    int cx(int x) const { return x < 0 ? 0 : (x >= w ? w - 1 : x); }
+    int cy(int y) const { return y < 0 ? 0 : (y >= h ? h - 1 : y); }
+    float ch(int x, int y, int c) const { return p[4 * ((size_t)cy(y) * (size_t)w + (size_t)cx(x)) + c]; }
+    float luma(int x, int y) const {
+        const float v = 0.299f * ch(x, y, 0) + 0.587f * ch(x, y, 1) + 0.114f * ch(x, y, 2);
+        return std::sqrt(v > 0.0f ? v : 0.0f);
+    }
+    // bilinear in luma (c < 0) or in channel c, at real pixel coordinates
+    float sample(float px, float py, int c) const {
+        const float fx0 = std::floor(px), fy0 = std::floor(py);
+        const float fx = px - fx0, fy = py - fy0;
+        const int x0 = (int)fx0, y0 = (int)fy0;
+        auto at = [&](int x, int y) { return c < 0 ? luma(x, y) : ch(x, y, c); };
+        const float a = at(x0, y0), b = at(x0 + 1, y0), d = at(x0, y0 + 1), e = at(x0 + 1, y0 + 1);
+        const float top = a + fx * (b - a);
+        const float bot = d + fx * (e - d);
+        return top + fy * (bot - top);
+    }
+};
+
+const float kEdgeMin = 0.0312f, kEdgeRel = 0.125f, kSubpix = 0.75f;
+const float kSteps[12] = {1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.5f, 2.0f, 2.0f, 2.0f, 2.0f, 4.0f, 8.0f};
+
+float d2(float a, float m, float b) { return std::fabs((a + b) - 2.0f * m); }
+
+void pixel(const Img& I, int x, int y, float* out) {
+    for (int c = 0; c < 4; ++c) out[c] = I.ch(x, y, c);
+    const float lM = I.luma(x, y), lN = I.luma(x, y - 1), lS = I.luma(x, y + 1);
+    const float lW = I.luma(x - 1, y), lE = I.luma(x + 1, y);
+    const float lo = std::min(lM, std::min(std::min(lN, lS), std::min(lW, lE)));
+    const float hi = std::max(lM, std::max(std::max(lN, lS), std::max(lW, lE)));
+    const float range = hi - lo;
+    if (range < std::max(kEdgeMin, hi * kEdgeRel)) return;
+    const float lNW = I.luma(x - 1, y - 1), lNE = I.luma(x + 1, y - 1);
+    const float lSW = I.luma(x - 1, y + 1), lSE = I.luma(x + 1, y + 1);
+    // 3. orientation
+    const float eH = (d2(lNW, lW, lSW) + 2.0f * d2(lN, lM, lS)) + d2(lNE, lE, lSE);
+    const float eV = (d2(lNW, lN, lNE) + 2.0f * d2(lW, lM, lE)) + d2(lSW, lS, lSE);
+    const bool horiz = eH >= eV;
+    // 4. side of the edge
+    const float l1 = horiz ? lN : lW, l2 = horiz ? lS : lE;
+    const float g1 = l1 - lM, g2 = l2 - lM;
+    const bool neg = std::fabs(g1) >= std::fabs(g2);
+    const float gs = 0.25f * std::max(std::fabs(g1), std::fabs(g2));
+    const float lLocal = neg ? 0.5f * (l1 + lM) : 0.5f * (l2 + lM);
+    const float sgn = neg ? -1.0f : 1.0f;
+    // 5. search along the edge, half a pixel across
+    const float fx = (float)x, fy = (float)y;
+    const float sx = horiz ? fx : fx + 0.5f * sgn, sy = horiz ? fy + 0.5f * sgn : fy;
+    float dist[2] = {0.0f, 0.0f}, end[2] = {0.0f, 0.0f};
+    for (int side = 0; side < 2; ++side) {
+        const float dir = side == 0 ? -1.0f : 1.0f;
+        for (int k = 0; k < 12; ++k) {
+            dist[side] = dist[side] + kSteps[k];
+            const float px = horiz ? sx + dir * dist[side] : sx;
+            const float py = horiz ? sy : sy + dir * dist[side];
+            end[side] = I.sample(px, py, -1) - lLocal;
+            if (std::fabs(end[side]) >= gs) break;
+        }
+    }
+    // 6. offsets
+    const float len = dist[0] + dist[1];
+    const bool near0 = dist[0] < dist[1];
+    const float dmin = near0 ? dist[0] : dist[1];
+    const float eNear = near0 ? end[0] : end[1];
+    const float off = ((lM < lLocal) != (eNear < 0.0f)) ? 0.5f - dmin / len : 0.0f;
+    const float sum4 = (lN + lS) + (lW + lE);
+    const float sumC = (lNW + lNE) + (lSW + lSE);
+    const float avg = (2.0f * sum4 + sumC) / 12.0f;
+    float sp = std::fabs(avg - lM) / range;
+    if (sp > 1.0f) sp = 1.0f;
+    sp = ((3.0f - 2.0f * sp) * sp) * sp;
+    const float sub = (sp * sp) * kSubpix;
+    const float f = std::max(off, sub);
+    // 7. resample across the edge
+    const float ox = horiz ? fx : fx + f * sgn, oy = horiz ? fy + f * sgn : fy;
+    for (int c = 0; c < 3; ++c) out[c] = I.sample(ox, oy, c);
+}
+
+}  // namespace fxaa
+
+// FXAA of a w x h RGBA32F image (row 0 at the top) into out (same layout).
+int orc_fxaa(const float* rgba, int w, int h, float* out, int threads) {
+    if (w <= 0 || h <= 0) return 0;
+    const fxaa::Img I{rgba, w, h};
+    parallel_for((int64_t)w * h, threads, [&](int64_t i) {
+        fxaa::pixel(I, (int)(i % w), (int)(i / w), out + 4 * i);
+    });
+    return 0;
 }
 
 }  // extern "C"
