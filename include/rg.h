@@ -177,6 +177,18 @@ rg_status rg_render(rg_scene* scene, const rg_camera* h_cam, uint32_t w, uint32_
 
 /* Wait for the scene's stream work and return the first device-side error
  * recorded since the last rg_sync (then clear it). */
+/* FXAA (Sec. 2.1: the engine's compute passes include fast approximate
+ * anti-aliasing; the method is Lottes' FXAA, 2009) of a w x h RGBA32F image,
+ * row 0 at the top, into d_out (same layout, must not alias d_in; both
+ * 16-byte aligned).  Per pixel, float32: gamma-2 luma; pixels whose local
+ * luma range is below max(0.0312, 0.125 x local max) are copied; otherwise
+ * the edge orientation, the side of the edge and its two ends (searched up
+ * to 26.5 pixels each way) give an offset across the edge, at least the
+ * sub-pixel offset 0.75 s^2 of the 3x3 contrast, and the colour is
+ * resampled bilinearly there (clamp-to-edge); alpha is copied.  Needs no
+ * scene; w or h = 0 does nothing. */
+rg_status rg_fxaa(const float* d_in, uint32_t w, uint32_t h, float* d_out, void* stream);
+
 rg_status rg_sync(rg_scene* scene);
 rg_status rg_get_stats(rg_scene* scene, rg_stats* out);
 rg_status rg_reset_stats(rg_scene* scene);

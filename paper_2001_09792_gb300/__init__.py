@@ -39,7 +39,7 @@ SYMBOLS = ["rg_scene_create", "rg_scene_destroy", "rg_blas_build", "rg_tlas_buil
            "rg_blas_export", "rg_tlas_export", "rg_wide_export", "rg_radix_sort_pairs_noalloc",
            "rg_server_create", "rg_server_destroy", "rg_server_add_scene", "rg_server_submit", "rg_server_step",
            "rg_server_drain", "rg_server_poll", "rg_server_get_stats", "rg_server_set_shape", "rg_server_get_shape",
-           "rg_server_autotune"]
+           "rg_server_autotune", "rg_fxaa"]
 RG_NOALLOC_SORT_MAX_PAIRS = 262144
 RG_SERVER_MAX_SLOTS = 32
 RG_SERVER_MAX_PIXELS = 1 << 23
@@ -154,6 +154,7 @@ def lib():
             "rg_server_set_shape": [P, u32, P],
             "rg_server_get_shape": [P, u32, P],
             "rg_server_autotune": [P, P, ctypes.c_char_p, u32, P],
+            "rg_fxaa": [P, u32, u32, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -303,6 +304,21 @@ def rg_render(scene, camera, width, height, max_depth, out=None, stream=None):
     cam = camera if isinstance(camera, rg_camera) else make_camera(camera)
     _check(lib().rg_render(scene, ctypes.byref(cam), width, height, max_depth, ctypes.c_void_p(out.data_ptr()),
                            _stream(stream)))
+    return out
+
+
+def rg_fxaa(image, out=None, stream=None):
+    """FXAA of an (h, w, 4) float32 CUDA image into `out` (allocated if None)."""
+    torch = _torch()
+    if image.dim() != 3 or image.shape[2] != 4 or image.dtype != torch.float32 or not image.is_cuda \
+            or not image.is_contiguous():
+        raise ValueError("image must be a contiguous (h, w, 4) float32 CUDA tensor")
+    if out is None:
+        out = torch.empty_like(image)
+    if out.shape != image.shape or out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous():
+        raise ValueError("out must match the image")
+    h, w = image.shape[0], image.shape[1]
+    _check(lib().rg_fxaa(ctypes.c_void_p(image.data_ptr()), w, h, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
     return out
 
 

@@ -691,6 +691,19 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
     return RG_OK;
 }
 
+rg_status rg_fxaa(const float* d_in, uint32_t w, uint32_t h, float* d_out, void* stream) {
+    if (w == 0 || h == 0) return RG_OK;
+    if (!d_in || !d_out) return fail(RG_ERR_INVALID_ARG, "NULL image");
+    if (d_in == d_out) return fail(RG_ERR_INVALID_ARG, "FXAA is out-of-place: input and output alias");
+    if ((uint64_t)w * h > (1ull << 28) || w > (1u << 24) || h > (1u << 24))
+        return fail(RG_ERR_INVALID_ARG, "image too large");
+    if (reinterpret_cast<uintptr_t>(d_in) % 16 || reinterpret_cast<uintptr_t>(d_out) % 16)
+        return fail(RG_ERR_INVALID_ARG, "images must be 16-byte aligned");
+    RG_CK(launch_fxaa(reinterpret_cast<const float4*>(d_in), w, h, reinterpret_cast<float4*>(d_out),
+                      static_cast<cudaStream_t>(stream)));
+    return RG_OK;
+}
+
 rg_status rg_sync(rg_scene* s) {
     rg_status r;
     if ((r = check_scene(s))) return r;

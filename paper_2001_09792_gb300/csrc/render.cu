@@ -352,6 +352,126 @@ __global__ void k_raygen_batch(const RaygenReq* __restrict__ reqs, const uint32_
     }
 }
 
+// ---------------------------------------------------------------- FXAA
+// Fast approximate anti-aliasing (Lottes 2009) of an RGBA32F image, one
+// thread per pixel, clamp-to-edge addressing, pixel centres at integer
+// coordinates.  Every step is a float32 threshold decision; this file is
+// compiled without FMA contraction so each operation rounds on its own.
+//  1. luma = sqrt(max(0.299 R + 0.587 G + 0.114 B, 0));
+//  2. pixels whose 5-point luma range is below max(0.0312, 0.125 max) are copied;
+//  3. the edge is horizontal if the vertical second differences of the 3x3
+//     block (weights 1, 2, 1) are at least the horizontal ones;
+//  4. it lies toward the neighbour across it with the larger luma step; the
+//     edge luma is the mean of that neighbour and the pixel;
+//  5. half a pixel across, the search steps along the edge both ways (1, 1,
+//     1, 1, 1, 1.5, 2, 2, 2, 2, 4, 8 pixels) until the bilinear luma leaves
+//     the edge luma by a quarter of the larger step;
+//  6. offset across the edge: 0.5 - (distance to the nearer end) / (edge
+//     length) for a pixel whose luma change is opposite to the one at that
+//     end, else 0; at least the sub-pixel offset 0.75 s^2, s the smoothstep
+//     of the contrast of the 3x3 mean (neighbours weighted 2, corners 1);
+//  7. output = bilinear colour at that offset; alpha kept.
+struct FxaaImg {
+    const float4* p;
+    int w, h;
+    __device__ __forceinline__ float4 at(int x, int y) const {
+        x = min(max(x, 0), w - 1);
+        y = min(max(y, 0), h - 1);
+        return __ldg(p + (size_t)y * (size_t)w + (size_t)x);
+    }
+    __device__ __forceinline__ float luma(int x, int y) const {
+        const float4 c = at(x, y);
+        const float v = 0.299f * c.x + 0.587f * c.y + 0.114f * c.z;
+        return sqrtf(v > 0.0f ? v : 0.0f);
+    }
+    __device__ __forceinline__ float luma_at(float px, float py) const {
+        const float fx0 = floorf(px), fy0 = floorf(py);
+        const float fx = px - fx0, fy = py - fy0;
+        const int x0 = (int)fx0, y0 = (int)fy0;
+        const float a = luma(x0, y0), b = luma(x0 + 1, y0), d = luma(x0, y0 + 1), e = luma(x0 + 1, y0 + 1);
+        const float top = a + fx * (b - a), bot = d + fx * (e - d);
+        return top + fy * (bot - top);
+    }
+    __device__ __forceinline__ float3 color_at(float px, float py) const {
+        const float fx0 = floorf(px), fy0 = floorf(py);
+        const float fx = px - fx0, fy = py - fy0;
+        const int x0 = (int)fx0, y0 = (int)fy0;
+        const float4 a = at(x0, y0), b = at(x0 + 1, y0), d = at(x0, y0 + 1), e = at(x0 + 1, y0 + 1);
+        float3 r;
+        float top = a.x + fx * (b.x - a.x), bot = d.x + fx * (e.x - d.x);
+        r.x = top + fy * (bot - top);
+        top = a.y + fx * (b.y - a.y);
+        bot = d.y + fx * (e.y - d.y);
+        r.y = top + fy * (bot - top);
+        top = a.z + fx * (b.z - a.z);
+        bot = d.z + fx * (e.z - d.z);
+        r.z = top + fy * (bot - top);
+        return r;
+    }
+};
+
+__device__ __forceinline__ float second_diff(float a, float m, float b) { return fabsf((a + b) - 2.0f * m); }
+
+__global__ void __launch_bounds__(256) k_fxaa(FxaaImg I, float4* __restrict__ out) {
+    const int x = blockIdx.x * 16 + (threadIdx.x & 15), y = blockIdx.y * 16 + (threadIdx.x >> 4);
+    if (x >= I.w || y >= I.h) return;
+    const float4 c = I.at(x, y);
+    float4 o = c;
+    const float lM = I.luma(x, y), lN = I.luma(x, y - 1), lS = I.luma(x, y + 1);
+    const float lW = I.luma(x - 1, y), lE = I.luma(x + 1, y);
+    const float lo = fminf(lM, fminf(fminf(lN, lS), fminf(lW, lE)));
+    const float hi = fmaxf(lM, fmaxf(fmaxf(lN, lS), fmaxf(lW, lE)));
+    const float range = hi - lo;
+    if (!(range < fmaxf(0.0312f, hi * 0.125f))) {
+        const float lNW = I.luma(x - 1, y - 1), lNE = I.luma(x + 1, y - 1);
+        const float lSW = I.luma(x - 1, y + 1), lSE = I.luma(x + 1, y + 1);
+        const float eH = (second_diff(lNW, lW, lSW) + 2.0f * second_diff(lN, lM, lS)) + second_diff(lNE, lE, lSE);
+        const float eV = (second_diff(lNW, lN, lNE) + 2.0f * second_diff(lW, lM, lE)) + second_diff(lSW, lS, lSE);
+        const bool horiz = eH >= eV;
+        const float l1 = horiz ? lN : lW, l2 = horiz ? lS : lE;
+        const float g1 = l1 - lM, g2 = l2 - lM;
+        const bool neg = fabsf(g1) >= fabsf(g2);
+        const float gs = 0.25f * fmaxf(fabsf(g1), fabsf(g2));
+        const float edge = neg ? 0.5f * (l1 + lM) : 0.5f * (l2 + lM);
+        const float sgn = neg ? -1.0f : 1.0f;
+        const float fx = (float)x, fy = (float)y;
+        const float sx = horiz ? fx : fx + 0.5f * sgn, sy = horiz ? fy + 0.5f * sgn : fy;
+        constexpr float kStep[12] = {1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.5f, 2.0f, 2.0f, 2.0f, 2.0f, 4.0f, 8.0f};
+        float dist[2], endl[2];
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const float dir = side == 0 ? -1.0f : 1.0f;
+            float d = 0.0f, e = 0.0f;
+            for (int k = 0; k < 12; ++k) {
+                d = d + kStep[k];
+                const float px = horiz ? sx + dir * d : sx;
+                const float py = horiz ? sy : sy + dir * d;
+                e = I.luma_at(px, py) - edge;
+                if (fabsf(e) >= gs) break;
+            }
+            dist[side] = d;
+            endl[side] = e;
+        }
+        const float len = dist[0] + dist[1];
+        const bool near0 = dist[0] < dist[1];
+        const float dmin = near0 ? dist[0] : dist[1];
+        const float e_near = near0 ? endl[0] : endl[1];
+        const float off = ((lM < edge) != (e_near < 0.0f)) ? 0.5f - __fdiv_rn(dmin, len) : 0.0f;
+        const float sum4 = (lN + lS) + (lW + lE);
+        const float sumc = (lNW + lNE) + (lSW + lSE);
+        const float avg = __fdiv_rn(2.0f * sum4 + sumc, 12.0f);
+        float sp = __fdiv_rn(fabsf(avg - lM), range);
+        if (sp > 1.0f) sp = 1.0f;
+        sp = ((3.0f - 2.0f * sp) * sp) * sp;
+        const float f = fmaxf(off, (sp * sp) * 0.75f);
+        const float3 r = I.color_at(horiz ? fx : fx + f * sgn, horiz ? fy + f * sgn : fy);
+        o.x = r.x;
+        o.y = r.y;
+        o.z = r.z;
+    }
+    out[(size_t)y * (size_t)I.w + (size_t)x] = o;
+}
+
 }  // namespace
 
 cudaError_t launch_raygen(const CameraDev& cam, uint32_t w, uint32_t h, float4* rays, Payload* payload,
@@ -380,6 +500,14 @@ cudaError_t launch_raygen_batch(const RaygenReq* reqs, const uint32_t* n_reqs, u
 
 cudaError_t launch_shade_batch(const ShadeArgs& a, cudaStream_t s) {
     k_shade_batch<<<device_sm_count() * 8, kShadeBlock, 0, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fxaa(const float4* in, uint32_t w, uint32_t h, float4* out, cudaStream_t s) {
+    if (w == 0 || h == 0) return cudaSuccess;
+    FxaaImg I{in, (int)w, (int)h};
+    k_fxaa<<<dim3((w + 15) / 16, (h + 15) / 16), 256, 0, s>>>(I, out);
     count_launches(1);
     return cudaGetLastError();
 }
