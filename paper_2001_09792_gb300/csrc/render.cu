@@ -55,16 +55,34 @@ __device__ __forceinline__ void camera_ray(const CameraDev& cam, uint32_t w, uin
     dir = make_float4(d.x, d.y, d.z, __int_as_float(0x7F800000));
 }
 
+// Pixel of primary ray i: rays run over 8x4 tiles (a warp's 32 rays cover
+// one tile, which keeps their paths together longer than a 32x1 strip).
+// The image is cut into bands of 4 rows (the last band may be thinner),
+// each band into blocks of 8 columns (the last may be narrower), pixels row
+// by row inside a block; a bijection of [0, w h) onto the pixels.
+__device__ __forceinline__ void tile_pixel(uint32_t i, uint32_t w, uint32_t h, uint32_t& x, uint32_t& y) {
+    const uint32_t band = i / (4u * w);
+    const uint32_t rows = min(4u, h - 4u * band);
+    const uint32_t local = i - band * 4u * w;
+    const uint32_t blk = local / (8u * rows);
+    const uint32_t bw = min(8u, w - 8u * blk);
+    const uint32_t rem = local - blk * 8u * rows;
+    y = 4u * band + rem / bw;
+    x = 8u * blk + rem % bw;
+}
+
 __global__ void k_raygen(CameraDev cam, uint32_t w, uint32_t h, float4* __restrict__ rays,
                          Payload* __restrict__ payload) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= w * h) return;
+    uint32_t x, y;
+    tile_pixel(i, w, h, x, y);
     float4 o, d;
-    camera_ray(cam, w, h, i % w, i / w, o, d);
+    camera_ray(cam, w, h, x, y, o, d);
     rays[2 * (size_t)i] = o;
     rays[2 * (size_t)i + 1] = d;
     Payload p;
-    p.pixel = i;
+    p.pixel = y * w + x;
     p.r = p.g = p.b = 1.0f;
     payload[i] = p;
 }
@@ -338,17 +356,19 @@ __global__ void k_raygen_batch(const RaygenReq* __restrict__ reqs, const uint32_
         const uint32_t i = r - q.offset;
         const uint32_t w = q.w, h = q.h;
         if (i >= w * h) continue;  // not a ray of any request (host offsets are dense)
-        const uint32_t x = i % w, y = i / w;
+        uint32_t x, y;
+        tile_pixel(i, w, h, x, y);
         float4 o, d;
         camera_ray(q.cam, w, h, x, y, o, d);
         const uint32_t e = (gen_base + r) & ring_mask;
         rays[2 * (size_t)e] = o;
         rays[2 * (size_t)e + 1] = d;
+        const uint32_t pix = y * w + x;
         Payload p;
-        p.pixel = pack_pixel(i, 1u, q.slot);
+        p.pixel = pack_pixel(pix, 1u, q.slot);
         p.r = p.g = p.b = 1.0f;
         payload[e] = p;
-        reinterpret_cast<float4*>(q.image)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        reinterpret_cast<float4*>(q.image)[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 

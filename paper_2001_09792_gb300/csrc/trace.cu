@@ -32,8 +32,9 @@ constexpr int kTraceBlock = 128;
 constexpr float kIze = 1.0f + 2.0f * (3.0f * 5.9604644775390625e-08f) / (1.0f - 3.0f * 5.9604644775390625e-08f);
 constexpr float kCullSlack = 1.0f + 1.0f / 4096.0f;
 
-// 1/d with IEEE semantics: a zero component gives +-inf.
-__device__ __forceinline__ float safe_rcp(float d) { return __fdiv_rn(1.0f, d); }
+// 1/d correctly rounded (the same value as the IEEE division 1/d): a zero
+// component gives +-inf.
+__device__ __forceinline__ float safe_rcp(float d) { return __frcp_rn(d); }
 
 struct SpaceRay {
     float ox, oy, oz;
@@ -96,7 +97,7 @@ __device__ __forceinline__ Shear make_shear_div(float ox, float oy, float oz, fl
     float dky = ky == 0 ? dx : (ky == 1 ? dy : dz);
     s.Sx = __fdiv_rn(dkx, dkz);
     s.Sy = __fdiv_rn(dky, dkz);
-    s.Sz = __fdiv_rn(1.0f, dkz);
+    s.Sz = __frcp_rn(dkz);  // = 1/d_kz, correctly rounded
     s.kx = kx;
     s.ky = ky;
     s.kz = kz;
