@@ -309,7 +309,9 @@ def run_native(args, world, rank, local):
                     "inst_per_ray": round(cst["inst_entries"] / cr, 3), "avg_launch_ms": round(launch_ms, 4),
                     "trace_share_of_frame": round(st["trace_ms"] / sum(ms), 3),
                     "shadow_share_of_frame": round(st["any_ms"] / sum(ms), 3),
-                    "shadow_nodes_per_ray": round(cst["any_node_visits"] / max(cst["shadow_rays"], 1), 2)}
+                    "shadow_nodes_per_ray": round(cst["any_node_visits"] / max(cst["shadow_rays"], 1), 2),
+                    "shadow_inst_per_ray": round(cst["any_inst_entries"] / max(cst["shadow_rays"], 1), 3),
+                    "shadow_tris_per_ray": round(cst["any_tri_tests"] / max(cst["shadow_rays"], 1), 2)}
         ms_sorted = sorted(ms)
         out = {
             "metric": METRIC,

@@ -50,7 +50,9 @@ def lib():
             L.orc_stable_sort.argtypes = [P, u32, P]
             L.orc_karras.argtypes = [P, u32, P, P, P]
             L.orc_range_boxes.argtypes = [P, u32, P, P, P]
-            L.orc_instance_prep.argtypes = [P, u32, P, P, P]
+            L.orc_instance_prep.argtypes = [P, u32, P, P, P, P]
+            L.orc_bound_r2.argtypes = [P, u32, P]
+            L.orc_bound_r2.restype = ctypes.c_float
             L.orc_scene_new.restype = P
             L.orc_scene_new.argtypes = []
             L.orc_scene_free.argtypes = [P]
@@ -123,14 +125,25 @@ def range_boxes(lohi_sorted, first, last):
     return out
 
 
-def instance_prep(M, obj_box):
-    """(Minv float64 (n,3,4), world box float32 (n,6), rc)."""
+def bound_r2(vtx, obj_box):
+    """Upward-rounded bound on the squared distance of the vertices from the
+    centre of the object box (float32)."""
+    vtx = _c(vtx, np.float32).reshape(-1, 3)
+    obj_box = _c(obj_box, np.float32).reshape(6)
+    return np.float32(lib().orc_bound_r2(_p(vtx), vtx.shape[0], _p(obj_box)))
+
+
+def instance_prep(M, obj_box, obj_r2=None):
+    """(Minv float64 (n,3,4), world box float32 (n,6), rc).  World box: Arvo's
+    box of the object box, intersected with the transformed bounding sphere's
+    box when obj_r2 (per instance) is given."""
     M = _c(M, np.float32).reshape(-1, 12)
     obj_box = _c(obj_box, np.float32).reshape(-1, 6)
     n = M.shape[0]
+    r2 = None if obj_r2 is None else _c(obj_r2, np.float32).reshape(n)
     Minv = np.empty((n, 12), np.float64)
     wbox = np.empty((n, 6), np.float32)
-    rc = lib().orc_instance_prep(_p(M), n, _p(obj_box), _p(Minv), _p(wbox))
+    rc = lib().orc_instance_prep(_p(M), n, _p(obj_box), None if r2 is None else _p(r2), _p(Minv), _p(wbox))
     return Minv.reshape(n, 3, 4), wbox, rc
 
 

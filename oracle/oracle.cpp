@@ -726,7 +726,36 @@ int orc_range_boxes(const float* lohi_sorted, uint32_t n, const int32_t* first, 
 // singular) and the world box of the object box by Arvo's method,
 //   lo_i = (((min(M_i0 a_0, M_i0 b_0) + min(M_i1 a_1, M_i1 b_1)) + min(M_i2 a_2, M_i2 b_2)) + t_i)
 // with every float32 product and sum rounded toward -inf (hi: max, toward +inf).
-int orc_instance_prep(const float* M, uint32_t n, const float* obj_box, double* Minv, float* wbox) {
+// Bound on the squared distance of a mesh's vertices from its root box centre
+// c = (lo + hi) * 0.5 (float32): the largest over the vertices of
+// (|dx|^2 + |dy|^2) + |dz|^2, every operation rounded upward.
+float orc_bound_r2(const float* vtx, uint32_t nv, const float* box) {
+    const int old = std::fegetround();
+    float c[3];
+    for (int i = 0; i < 3; ++i) c[i] = (box[i] + box[3 + i]) * 0.5f;
+    std::fesetround(FE_UPWARD);
+    volatile float best = 0.0f;
+    for (uint32_t v = 0; v < nv; ++v) {
+        volatile float e[3];
+        for (int i = 0; i < 3; ++i) {
+            const float x = vtx[3 * (size_t)v + i];
+            e[i] = x >= c[i] ? x - c[i] : c[i] - x;
+        }
+        volatile float sx = e[0] * e[0], sy = e[1] * e[1], sz = e[2] * e[2];
+        volatile float d2 = sx + sy;
+        d2 = d2 + sz;
+        if (d2 > best) best = d2;
+    }
+    std::fesetround(old);
+    return best;
+}
+
+// Instance prep: float64 inverse, and the world box of the instance: Arvo's
+// box of the transformed object box, intersected (when obj_r2 is given) with
+// the box of the transformed bounding sphere (centre c of the object box,
+// radius sqrt(r2)): A c + t -/+ r |row_i(A)|, with outward rounding.
+int orc_instance_prep(const float* M, uint32_t n, const float* obj_box, const float* obj_r2, double* Minv,
+                      float* wbox) {
     int rc = 0;
     const int old = std::fegetround();
     for (uint32_t k = 0; k < n; ++k) {
@@ -755,8 +784,38 @@ int orc_instance_prep(const float* M, uint32_t n, const float* obj_box, double* 
             }
             volatile float hi = S + M[12 * k + 4 * i + 3];
             std::fesetround(old);
-            wbox[6 * (size_t)k + i] = lo;
-            wbox[6 * (size_t)k + 3 + i] = hi;
+            float blo = lo, bhi = hi;
+            if (obj_r2) {
+                const float* row = M + 12 * (size_t)k + 4 * i;
+                float c[3];
+                for (int j = 0; j < 3; ++j) c[j] = (a[j] + a[3 + j]) * 0.5f;
+                std::fesetround(FE_DOWNWARD);
+                volatile float cl = row[0] * c[0];
+                volatile float t1 = row[1] * c[1], t2 = row[2] * c[2];
+                cl = cl + t1;
+                cl = cl + t2;
+                cl = cl + row[3];
+                std::fesetround(FE_UPWARD);
+                volatile float ch = row[0] * c[0];
+                volatile float u1 = row[1] * c[1], u2 = row[2] * c[2];
+                ch = ch + u1;
+                ch = ch + u2;
+                ch = ch + row[3];
+                volatile float q0 = row[0] * row[0], q1 = row[1] * row[1], q2 = row[2] * row[2];
+                volatile float nn = q0 + q1;
+                nn = nn + q2;
+                volatile float norm = std::sqrt((float)nn);
+                volatile float r = std::sqrt(obj_r2[k]);
+                volatile float R = r * norm;
+                volatile float shi = ch + R;
+                std::fesetround(FE_DOWNWARD);
+                volatile float slo = cl - R;
+                std::fesetround(old);
+                blo = std::max((float)lo, (float)slo);
+                bhi = std::min((float)hi, (float)shi);
+            }
+            wbox[6 * (size_t)k + i] = blo;
+            wbox[6 * (size_t)k + 3 + i] = bhi;
         }
     }
     std::fesetround(old);

@@ -447,6 +447,7 @@ rg_status rg_blas_build(rg_scene* s, const float* d_vtx, uint32_t nv, const uint
              RG_CK(launch_blas_leaves_refit(d_vtx, d_idx, static_cast<uint32_t*>(perm), static_cast<float*>(lohi), nt,
                                             static_cast<uint32_t*>(parents), b.nodes, static_cast<uint32_t*>(fl), b.tris,
                                             s->d_blas.p + id, s->st, st));
+             RG_CK(launch_bound_sphere(d_vtx, nv, s->d_blas.p + id, st));
              if (wide) {
                  WideOut out{b.nodes8, b.src8, b.item_src8, b.counts8, static_cast<uint2*>(tasks)};
                  const float* leaf_box = reinterpret_cast<const float*>(reinterpret_cast<const char*>(s->d_blas.p + id) +

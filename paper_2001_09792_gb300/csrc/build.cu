@@ -401,6 +401,28 @@ __global__ void k_blas_leaves_refit(const float* __restrict__ vtx, const uint32_
 
 // check_blas: a refit; the BLAS id of instance k must equal the one stored in
 // tmp[k] by the build (read before tmp[k] is overwritten by the same thread).
+// Bounding sphere: the largest upward-rounded squared distance of a vertex
+// from the root box centre, reduced per warp, one atomicMax per warp.
+__global__ void k_bound_sphere(const float* __restrict__ vtx, uint32_t nv, BlasDev* blas) {
+    float c[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) c[q] = __fmul_rn(__fadd_rn(blas->lo[q], blas->hi[q]), 0.5f);
+    uint32_t best = 0;  // bits of a non-negative float: integer order = float order
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
+        float e[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float x = vtx[3 * (size_t)v + q];
+            e[q] = x >= c[q] ? __fsub_ru(x, c[q]) : __fsub_ru(c[q], x);
+        }
+        const float d2 = __fadd_ru(__fadd_ru(__fmul_ru(e[0], e[0]), __fmul_ru(e[1], e[1])), __fmul_ru(e[2], e[2]));
+        best = max(best, __float_as_uint(d2));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) best = max(best, __shfl_xor_sync(0xFFFFFFFFu, best, off));
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(&blas->r2_bits, best);
+}
+
 __global__ void k_instance_prep(const rg_instance* __restrict__ in, uint32_t n, const BlasDev* __restrict__ blas,
                                 uint32_t nblas, InstDev* tmp, float* __restrict__ wbox, int* cb_ord, bool check_blas,
                                 DevStatus* st) {
@@ -467,6 +489,22 @@ __global__ void k_instance_prep(const rg_instance* __restrict__ in, uint32_t n, 
             }
             lo = __fadd_rd(lo, m[4 * r + 3]);
             hi = __fadd_ru(hi, m[4 * r + 3]);
+            // intersect with the box of the transformed bounding sphere:
+            // A c + t -/+ r |row_r(A)|, outward rounded (a rotation leaves a
+            // sphere's box unchanged, where it inflates the Arvo box)
+            const float* row = m + 4 * r;
+            float cx[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) cx[q] = __fmul_rn(__fadd_rn(B.lo[q], B.hi[q]), 0.5f);
+            float cl = __fadd_rd(__fadd_rd(__fadd_rd(__fmul_rd(row[0], cx[0]), __fmul_rd(row[1], cx[1])),
+                                           __fmul_rd(row[2], cx[2])), row[3]);
+            float ch = __fadd_ru(__fadd_ru(__fadd_ru(__fmul_ru(row[0], cx[0]), __fmul_ru(row[1], cx[1])),
+                                           __fmul_ru(row[2], cx[2])), row[3]);
+            const float norm = __fsqrt_ru(__fadd_ru(__fadd_ru(__fmul_ru(row[0], row[0]), __fmul_ru(row[1], row[1])),
+                                                    __fmul_ru(row[2], row[2])));
+            const float R = __fmul_ru(__fsqrt_ru(__uint_as_float(B.r2_bits)), norm);
+            lo = fmaxf(lo, __fsub_rd(cl, R));
+            hi = fminf(hi, __fadd_ru(ch, R));
             wbox[6 * (size_t)k + r] = lo;
             wbox[6 * (size_t)k + 3 + r] = hi;
             c[r] = f2ord(centroid(lo, hi));
@@ -592,6 +630,14 @@ cudaError_t launch_blas_leaves_refit(const float* vtx, const uint32_t* idx, cons
                                      float4* tris, BlasDev* blas_out, DevStatus* st, cudaStream_t s) {
     k_blas_leaves_refit<<<grid_for(n), kBlock, 0, s>>>(vtx, idx, perm, lohi, n, parents, nodes, flags, tris, blas_out,
                                                        st);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bound_sphere(const float* vtx, uint32_t nv, BlasDev* blas, cudaStream_t s) {
+    if (nv == 0) return cudaSuccess;
+    const uint32_t blocks = (uint32_t)min((nv + 255u) / 256u, (uint32_t)device_sm_count() * 4u);
+    k_bound_sphere<<<blocks, 256, 0, s>>>(vtx, nv, blas);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -50,8 +50,12 @@ struct __align__(16) BlasDev {
     float hi[3];
     const float4* nodes8;   // compressed 8-wide BVH (null if not built)
     const float4* tris8;    // its triangles, in wide-leaf order
+    // bound on |v - c|^2 over the vertices, c = (lo + hi) * 0.5, every
+    // operation rounded upward (bits of a non-negative float, atomicMax-able)
+    uint32_t r2_bits;
+    uint32_t pad[3];
 };
-static_assert(sizeof(BlasDev) == 64, "BLAS descriptor is 64 B");
+static_assert(sizeof(BlasDev) == 80, "BLAS descriptor is 80 B");
 
 // ---------------------------------------------------------------- wide BVH
 // Compressed 8-wide node, 80 B (five 16 B words):
@@ -168,6 +172,9 @@ cudaError_t launch_karras(const void* keys, uint32_t n, int key_bits, uint32_t* 
 cudaError_t launch_blas_leaves_refit(const float* vtx, const uint32_t* idx, const uint32_t* perm, const float* lohi,
                                      uint32_t n, const uint32_t* parents, float4* nodes, uint32_t* flags,
                                      float4* tris, BlasDev* blas_out, DevStatus* st, cudaStream_t s);
+// Bounding sphere of a mesh about its root box centre (after the BLAS refit
+// wrote the root box): blas->r2_bits = max over the vertices.
+cudaError_t launch_bound_sphere(const float* vtx, uint32_t nv, BlasDev* blas, cudaStream_t s);
 cudaError_t launch_instance_prep(const rg_instance* in, uint32_t n, const BlasDev* blas, uint32_t nblas,
                                  InstDev* tmp, float* wbox, int* cb_ord, bool check_blas, DevStatus* st,
                                  cudaStream_t s);

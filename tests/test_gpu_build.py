@@ -170,13 +170,20 @@ def blas_root_box(v, i):
     return np.r_[lohi[:, :3].min(0), lohi[:, 3:].max(0)].astype(np.float32)
 
 
+def object_bounds(s):
+    """Per instance: its mesh's root box and bounding-sphere bound r2."""
+    boxes = [blas_root_box(*m) for m in s.meshes]
+    r2 = [oracle.bound_r2(m[0], b) for m, b in zip(s.meshes, boxes)]
+    return np.stack([boxes[m] for m in s.mesh_id]), np.array([r2[m] for m in s.mesh_id], np.float32)
+
+
 @pytest.mark.parametrize("n_inst", [1, 2, 3, 300, 4099])
 def test_tlas_matches_reference(n_inst):
     s = small_instanced_scene(n_inst, n_inst)
     with rg.GpuScene(s) as gs:
         ex = rg.rg_tlas_export(gs.h, n_inst)
-    obj_box = np.stack([blas_root_box(*s.meshes[m]) for m in s.mesh_id])
-    Minv, wbox, rc = oracle.instance_prep(s.M, obj_box)
+    obj_box, obj_r2 = object_bounds(s)
+    Minv, wbox, rc = oracle.instance_prep(s.M, obj_box, obj_r2)
     assert rc == 0
     assert np.array_equal(ex["wbox"], wbox)
     # float32 inverse = float32 rounding of the float64 inverse (within one ulp)
@@ -207,10 +214,10 @@ def test_tlas_refit_boxes_match_reference():
         rg.rg_sync(gs.h)
         ex = rg.rg_tlas_export(gs.h, 257)
     assert np.array_equal(ex["order"], order0)            # topology unchanged
-    obj_box = np.stack([blas_root_box(*s.meshes[m]) for m in s.mesh_id])
-    _, wbox, _ = oracle.instance_prep(M2, obj_box)
+    obj_box, obj_r2 = object_bounds(s)
+    _, wbox, _ = oracle.instance_prep(M2, obj_box, obj_r2)
     assert np.array_equal(ex["wbox"], wbox)
-    codes, _ = oracle.morton(oracle.instance_prep(s.M, obj_box)[1], 10)
+    codes, _ = oracle.morton(oracle.instance_prep(s.M, obj_box, obj_r2)[1], 10)
     first, last, split = oracle.karras(codes[order0])
     lo0, hi0, lo1, hi1, ch = node_fields(ex["nodes"])
     ws = wbox[order0]

@@ -169,6 +169,47 @@ def test_instance_prep_inverse_and_arvo_box():
         assert np.all(lo - wbox[k, :3] < 1e-5 * ext) and np.all(wbox[k, 3:] - hi < 1e-5 * ext)
 
 
+def test_bounding_sphere_bound():
+    """r2 bounds |v - c|^2 from above, c the root box centre: exact for the
+    cube's corners (0.75 = 3 x 0.25), and for the 5-radius icosphere within a
+    few ulps above its largest |v|^2."""
+    v, _ = g.cube_mesh(0.5)
+    box = np.r_[v.min(0), v.max(0)].astype(np.float32)
+    assert oracle.bound_r2(v, box) == np.float32(0.75)
+    v, _ = g.make_mesh("ico", 3)
+    box = np.r_[v.min(0), v.max(0)].astype(np.float32)
+    c = (box[:3].astype(np.float64) + box[3:]) / 2
+    exact = ((v.astype(np.float64) - c) ** 2).sum(1).max()
+    r2 = float(oracle.bound_r2(v, box))
+    assert exact <= r2 <= exact * (1 + 1e-6)
+
+
+def test_instance_box_takes_the_sphere_where_tighter():
+    """A sphere of radius 5 at the origin, scaled x2 and turned 45 degrees
+    about z: the rotated sphere's box is t +- 10 on every axis (a rotation
+    leaves it alone), where Arvo's box of the rotated cube [-5,5]^3 is
+    t +- 10 sqrt 2 along x and y and t +- 10 along z.  The intersection is the
+    sphere's box; it still holds every transformed vertex."""
+    v, _ = g.make_mesh("ico", 3)
+    box = np.r_[v.min(0), v.max(0)].astype(np.float32)
+    r2 = oracle.bound_r2(v, box)
+    t = np.array([5.0, -2.0, 3.0])
+    M = g.affine(g.axis_angle(np.array([0.0, 0.0, 1.0]), math.radians(45)), t, 2.0)[None]
+    _, arvo, _ = oracle.instance_prep(M, box[None])
+    _, both, _ = oracle.instance_prep(M, box[None], [r2])
+    np.testing.assert_allclose(arvo[0, :2], t[:2] - 10 * math.sqrt(2), atol=1e-4)
+    np.testing.assert_allclose(both[0, :3], t - 10, atol=1e-4)
+    np.testing.assert_allclose(both[0, 3:], t + 10, atol=1e-4)
+    assert np.all(both[0, :3] >= arvo[0, :3]) and np.all(both[0, 3:] <= arvo[0, 3:])
+    w = v.astype(np.float64) @ M[0, :, :3].astype(np.float64).T + M[0, :, 3]
+    assert np.all(w >= both[0, :3]) and np.all(w <= both[0, 3:])
+    # an axis-aligned stretch: Arvo's box is exact there and wins on the long axis
+    S = g.affine(np.diag([3.0, 1.0, 1.0]), [0, 0, 0])[None]
+    _, a2, _ = oracle.instance_prep(S, box[None])
+    _, b2, _ = oracle.instance_prep(S, box[None], [r2])
+    assert np.array_equal(a2, b2)
+
+
 def test_singular_instance_rejected():
     M = np.zeros((1, 3, 4), np.float32)
     _, _, rc = oracle.instance_prep(M, np.zeros((1, 6), np.float32))
