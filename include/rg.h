@@ -201,9 +201,10 @@ const char* rg_last_error(void);
  * the triangle's vertices. */
 rg_status rg_tri_bounds(const float* d_vtx, uint32_t nv, const uint32_t* d_idx, uint32_t nt, float* d_lohi,
                         void* stream);
-/* Morton code of each box centroid c = (lo+hi)*0.5: per axis s = 2^b/(cmax-cmin)
- * (q = 0 on an axis with cmax == cmin), q = clamp(floor((c-cmin)*s), 0, 2^b-1),
- * bits interleaved x (most significant), y, z.  bits = 10 writes uint32 codes,
+/* Morton code of each box centroid c = (lo+hi)*0.5 on one cubic grid: a single
+ * scale s = 2^b / max over the axes of (cmax-cmin) (q = 0 on an axis with
+ * cmax == cmin), q = clamp(floor((c-cmin)*s), 0, 2^b-1), bits interleaved x
+ * (most significant), y, z.  bits = 10 writes uint32 codes,
  * bits = 21 uint64 codes.  d_cbounds (6 floats, may be NULL) receives the
  * centroid bounds {cmin.xyz, cmax.xyz}. */
 rg_status rg_morton_codes(const float* d_lohi, uint32_t n, uint32_t bits, void* d_codes, float* d_cbounds,

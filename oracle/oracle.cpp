@@ -14,7 +14,8 @@
 //    Karras hierarchy, box refit, instance boxes) are restated here in their
 //    plain definitions, in float32 where the product computes in float32, so
 //    that their results can be compared bit for bit:
-//      - Morton codes: quantised centroids, bits interleaved x,y,z (MSB first).
+//      - Morton codes: centroids quantised on one cubic grid (a single scale
+//        from the largest centroid extent), bits interleaved x,y,z (MSB first).
 //      - Sort: std::stable_sort (not a radix sort).
 //      - Hierarchy: top-down recursive split at the highest differing bit of
 //        (key, index) (Karras 2012, Sec. 4 defines the same tree bottom-up).
@@ -648,19 +649,21 @@ int orc_morton(const float* lohi, uint32_t n, int bits, uint64_t* codes, float* 
             cmin[a] = std::min(cmin[a], ca);
             cmax[a] = std::max(cmax[a], ca);
         }
+    // one scale 2^bits / (largest centroid extent) for all three axes
     const float full = (float)(1u << bits);
     const float qmax = (float)((1u << bits) - 1u);
-    float scale[3];
+    float ext = 0.0f;
     for (int a = 0; a < 3; ++a) {
-        volatile float ext = cmax[a] - cmin[a];
-        scale[a] = ext > 0.0f ? full / ext : 0.0f;
+        volatile float e = cmax[a] - cmin[a];
+        if (cmax[a] > cmin[a] && e > ext) ext = e;
     }
+    volatile float scale = ext > 0.0f ? full / ext : 0.0f;
     for (uint32_t i = 0; i < n; ++i) {
         uint64_t q[3];
         for (int a = 0; a < 3; ++a) {
             if (!(cmax[a] > cmin[a])) { q[a] = 0; continue; }
             volatile float off = c[3 * (size_t)i + a] - cmin[a];
-            volatile float f = off * scale[a];
+            volatile float f = off * scale;
             float fl = std::floor((float)f);
             fl = std::min(std::max(fl, 0.0f), qmax);
             q[a] = (uint64_t)fl;

@@ -106,15 +106,19 @@ template <int BITS>
 __global__ void k_morton(const float* __restrict__ lohi, uint32_t n, const int* __restrict__ cb_ord,
                          void* __restrict__ codes, uint32_t* __restrict__ vals, float* cb_out) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    float cmin[3], cmax[3], scale[3];
+    // one scale for all axes (a cubic grid over the centroid box): a flat
+    // mesh keeps its thin axis thin instead of being split across it first
+    float cmin[3], cmax[3];
     const float full = (float)(1u << BITS);
     const float qmax = (float)((1u << BITS) - 1u);
+    float ext = 0.0f;
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         cmin[ax] = ord2f(cb_ord[ax]);
         cmax[ax] = ord2f(cb_ord[3 + ax]);
-        scale[ax] = cmax[ax] > cmin[ax] ? __fdiv_rn(full, __fsub_rn(cmax[ax], cmin[ax])) : 0.0f;
+        if (cmax[ax] > cmin[ax]) ext = fmaxf(ext, __fsub_rn(cmax[ax], cmin[ax]));
     }
+    const float scale = ext > 0.0f ? __fdiv_rn(full, ext) : 0.0f;
     if (cb_out && i == 0) {
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
@@ -131,7 +135,7 @@ __global__ void k_morton(const float* __restrict__ lohi, uint32_t n, const int* 
             continue;
         }
         float c = centroid(lohi[6 * (size_t)i + ax], lohi[6 * (size_t)i + 3 + ax]);
-        float f = floorf(__fmul_rn(__fsub_rn(c, cmin[ax]), scale[ax]));
+        float f = floorf(__fmul_rn(__fsub_rn(c, cmin[ax]), scale));
         f = fminf(fmaxf(f, 0.0f), qmax);
         q[ax] = (uint32_t)f;
     }

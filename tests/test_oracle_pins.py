@@ -323,14 +323,16 @@ def test_brute_force_first_principles_tiny():
 
 # ----------------------------------------------------------- LBVH reference steps
 
-def test_morton_hand_worked():
-    rows = read_golden("morton_hand.txt")
+@pytest.mark.parametrize("name,bounds", [("morton_hand.txt", [0, 0, 0, 1, 1, 1]),
+                                         ("morton_hand_flat.txt", [0, 0, 0, 2, 1, 0.5])])
+def test_morton_hand_worked(name, bounds):
+    rows = read_golden(name)
     pts = np.array([[float(x) for x in r[1:4]] for r in rows], np.float32)
     want = np.array([int(r[4]) for r in rows], np.uint64)
     lohi = np.c_[pts, pts]
     codes, cb = oracle.morton(lohi, 10)
     assert np.array_equal(codes, want)
-    assert np.array_equal(cb, np.array([0, 0, 0, 1, 1, 1], np.float32))
+    assert np.array_equal(cb, np.array(bounds, np.float32))
 
 
 def test_morton_63_bit_and_degenerate_axis():
