@@ -59,7 +59,7 @@ __device__ __forceinline__ float nan_max(float a, float b) {
 }
 
 __device__ __forceinline__ bool slab(float lx, float ly, float lz, float hx, float hy, float hz, const SpaceRay& r,
-                                     float tmin, float tlim, float& tnear) {
+                                     float tmin, float tlim, float& tnear, float& tfar) {
     float t0x = __fmul_rn(__fsub_rn(lx, r.ox), r.ix), t1x = __fmul_rn(__fsub_rn(hx, r.ox), r.ix);
     float t0y = __fmul_rn(__fsub_rn(ly, r.oy), r.iy), t1y = __fmul_rn(__fsub_rn(hy, r.oy), r.iy);
     float t0z = __fmul_rn(__fsub_rn(lz, r.oz), r.iz), t1z = __fmul_rn(__fsub_rn(hz, r.oz), r.iz);
@@ -67,7 +67,17 @@ __device__ __forceinline__ bool slab(float lx, float ly, float lz, float hx, flo
     float tf = fminf(fminf(nan_max(t0x, t1x), nan_max(t0y, t1y)), nan_max(t0z, t1z));
     tf = fminf(__fmul_rn(tf, kIze), tlim);
     tnear = tn;
+    tfar = tf;
     return tn <= tf;
+}
+
+// Which of two hit children a ray visits first.  Closest hit: the nearer
+// entry.  Any hit: the child whose box covers the longer stretch of the ray's
+// segment (more likely to hold an occluder; on the medium frame's shadow
+// rays this halves the nodes visited against nearest-first).
+template <bool ANY>
+__device__ __forceinline__ bool visit_first0(float tn0, float tf0, float tn1, float tf1) {
+    return ANY ? (tf0 - tn0) >= (tf1 - tn1) : tn0 <= tn1;
 }
 
 __device__ __forceinline__ float sel(float4 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
@@ -309,13 +319,14 @@ __global__ void __launch_bounds__(BLOCK) k_trace_warp(TraceArgs a) {
                 const uint4 n3 = __ldg(reinterpret_cast<const uint4*>(nd + 3));
                 if (STATS) ++c_nodes;
                 const float tlim = kAny ? __fmul_rn(tmax, kCullSlack) : __fmul_rn(best_t, kCullSlack);
-                float tn0, tn1;
-                bool h0 = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, cr, tmin, tlim, tn0);
-                bool h1 = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, cr, tmin, tlim, tn1);
+                float tn0, tn1, tf0, tf1;
+                bool h0 = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, cr, tmin, tlim, tn0, tf0);
+                bool h1 = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, cr, tmin, tlim, tn1, tf1);
                 if (BRUTE) h0 = h1 = true;
                 if (h0 && h1) {
-                    uint32_t nearc = tn0 <= tn1 ? n3.x : n3.y;
-                    uint32_t farc = tn0 <= tn1 ? n3.y : n3.x;
+                    const bool f0 = visit_first0<kAny>(tn0, tf0, tn1, tf1);
+                    uint32_t nearc = f0 ? n3.x : n3.y;
+                    uint32_t farc = f0 ? n3.y : n3.x;
                     if (sp >= kStack) {
                         record_error(a.st, RG_ERR_STACK);
                         ok = false;
@@ -492,9 +503,9 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
             const uint4 n3 = __ldg(reinterpret_cast<const uint4*>(nd + 3));
             if (STATS) ++c_nodes;
             const float tlim = kAny ? __fmul_rn(tmax, kCullSlack) : __fmul_rn(best_t, kCullSlack);
-            float tn0, tn1;
-            bool h0 = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, cr, tmin, tlim, tn0);
-            bool h1 = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, cr, tmin, tlim, tn1);
+            float tn0, tn1, tf0, tf1;
+            bool h0 = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, cr, tmin, tlim, tn0, tf0);
+            bool h1 = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, cr, tmin, tlim, tn1, tf1);
             if (BRUTE) h0 = h1 = true;
             if (h0 && h1) {
                 if (sp >= kStack) {
@@ -502,7 +513,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
                     ok = false;
                     finished = true;
                 } else {
-                    const bool first0 = tn0 <= tn1;
+                    const bool first0 = visit_first0<kAny>(tn0, tf0, tn1, tf1);
                     stack[sp++] = first0 ? n3.y : n3.x;
                     ref = first0 ? n3.x : n3.y;
                 }
