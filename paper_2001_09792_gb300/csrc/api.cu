@@ -470,6 +470,24 @@ rg_status rg_blas_build(rg_scene* s, const float* d_vtx, uint32_t nv, const uint
 static rg_status tlas_common(rg_scene* s, const rg_instance* d_inst, uint32_t n, cudaStream_t st, bool refit) {
     rg_status r;
     TempAlloc tmp(st);
+    if (n <= kTlasSmallMax) {
+        // one single-block launch for the whole build or refit
+        void* ranges = nullptr;
+        if (!refit && s->wide && n > 1 && (r = tmp.get(&ranges, (size_t)(n - 1) * 8, "ranges"))) return r;
+        RG_CK(launch_tlas_small(d_inst, n, s->d_blas.p, (uint32_t)s->blas.size(), s->inst_tmp.p, s->wbox.p, refit,
+                                s->tlas_nodes.p, s->perm.p, s->parents.p, s->flags.p, static_cast<uint32_t*>(ranges),
+                                s->inst.p, s->st, st));
+        if (s->wide) {
+            WideOut out{s->tlas8.p, s->src8.p, s->item_src8.p, s->counts8.p, s->tasks8.p};
+            if (refit)
+                RG_CK(launch_wide_refit(s->tlas_nodes.p, s->wbox.p, s->perm.p, n, s->inst.p, s->inst8.p, s->d_blas.p,
+                                        out, s->st, st));
+            else
+                RG_CK(launch_collapse(s->tlas_nodes.p, static_cast<uint32_t*>(ranges), n, s->wbox.p, nullptr, nullptr,
+                                      s->inst.p, s->inst8.p, s->d_blas.p, out, s->st, st, 1u));
+        }
+        return RG_OK;
+    }
     void* cb;
     if ((r = tmp.get(&cb, 64, "centroid bounds"))) return r;
     if (!refit) RG_CK(launch_init_bounds(static_cast<int*>(cb), st));

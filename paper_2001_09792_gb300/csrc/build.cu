@@ -102,46 +102,68 @@ __global__ void k_centroid_bounds(const float* __restrict__ lohi, uint32_t n, in
     reduce_bounds(cb_ord, c[0], c[1], c[2], valid);
 }
 
+// Morton quantisation on one cubic grid over the centroid box: a single scale
+// for all axes, so a flat mesh keeps its thin axis thin instead of being
+// split across it first.
+struct MortonGrid {
+    float cmin[3], cmax[3], scale;
+};
+
+__device__ __forceinline__ MortonGrid morton_grid(const int* cb_ord, int bits) {
+    MortonGrid g;
+    const float full = (float)(1u << bits);
+    float ext = 0.0f;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        g.cmin[ax] = ord2f(cb_ord[ax]);
+        g.cmax[ax] = ord2f(cb_ord[3 + ax]);
+        if (g.cmax[ax] > g.cmin[ax]) ext = fmaxf(ext, __fsub_rn(g.cmax[ax], g.cmin[ax]));
+    }
+    g.scale = ext > 0.0f ? __fdiv_rn(full, ext) : 0.0f;
+    return g;
+}
+
+// Quantised centroid of box b (lo.xyz, hi.xyz).
+template <int BITS>
+__device__ __forceinline__ void morton_q(const MortonGrid& g, const float* b, uint32_t* q) {
+    const float qmax = (float)((1u << BITS) - 1u);
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        if (!(g.cmax[ax] > g.cmin[ax])) {
+            q[ax] = 0;
+            continue;
+        }
+        float c = centroid(b[ax], b[3 + ax]);
+        float f = floorf(__fmul_rn(__fsub_rn(c, g.cmin[ax]), g.scale));
+        f = fminf(fmaxf(f, 0.0f), qmax);
+        q[ax] = (uint32_t)f;
+    }
+}
+
+__device__ __forceinline__ uint32_t morton30(const MortonGrid& g, const float* b) {
+    uint32_t q[3];
+    morton_q<10>(g, b, q);
+    return (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+}
+
 template <int BITS>
 __global__ void k_morton(const float* __restrict__ lohi, uint32_t n, const int* __restrict__ cb_ord,
                          void* __restrict__ codes, uint32_t* __restrict__ vals, float* cb_out) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    // one scale for all axes (a cubic grid over the centroid box): a flat
-    // mesh keeps its thin axis thin instead of being split across it first
-    float cmin[3], cmax[3];
-    const float full = (float)(1u << BITS);
-    const float qmax = (float)((1u << BITS) - 1u);
-    float ext = 0.0f;
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-        cmin[ax] = ord2f(cb_ord[ax]);
-        cmax[ax] = ord2f(cb_ord[3 + ax]);
-        if (cmax[ax] > cmin[ax]) ext = fmaxf(ext, __fsub_rn(cmax[ax], cmin[ax]));
-    }
-    const float scale = ext > 0.0f ? __fdiv_rn(full, ext) : 0.0f;
+    const MortonGrid g = morton_grid(cb_ord, BITS);
     if (cb_out && i == 0) {
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
-            cb_out[ax] = cmin[ax];
-            cb_out[3 + ax] = cmax[ax];
+            cb_out[ax] = g.cmin[ax];
+            cb_out[3 + ax] = g.cmax[ax];
         }
     }
     if (i >= n) return;
-    uint32_t q[3];
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-        if (!(cmax[ax] > cmin[ax])) {
-            q[ax] = 0;
-            continue;
-        }
-        float c = centroid(lohi[6 * (size_t)i + ax], lohi[6 * (size_t)i + 3 + ax]);
-        float f = floorf(__fmul_rn(__fsub_rn(c, cmin[ax]), scale));
-        f = fminf(fmaxf(f, 0.0f), qmax);
-        q[ax] = (uint32_t)f;
-    }
     if (BITS == 10) {
-        static_cast<uint32_t*>(codes)[i] = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+        static_cast<uint32_t*>(codes)[i] = morton30(g, lohi + 6 * (size_t)i);
     } else {
+        uint32_t q[3];
+        morton_q<21>(g, lohi + 6 * (size_t)i, q);
         static_cast<uint64_t*>(codes)[i] = (spread21(q[0]) << 2) | (spread21(q[1]) << 1) | spread21(q[2]);
     }
     if (vals) vals[i] = i;
@@ -285,11 +307,13 @@ __device__ __forceinline__ int delta(const K* __restrict__ k, int64_t n, int64_t
     return (int)(8 * sizeof(K)) + __clz((uint32_t)i ^ (uint32_t)j);
 }
 
+// Internal node i of the Karras hierarchy over n sorted keys: its children
+// (bit 31 marks a leaf) into child_base[i * stride], its key range into
+// ranges (optional), its children's parent entries (optional).
 template <class K>
-__global__ void k_karras(const K* __restrict__ keys, uint32_t n, uint32_t* __restrict__ child_base, int stride,
-                         uint32_t* __restrict__ parents, uint32_t* __restrict__ ranges) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)n - 1) return;
+__device__ __forceinline__ void karras_node(const K* __restrict__ keys, uint32_t n, int64_t i,
+                                            uint32_t* __restrict__ child_base, int stride, uint32_t* __restrict__ parents,
+                                            uint32_t* __restrict__ ranges) {
     const int64_t N = n;
     int d = (delta(keys, N, i, i + 1) - delta(keys, N, i, i - 1)) >= 0 ? 1 : -1;
     int dmin = delta(keys, N, i, i - d);
@@ -322,6 +346,14 @@ __global__ void k_karras(const K* __restrict__ keys, uint32_t n, uint32_t* __res
         parents[(right & kLeaf) ? (size_t)(n - 1) + (right & ~kLeaf) : right] = (uint32_t)i;
         if (i == 0) parents[0] = kNone;
     }
+}
+
+template <class K>
+__global__ void k_karras(const K* __restrict__ keys, uint32_t n, uint32_t* __restrict__ child_base, int stride,
+                         uint32_t* __restrict__ parents, uint32_t* __restrict__ ranges) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n - 1) return;
+    karras_node(keys, n, i, child_base, stride, parents, ranges);
 }
 
 // ---------------------------------------------------------------- refit
@@ -427,13 +459,12 @@ __global__ void k_bound_sphere(const float* __restrict__ vtx, uint32_t nv, BlasD
     if ((threadIdx.x & 31) == 0 && best) atomicMax(&blas->r2_bits, best);
 }
 
-__global__ void k_instance_prep(const rg_instance* __restrict__ in, uint32_t n, const BlasDev* __restrict__ blas,
-                                uint32_t nblas, InstDev* tmp, float* __restrict__ wbox, int* cb_ord, bool check_blas,
-                                DevStatus* st) {
-    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    bool valid = k < n;
-    int c[3] = {0, 0, 0};
-    if (valid) {
+// Instance k: float64 inverse, InstDev record into tmp[k], world box into
+// wbox[k]; c receives the box centroid as ordered ints.
+__device__ __forceinline__ void instance_prep_one(const rg_instance* __restrict__ in, uint32_t k,
+                                                  const BlasDev* __restrict__ blas, uint32_t nblas, InstDev* tmp,
+                                                  float* __restrict__ wbox, bool check_blas, DevStatus* st, int* c) {
+    {
         const rg_instance& I = in[k];
         float m[12];
 #pragma unroll
@@ -514,6 +545,15 @@ __global__ void k_instance_prep(const rg_instance* __restrict__ in, uint32_t n, 
             c[r] = f2ord(centroid(lo, hi));
         }
     }
+}
+
+__global__ void k_instance_prep(const rg_instance* __restrict__ in, uint32_t n, const BlasDev* __restrict__ blas,
+                                uint32_t nblas, InstDev* tmp, float* __restrict__ wbox, int* cb_ord, bool check_blas,
+                                DevStatus* st) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = k < n;
+    int c[3] = {0, 0, 0};
+    if (valid) instance_prep_one(in, k, blas, nblas, tmp, wbox, check_blas, st, c);
     if (cb_ord) reduce_bounds(cb_ord, c[0], c[1], c[2], valid);
 }
 
@@ -529,6 +569,99 @@ __global__ void k_tlas_leaves_refit(const InstDev* __restrict__ tmp, const float
     for (int a = 0; a < 6; ++a) box[a] = wbox[6 * (size_t)k + a];
     float root_box[6];
     climb(j, n, box, parents, nodes, flags, root_box, st);
+}
+
+// The whole TLAS build (or refit) of up to kTlasSmallMax instances in one
+// block, thread k = instance k: instance prep, centroid bounds, Morton codes,
+// a stable sort, the Karras hierarchy and the bottom-up box refit.  Same
+// per-element code and the same results as the multi-kernel path; a small
+// TLAS is otherwise bound by the issue of its 17 launches.  The sort is an
+// LSD sort by single bits (30 stable splits, each a block-wide prefix count
+// of zeros), which starting from instance order gives the (key, index) order.
+__global__ void __launch_bounds__(kTlasSmallMax) k_tlas_small(const rg_instance* __restrict__ in, uint32_t n,
+                                                              const BlasDev* __restrict__ blas, uint32_t nblas,
+                                                              InstDev* tmp, float* wbox, bool refit, float4* nodes,
+                                                              uint32_t* perm, uint32_t* parents, uint32_t* flags,
+                                                              uint32_t* ranges, InstDev* inst_out, DevStatus* st) {
+    __shared__ int s_cb[6];
+    __shared__ uint32_t s_key[kTlasSmallMax], s_val[kTlasSmallMax];
+    __shared__ uint32_t s_warp[32], s_total;
+    const uint32_t t = threadIdx.x, lane = t & 31u, warp = t >> 5;
+    const uint32_t n_warps = blockDim.x >> 5;
+    const bool valid = t < n;
+    if (t < 3) s_cb[t] = f2ord(__int_as_float(0x7F800000));
+    else if (t < 6) s_cb[t] = f2ord(__int_as_float(0xFF800000));
+    __syncthreads();
+    int c[3] = {INT_MAX, INT_MAX, INT_MAX};
+    if (valid) instance_prep_one(in, t, blas, nblas, tmp, wbox, refit, st, c);
+    if (!refit) {
+        int mn[3] = {c[0], c[1], c[2]}, mx[3] = {valid ? c[0] : INT_MIN, valid ? c[1] : INT_MIN, valid ? c[2] : INT_MIN};
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                mn[a] = min(mn[a], __shfl_xor_sync(0xFFFFFFFFu, mn[a], off));
+                mx[a] = max(mx[a], __shfl_xor_sync(0xFFFFFFFFu, mx[a], off));
+            }
+        if (lane == 0 && mn[0] != INT_MAX)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                atomicMin(s_cb + a, mn[a]);
+                atomicMax(s_cb + 3 + a, mx[a]);
+            }
+        __syncthreads();
+        const MortonGrid g = morton_grid(s_cb, 10);
+        if (valid) {
+            float b[6];
+#pragma unroll
+            for (int a = 0; a < 6; ++a) b[a] = wbox[6 * (size_t)t + a];
+            s_key[t] = morton30(g, b);
+            s_val[t] = t;
+        }
+        // stable LSD sort by single bits
+        for (int bit = 0; bit < 30; ++bit) {
+            __syncthreads();
+            const uint32_t k = valid ? s_key[t] : 0u, v = valid ? s_val[t] : 0u;
+            const bool zero = valid && !((k >> bit) & 1u);
+            const uint32_t zb = __ballot_sync(0xFFFFFFFFu, zero);
+            if (lane == 0) s_warp[warp] = __popc(zb);
+            __syncthreads();
+            if (warp == 0) {
+                const uint32_t x = lane < n_warps ? s_warp[lane] : 0u;
+                uint32_t inc = x;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, off);
+                    if ((int)lane >= off) inc += y;
+                }
+                if (lane < n_warps) s_warp[lane] = inc - x;
+                if (lane == 31) s_total = inc;
+            }
+            __syncthreads();
+            // (every read of s_key in this pass came before the barrier above)
+            const uint32_t zeros_before = s_warp[warp] + __popc(zb & ((1u << lane) - 1u));
+            const uint32_t pos = zero ? zeros_before : s_total + (t - zeros_before);
+            if (valid) {
+                s_key[pos] = k;
+                s_val[pos] = v;
+            }
+        }
+        __syncthreads();
+        if (valid) perm[t] = s_val[t];
+        if (t + 1 < n) karras_node(s_key, n, t, reinterpret_cast<uint32_t*>(nodes) + 12, 16, parents, ranges);
+    }
+    if (t + 1 < n) flags[t] = 0;
+    __syncthreads();
+    __threadfence();
+    if (valid) {
+        const uint32_t k = perm[t];
+        inst_out[t] = tmp[k];
+        float box[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) box[a] = wbox[6 * (size_t)k + a];
+        float root_box[6];
+        climb(t, n, box, parents, nodes, flags, root_box, st);
+    }
 }
 
 inline unsigned grid_for(size_t n, int block = kBlock) { return (unsigned)((n + block - 1) / block); }
@@ -658,6 +791,17 @@ cudaError_t launch_tlas_leaves_refit(const InstDev* tmp, const float* wbox, cons
                                      const uint32_t* parents, float4* nodes, uint32_t* flags, InstDev* inst_out,
                                      DevStatus* st, cudaStream_t s) {
     k_tlas_leaves_refit<<<grid_for(n), kBlock, 0, s>>>(tmp, wbox, perm, n, parents, nodes, flags, inst_out, st);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tlas_small(const rg_instance* in, uint32_t n, const BlasDev* blas, uint32_t nblas, InstDev* tmp,
+                              float* wbox, bool refit, float4* nodes, uint32_t* perm, uint32_t* parents,
+                              uint32_t* flags, uint32_t* ranges, InstDev* inst_out, DevStatus* st, cudaStream_t s) {
+    if (n == 0 || n > kTlasSmallMax) return cudaErrorInvalidValue;
+    const uint32_t threads = (n + 31u) & ~31u;
+    k_tlas_small<<<1, threads, 0, s>>>(in, n, blas, nblas, tmp, wbox, refit, nodes, perm, parents, flags, ranges,
+                                       inst_out, st);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -178,6 +178,13 @@ cudaError_t launch_bound_sphere(const float* vtx, uint32_t nv, BlasDev* blas, cu
 cudaError_t launch_instance_prep(const rg_instance* in, uint32_t n, const BlasDev* blas, uint32_t nblas,
                                  InstDev* tmp, float* wbox, int* cb_ord, bool check_blas, DevStatus* st,
                                  cudaStream_t s);
+// The whole TLAS build (refit = false) or refit of n <= kTlasSmallMax
+// instances in one single-block launch; same results as instance prep +
+// bounds + Morton + sort + Karras + leaves refit.  ranges may be NULL.
+constexpr uint32_t kTlasSmallMax = 1024;
+cudaError_t launch_tlas_small(const rg_instance* in, uint32_t n, const BlasDev* blas, uint32_t nblas, InstDev* tmp,
+                              float* wbox, bool refit, float4* nodes, uint32_t* perm, uint32_t* parents,
+                              uint32_t* flags, uint32_t* ranges, InstDev* inst_out, DevStatus* st, cudaStream_t s);
 cudaError_t launch_tlas_leaves_refit(const InstDev* tmp, const float* wbox, const uint32_t* perm, uint32_t n,
                                      const uint32_t* parents, float4* nodes, uint32_t* flags, InstDev* inst_out,
                                      DevStatus* st, cudaStream_t s);
