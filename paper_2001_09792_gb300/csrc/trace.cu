@@ -239,8 +239,8 @@ __device__ __forceinline__ void flush_counts(const TraceArgs& a, unsigned long l
 
 // Binary traversal, whole-warp refill: a warp takes 32 rays from the work
 // counter, each lane runs its ray to completion (one loop iteration per node
-// visit, stack pop, instance entry or triangle test), and the warp takes the
-// next 32 when all its lanes are done.  Best when the rays of a warp take
+// visit, instance entry or triangle test; a stack pop joins the step that
+// follows it), and the warp takes the next 32 when all its lanes are done.  Best when the rays of a warp take
 // similar work (camera and secondary rays).
 template <int MODE, bool BRUTE, bool STATS, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_trace_warp(TraceArgs a) {
@@ -303,15 +303,16 @@ __global__ void __launch_bounds__(BLOCK) k_trace_warp(TraceArgs a) {
                 break;
             }
             if (ref == kNone) {
+                // pop, and go on with the popped entry in this iteration
                 if (sp == 0) break;
                 ref = stack[--sp];
                 if (ref == kMarker) {
                     in_blas = false;
                     nodes = tlas_nodes;
                     cr = wr;
-                    ref = kNone;
+                    if (sp == 0) break;
+                    ref = stack[--sp];  // a TLAS entry: markers never follow each other
                 }
-                continue;
             }
             if (!(ref & kLeaf)) {
                 const float4* nd = nodes + 4 * (size_t)ref;
