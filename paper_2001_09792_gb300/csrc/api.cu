@@ -169,7 +169,8 @@ struct rg_scene {
     DevBuf<HitDev> hits;
     DevBuf<uint32_t> counters;     // [0] closest work, [1] next count, [2] shadow work, [3] unused,
                                    // [4 + l] shadow rays toward light l
-    uint32_t* h_counts = nullptr;  // pinned, 4 entries
+    uint32_t* h_counts = nullptr;  // pinned, 16 entries
+    cudaEvent_t count_ev = nullptr;  // the next level's ray count has reached h_counts
     // statistics and timing
     uint64_t closest_rays = 0, shadow_rays_host = 0;
     std::vector<EventPair> events, free_events;
@@ -309,6 +310,7 @@ rg_status rg_scene_create(rg_scene** out, const rg_scene_desc* desc) {
     }
     cudaError_t e = cudaMemset(s->st, 0, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&s->h_counts), 16 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->count_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaFree(s->st);
         s->counters.release();
@@ -350,6 +352,7 @@ rg_status rg_scene_destroy(rg_scene* s) {
     s->counters.release();
     if (s->st) cudaFree(s->st);
     if (s->h_counts) cudaFreeHost(s->h_counts);
+    if (s->count_ev) cudaEventDestroy(s->count_ev);
     for (EventPair& ep : s->events) {
         cudaEventDestroy(ep.a);
         cudaEventDestroy(ep.b);
@@ -633,34 +636,53 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const uint32_t N = w * h;
     const uint32_t L = s->n_lights;
+    // Per depth level: closest-hit traversal, shading, shadow traversal.  The
+    // host learns each level's ray count one step late: the count is copied
+    // back while the GPU runs the shadow rays of this level and the
+    // closest-hit rays of the next (whose traversal reads the count on the
+    // device), so the stream never waits for the host.  Counters: one block
+    // per level, [0] closest work, [1] rays of the next level, [2] shadow
+    // work, [4 + l] shadow rays toward light l.
+    const size_t CB = 4 + kMaxLights;
+    if ((r = s->counters.ensure(CB * ((size_t)max_depth + 1), "counters"))) return r;
     if ((r = s->q_rays[0].ensure(2 * (size_t)N, "ray queue"))) return r;
     if ((r = s->q_pay[0].ensure(N, "payload queue"))) return r;
+    if ((r = s->hits.ensure(N, "hit queue"))) return r;
+    RG_CK(cudaMemsetAsync(s->counters.p, 0, CB * ((size_t)max_depth + 1) * sizeof(uint32_t), st));
     RG_CK(cudaMemsetAsync(d_rgba, 0, (size_t)N * 16, st));
     CameraDev cd;
     std::memcpy(&cd, cam, sizeof cd);
     RG_CK(launch_raygen(cd, w, h, s->q_rays[0].p, s->q_pay[0].p, st));
+
+    // closest-hit traversal of level d (count on the host, or on the device)
+    auto trace_closest = [&](int q, uint32_t n_host, const uint32_t* d_count, uint32_t* c) -> rg_status {
+        TraceArgs a = base_trace_args(s, true);
+        a.rays = s->q_rays[q].p;
+        a.n = n_host;
+        a.d_count = d_count;
+        a.hits_render = s->hits.p;
+        a.work_counter = c + 0;
+        EventPair* ev;
+        rg_status rr;
+        if ((rr = event_begin(s, 0, st, &ev))) return rr;
+        RG_CK(launch_trace(kModeClosestRender, false, s->desc.flags & RG_SCENE_COUNT, a, st));
+        return event_end(s, st);
+    };
+
     uint32_t n = N;
     int cur = 0;
-    for (uint32_t depth = 1; depth <= max_depth && n > 0; ++depth) {
+    if ((r = trace_closest(cur, N, nullptr, s->counters.p))) return r;
+    for (uint32_t depth = 1; depth <= max_depth; ++depth) {
         const bool last = depth == max_depth;
-        if ((r = s->hits.ensure(n, "hit queue"))) return r;
+        uint32_t* c = s->counters.p + CB * (depth - 1);
+        s->closest_rays += n;
+        // room for what this level's shading writes (growing a buffer waits for the device)
         if (L && (r = s->s_rays.ensure(2 * (size_t)n * L, "shadow queue"))) return r;
         if (L && (r = s->s_pay.ensure((size_t)n * L, "shadow payload"))) return r;
         if (!last) {
             if ((r = s->q_rays[1 - cur].ensure(4 * (size_t)n, "ray queue"))) return r;
             if ((r = s->q_pay[1 - cur].ensure(2 * (size_t)n, "payload queue"))) return r;
         }
-        RG_CK(cudaMemsetAsync(s->counters.p, 0, (4 + L) * sizeof(uint32_t), st));
-        TraceArgs a = base_trace_args(s, true);
-        a.rays = s->q_rays[cur].p;
-        a.n = n;
-        a.hits_render = s->hits.p;
-        a.work_counter = s->counters.p + 0;
-        EventPair* ev;
-        if ((r = event_begin(s, 0, st, &ev))) return r;
-        RG_CK(launch_trace(kModeClosestRender, false, s->desc.flags & RG_SCENE_COUNT, a, st));
-        if ((r = event_end(s, st))) return r;
-        s->closest_rays += n;
 
         ShadeArgs sa{};
         sa.rays = s->q_rays[cur].p;
@@ -680,32 +702,41 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
         sa.image = d_rgba;
         sa.next_rays = last ? nullptr : s->q_rays[1 - cur].p;
         sa.next_payload = last ? nullptr : s->q_pay[1 - cur].p;
-        sa.next_count = s->counters.p + 1;
+        sa.next_count = c + 1;
         sa.shadow_rays = s->s_rays.p;
         sa.shadow_payload = s->s_pay.p;
-        sa.shadow_count = s->counters.p + 4;
+        sa.shadow_count = c + 4;
         sa.shadow_stride = n;
         sa.st = s->st;
         RG_CK(launch_shade(sa, n, st));
+        if (!last) {
+            RG_CK(cudaMemcpyAsync(s->h_counts, c + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            RG_CK(cudaEventRecord(s->count_ev, st));
+        }
 
         if (L) {
             TraceArgs b = base_trace_args(s, true);
             b.rays = s->s_rays.p;
-            b.sub_counts = s->counters.p + 4;
+            b.sub_counts = c + 4;
             b.n_sub = L;
             b.sub_stride = n;
             b.payload = s->s_pay.p;
             b.image = d_rgba;
-            b.work_counter = s->counters.p + 2;
+            b.work_counter = c + 2;
+            EventPair* ev;
             if ((r = event_begin(s, 1, st, &ev))) return r;
             RG_CK(launch_trace(kModeShadowRender, false, s->desc.flags & RG_SCENE_COUNT, b, st));
             if ((r = event_end(s, st))) return r;
         }
         if (last) break;
-        RG_CK(cudaMemcpyAsync(s->h_counts, s->counters.p + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-        RG_CK(cudaStreamSynchronize(st));
+        // the next level's rays (at most 2 per ray of this level) are traced
+        // before the host knows how many there are
+        if ((r = s->hits.ensure(2 * (size_t)n, "hit queue"))) return r;
+        if ((r = trace_closest(1 - cur, 0, c + 1, c + CB))) return r;
+        RG_CK(cudaEventSynchronize(s->count_ev));
         n = s->h_counts[0];
         cur = 1 - cur;
+        if (n == 0) break;
     }
     return RG_OK;
 }
