@@ -286,9 +286,10 @@ rg_status rg_radix_sort_pairs_noalloc(const void* d_keys, const uint32_t* d_vals
  *
  * Admission is by free ring memory: a request of w*h pixels is admitted, in
  * arrival order, when a request slot is free (at most RG_SERVER_MAX_SLOTS in
- * flight) and the rays in the ring plus its w*h primary rays fit in half the
- * ring; the other half takes the rays steps spawn (at most two per traced
- * ray).  A step traces up to min(batch_rays, shadow capacity / max lights)
+ * flight) and the rays in the ring plus its w*h primary rays fit in the
+ * admission bound (admit_rays, by default one batch; at most half the ring:
+ * the other half takes the rays steps spawn, at most two per traced ray).  A
+ * request larger than the bound is admitted alone, into an empty ring.  A step traces up to min(batch_rays, shadow capacity / max lights)
  * rays, oldest first, as many as the free ring takes in the worst case.  When
  * that is under a quarter of a batch (glass doubling the rays of deep ray
  * trees), steps take the newest rays instead (the deepest: the trees are then
@@ -312,6 +313,10 @@ typedef struct {
     uint32_t max_lights;  /* shadow queue = batch_rays * max_lights rays (48 B each); 0 = 4; scenes with
                              more lights are refused */
     uint32_t flags;       /* RG_SERVER_NO_GRAPH: launch each step's kernels directly, no CUDA graph */
+    uint32_t admit_rays;  /* admission bound on the rays in the ring plus a new request's primary rays;
+                             0 = batch_rays (what one step can take); at most half the ring.  A
+                             smaller bound keeps fewer requests in flight: large requests run closer
+                             to one after another (shorter tail latency), small ones still share steps */
 } rg_server_desc;
 #define RG_SERVER_NO_GRAPH 1u
 

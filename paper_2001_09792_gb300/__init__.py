@@ -77,7 +77,7 @@ class rg_stats(ctypes.Structure):
 
 class rg_server_desc(ctypes.Structure):
     _fields_ = [("ring_log2", ctypes.c_uint32), ("batch_rays", ctypes.c_uint32), ("max_lights", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("admit_rays", ctypes.c_uint32)]
 
 
 class rg_request(ctypes.Structure):
@@ -442,8 +442,8 @@ def rg_tlas_export(scene, n):
 
 # ---------------------------------------------------------------- render server
 
-def rg_server_create(ring_log2=0, batch_rays=0, max_lights=0, flags=0):
-    d = rg_server_desc(int(ring_log2), int(batch_rays), int(max_lights), int(flags))
+def rg_server_create(ring_log2=0, batch_rays=0, max_lights=0, flags=0, admit_rays=0):
+    d = rg_server_desc(int(ring_log2), int(batch_rays), int(max_lights), int(flags), int(admit_rays))
     h = ctypes.c_void_p()
     _check(lib().rg_server_create(ctypes.byref(h), ctypes.byref(d)))
     return h

@@ -188,7 +188,7 @@ const char* device_error_text(int err) {
 
 struct rg_server {
     int device = 0;
-    uint32_t ring_cap = 0, ring_mask = 0, batch = 0, max_lights = 0, flags = 0;
+    uint32_t ring_cap = 0, ring_mask = 0, batch = 0, max_lights = 0, flags = 0, admit = 0;
     size_t shadow_cap = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t done_ev = nullptr, t0 = nullptr, t1 = nullptr;
@@ -435,7 +435,10 @@ rg_status admit(rg_server* s, uint32_t* n_new) {
     while (!s->pending.empty()) {
         Pending& p = s->pending.front();
         const uint32_t px = p.r.width * p.r.height;
-        if ((uint64_t)s->ring_rays_now + rays + px > s->ring_cap / 2) break;
+        const uint64_t after = (uint64_t)s->ring_rays_now + rays + px;
+        // within the admission bound, or alone in an empty ring (within half the ring)
+        const bool alone = s->ring_rays_now == 0 && rays == 0 && px <= s->ring_cap / 2;
+        if (after > s->admit && !alone) break;
         uint32_t k = 0;
         while (k < kMaxSlots && s->active[k].on) ++k;
         if (k == kMaxSlots) break;
@@ -663,6 +666,7 @@ rg_status rg_server_create(rg_server** out, const rg_server_desc* desc) {
     }
     s->shadow_cap = (size_t)s->batch * s->max_lights;
     s->flags = d.flags;
+    s->admit = std::min(d.admit_rays ? d.admit_rays : s->batch, s->ring_cap / 2);
     rg_status r = RG_OK;
     auto bail = [&](rg_status code) {
         rg_server_destroy(s);

@@ -115,7 +115,7 @@ def test_mix_equals_alone(scenes):
     steps interleave them."""
     descs, gss = scenes
     reqs = make_requests(descs, 24, seed=7, sizes=[(160, 120), (320, 240), (640, 360), (97, 33)])
-    imgs, done, st = run_server(gss, reqs, ring_log2=22, batch_rays=1 << 18)
+    imgs, done, st = run_server(gss, reqs, ring_log2=22, batch_rays=1 << 18, admit_rays=1 << 21)
     assert sorted(d["tag"] for d in done) == list(range(len(reqs)))
     # requests were in flight together and finished over many steps
     spans = [(d["admitted_step"], d["completed_step"]) for d in done]
@@ -129,7 +129,7 @@ def test_mix_equals_alone(scenes):
 def test_small_ring_wraps_and_admits_mid_flight(scenes):
     descs, gss = scenes
     reqs = make_requests(descs, 20, seed=11, sizes=[(128, 96), (160, 120), (61, 17)], depths=[2, 4, 8])
-    imgs, done, st = run_server(gss, reqs, feed_every=3, ring_log2=16, batch_rays=1 << 13)
+    imgs, done, st = run_server(gss, reqs, feed_every=3, ring_log2=16, batch_rays=1 << 13, admit_rays=1 << 15)
     # the ring (65,536 rays) is passed several times over, and fills up
     # enough for newest-first steps
     assert st["closest_rays"] > 2 * (1 << 16)
@@ -227,3 +227,18 @@ def test_bad_requests_rejected(scenes):
         assert e.value.status == rg.RG_ERR_SINGULAR
     finally:
         rg.rg_server_destroy(srv)
+
+
+def test_admission_bound_keeps_requests_apart(scenes):
+    """With the default bound (one batch of rays in flight), a request larger
+    than the bound is admitted alone into the empty ring; the small ones are
+    admitted together once the rays in flight fall below the bound."""
+    descs, gss = scenes
+    reqs = [dict(scene=1, w=320, h=240, depth=3, M=descs[1].M, camera=descs[1].camera),
+            dict(scene=2, w=64, h=48, depth=3, M=descs[2].M, camera=descs[2].camera),
+            dict(scene=3, w=64, h=48, depth=3, M=descs[3].M, camera=descs[3].camera)]
+    imgs, done, st = run_server(gss, reqs, batch_rays=1 << 16)   # 76,800 px > 65,536: alone
+    spans = {d["tag"]: (d["admitted_step"], d["completed_step"]) for d in done}
+    assert spans[0][0] == 1 and spans[1][0] > 1             # the large one alone first
+    assert spans[1][0] == spans[2][0]                       # the small ones together
+    check_against_alone(descs, gss, reqs, imgs, st)
