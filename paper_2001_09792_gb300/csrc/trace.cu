@@ -2,8 +2,9 @@
 // Sec. 1: per ray, the closest-hit or any-hit shader runs when the ray meets a
 // triangle, the miss shader when it meets none).
 //
-// Persistent warps pull 32-ray batches from a global counter.  Each thread
-// runs a stack traversal: TLAS nodes in world space; at an instance leaf the
+// Persistent warps pull rays from a global counter (32 at a time, or as lanes
+// fall idle: k_trace_warp / k_trace_lane).  Each thread runs a stack
+// traversal: TLAS nodes in world space; at an instance leaf the
 // ray is moved to object space with the instance's float32 inverse (t is
 // shared, the direction is not renormalised), a marker is pushed, and the
 // BLAS is traversed; popping the marker restores the world ray.  Nodes are
@@ -17,7 +18,8 @@
 // with the far distance scaled by 1 + 2*gamma_3 (Ize, "Robust BVH Ray
 // Traversal", JCGT 2013), and a relative slack of 2^-12 on the culling
 // distance, so that a box is never culled while a triangle inside it can
-// still win.  Ties in t are broken by (instance, prim), which makes the
+// still win.  Child order: nearer entry first for closest hit, longer
+// overlap with the ray's segment first for any hit.  Ties in t are broken by (instance, prim), which makes the
 // result independent of the visit order (BVH == brute force).
 #include "rg_internal.cuh"
 
