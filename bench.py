@@ -139,14 +139,26 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def code_sha(path):
+    """Hash of a source file's code: // comments, trailing spaces and blank
+    lines removed (a comment edit leaves the kernel, and its counters, as they
+    were)."""
+    lines = []
+    for line in open(path).read().splitlines():
+        code = re.sub(r"//.*$", "", line).rstrip()
+        if code.strip():
+            lines.append(code)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
+
+
 def traffic_record():
     """Per-ray DRAM bytes of the closest-hit traversal from the committed ncu
-    summary, valid only while the traversal source is unchanged."""
+    summary, valid only while the traversal code is unchanged."""
     path = os.path.join(ROOT, "profiles", "trace_closest_medium.md")
     src = os.path.join(ROOT, "paper_2001_09792_gb300", "csrc", "trace.cu")
     try:
         txt = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = code_sha(src)
         m = re.search(r"dram_bytes_per_closest_ray:\s*([0-9.]+)", txt)
         s = re.search(r"trace_cu_sha256_16:\s*([0-9a-f]+)", txt)
         if m and s and s.group(1) == sha:
