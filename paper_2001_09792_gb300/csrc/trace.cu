@@ -91,9 +91,10 @@ struct Shear {
     int kx, ky, kz;
 };
 
-// Shear of the watertight test, with IEEE divisions (both traversals use it,
-// so their hit records are bit-identical).
-__device__ __forceinline__ Shear make_shear_div(float ox, float oy, float oz, float dx, float dy, float dz) {
+// Shear of the watertight test: Sz = 1/d_kz and Sx, Sy = d_kx, d_ky times it,
+// each correctly rounded.  Any fixed shear keeps the test watertight for the
+// ray; all traversals use this one, so their hit records are bit-identical.
+__device__ __forceinline__ Shear make_shear(float ox, float oy, float oz, float dx, float dy, float dz) {
     Shear s;
     float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
     int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
@@ -107,9 +108,9 @@ __device__ __forceinline__ Shear make_shear_div(float ox, float oy, float oz, fl
     }
     float dkx = kx == 0 ? dx : (kx == 1 ? dy : dz);
     float dky = ky == 0 ? dx : (ky == 1 ? dy : dz);
-    s.Sx = __fdiv_rn(dkx, dkz);
-    s.Sy = __fdiv_rn(dky, dkz);
-    s.Sz = __frcp_rn(dkz);  // = 1/d_kz, correctly rounded
+    s.Sz = __frcp_rn(dkz);  // 1/d_kz, correctly rounded
+    s.Sx = __fmul_rn(dkx, s.Sz);
+    s.Sy = __fmul_rn(dky, s.Sz);
     s.kx = kx;
     s.ky = ky;
     s.kz = kz;
@@ -362,7 +363,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace_warp(TraceArgs a) {
                 float ddz = fmaf(m2.x, dx, fmaf(m2.y, dy, __fmul_rn(m2.z, dz)));
                 cr.ox = ox; cr.oy = oy; cr.oz = oz;
                 cr.ix = safe_rcp(ddx); cr.iy = safe_rcp(ddy); cr.iz = safe_rcp(ddz);
-                sh = make_shear_div(ox, oy, oz, ddx, ddy, ddz);
+                sh = make_shear(ox, oy, oz, ddx, ddy, ddz);
                 const unsigned long long pn = ((unsigned long long)__float_as_uint(meta0.y) << 32) | __float_as_uint(meta0.x);
                 const unsigned long long pt = ((unsigned long long)__float_as_uint(meta0.w) << 32) | __float_as_uint(meta0.z);
                 nodes = reinterpret_cast<const float4*>(pn);
@@ -544,7 +545,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
             } else {
                 cr.ox = ox; cr.oy = oy; cr.oz = oz;
                 cr.ix = safe_rcp(ddx); cr.iy = safe_rcp(ddy); cr.iz = safe_rcp(ddz);
-                sh = make_shear_div(ox, oy, oz, ddx, ddy, ddz);
+                sh = make_shear(ox, oy, oz, ddx, ddy, ddz);
                 nodes = reinterpret_cast<const float4*>(
                     ((unsigned long long)__float_as_uint(meta0.y) << 32) | __float_as_uint(meta0.x));
                 tris = reinterpret_cast<const float4*>(
@@ -791,7 +792,7 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace8(TraceArgs a) {
                         cr.ox = ox; cr.oy = oy; cr.oz = oz;
                         cr.ix = safe_rcp(ddx); cr.iy = safe_rcp(ddy); cr.iz = safe_rcp(ddz);
                         oct = oct_of(cr);
-                        sh = make_shear_div(ox, oy, oz, ddx, ddy, ddz);
+                        sh = make_shear(ox, oy, oz, ddx, ddy, ddz);
                         const unsigned long long pn =
                             ((unsigned long long)__float_as_uint(meta0.y) << 32) | __float_as_uint(meta0.x);
                         const unsigned long long pt =
