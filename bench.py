@@ -2,7 +2,7 @@
 """Frame benchmark of the GB300 ray tracer.
 
 One step = one frame of the medium workload (64 instances of 4 procedural
-meshes, 158,964 unique triangles, 1920x1080, 4 point lights, max depth 4):
+meshes, 157,964 unique triangles, 1920x1080, 4 point lights, max depth 4):
 seeded per-instance motion, a full TLAS rebuild (float64 instance inverses,
 Arvo boxes, Morton codes, radix sort, Karras hierarchy, refit), then the
 Whitted render (ray generation, closest-hit traversal, shading and queue
@@ -44,7 +44,7 @@ import scenegen as g  # noqa: E402
 
 METRIC = "Mrays/s closest-hit at 1 GB300 vs plain path & oracle; p50/p99 frame latency"
 WORKLOAD = ("medium: 64 instances of 4 procedural meshes (UV sphere 80x40, icosphere s5, cube, 256^2 heightfield; "
-            "158,964 unique tris) with seeded affine transforms in a 100^3 box, materials diffuse/mirror/glass "
+            "157,964 unique tris) with seeded affine transforms in a 100^3 box, materials diffuse/mirror/glass "
             "60/20/20%, 4 point lights, 1920x1080, max_depth 4; per frame seeded motion + full TLAS rebuild + render")
 
 
@@ -209,6 +209,7 @@ def run_native(args, world, rank, local):
     gs = rg.GpuScene(s, flags=rg.RG_SCENE_TIMING | path_flag(args))
     torch.cuda.synchronize()
     blas_build_ms = (time.perf_counter() - t0) * 1e3  # four BLAS + first TLAS, host-timed incl. uploads
+    blas_build = blas_build_rate(s)
     blas_ids = [gs.blas[m] for m in s.mesh_id]
     inst_host = [rg.pack_instances(M, blas_ids, s.material_id) for M in motions]
     inst_dev = [torch.from_numpy(x).cuda() for x in inst_host]
@@ -358,7 +359,8 @@ def run_native(args, world, rank, local):
                        "closest_mrays_s": round(st["closest_rays"] / total_s / 1e6, 2),
                        "p50_ms": round(ms_sorted[len(ms) // 2], 3),
                        "p99_ms": round(ms_sorted[min(len(ms) - 1, math.ceil(0.99 * len(ms)) - 1)], 3),
-                       "blas_build_ms": round(blas_build_ms, 2), "l2": "flushed before each step (256 MiB write)",
+                       "blas_build_ms": round(blas_build_ms, 2), "blas_build": blas_build,
+                       "l2": "flushed before each step (256 MiB write)",
                        "fxaa": {"ms": round(fxaa_ms, 4), "gbs": round(W * H * 32 / (fxaa_ms / 1e3) / 1e9, 1),
                                 "bytes_per_pixel": 32, "note": "k_fxaa on the frame, timed alone, not in the step"},
                        "parallelism": f"replicas x{world}", "bvh": "compressed 8-wide" if args.compressed else "binary float32"},
@@ -517,6 +519,33 @@ def gpu_index(local):
 
 # ---------------------------------------------------------------- oracle arms
 
+def blas_build_rate(scene, reps=3):
+    """BLAS builds of the scene's meshes (LBVH: boxes, Morton codes, radix
+    sort, Karras hierarchy, refit, bounding sphere), inputs already on the
+    device, CUDA events around the builds; the median of `reps` builds."""
+    import torch
+    import paper_2001_09792_gb300 as rg
+    meshes = [(torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda(),
+               torch.from_numpy(np.ascontiguousarray(i, np.uint32).view(np.int32)).cuda()) for v, i in scene.meshes]
+    tris = sum(int(i.shape[0]) for _, i in scene.meshes)
+    ms = []
+    for _ in range(reps + 1):
+        h = rg.rg_scene_create()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for tv, ti in meshes:
+            rg.rg_blas_build(h, tv, ti)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        rg.rg_scene_destroy(h)
+    t = statistics.median(ms[1:])
+    return {"ms": round(t, 3), "tris": tris, "mtris_s": round(tris / t / 1e3, 1),
+            "note": "the four BLAS, median of 3 after one warm-up build, inputs resident"}
+
+
 def oracle_frames(scene, motions, budget_s, min_frames=1):
     """Render whole frames with the float64 oracle until the budget is spent."""
     import oracle
@@ -538,10 +567,22 @@ def oracle_frames(scene, motions, budget_s, min_frames=1):
 
 
 def cpu_baseline(scene, motions, budget_s):
+    import oracle
     cores = len(os.sched_getaffinity(0))
     rays, secs, frames, _ = oracle_frames(scene, motions, budget_s)
+    # one thread, on a seeded eighth of one frame's pixels
+    O = oracle.OracleScene(scene)
+    O.set_instances(motions[0], scene.mesh_id, scene.material_id)
+    n_px = scene.width * scene.height
+    pix = np.sort(np.random.default_rng(7).choice(n_px, n_px // 8, replace=False)).astype(np.uint32)
+    t0 = time.perf_counter()
+    r = O.render(scene.camera, scene.width, scene.height, scene.max_depth, pixels=pix, threads=1)
+    t1 = time.perf_counter() - t0
+    one = (r["closest_rays"] + r["shadow_rays"]) / t1 / 1e6
     return {"value": round(rays / secs / 1e6, 3), "unit": "Mrays/s", "cores": cores, "kind": "oracle",
-            "sample": f"{frames} whole frame(s) of the same workload (float64, {cores} threads), {secs:.1f} s"}
+            "sample": f"{frames} whole frame(s) of the same workload (float64, {cores} threads), {secs:.1f} s",
+            "one_thread": {"value": round(one, 3), "unit": "Mrays/s",
+                           "sample": f"a seeded eighth of one frame's pixels, 1 thread, {t1:.1f} s"}}
 
 
 def run_reference(args, world, rank, local):
