@@ -362,7 +362,7 @@ def run_native(args, world, rank, local):
                        "blas_build_ms": round(blas_build_ms, 2), "blas_build": blas_build,
                        "l2": "flushed before each step (256 MiB write)",
                        "fxaa": {"ms": round(fxaa_ms, 4), "gbs": round(W * H * 32 / (fxaa_ms / 1e3) / 1e9, 1),
-                                "bytes_per_pixel": 32, "note": "k_fxaa on the frame, timed alone, not in the step"},
+                                "bytes_per_pixel": 32, "note": "k_fxaa_luma + k_fxaa on the frame, timed alone, not in the step"},
                        "parallelism": f"replicas x{world}", "bvh": "compressed 8-wide" if args.compressed else "binary float32"},
             "roofline": roofline,
             "gpu_launches": int(st["kernel_launches"]),

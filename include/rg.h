@@ -186,7 +186,8 @@ rg_status rg_render(rg_scene* scene, const rg_camera* h_cam, uint32_t w, uint32_
  * to 26.5 pixels each way) give an offset across the edge, at least the
  * sub-pixel offset 0.75 s^2 of the 3x3 contrast, and the colour is
  * resampled bilinearly there (clamp-to-edge); alpha is copied.  Needs no
- * scene; w or h = 0 does nothing. */
+ * scene; w or h = 0 does nothing.  Takes w*h*4 bytes of stream-ordered
+ * temporary device memory (the luma image) for the duration of the call. */
 rg_status rg_fxaa(const float* d_in, uint32_t w, uint32_t h, float* d_out, void* stream);
 
 rg_status rg_sync(rg_scene* scene);

@@ -749,8 +749,13 @@ rg_status rg_fxaa(const float* d_in, uint32_t w, uint32_t h, float* d_out, void*
         return fail(RG_ERR_INVALID_ARG, "image too large");
     if (reinterpret_cast<uintptr_t>(d_in) % 16 || reinterpret_cast<uintptr_t>(d_out) % 16)
         return fail(RG_ERR_INVALID_ARG, "images must be 16-byte aligned");
-    RG_CK(launch_fxaa(reinterpret_cast<const float4*>(d_in), w, h, reinterpret_cast<float4*>(d_out),
-                      static_cast<cudaStream_t>(stream)));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    TempAlloc tmp(st);
+    void* lum;
+    rg_status r;
+    if ((r = tmp.get(&lum, (size_t)w * h * sizeof(float), "luma image"))) return r;
+    RG_CK(launch_fxaa(reinterpret_cast<const float4*>(d_in), w, h, static_cast<float*>(lum),
+                      reinterpret_cast<float4*>(d_out), st));
     return RG_OK;
 }
 

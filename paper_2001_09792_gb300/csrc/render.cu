@@ -391,8 +391,22 @@ __global__ void k_raygen_batch(const RaygenReq* __restrict__ reqs, const uint32_
 //     end, else 0; at least the sub-pixel offset 0.75 s^2, s the smoothstep
 //     of the contrast of the 3x3 mean (neighbours weighted 2, corners 1);
 //  7. output = bilinear colour at that offset; alpha kept.
+// luma of one RGBA pixel (step 1)
+__device__ __forceinline__ float fxaa_luma(float4 c) {
+    const float v = 0.299f * c.x + 0.587f * c.y + 0.114f * c.z;
+    return sqrtf(v > 0.0f ? v : 0.0f);
+}
+
+// The luma image, once per pixel: the main kernel reads 4 B lumas instead of
+// recomputing them from 16 B pixels (an edge pixel looks up about a hundred).
+__global__ void __launch_bounds__(256) k_fxaa_luma(const float4* __restrict__ in, uint32_t n, float* __restrict__ lum) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        lum[i] = fxaa_luma(__ldg(in + i));
+}
+
 struct FxaaImg {
     const float4* p;
+    const float* lum;  // fxaa_luma of every pixel
     int w, h;
     __device__ __forceinline__ float4 at(int x, int y) const {
         x = min(max(x, 0), w - 1);
@@ -400,9 +414,9 @@ struct FxaaImg {
         return __ldg(p + (size_t)y * (size_t)w + (size_t)x);
     }
     __device__ __forceinline__ float luma(int x, int y) const {
-        const float4 c = at(x, y);
-        const float v = 0.299f * c.x + 0.587f * c.y + 0.114f * c.z;
-        return sqrtf(v > 0.0f ? v : 0.0f);
+        x = min(max(x, 0), w - 1);
+        y = min(max(y, 0), h - 1);
+        return __ldg(lum + (size_t)y * (size_t)w + (size_t)x);
     }
     __device__ __forceinline__ float luma_at(float px, float py) const {
         const float fx0 = floorf(px), fy0 = floorf(py);
@@ -524,11 +538,13 @@ cudaError_t launch_shade_batch(const ShadeArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_fxaa(const float4* in, uint32_t w, uint32_t h, float4* out, cudaStream_t s) {
+cudaError_t launch_fxaa(const float4* in, uint32_t w, uint32_t h, float* lum, float4* out, cudaStream_t s) {
     if (w == 0 || h == 0) return cudaSuccess;
-    FxaaImg I{in, (int)w, (int)h};
+    const uint32_t n = w * h;
+    k_fxaa_luma<<<min((n + 255u) / 256u, (uint32_t)device_sm_count() * 16u), 256, 0, s>>>(in, n, lum);
+    FxaaImg I{in, lum, (int)w, (int)h};
     k_fxaa<<<dim3((w + 15) / 16, (h + 15) / 16), 256, 0, s>>>(I, out);
-    count_launches(1);
+    count_launches(2);
     return cudaGetLastError();
 }
 

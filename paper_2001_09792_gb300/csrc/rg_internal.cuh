@@ -304,8 +304,9 @@ cudaError_t launch_raygen_batch(const RaygenReq* reqs, const uint32_t* n_reqs, u
 // Shading of a mixed queue: count read on the device (*a.d_count), per-ray
 // slot, depth and pixel from the payload, per-slot tables from a.slots.
 cudaError_t launch_shade_batch(const ShadeArgs& a, cudaStream_t s);
-// FXAA of a w x h RGBA32F image into out (out-of-place).
-cudaError_t launch_fxaa(const float4* in, uint32_t w, uint32_t h, float4* out, cudaStream_t s);
+// FXAA of a w x h RGBA32F image into out (out-of-place); lum: w*h floats of
+// scratch (the luma image).
+cudaError_t launch_fxaa(const float4* in, uint32_t w, uint32_t h, float* lum, float4* out, cudaStream_t s);
 
 int device_sm_count();
 
