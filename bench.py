@@ -64,6 +64,8 @@ def parse():
                         "serve: the continuous-batching render server alone")
     p.add_argument("--requests", type=int, default=400, help="serving: requests in the Poisson stream")
     p.add_argument("--no-serving", action="store_true", help="medium: skip the serving measurement")
+    p.add_argument("--no-pair", action="store_true",
+                   help="medium: trace each level's shadow rays and the next level's closest-hit rays in separate launches")
     return p.parse_args()
 
 
@@ -170,7 +172,8 @@ def traffic_record():
 
 def path_flag(args):
     import paper_2001_09792_gb300 as rg
-    return rg.RG_SCENE_COMPRESSED if args.compressed else 0
+    return ((rg.RG_SCENE_COMPRESSED if args.compressed else 0)
+            | (rg.RG_SCENE_NO_PAIR if getattr(args, "no_pair", False) else 0))
 
 
 def node_bytes(args):
@@ -178,6 +181,9 @@ def node_bytes(args):
 
 
 def kernel_name(args, where):
+    if where == "render":
+        return ("k_trace8 closest-hit and any-hit, compressed 8-wide BVH (render)" if args.compressed
+                else "k_trace_warp / k_trace_pair closest-hit and any-hit, binary float32 BVH (render)")
     return (f"k_trace8 closest-hit, compressed 8-wide BVH ({where})" if args.compressed
             else f"k_trace closest-hit, binary float32 BVH ({where})")
 
@@ -321,23 +327,38 @@ def run_native(args, world, rank, local):
 
     if rank == 0:
         peak, peak_kind = measured_peaks()
-        cr = max(cst["closest_rays"], 1)
-        bytes_per_ray = 32 + 16 + node_bytes(args) * cst["node_visits"] / cr + 48 * cst["tri_tests"] / cr + 80 * cst["inst_entries"] / cr
-        launch_ms = st["trace_ms"] / max(st["trace_launches"], 1)
-        rays_per_launch = st["closest_rays"] / max(st["trace_launches"], 1)
-        achieved = bytes_per_ray * rays_per_launch / (launch_ms / 1e3) / 1e9
+        # the traversal launches of the timed frames (closest-hit alone for the
+        # camera rays, shadow + next level's closest-hit pairs, shadow alone for
+        # the last level): the algorithmic bytes of all their rays over their
+        # summed device time
+        cr, sr = max(cst["closest_rays"], 1), max(cst["shadow_rays"], 1)
+        nb = node_bytes(args)
+        bytes_per_ray = 32 + 16 + nb * cst["node_visits"] / cr + 48 * cst["tri_tests"] / cr + 80 * cst["inst_entries"] / cr
+        bytes_per_shadow = (32 + 16 + nb * cst["any_node_visits"] / sr + 48 * cst["any_tri_tests"] / sr
+                            + 80 * cst["any_inst_entries"] / sr)
+        trav_ms = st["trace_ms"] + st["any_ms"] + st["pair_ms"]
+        trav_launches = max(st["trace_launches"] + st["any_launches"] + st["pair_launches"], 1)
+        trav_bytes = bytes_per_ray * st["closest_rays"] + bytes_per_shadow * st["shadow_rays"]
+        launch_ms = trav_ms / trav_launches
+        rays_per_launch = (st["closest_rays"] + st["shadow_rays"]) / trav_launches
+        achieved = trav_bytes / trav_launches / (launch_ms / 1e3) / 1e9
         tr = None if args.compressed else traffic_record()
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(achieved / peak, 4), "traffic": None if tr is None else round(tr * rays_per_launch),
                     "kernel": kernel_name(args, "render"), "peak_kind": peak_kind,
-                    "algorithmic_bytes_per_ray": round(bytes_per_ray, 1),
+                    "algorithmic_bytes_per_launch": round(trav_bytes / trav_launches),
+                    "algorithmic_bytes_per_closest_ray": round(bytes_per_ray, 1),
+                    "algorithmic_bytes_per_shadow_ray": round(bytes_per_shadow, 1),
+                    "launches_per_frame": round(trav_launches / args.steps, 2),
                     "nodes_per_ray": round(cst["node_visits"] / cr, 2), "tris_per_ray": round(cst["tri_tests"] / cr, 2),
                     "inst_per_ray": round(cst["inst_entries"] / cr, 3), "avg_launch_ms": round(launch_ms, 4),
-                    "trace_share_of_frame": round(st["trace_ms"] / sum(ms), 3),
-                    "shadow_share_of_frame": round(st["any_ms"] / sum(ms), 3),
-                    "shadow_nodes_per_ray": round(cst["any_node_visits"] / max(cst["shadow_rays"], 1), 2),
-                    "shadow_inst_per_ray": round(cst["any_inst_entries"] / max(cst["shadow_rays"], 1), 3),
-                    "shadow_tris_per_ray": round(cst["any_tri_tests"] / max(cst["shadow_rays"], 1), 2)}
+                    "traversal_share_of_frame": round(trav_ms / sum(ms), 3),
+                    "shares": {"closest_alone": round(st["trace_ms"] / sum(ms), 3),
+                               "shadow_closest_pairs": round(st["pair_ms"] / sum(ms), 3),
+                               "shadow_alone": round(st["any_ms"] / sum(ms), 3)},
+                    "shadow_nodes_per_ray": round(cst["any_node_visits"] / sr, 2),
+                    "shadow_inst_per_ray": round(cst["any_inst_entries"] / sr, 3),
+                    "shadow_tris_per_ray": round(cst["any_tri_tests"] / sr, 2)}
         ms_sorted = sorted(ms)
         out = {
             "metric": METRIC,

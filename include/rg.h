@@ -84,8 +84,10 @@ typedef struct { float pos[3]; float intensity[3]; } rg_light;
  * compressed 8-wide BVH whose child boxes are 8-bit integers against a
  * float32 parent origin and per-axis power-of-two scale, rounded outward (80 B
  * per 8 children instead of 64 B per 2), and traces and renders with it; hit
- * records are bit-identical to the binary float32 path. */
-enum { RG_SCENE_TIMING = 1u, RG_SCENE_COUNT = 2u, RG_SCENE_COMPRESSED = 4u };
+ * records are bit-identical to the binary float32 path.  rg_render traces
+ * each depth level's shadow rays and the next level's closest-hit rays in one
+ * launch (binary BVH); RG_SCENE_NO_PAIR makes them two launches. */
+enum { RG_SCENE_TIMING = 1u, RG_SCENE_COUNT = 2u, RG_SCENE_COMPRESSED = 4u, RG_SCENE_NO_PAIR = 8u };
 typedef struct { float background[3]; float ambient; uint32_t flags; } rg_scene_desc;
 
 /* Counters since the last rg_reset_stats. */
@@ -103,6 +105,8 @@ typedef struct {
     uint64_t any_tri_tests;
     uint64_t any_inst_entries;
     uint64_t kernel_launches; /* kernels launched by the library (all scenes of the process) */
+    uint64_t pair_launches;   /* timed launches that trace one level's shadow rays together with */
+    double pair_ms;           /*   the next level's closest-hit rays, and their summed device time */
 } rg_stats;
 
 /* ---- scene lifetime ---------------------------------------------------- */

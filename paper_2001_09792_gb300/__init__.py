@@ -27,6 +27,7 @@ RG_CLOSEST, RG_ANY, RG_TRACE_BRUTE, RG_TRACE_STATS, RG_TRACE_PLAIN = 0, 1, 2, 4,
 RG_SCENE_TIMING = 1
 RG_SCENE_COUNT = 2
 RG_SCENE_COMPRESSED = 4
+RG_SCENE_NO_PAIR = 8
 RG_COMPRESSED = 2
 RG_TLAS_ID = 0xFFFFFFFF
 RG_MAT_DIFFUSE, RG_MAT_MIRROR, RG_MAT_GLASS = 0, 1, 2
@@ -72,7 +73,8 @@ class rg_stats(ctypes.Structure):
                 ("any_launches", ctypes.c_uint64), ("any_ms", ctypes.c_double),
                 ("node_visits", ctypes.c_uint64), ("tri_tests", ctypes.c_uint64), ("inst_entries", ctypes.c_uint64),
                 ("any_node_visits", ctypes.c_uint64), ("any_tri_tests", ctypes.c_uint64),
-                ("any_inst_entries", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
+                ("any_inst_entries", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
+                ("pair_launches", ctypes.c_uint64), ("pair_ms", ctypes.c_double)]
 
 
 class rg_server_desc(ctypes.Structure):

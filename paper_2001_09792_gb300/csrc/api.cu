@@ -131,7 +131,7 @@ void free_blas(BlasHost& b) {
 
 struct EventPair {
     cudaEvent_t a, b;
-    int kind;  // 0 closest, 1 any
+    int kind;  // 0 closest, 1 any, 2 shadow + closest pair
 };
 
 }  // namespace
@@ -174,8 +174,8 @@ struct rg_scene {
     // statistics and timing
     uint64_t closest_rays = 0, shadow_rays_host = 0;
     std::vector<EventPair> events, free_events;
-    double trace_ms = 0, any_ms = 0;
-    uint64_t trace_launches = 0, any_launches = 0;
+    double trace_ms = 0, any_ms = 0, pair_ms = 0;
+    uint64_t trace_launches = 0, any_launches = 0, pair_launches = 0;
     unsigned long long launch_base = 0;
 };
 
@@ -225,9 +225,12 @@ rg_status collect_events(rg_scene* s) {
         if (ep.kind == 0) {
             s->trace_ms += ms;
             s->trace_launches++;
-        } else {
+        } else if (ep.kind == 1) {
             s->any_ms += ms;
             s->any_launches++;
+        } else {
+            s->pair_ms += ms;
+            s->pair_launches++;
         }
         s->free_events.push_back(ep);
     }
@@ -637,12 +640,14 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
     const uint32_t N = w * h;
     const uint32_t L = s->n_lights;
     // Per depth level: closest-hit traversal, shading, shadow traversal.  The
-    // host learns each level's ray count one step late: the count is copied
-    // back while the GPU runs the shadow rays of this level and the
-    // closest-hit rays of the next (whose traversal reads the count on the
-    // device), so the stream never waits for the host.  Counters: one block
+    // shadow rays of a level and the closest-hit rays of the next depend only
+    // on the level's shading and share one launch (k_trace_pair) unless
+    // RG_SCENE_NO_PAIR is set or the BVH is the compressed one.  The host
+    // learns each level's ray count one step late: the count is copied back
+    // while the GPU traces, and the closest-hit traversal reads the count on
+    // the device, so the stream never waits for the host.  Counters: one block
     // per level, [0] closest work, [1] rays of the next level, [2] shadow
-    // work, [4 + l] shadow rays toward light l.
+    // work (and the pair's), [4 + l] shadow rays toward light l.
     const size_t CB = 4 + kMaxLights;
     if ((r = s->counters.ensure(CB * ((size_t)max_depth + 1), "counters"))) return r;
     if ((r = s->q_rays[0].ensure(2 * (size_t)N, "ray queue"))) return r;
@@ -714,8 +719,9 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
             RG_CK(cudaEventRecord(s->count_ev, st));
         }
 
+        TraceArgs b{};
         if (L) {
-            TraceArgs b = base_trace_args(s, true);
+            b = base_trace_args(s, true);
             b.rays = s->s_rays.p;
             b.sub_counts = c + 4;
             b.n_sub = L;
@@ -723,6 +729,9 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
             b.payload = s->s_pay.p;
             b.image = d_rgba;
             b.work_counter = c + 2;
+        }
+        const bool pair = L && !last && !s->wide && !(s->desc.flags & RG_SCENE_NO_PAIR);
+        if (L && !pair) {
             EventPair* ev;
             if ((r = event_begin(s, 1, st, &ev))) return r;
             RG_CK(launch_trace(kModeShadowRender, false, s->desc.flags & RG_SCENE_COUNT, b, st));
@@ -732,7 +741,18 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
         // the next level's rays (at most 2 per ray of this level) are traced
         // before the host knows how many there are
         if ((r = s->hits.ensure(2 * (size_t)n, "hit queue"))) return r;
-        if ((r = trace_closest(1 - cur, 0, c + 1, c + CB))) return r;
+        if (pair) {
+            TraceArgs a = base_trace_args(s, true);
+            a.rays = s->q_rays[1 - cur].p;
+            a.d_count = c + 1;
+            a.hits_render = s->hits.p;
+            EventPair* ev;
+            if ((r = event_begin(s, 2, st, &ev))) return r;
+            RG_CK(launch_trace_pair(s->desc.flags & RG_SCENE_COUNT, b, a, st));
+            if ((r = event_end(s, st))) return r;
+        } else if ((r = trace_closest(1 - cur, 0, c + 1, c + CB))) {
+            return r;
+        }
         RG_CK(cudaEventSynchronize(s->count_ev));
         n = s->h_counts[0];
         cur = 1 - cur;
@@ -800,6 +820,8 @@ rg_status rg_get_stats(rg_scene* s, rg_stats* out) {
     out->any_tri_tests = d.count[1][1];
     out->any_inst_entries = d.count[1][2];
     out->kernel_launches = launches_so_far() - s->launch_base;
+    out->pair_launches = s->pair_launches;
+    out->pair_ms = s->pair_ms;
     return RG_OK;
 }
 
@@ -810,8 +832,8 @@ rg_status rg_reset_stats(rg_scene* s) {
     RG_CK(cudaDeviceSynchronize());
     if ((r = collect_events(s))) return r;
     s->closest_rays = s->shadow_rays_host = 0;
-    s->trace_ms = s->any_ms = 0;
-    s->trace_launches = s->any_launches = 0;
+    s->trace_ms = s->any_ms = s->pair_ms = 0;
+    s->trace_launches = s->any_launches = s->pair_launches = 0;
     s->launch_base = launches_so_far();
     RG_CK(cudaMemset(reinterpret_cast<char*>(s->st) + offsetof(DevStatus, closest_rays), 0,
                      sizeof(DevStatus) - offsetof(DevStatus, closest_rays)));

@@ -250,6 +250,9 @@ struct TraceArgs {
 constexpr uint32_t kMaxLights = 64;  // lights per scene (one shadow sub-queue each)
 cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a, cudaStream_t s,
                          const TraceShape& shape = TraceShape());
+// The shadow rays of sa (kModeShadowRender) and the closest-hit rays of ca
+// (kModeClosestRender) in one launch; sa.work_counter serves both.  Binary BVH only.
+cudaError_t launch_trace_pair(bool stats, const TraceArgs& sa, const TraceArgs& ca, cudaStream_t s);
 
 // render.cu
 struct CameraDev {

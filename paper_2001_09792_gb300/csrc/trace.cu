@@ -3,7 +3,9 @@
 // triangle, the miss shader when it meets none).
 //
 // Persistent warps pull rays from a global counter (32 at a time, or as lanes
-// fall idle: k_trace_warp / k_trace_lane).  Each thread runs a stack
+// fall idle: k_trace_warp / k_trace_lane; k_trace_pair serves a renderer's
+// shadow rays of one depth level and closest-hit rays of the next from one
+// counter, in one launch).  Each thread runs a stack
 // traversal: TLAS nodes in world space; at an instance leaf the
 // ray is moved to object space with the instance's float32 inverse (t is
 // shared, the direction is not renormalised), a marker is pushed, and the
@@ -240,175 +242,223 @@ __device__ __forceinline__ void flush_counts(const TraceArgs& a, unsigned long l
     }
 }
 
-// Binary traversal, whole-warp refill: a warp takes 32 rays from the work
-// counter, each lane runs its ray to completion (one loop iteration per node
-// visit, instance entry or triangle test; a stack pop joins the step that
-// follows it), and the warp takes the next 32 when all its lanes are done.  Best when the rays of a warp take
-// similar work (camera and secondary rays).
-template <int MODE, bool BRUTE, bool STATS, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_trace_warp(TraceArgs a) {
+// Counting-traversal tallies of one thread.
+struct TraceCounts {
+    unsigned long long nodes = 0, tris = 0, inst = 0;
+};
+
+// One ray, run to completion: one loop iteration per node visit, instance
+// entry or triangle test; a stack pop joins the step that follows it.  i is
+// the ray's dense index (queue entry via the sub-queues or the ring).
+template <int MODE, bool BRUTE, bool STATS>
+__device__ __forceinline__ void trace_ray(const TraceArgs& a, const uint32_t* pre, uint32_t head, uint32_t i,
+                                          TraceCounts& cnt) {
     const uint32_t iter_cap = a.iter_cap;
     constexpr bool kAny = (MODE == kModeAnyAbi || MODE == kModeShadowRender || MODE == kModeShadowBatch);
     constexpr bool kBatch = (MODE == kModeClosestBatch || MODE == kModeShadowBatch);
+    const uint32_t j = MODE == kModeClosestBatch ? ((head + i) & a.ring_mask) : sub_entry(a, pre, i);
+
+    // the TLAS of this ray (per request slot in the batched modes)
+    const float4* tlas_nodes = a.tlas_nodes;
+    const InstDev* tlas_inst = a.inst;
+    uint32_t tlas_root = a.tlas_root;
+    if (kBatch) {
+        const SlotDev* S = a.slots + slot_of_px(a.payload[j].pixel);
+        tlas_nodes = S->tlas_nodes;
+        tlas_inst = S->inst;
+        tlas_root = S->tlas_root;
+    }
+
+    const float4 r0 = __ldg(a.rays + 2 * (size_t)j), r1 = __ldg(a.rays + 2 * (size_t)j + 1);
+    const float tmin = r0.w, tmax = r1.w;
+    SpaceRay wr;
+    wr.ox = r0.x; wr.oy = r0.y; wr.oz = r0.z;
+    wr.ix = safe_rcp(r1.x); wr.iy = safe_rcp(r1.y); wr.iz = safe_rcp(r1.z);
+    SpaceRay cr = wr;  // ray of the current space
+    Shear sh;
+
+    float best_t = tmax;
+    uint32_t best_id = kMiss, best_prim = kMiss;
+    uint32_t best_il = kMiss, best_tl = kMiss;
+    float best_V = 0.f, best_W = 0.f, best_det = 1.f;
+    bool found = false;
+
+    uint32_t stack[kStack];
+    int sp = 0;
+    uint32_t ref = tlas_root;
+    bool in_blas = false;
+    const float4* nodes = tlas_nodes;
+    const float4* tris = nullptr;
+    uint32_t cur_id = 0, cur_leaf = 0;
+    bool ok = true;
+
+    for (uint32_t iter = 0;; ++iter) {
+        if (iter >= iter_cap) {
+            record_error(a.st, RG_ERR_TIMEOUT);
+            ok = false;
+            break;
+        }
+        if (ref == kNone) {
+            // pop, and go on with the popped entry in this iteration
+            if (sp == 0) break;
+            ref = stack[--sp];
+            if (ref == kMarker) {
+                in_blas = false;
+                nodes = tlas_nodes;
+                cr = wr;
+                if (sp == 0) break;
+                ref = stack[--sp];  // a TLAS entry: markers never follow each other
+            }
+        }
+        if (!(ref & kLeaf)) {
+            const float4* nd = nodes + 4 * (size_t)ref;
+            const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2);
+            const uint4 n3 = __ldg(reinterpret_cast<const uint4*>(nd + 3));
+            if (STATS) ++cnt.nodes;
+            const float tlim = kAny ? __fmul_rn(tmax, kCullSlack) : __fmul_rn(best_t, kCullSlack);
+            float tn0, tn1, tf0, tf1;
+            bool h0 = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, cr, tmin, tlim, tn0, tf0);
+            bool h1 = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, cr, tmin, tlim, tn1, tf1);
+            if (BRUTE) h0 = h1 = true;
+            if (h0 && h1) {
+                const bool f0 = visit_first0<kAny>(tn0, tf0, tn1, tf1);
+                uint32_t nearc = f0 ? n3.x : n3.y;
+                uint32_t farc = f0 ? n3.y : n3.x;
+                if (sp >= kStack) {
+                    record_error(a.st, RG_ERR_STACK);
+                    ok = false;
+                    break;
+                }
+                stack[sp++] = farc;
+                ref = nearc;
+            } else if (h0) {
+                ref = n3.x;
+            } else if (h1) {
+                ref = n3.y;
+            } else {
+                ref = kNone;
+            }
+            continue;
+        }
+        const uint32_t leaf = ref & ~kLeaf;
+        if (!in_blas) {
+            const InstDev* I = tlas_inst + leaf;
+            const float4 m0 = __ldg(&I->inv[0]), m1 = __ldg(&I->inv[1]), m2 = __ldg(&I->inv[2]);
+            const float4 meta0 = __ldg(reinterpret_cast<const float4*>(&I->nodes));        // nodes, tris
+            const uint4 meta1 = __ldg(reinterpret_cast<const uint4*>(&I->root));           // root, id, mat, blas
+            if (STATS) ++cnt.inst;
+            const float dx = r1.x, dy = r1.y, dz = r1.z;
+            float ox = fmaf(m0.x, wr.ox, fmaf(m0.y, wr.oy, fmaf(m0.z, wr.oz, m0.w)));
+            float oy = fmaf(m1.x, wr.ox, fmaf(m1.y, wr.oy, fmaf(m1.z, wr.oz, m1.w)));
+            float oz = fmaf(m2.x, wr.ox, fmaf(m2.y, wr.oy, fmaf(m2.z, wr.oz, m2.w)));
+            float ddx = fmaf(m0.x, dx, fmaf(m0.y, dy, __fmul_rn(m0.z, dz)));
+            float ddy = fmaf(m1.x, dx, fmaf(m1.y, dy, __fmul_rn(m1.z, dz)));
+            float ddz = fmaf(m2.x, dx, fmaf(m2.y, dy, __fmul_rn(m2.z, dz)));
+            cr.ox = ox; cr.oy = oy; cr.oz = oz;
+            cr.ix = safe_rcp(ddx); cr.iy = safe_rcp(ddy); cr.iz = safe_rcp(ddz);
+            sh = make_shear(ox, oy, oz, ddx, ddy, ddz);
+            const unsigned long long pn = ((unsigned long long)__float_as_uint(meta0.y) << 32) | __float_as_uint(meta0.x);
+            const unsigned long long pt = ((unsigned long long)__float_as_uint(meta0.w) << 32) | __float_as_uint(meta0.z);
+            nodes = reinterpret_cast<const float4*>(pn);
+            tris = reinterpret_cast<const float4*>(pt);
+            cur_id = meta1.y;
+            cur_leaf = leaf;
+            in_blas = true;
+            if (sp >= kStack) {
+                record_error(a.st, RG_ERR_STACK);
+                ok = false;
+                break;
+            }
+            stack[sp++] = kMarker;
+            ref = meta1.x;
+            continue;
+        }
+        // triangle leaf
+        {
+            const float4* tp = tris + 3 * (size_t)leaf;
+            const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+            if (STATS) ++cnt.tris;
+            TriResult h = tri_test(sh, v0, v1, v2, tmin, kAny ? tmax : best_t);
+            ref = kNone;
+            if (h.hit) {
+                const uint32_t prim = __float_as_uint(v0.w);
+                if (kAny) {
+                    best_t = h.t; best_id = cur_id; best_prim = prim;
+                    best_V = h.V; best_W = h.W; best_det = h.det;
+                    found = true;
+                    break;
+                }
+                bool better = h.t < best_t || cur_id < best_id || (cur_id == best_id && prim < best_prim);
+                if (better) {
+                    best_t = h.t; best_id = cur_id; best_prim = prim;
+                    best_il = cur_leaf; best_tl = leaf;
+                    best_V = h.V; best_W = h.W; best_det = h.det;
+                    found = true;
+                }
+            }
+        }
+    }
+    if (!ok) found = false;
+    emit<MODE>(a, i, j, found, ok, best_t, best_id, best_prim, best_il, best_tl, best_V, best_W, best_det);
+}
+
+// Binary traversal, whole-warp refill: a warp takes 32 rays from the work
+// counter, each lane runs its ray to completion, and the warp takes the next
+// 32 when all its lanes are done.  Best when the rays of a warp take similar
+// work (camera and secondary rays).
+template <int MODE, bool BRUTE, bool STATS, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_trace_warp(TraceArgs a) {
+    constexpr bool kAny = (MODE == kModeAnyAbi || MODE == kModeShadowRender || MODE == kModeShadowBatch);
     __shared__ uint32_t pre[kMaxLights + 1];
     const uint32_t n = ray_count(a, pre);
     const int lane = threadIdx.x & 31;
     // batched closest-hit rays sit in a ring of 2^k entries from *ring_head
     const uint32_t head = MODE == kModeClosestBatch ? *a.ring_head : 0u;
-    unsigned long long c_nodes = 0, c_tris = 0, c_inst = 0;
+    TraceCounts cnt;
     for (;;) {
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(a.work_counter, 32u);
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
         if (base >= n) break;
         const uint32_t i = base + lane;
-        if (i >= n) continue;
-        const uint32_t j = MODE == kModeClosestBatch ? ((head + i) & a.ring_mask) : sub_entry(a, pre, i);
-
-        // the TLAS of this ray (per request slot in the batched modes)
-        const float4* tlas_nodes = a.tlas_nodes;
-        const InstDev* tlas_inst = a.inst;
-        uint32_t tlas_root = a.tlas_root;
-        if (kBatch) {
-            const SlotDev* S = a.slots + slot_of_px(a.payload[j].pixel);
-            tlas_nodes = S->tlas_nodes;
-            tlas_inst = S->inst;
-            tlas_root = S->tlas_root;
-        }
-
-        const float4 r0 = __ldg(a.rays + 2 * (size_t)j), r1 = __ldg(a.rays + 2 * (size_t)j + 1);
-        const float tmin = r0.w, tmax = r1.w;
-        SpaceRay wr;
-        wr.ox = r0.x; wr.oy = r0.y; wr.oz = r0.z;
-        wr.ix = safe_rcp(r1.x); wr.iy = safe_rcp(r1.y); wr.iz = safe_rcp(r1.z);
-        SpaceRay cr = wr;  // ray of the current space
-        Shear sh;
-
-        float best_t = tmax;
-        uint32_t best_id = kMiss, best_prim = kMiss;
-        uint32_t best_il = kMiss, best_tl = kMiss;
-        float best_V = 0.f, best_W = 0.f, best_det = 1.f;
-        bool found = false;
-
-        uint32_t stack[kStack];
-        int sp = 0;
-        uint32_t ref = tlas_root;
-        bool in_blas = false;
-        const float4* nodes = tlas_nodes;
-        const float4* tris = nullptr;
-        uint32_t cur_id = 0, cur_leaf = 0;
-        bool ok = true;
-
-        for (uint32_t iter = 0;; ++iter) {
-            if (iter >= iter_cap) {
-                record_error(a.st, RG_ERR_TIMEOUT);
-                ok = false;
-                break;
-            }
-            if (ref == kNone) {
-                // pop, and go on with the popped entry in this iteration
-                if (sp == 0) break;
-                ref = stack[--sp];
-                if (ref == kMarker) {
-                    in_blas = false;
-                    nodes = tlas_nodes;
-                    cr = wr;
-                    if (sp == 0) break;
-                    ref = stack[--sp];  // a TLAS entry: markers never follow each other
-                }
-            }
-            if (!(ref & kLeaf)) {
-                const float4* nd = nodes + 4 * (size_t)ref;
-                const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2);
-                const uint4 n3 = __ldg(reinterpret_cast<const uint4*>(nd + 3));
-                if (STATS) ++c_nodes;
-                const float tlim = kAny ? __fmul_rn(tmax, kCullSlack) : __fmul_rn(best_t, kCullSlack);
-                float tn0, tn1, tf0, tf1;
-                bool h0 = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, cr, tmin, tlim, tn0, tf0);
-                bool h1 = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, cr, tmin, tlim, tn1, tf1);
-                if (BRUTE) h0 = h1 = true;
-                if (h0 && h1) {
-                    const bool f0 = visit_first0<kAny>(tn0, tf0, tn1, tf1);
-                    uint32_t nearc = f0 ? n3.x : n3.y;
-                    uint32_t farc = f0 ? n3.y : n3.x;
-                    if (sp >= kStack) {
-                        record_error(a.st, RG_ERR_STACK);
-                        ok = false;
-                        break;
-                    }
-                    stack[sp++] = farc;
-                    ref = nearc;
-                } else if (h0) {
-                    ref = n3.x;
-                } else if (h1) {
-                    ref = n3.y;
-                } else {
-                    ref = kNone;
-                }
-                continue;
-            }
-            const uint32_t leaf = ref & ~kLeaf;
-            if (!in_blas) {
-                const InstDev* I = tlas_inst + leaf;
-                const float4 m0 = __ldg(&I->inv[0]), m1 = __ldg(&I->inv[1]), m2 = __ldg(&I->inv[2]);
-                const float4 meta0 = __ldg(reinterpret_cast<const float4*>(&I->nodes));        // nodes, tris
-                const uint4 meta1 = __ldg(reinterpret_cast<const uint4*>(&I->root));           // root, id, mat, blas
-                if (STATS) ++c_inst;
-                const float dx = r1.x, dy = r1.y, dz = r1.z;
-                float ox = fmaf(m0.x, wr.ox, fmaf(m0.y, wr.oy, fmaf(m0.z, wr.oz, m0.w)));
-                float oy = fmaf(m1.x, wr.ox, fmaf(m1.y, wr.oy, fmaf(m1.z, wr.oz, m1.w)));
-                float oz = fmaf(m2.x, wr.ox, fmaf(m2.y, wr.oy, fmaf(m2.z, wr.oz, m2.w)));
-                float ddx = fmaf(m0.x, dx, fmaf(m0.y, dy, __fmul_rn(m0.z, dz)));
-                float ddy = fmaf(m1.x, dx, fmaf(m1.y, dy, __fmul_rn(m1.z, dz)));
-                float ddz = fmaf(m2.x, dx, fmaf(m2.y, dy, __fmul_rn(m2.z, dz)));
-                cr.ox = ox; cr.oy = oy; cr.oz = oz;
-                cr.ix = safe_rcp(ddx); cr.iy = safe_rcp(ddy); cr.iz = safe_rcp(ddz);
-                sh = make_shear(ox, oy, oz, ddx, ddy, ddz);
-                const unsigned long long pn = ((unsigned long long)__float_as_uint(meta0.y) << 32) | __float_as_uint(meta0.x);
-                const unsigned long long pt = ((unsigned long long)__float_as_uint(meta0.w) << 32) | __float_as_uint(meta0.z);
-                nodes = reinterpret_cast<const float4*>(pn);
-                tris = reinterpret_cast<const float4*>(pt);
-                cur_id = meta1.y;
-                cur_leaf = leaf;
-                in_blas = true;
-                if (sp >= kStack) {
-                    record_error(a.st, RG_ERR_STACK);
-                    ok = false;
-                    break;
-                }
-                stack[sp++] = kMarker;
-                ref = meta1.x;
-                continue;
-            }
-            // triangle leaf
-            {
-                const float4* tp = tris + 3 * (size_t)leaf;
-                const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
-                if (STATS) ++c_tris;
-                TriResult h = tri_test(sh, v0, v1, v2, tmin, kAny ? tmax : best_t);
-                ref = kNone;
-                if (h.hit) {
-                    const uint32_t prim = __float_as_uint(v0.w);
-                    if (kAny) {
-                        best_t = h.t; best_id = cur_id; best_prim = prim;
-                        best_V = h.V; best_W = h.W; best_det = h.det;
-                        found = true;
-                        break;
-                    }
-                    bool better = h.t < best_t || cur_id < best_id || (cur_id == best_id && prim < best_prim);
-                    if (better) {
-                        best_t = h.t; best_id = cur_id; best_prim = prim;
-                        best_il = cur_leaf; best_tl = leaf;
-                        best_V = h.V; best_W = h.W; best_det = h.det;
-                        found = true;
-                    }
-                }
-            }
-        }
-        if (!ok) found = false;
-        emit<MODE>(a, i, j, found, ok, best_t, best_id, best_prim, best_il, best_tl, best_V, best_W, best_det);
+        if (i < n) trace_ray<MODE, BRUTE, STATS>(a, pre, head, i, cnt);
     }
-    flush_counts<kAny, STATS>(a, c_nodes, c_tris, c_inst);
+    flush_counts<kAny, STATS>(a, cnt.nodes, cnt.tris, cnt.inst);
+}
+
+// The shadow rays of one depth level and the closest-hit rays of the next in
+// one persistent launch (both depend only on the shading of the level): one
+// work counter runs over the shadow rays (in whole warps of 32) and then over
+// the closest-hit rays, so warps that run out of one kind take the other and
+// the SMs stay busy until the last batch of both, instead of idling through
+// the tail of two separate launches.
+// Held to 64 registers (8 blocks of 128 per SM, as the single-mode kernels):
+// with both ray kinds inlined it would take 76 and fit 6 blocks, which
+// measured slower than the few spilled values cost.
+template <bool STATS, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 8) k_trace_pair(TraceArgs sa, TraceArgs ca) {
+    __shared__ uint32_t pre[kMaxLights + 1];
+    const uint32_t ns = ray_count(sa, pre);
+    const uint32_t nc = ca.d_count ? *ca.d_count : ca.n;
+    const uint32_t ns_pad = (ns + 31u) & ~31u;
+    const int lane = threadIdx.x & 31;
+    TraceCounts cs, cc;
+    for (;;) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(sa.work_counter, 32u);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (base < ns_pad) {
+            const uint32_t i = base + lane;
+            if (i < ns) trace_ray<kModeShadowRender, false, STATS>(sa, pre, 0u, i, cs);
+        } else {
+            const uint32_t b = base - ns_pad;
+            if (b >= nc) break;
+            const uint32_t i = b + lane;
+            if (i < nc) trace_ray<kModeClosestRender, false, STATS>(ca, nullptr, 0u, i, cc);
+        }
+    }
+    flush_counts<true, STATS>(sa, cs.nodes, cs.tris, cs.inst);
+    flush_counts<false, STATS>(ca, cc.nodes, cc.tris, cc.inst);
 }
 
 // Binary traversal, per-lane refill.  Each lane holds one ray and advances it
@@ -888,6 +938,20 @@ cudaError_t launch_block(const TraceArgs& a, int blocks_per_sm, cudaStream_t s) 
     return cudaGetLastError();
 }
 
+template <bool STATS>
+cudaError_t launch_pair_t(const TraceArgs& sa, const TraceArgs& ca, cudaStream_t s) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_pair<STATS, kTraceBlock>,
+                                                                      kTraceBlock, 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm <= 0) per_sm = 1;
+    }
+    k_trace_pair<STATS, kTraceBlock><<<device_sm_count() * per_sm, kTraceBlock, 0, s>>>(sa, ca);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 // Refill threshold when the shape leaves it open (0): per-lane refill (8 idle
 // lanes) for the closest-hit queries of rg_trace_rays, whose rays are often
 // incoherent; whole-warp refill elsewhere (faster on camera, secondary and
@@ -959,6 +1023,11 @@ cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a0, 
             return launch_mode<kModeShadowBatch, false, false>(a, s, shape);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_trace_pair(bool stats, const TraceArgs& sa, const TraceArgs& ca, cudaStream_t s) {
+    if (sa.tlas_nodes8 || ca.tlas_nodes8) return cudaErrorInvalidValue;  // binary BVH only
+    return stats ? launch_pair_t<true>(sa, ca, s) : launch_pair_t<false>(sa, ca, s);
 }
 
 }  // namespace rg

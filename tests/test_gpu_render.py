@@ -168,3 +168,28 @@ def test_render_repeatable(tmp_path):
         a = render(s, gs=gs)
         b = render(s, gs=gs)
     np.testing.assert_allclose(a, b, atol=1e-5)
+
+
+@pytest.mark.parametrize("lights", [4, 1])
+def test_paired_launches_equal_separate_launches(lights):
+    """Tracing a level's shadow rays in one launch with the next level's
+    closest-hit rays gives the image of separate launches (up to the order of
+    float additions into a pixel) from the same rays, in max_depth - 1 pairs."""
+    s = g.medium_scene(width=480, height=270, max_depth=5)
+    s.light_pos, s.light_I = s.light_pos[:lights], s.light_I[:lights]
+    out = {}
+    for name, flags in [("pair", rg.RG_SCENE_TIMING | rg.RG_SCENE_COUNT),
+                        ("apart", rg.RG_SCENE_TIMING | rg.RG_SCENE_COUNT | rg.RG_SCENE_NO_PAIR)]:
+        with rg.GpuScene(s, flags=flags) as gs:
+            rg.rg_reset_stats(gs.h)
+            img = render(s, gs=gs)
+            out[name] = (img, rg.rg_get_stats(gs.h))
+    (a, sa), (b, sb) = out["pair"], out["apart"]
+    np.testing.assert_allclose(a, b, atol=1e-5)
+    for k in ["closest_rays", "shadow_rays", "node_visits", "tri_tests", "inst_entries", "any_node_visits",
+              "any_tri_tests", "any_inst_entries"]:
+        assert sa[k] == sb[k], k
+    assert sa["pair_launches"] == s.max_depth - 1 and sb["pair_launches"] == 0
+    assert sa["trace_launches"] == 1 and sa["any_launches"] == 1
+    assert sb["trace_launches"] == s.max_depth and sb["any_launches"] == s.max_depth
+    assert sa["kernel_launches"] == sb["kernel_launches"] - (s.max_depth - 1)
