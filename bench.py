@@ -141,28 +141,33 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def code_sha(path):
-    """Hash of a source file's code: // comments, trailing spaces and blank
-    lines removed (a comment edit leaves the kernel, and its counters, as they
-    were)."""
+def code_sha(*paths):
+    """Hash of source files' code: // comments, trailing spaces and blank
+    lines removed (a comment edit leaves the kernels, and their counters, as
+    they were)."""
     lines = []
-    for line in open(path).read().splitlines():
-        code = re.sub(r"//.*$", "", line).rstrip()
-        if code.strip():
-            lines.append(code)
+    for path in paths:
+        for line in open(path).read().splitlines():
+            code = re.sub(r"//.*$", "", line).rstrip()
+            if code.strip():
+                lines.append(code)
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
 
 
+TRAVERSAL_SOURCES = [os.path.join(ROOT, "paper_2001_09792_gb300", "csrc", f) for f in ("trace.cu", "api.cu")]
+
+
 def traffic_record():
-    """Per-ray DRAM bytes of the closest-hit traversal from the committed ncu
-    summary, valid only while the traversal code is unchanged."""
-    path = os.path.join(ROOT, "profiles", "trace_closest_medium.md")
-    src = os.path.join(ROOT, "paper_2001_09792_gb300", "csrc", "trace.cu")
+    """DRAM bytes per traversal launch of the medium frame (the frame's
+    closest-hit, pair and shadow launches, averaged) from the committed ncu
+    summary, valid only while the traversal kernels (trace.cu) and the launch
+    sequence of a frame (api.cu) are unchanged."""
+    path = os.path.join(ROOT, "profiles", "trace_pair_medium.md")
     try:
         txt = open(path).read()
-        sha = code_sha(src)
-        m = re.search(r"dram_bytes_per_closest_ray:\s*([0-9.]+)", txt)
-        s = re.search(r"trace_cu_sha256_16:\s*([0-9a-f]+)", txt)
+        sha = code_sha(*TRAVERSAL_SOURCES)
+        m = re.search(r"dram_bytes_per_traversal_launch:\s*([0-9.]+)", txt)
+        s = re.search(r"traversal_code_sha256_16:\s*([0-9a-f]+)", txt)
         if m and s and s.group(1) == sha:
             return float(m.group(1))
     except OSError:
@@ -344,7 +349,7 @@ def run_native(args, world, rank, local):
         achieved = trav_bytes / trav_launches / (launch_ms / 1e3) / 1e9
         tr = None if args.compressed else traffic_record()
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                    "frac": round(achieved / peak, 4), "traffic": None if tr is None else round(tr * rays_per_launch),
+                    "frac": round(achieved / peak, 4), "traffic": None if tr is None else round(tr),
                     "kernel": kernel_name(args, "render"), "peak_kind": peak_kind,
                     "algorithmic_bytes_per_launch": round(trav_bytes / trav_launches),
                     "algorithmic_bytes_per_closest_ray": round(bytes_per_ray, 1),
