@@ -65,7 +65,7 @@ def parse():
     p.add_argument("--requests", type=int, default=400, help="serving: requests in the Poisson stream")
     p.add_argument("--no-serving", action="store_true", help="medium: skip the serving measurement")
     p.add_argument("--no-pair", action="store_true",
-                   help="medium: trace each level's shadow rays and the next level's closest-hit rays in separate launches")
+                   help="trace each level's (server: step's) shadow rays and the next one's closest-hit rays in separate launches")
     return p.parse_args()
 
 
@@ -401,7 +401,7 @@ def run_native(args, world, rank, local):
                           "note": "frames back to back, image readback overlapped with the next frame "
                                   "(two device images, a copy stream); one timed region incl. L2 flushes"}
         if world == 1 and not args.no_serving:
-            out["serving"] = run_serving(args.requests)
+            out["serving"] = run_serving(args.requests, pair=not args.no_pair)
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(s, motions[args.warmup:], args.cpu_seconds)
         print(json.dumps(out), flush=True)
@@ -421,7 +421,7 @@ def pct(xs, q):
     return xs[min(len(xs) - 1, max(0, math.ceil(q * len(xs)) - 1))]
 
 
-def run_serving(n_requests, admit_rays=0):
+def run_serving(n_requests, admit_rays=0, pair=True):
     """The request stream through the continuous-batching server in real time,
     then the same stream one request at a time (rg_tlas_refit + rg_render each,
     in arrival order, against the same arrival clock).  Latency = arrival to
@@ -431,10 +431,10 @@ def run_serving(n_requests, admit_rays=0):
 
     scenes = g.serving_scenes()
     reqs = g.serving_requests(n_requests)
-    gss = [rg.GpuScene(sc) for sc in scenes]
+    gss = [rg.GpuScene(sc, flags=0 if pair else rg.RG_SCENE_NO_PAIR) for sc in scenes]
     trans = [g.motion(scenes[q["scene"]].M, q["motion_seed"]) for q in reqs]
     cams = [rg.make_camera(sc.camera) for sc in scenes]
-    srv = rg.rg_server_create(admit_rays=admit_rays)
+    srv = rg.rg_server_create(admit_rays=admit_rays, flags=0 if pair else rg.RG_SERVER_NO_PAIR)
     try:
         for gsc in gss:
             rg.rg_server_add_scene(srv, gsc.h)
@@ -758,7 +758,7 @@ def run_native_serve(args, world, rank, local):
     _build.build()
     if rank != 0:
         return
-    r = run_serving(args.requests)
+    r = run_serving(args.requests, pair=not args.no_pair)
     out = {"metric": "served Mrays/s and p50/p99 request latency (continuous batching) vs one request at a time",
            "value": r["mrays_s"], "unit": "Mrays/s", "n_gpus": 1, "steps": r["steps"], "warmup": len(g.serving_scenes()),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

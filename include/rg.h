@@ -280,8 +280,11 @@ rg_status rg_radix_sort_pairs_noalloc(const void* d_keys, const uint32_t* d_vals
  * dispatched and recursively traced); the server keeps that per-ray work and
  * batches it: the path rays (primary, reflected, refracted) of every request
  * in flight share one ring of rays; each rg_server_step traces and shades a
- * batch of them (closest hit, then the shadow rays the shading spawned) and
- * appends the rays it spawns, so requests of different scenes, resolutions
+ * batch of them and appends the rays it spawns; the shadow rays the shading
+ * spawns are traced by the next step, in one launch with its closest-hit
+ * rays (RG_SERVER_NO_PAIR: by the same step, after shading), so a request
+ * completes one step after its last path ray (an otherwise idle step traces
+ * only those shadow rays).  Requests of different scenes, resolutions
  * and depths are traced in the same launches.  Requests join as earlier ones
  * complete (continuous batching).  Each request carries its own instance
  * transforms: on admission the server refits a private copy of the scene's
@@ -317,13 +320,17 @@ typedef struct {
     uint32_t batch_rays;  /* rays traced per step at most; 0 = 2^23 */
     uint32_t max_lights;  /* shadow queue = batch_rays * max_lights rays (48 B each); 0 = 4; scenes with
                              more lights are refused */
-    uint32_t flags;       /* RG_SERVER_NO_GRAPH: launch each step's kernels directly, no CUDA graph */
+    uint32_t flags;       /* RG_SERVER_NO_GRAPH: launch each step's kernels directly, no CUDA graph;
+                             RG_SERVER_NO_PAIR: trace a step's shadow rays in the step, after shading
+                             (default: in the next step, one launch with its closest-hit rays, using
+                             the closest-hit shape; a request then completes one step later) */
     uint32_t admit_rays;  /* admission bound on the rays in the ring plus a new request's primary rays;
                              0 = batch_rays (what one step can take); at most half the ring.  A
                              smaller bound keeps fewer requests in flight: large requests run closer
                              to one after another (shorter tail latency), small ones still share steps */
 } rg_server_desc;
 #define RG_SERVER_NO_GRAPH 1u
+#define RG_SERVER_NO_PAIR 2u
 
 /* One render request.  h_transforms: n_inst 3x4 row-major object-to-world
  * matrices (12 floats each) in the order of the scene's rg_tlas_build, or

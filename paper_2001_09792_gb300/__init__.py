@@ -46,6 +46,7 @@ RG_SERVER_MAX_SLOTS = 32
 RG_SERVER_MAX_PIXELS = 1 << 23
 RG_SERVER_MAX_DEPTH = 15
 RG_SERVER_NO_GRAPH = 1
+RG_SERVER_NO_PAIR = 2
 RG_TUNE_FORCE = 1
 
 f32x3 = ctypes.c_float * 3

@@ -748,7 +748,7 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
             a.hits_render = s->hits.p;
             EventPair* ev;
             if ((r = event_begin(s, 2, st, &ev))) return r;
-            RG_CK(launch_trace_pair(s->desc.flags & RG_SCENE_COUNT, b, a, st));
+            RG_CK(launch_trace_pair(false, s->desc.flags & RG_SCENE_COUNT, b, a, st));
             if ((r = event_end(s, st))) return r;
         } else if ((r = trace_closest(1 - cur, 0, c + 1, c + CB))) {
             return r;

@@ -250,9 +250,12 @@ struct TraceArgs {
 constexpr uint32_t kMaxLights = 64;  // lights per scene (one shadow sub-queue each)
 cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a, cudaStream_t s,
                          const TraceShape& shape = TraceShape());
-// The shadow rays of sa (kModeShadowRender) and the closest-hit rays of ca
-// (kModeClosestRender) in one launch; sa.work_counter serves both.  Binary BVH only.
-cudaError_t launch_trace_pair(bool stats, const TraceArgs& sa, const TraceArgs& ca, cudaStream_t s);
+// The shadow rays of sa and the closest-hit rays of ca in one launch
+// (kModeShadowRender + kModeClosestRender, or with batch the two batched
+// modes, whose launch takes shape.block and shape.blocks_per_sm);
+// sa.work_counter serves both.  Binary BVH only.
+cudaError_t launch_trace_pair(bool batch, bool stats, const TraceArgs& sa, const TraceArgs& ca, cudaStream_t s,
+                              const TraceShape& shape = TraceShape());
 
 // render.cu
 struct CameraDev {

@@ -8,7 +8,10 @@
 //    the ray depth, so one launch traces rays of many requests;
 //  * a step traces the m oldest rays of the ring (closest hit), shades them
 //    (shadow rays into a dense queue, reflected / refracted rays appended to
-//    the ring), traces the shadow rays, and advances the ring head;
+//    the ring), and advances the ring head; the shadow rays a step makes are
+//    traced by the next step, in one launch with its closest-hit rays (or,
+//    with RG_SERVER_NO_PAIR, by the same step after shading), so a request
+//    completes one step after its last path ray;
 //  * per-slot live counts (path rays still in the ring) tell the host which
 //    requests finished;
 //  * per-request TLAS: on admission, a slot's private copy of the scene's TLAS
@@ -42,7 +45,8 @@ struct RingState {
     uint32_t work_closest, next_count, work_shadow;
     uint32_t pad[4];
     int slot_live[kMaxSlots];   // path rays of each slot in the ring
-    uint32_t shadow_count[kMaxLights];  // shadow rays toward each light (one sub-queue each)
+    uint32_t shadow_count[kMaxLights];       // shadow rays toward each light made by this step (one sub-queue each)
+    uint32_t prev_shadow_count[kMaxLights];  // the same for the previous step (traced by this one when paired)
 };
 
 // Host -> device once per step.
@@ -65,7 +69,8 @@ struct __align__(16) StepOut {
     int slot_live[kMaxSlots];
 };
 
-constexpr unsigned kStepKernels = 7;   // begin, raygen, closest, shade, shadow, close gap, end
+// begin, raygen, closest + previous shadow (paired) or closest and shadow, shade, close gap, end
+constexpr unsigned kStepKernelsPaired = 6, kStepKernelsApart = 7;
 constexpr unsigned kRefitKernels = 2;  // instance prep, TLAS leaf refit
 
 __global__ void k_step_begin(const StepHdr* __restrict__ hdr, RingState* __restrict__ rs) {
@@ -82,7 +87,10 @@ __global__ void k_step_begin(const StepHdr* __restrict__ hdr, RingState* __restr
         rs->next_count = 0;
         rs->work_shadow = 0;
     }
-    for (uint32_t k = l; k < kMaxLights; k += blockDim.x) rs->shadow_count[k] = 0;
+    for (uint32_t k = l; k < kMaxLights; k += blockDim.x) {
+        rs->prev_shadow_count[k] = rs->shadow_count[k];
+        rs->shadow_count[k] = 0;
+    }
 }
 
 // Newest-first steps leave the consumed rays [T - m, T) as a gap below the
@@ -172,6 +180,7 @@ struct Pending {
 
 struct Active {
     bool on = false;
+    bool flushing = false;  // no path rays left; its last shadow rays are traced by the next step
     uint64_t id = 0, tag = 0;
     uint32_t scene = 0, admitted_step = 0;
 };
@@ -222,6 +231,17 @@ namespace {
 rg_status set_dev(rg_server* s) {
     SV_CK(cudaSetDevice(s->device));
     return RG_OK;
+}
+
+// Shadow rays traced by the next step, with its closest-hit rays.
+bool paired(const rg_server* s) { return !(s->flags & RG_SERVER_NO_PAIR); }
+
+// Whether a step must run although the ring is empty: paired steps leave the
+// last shadow rays of finished requests to the next step.
+bool shadow_flush_due(const rg_server* s) {
+    for (const Active& a : s->active)
+        if (a.on && a.flushing) return true;
+    return false;
 }
 
 void free_slot_bufs(SlotBufs& b) {
@@ -288,10 +308,10 @@ TraceArgs closest_args(rg_server* s, const uint32_t* d_count) {
     return a;
 }
 
-TraceArgs shadow_args(rg_server* s) {
+TraceArgs shadow_args(rg_server* s, const uint32_t* counts) {
     TraceArgs b{};
     b.rays = s->s_rays;
-    b.sub_counts = s->d_rs->shadow_count;
+    b.sub_counts = counts;
     b.n_sub = s->max_lights;
     b.sub_stride = s->batch;
     b.payload = s->s_pay;
@@ -334,9 +354,18 @@ rg_status enqueue_step(rg_server* s) {
     SV_CK(cudaGetLastError());
     SV_CK(launch_raygen_batch(s->d_hdr->reqs, &s->d_hdr->n_reqs, s->ring_cap / 2, &s->d_hdr->n_new_rays,
                               &s->d_rs->gen_base, s->ring_mask, s->ring_rays, s->ring_pay, s->stream));
-    SV_CK(launch_trace(kModeClosestBatch, false, false, closest_args(s, &s->d_hdr->m), s->stream, s->shape[0]));
-    SV_CK(launch_shade_batch(shade_args(s, &s->d_hdr->m), s->stream));
-    SV_CK(launch_trace(kModeShadowBatch, false, false, shadow_args(s), s->stream, s->shape[1]));
+    if (paired(s)) {
+        // the previous step's shadow rays with this step's closest-hit rays;
+        // shading then refills the shadow queue
+        SV_CK(launch_trace_pair(true, false, shadow_args(s, s->d_rs->prev_shadow_count), closest_args(s, &s->d_hdr->m),
+                                s->stream, s->shape[0]));
+        SV_CK(launch_shade_batch(shade_args(s, &s->d_hdr->m), s->stream));
+    } else {
+        SV_CK(launch_trace(kModeClosestBatch, false, false, closest_args(s, &s->d_hdr->m), s->stream, s->shape[0]));
+        SV_CK(launch_shade_batch(shade_args(s, &s->d_hdr->m), s->stream));
+        SV_CK(launch_trace(kModeShadowBatch, false, false, shadow_args(s, s->d_rs->shadow_count), s->stream,
+                           s->shape[1]));
+    }
     k_close_gap<<<device_sm_count() * 4, 256, 0, s->stream>>>(s->d_hdr, s->d_rs, s->ring_mask, s->ring_rays,
                                                               s->ring_pay);
     count_launches(1);
@@ -383,8 +412,9 @@ rg_status run_step_work(rg_server* s) {
     rg_status r;
     if (!s->step_exec && (r = capture(s, [&] { return enqueue_step(s); }, &s->step_exec))) return r;
     SV_CK(cudaGraphLaunch(s->step_exec, s->stream));
-    count_launches(kStepKernels);
-    s->stats.kernel_launches += kStepKernels;
+    const unsigned k = paired(s) ? kStepKernelsPaired : kStepKernelsApart;
+    count_launches(k);
+    s->stats.kernel_launches += k;
     s->stats.graph_launches++;
     return RG_OK;
 }
@@ -521,6 +551,10 @@ rg_status finish_step(rg_server* s, uint32_t* n_completed) {
         }
         if (O.slot_live[k] < 0) return sfail(RG_ERR_CUDA, "render server: negative live ray count");
         live_sum += O.slot_live[k];
+        if (O.slot_live[k] == 0 && paired(s) && s->max_lights && !s->active[k].flushing) {
+            s->active[k].flushing = true;  // complete after the next step traces its last shadow rays
+            continue;
+        }
         if (O.slot_live[k] == 0) {
             rg_completion c;
             c.id = s->active[k].id;
@@ -802,10 +836,11 @@ rg_status rg_server_step(rg_server* s, uint32_t* n_completed) {
     uint32_t n_new = 0;
     if ((r = admit(s, &n_new))) return r;
     const uint32_t avail = s->ring_rays_now + n_new;
-    if (avail == 0) return RG_OK;
+    // an empty ring still takes a step while finished requests wait for their last shadow rays
+    if (avail == 0 && !shadow_flush_due(s)) return RG_OK;
     bool newest = false;
-    const uint32_t m = step_batch(s, avail, &newest);
-    if (m == 0) return sfail(RG_ERR_OOM, "ray ring full: no room for the rays a step spawns");
+    const uint32_t m = avail ? step_batch(s, avail, &newest) : 0u;
+    if (avail && m == 0) return sfail(RG_ERR_OOM, "ray ring full: no room for the rays a step spawns");
     s->h_hdr->m = m;
     s->h_hdr->newest_first = newest ? 1u : 0u;
     if (newest) s->stats.newest_first_steps++;
@@ -911,7 +946,8 @@ rg_status rg_server_autotune(rg_server* s, const rg_request* sample, const char*
                 if (which == 0)
                     SV_CK(launch_trace(kModeClosestBatch, false, false, closest_args(s, s->d_tune_count), s->stream, t));
                 else
-                    SV_CK(launch_trace(kModeShadowBatch, false, false, shadow_args(s), s->stream, t));
+                    SV_CK(launch_trace(kModeShadowBatch, false, false, shadow_args(s, s->d_rs->shadow_count),
+                                       s->stream, t));
                 SV_CK(cudaEventRecord(s->t1, s->stream));
                 SV_CK(cudaEventSynchronize(s->t1));
                 float e = 0;

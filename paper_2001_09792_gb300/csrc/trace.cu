@@ -427,20 +427,23 @@ __global__ void __launch_bounds__(BLOCK) k_trace_warp(TraceArgs a) {
 }
 
 // The shadow rays of one depth level and the closest-hit rays of the next in
-// one persistent launch (both depend only on the shading of the level): one
-// work counter runs over the shadow rays (in whole warps of 32) and then over
-// the closest-hit rays, so warps that run out of one kind take the other and
-// the SMs stay busy until the last batch of both, instead of idling through
-// the tail of two separate launches.
-// Held to 64 registers (8 blocks of 128 per SM, as the single-mode kernels):
-// with both ray kinds inlined it would take 76 and fit 6 blocks, which
-// measured slower than the few spilled values cost.
-template <bool STATS, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 8) k_trace_pair(TraceArgs sa, TraceArgs ca) {
+// one persistent launch (both depend only on the shading of the level; in the
+// render server, the shadow rays of the previous step and the closest-hit
+// rays of this one): one work counter runs over the shadow rays (in whole
+// warps of 32) and then over the closest-hit rays, so warps that run out of
+// one kind take the other and the SMs stay busy until the last batch of both,
+// instead of idling through the tail of two separate launches.
+// Held to 64 registers (1024 threads per SM, as the single-mode kernels):
+// with both ray kinds inlined it would take 76 and fit 768, which measured
+// slower than the few spilled values cost.
+template <int SMODE, int CMODE, bool STATS, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_trace_pair(TraceArgs sa, TraceArgs ca) {
     __shared__ uint32_t pre[kMaxLights + 1];
     const uint32_t ns = ray_count(sa, pre);
     const uint32_t nc = ca.d_count ? *ca.d_count : ca.n;
     const uint32_t ns_pad = (ns + 31u) & ~31u;
+    // batched closest-hit rays sit in a ring of 2^k entries from *ring_head
+    const uint32_t head = CMODE == kModeClosestBatch ? *ca.ring_head : 0u;
     const int lane = threadIdx.x & 31;
     TraceCounts cs, cc;
     for (;;) {
@@ -449,12 +452,12 @@ __global__ void __launch_bounds__(BLOCK, 8) k_trace_pair(TraceArgs sa, TraceArgs
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
         if (base < ns_pad) {
             const uint32_t i = base + lane;
-            if (i < ns) trace_ray<kModeShadowRender, false, STATS>(sa, pre, 0u, i, cs);
+            if (i < ns) trace_ray<SMODE, false, STATS>(sa, pre, 0u, i, cs);
         } else {
             const uint32_t b = base - ns_pad;
             if (b >= nc) break;
             const uint32_t i = b + lane;
-            if (i < nc) trace_ray<kModeClosestRender, false, STATS>(ca, nullptr, 0u, i, cc);
+            if (i < nc) trace_ray<CMODE, false, STATS>(ca, nullptr, head, i, cc);
         }
     }
     flush_counts<true, STATS>(sa, cs.nodes, cs.tris, cs.inst);
@@ -938,16 +941,17 @@ cudaError_t launch_block(const TraceArgs& a, int blocks_per_sm, cudaStream_t s) 
     return cudaGetLastError();
 }
 
-template <bool STATS>
-cudaError_t launch_pair_t(const TraceArgs& sa, const TraceArgs& ca, cudaStream_t s) {
+template <int SMODE, int CMODE, bool STATS, int BLOCK>
+cudaError_t launch_pair_t(const TraceArgs& sa, const TraceArgs& ca, int blocks_per_sm, cudaStream_t s) {
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_pair<STATS, kTraceBlock>,
-                                                                      kTraceBlock, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_pair<SMODE, CMODE, STATS, BLOCK>,
+                                                                      BLOCK, 0);
         if (e != cudaSuccess) return e;
         if (per_sm <= 0) per_sm = 1;
     }
-    k_trace_pair<STATS, kTraceBlock><<<device_sm_count() * per_sm, kTraceBlock, 0, s>>>(sa, ca);
+    const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
+    k_trace_pair<SMODE, CMODE, STATS, BLOCK><<<device_sm_count() * b, BLOCK, 0, s>>>(sa, ca);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1025,9 +1029,19 @@ cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a0, 
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_trace_pair(bool stats, const TraceArgs& sa, const TraceArgs& ca, cudaStream_t s) {
+cudaError_t launch_trace_pair(bool batch, bool stats, const TraceArgs& sa, const TraceArgs& ca, cudaStream_t s,
+                              const TraceShape& shape) {
     if (sa.tlas_nodes8 || ca.tlas_nodes8) return cudaErrorInvalidValue;  // binary BVH only
-    return stats ? launch_pair_t<true>(sa, ca, s) : launch_pair_t<false>(sa, ca, s);
+    if (batch) {
+        if (stats) return cudaErrorInvalidValue;
+        if (shape.block == 64)
+            return launch_pair_t<kModeShadowBatch, kModeClosestBatch, false, 64>(sa, ca, shape.blocks_per_sm, s);
+        if (shape.block == 256)
+            return launch_pair_t<kModeShadowBatch, kModeClosestBatch, false, 256>(sa, ca, shape.blocks_per_sm, s);
+        return launch_pair_t<kModeShadowBatch, kModeClosestBatch, false, 128>(sa, ca, shape.blocks_per_sm, s);
+    }
+    return stats ? launch_pair_t<kModeShadowRender, kModeClosestRender, true, kTraceBlock>(sa, ca, 0, s)
+                 : launch_pair_t<kModeShadowRender, kModeClosestRender, false, kTraceBlock>(sa, ca, 0, s);
 }
 
 }  // namespace rg

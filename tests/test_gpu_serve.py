@@ -242,3 +242,33 @@ def test_admission_bound_keeps_requests_apart(scenes):
     assert spans[0][0] == 1 and spans[1][0] > 1             # the large one alone first
     assert spans[1][0] == spans[2][0]                       # the small ones together
     check_against_alone(descs, gss, reqs, imgs, st)
+
+
+def test_paired_steps_equal_separate_steps(scenes):
+    """Tracing a step's shadow rays in the next step (one launch with its
+    closest-hit rays) gives the images and ray counts of tracing them in the
+    step itself; each request then completes exactly one step later."""
+    descs, gss = scenes
+    reqs = make_requests(descs, 10, seed=19, sizes=[(160, 120), (97, 33), (320, 180)], depths=[1, 3, 6])
+    a, da, sa = run_server(gss, reqs, batch_rays=1 << 16)
+    b, db, sb = run_server(gss, reqs, batch_rays=1 << 16, flags=rg.RG_SERVER_NO_PAIR)
+    for x, y in zip(a, b):
+        np.testing.assert_allclose(x, y, atol=ATOL, rtol=0)
+    assert sa["closest_rays"] == sb["closest_rays"] and sa["shadow_rays"] == sb["shadow_rays"]
+    ca = {d["tag"]: (d["admitted_step"], d["completed_step"]) for d in da}
+    cb = {d["tag"]: (d["admitted_step"], d["completed_step"]) for d in db}
+    for t in ca:
+        assert ca[t][0] == cb[t][0] and ca[t][1] == cb[t][1] + 1, (t, ca[t], cb[t])
+    # six kernels per paired step, seven apart
+    assert sa["kernel_launches"] - 6 * sa["steps"] == sb["kernel_launches"] - 7 * sb["steps"]
+
+
+def test_single_request_completes_after_its_shadow_rays(scenes):
+    """A depth-1 request: its rays are traced and shaded in the first step;
+    the second step (an otherwise empty ring) traces its shadow rays."""
+    descs, gss = scenes
+    s = descs[1]
+    req = [dict(scene=1, w=64, h=48, depth=1, M=s.M, camera=s.camera)]
+    imgs, done, st = run_server(gss, req)
+    assert done[0]["admitted_step"] == 1 and done[0]["completed_step"] == 2 and st["steps"] == 2
+    check_against_alone(descs, gss, req, imgs, st)
