@@ -387,13 +387,13 @@ rg_status rg_blas_build(rg_scene* s, const float* d_vtx, uint32_t nv, const uint
     b.nt = nt;
     b.root = nt == 1 ? kLeaf : 0u;
     if ((r = dev_alloc(reinterpret_cast<void**>(&b.nodes), n_int * 64, "BLAS nodes"))) return r;
-    if ((r = dev_alloc(reinterpret_cast<void**>(&b.tris), (size_t)nt * 48, "BLAS triangles"))) {
+    if ((r = dev_alloc(reinterpret_cast<void**>(&b.tris), (size_t)nt * kTriRecord, "BLAS triangles"))) {
         free_blas(b);
         return r;
     }
     if (wide) {
         if ((r = dev_alloc(reinterpret_cast<void**>(&b.nodes8), n_int * 80, "wide BLAS nodes")) ||
-            (r = dev_alloc(reinterpret_cast<void**>(&b.tris8), (size_t)nt * 48, "wide BLAS triangles")) ||
+            (r = dev_alloc(reinterpret_cast<void**>(&b.tris8), (size_t)nt * kTriRecord, "wide BLAS triangles")) ||
             (r = dev_alloc(reinterpret_cast<void**>(&b.src8), n_int * 32, "wide BLAS slot sources")) ||
             (r = dev_alloc(reinterpret_cast<void**>(&b.item_src8), (size_t)nt * 4, "wide BLAS item sources")) ||
             (r = dev_alloc(reinterpret_cast<void**>(&b.counts8), 16, "wide BLAS counts"))) {
@@ -894,7 +894,8 @@ rg_status rg_blas_export(rg_scene* s, uint32_t blas_id, void* h_nodes, void* h_t
     RG_CK(cudaDeviceSynchronize());
     const BlasHost& b = s->blas[blas_id];
     if (h_nodes && b.nt > 1) RG_CK(cudaMemcpy(h_nodes, b.nodes, (size_t)(b.nt - 1) * 64, cudaMemcpyDeviceToHost));
-    if (h_tris) RG_CK(cudaMemcpy(h_tris, b.tris, (size_t)b.nt * 48, cudaMemcpyDeviceToHost));
+    // the (x, y, z) order of each triangle record
+    if (h_tris) RG_CK(cudaMemcpy2D(h_tris, 48, b.tris, kTriRecord, 48, b.nt, cudaMemcpyDeviceToHost));
     if (h_root) *h_root = b.root;
     return RG_OK;
 }

@@ -424,10 +424,16 @@ __global__ void k_blas_leaves_refit(const float* __restrict__ vtx, const uint32_
     if (j >= n) return;
     uint32_t prim = perm[j];
     uint32_t vi[3] = {idx[3 * (size_t)prim], idx[3 * (size_t)prim + 1], idx[3 * (size_t)prim + 2]};
+    // the triangle record: its vertices in the axis orders (x, y, z), (y, z, x)
+    // and (z, x, y), prim in the first vertex's w of each
+    float4* t = tris + 9 * (size_t)j;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         float x = vtx[3 * (size_t)vi[c]], y = vtx[3 * (size_t)vi[c] + 1], z = vtx[3 * (size_t)vi[c] + 2];
-        tris[3 * (size_t)j + c] = make_float4(x, y, z, c == 0 ? __uint_as_float(prim) : 0.0f);
+        const float w = c == 0 ? __uint_as_float(prim) : 0.0f;
+        t[c] = make_float4(x, y, z, w);
+        t[3 + c] = make_float4(y, z, x, w);
+        t[6 + c] = make_float4(z, x, y, w);
     }
     float box[6];
 #pragma unroll

@@ -194,7 +194,7 @@ __device__ __forceinline__ void shade_one(const ShadeArgs& a, uint32_t head, uin
             if (c.depth == 1) px[3] = 1.0f;
             const InstDev* I = c.inst + hd.inst_leaf;
             const float4 i0 = I->inv[0], i1 = I->inv[1], i2 = I->inv[2];
-            const float4* tp = I->tris + 3 * (size_t)hd.tri_leaf;
+            const float4* tp = I->tris + kTriStride * (size_t)hd.tri_leaf;  // the (x, y, z) order
             const float4 v0 = tp[0], v1 = tp[1], v2 = tp[2];
             float3 e1 = f3(v1.x - v0.x, v1.y - v0.y, v1.z - v0.z);
             float3 e2 = f3(v2.x - v0.x, v2.y - v0.y, v2.z - v0.z);

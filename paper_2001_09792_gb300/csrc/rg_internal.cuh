@@ -29,10 +29,17 @@ constexpr uint32_t kLeaf = 0x80000000u;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kMiss = 0xFFFFFFFFu;
 
+// A BLAS triangle record: the three vertices (float4 each, prim in the first
+// one's w) in the axis orders (x, y, z), (y, z, x) and (z, x, y), 144 B.  The
+// watertight test reads the order whose last axis is the ray's dominant one,
+// so it needs no per-coordinate selection; shading reads the first.
+constexpr size_t kTriRecord = 144;
+constexpr uint32_t kTriStride = 9;  // float4s per triangle record
+
 struct __align__(16) InstDev {
     float4 inv[3];          // world -> object rows (float32 of the float64 inverse)
     const float4* nodes;    // BLAS nodes
-    const float4* tris;     // BLAS triangles
+    const float4* tris;     // BLAS triangle records (kTriRecord each)
     uint32_t root;          // BLAS root reference
     uint32_t id;            // index in the caller's instance array
     uint32_t material;

@@ -84,18 +84,22 @@ __device__ __forceinline__ bool visit_first0(float tn0, float tf0, float tn1, fl
     return ANY ? (tf0 - tn0) >= (tf1 - tn1) : tn0 <= tn1;
 }
 
-__device__ __forceinline__ float sel(float4 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
 
 // Watertight-test state of the object-space ray.
 struct Shear {
-    float ox, oy, oz;  // origin permuted to (kx, ky, kz)
+    float ox, oy, oz;  // origin in the axis order (kx, ky, kz)
     float Sx, Sy, Sz;
-    int kx, ky, kz;
+    uint32_t order;    // which order of the triangle records: 0 (x, y, z), 1 (y, z, x), 2 (z, x, y)
 };
 
-// Shear of the watertight test: Sz = 1/d_kz and Sx, Sy = d_kx, d_ky times it,
-// each correctly rounded.  Any fixed shear keeps the test watertight for the
-// ray; all traversals use this one, so their hit records are bit-identical.
+// Shear of the watertight test: kz is the dominant axis of the direction,
+// (kx, ky, kz) the cyclic order ending in it; Sz = 1/d_kz and Sx, Sy = d_kx,
+// d_ky times it, each correctly rounded.  Any fixed shear keeps the test
+// watertight for the ray; all traversals use this one, so their hit records
+// are bit-identical.  (Woop et al. swap kx and ky when d_kz < 0 to keep the
+// winding for back-face culling; without culling the swap only negates U, V,
+// W, det and T together, which leaves t and the barycentrics exactly as
+// they are, so the order stays cyclic and matches a stored record.)
 __device__ __forceinline__ Shear make_shear(float ox, float oy, float oz, float dx, float dy, float dz) {
     Shear s;
     float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
@@ -103,23 +107,22 @@ __device__ __forceinline__ Shear make_shear(float ox, float oy, float oz, float 
     int kx = kz == 2 ? 0 : kz + 1;
     int ky = kx == 2 ? 0 : kx + 1;
     float dkz = kz == 0 ? dx : (kz == 1 ? dy : dz);
-    if (dkz < 0.0f) {
-        int t = kx;
-        kx = ky;
-        ky = t;
-    }
     float dkx = kx == 0 ? dx : (kx == 1 ? dy : dz);
     float dky = ky == 0 ? dx : (ky == 1 ? dy : dz);
     s.Sz = __frcp_rn(dkz);  // 1/d_kz, correctly rounded
     s.Sx = __fmul_rn(dkx, s.Sz);
     s.Sy = __fmul_rn(dky, s.Sz);
-    s.kx = kx;
-    s.ky = ky;
-    s.kz = kz;
+    s.order = (uint32_t)kx;  // (kx, ky, kz) = (0, 1, 2), (1, 2, 0) or (2, 0, 1)
     s.ox = kx == 0 ? ox : (kx == 1 ? oy : oz);
     s.oy = ky == 0 ? ox : (ky == 1 ? oy : oz);
     s.oz = kz == 0 ? ox : (kz == 1 ? oy : oz);
     return s;
+}
+
+// The vertices of triangle `leaf` in the ray's axis order (tris: the BLAS
+// records offset by 3 * Shear::order at the instance entry).
+__device__ __forceinline__ const float4* tri_rec(const float4* tris, uint32_t leaf) {
+    return tris + kTriStride * (size_t)leaf;
 }
 
 struct TriResult {
@@ -127,18 +130,19 @@ struct TriResult {
     float t, V, W, det;
 };
 
-// Woop-Benthin-Wald watertight test; returns the hit if t in [tmin, tmax_incl].
+// Woop-Benthin-Wald watertight test on vertices given in the ray's axis order
+// (x = kx, y = ky, z = kz); returns the hit if t in [tmin, tmax_incl].
 __device__ __forceinline__ TriResult tri_test(const Shear& s, float4 v0, float4 v1, float4 v2, float tmin,
                                               float tmax_incl) {
     TriResult r;
     r.hit = false;
-    float az = __fsub_rn(sel(v0, s.kz), s.oz), bz = __fsub_rn(sel(v1, s.kz), s.oz), cz = __fsub_rn(sel(v2, s.kz), s.oz);
-    float Ax = __fsub_rn(__fsub_rn(sel(v0, s.kx), s.ox), __fmul_rn(s.Sx, az));
-    float Ay = __fsub_rn(__fsub_rn(sel(v0, s.ky), s.oy), __fmul_rn(s.Sy, az));
-    float Bx = __fsub_rn(__fsub_rn(sel(v1, s.kx), s.ox), __fmul_rn(s.Sx, bz));
-    float By = __fsub_rn(__fsub_rn(sel(v1, s.ky), s.oy), __fmul_rn(s.Sy, bz));
-    float Cx = __fsub_rn(__fsub_rn(sel(v2, s.kx), s.ox), __fmul_rn(s.Sx, cz));
-    float Cy = __fsub_rn(__fsub_rn(sel(v2, s.ky), s.oy), __fmul_rn(s.Sy, cz));
+    float az = __fsub_rn(v0.z, s.oz), bz = __fsub_rn(v1.z, s.oz), cz = __fsub_rn(v2.z, s.oz);
+    float Ax = __fsub_rn(__fsub_rn(v0.x, s.ox), __fmul_rn(s.Sx, az));
+    float Ay = __fsub_rn(__fsub_rn(v0.y, s.oy), __fmul_rn(s.Sy, az));
+    float Bx = __fsub_rn(__fsub_rn(v1.x, s.ox), __fmul_rn(s.Sx, bz));
+    float By = __fsub_rn(__fsub_rn(v1.y, s.oy), __fmul_rn(s.Sy, bz));
+    float Cx = __fsub_rn(__fsub_rn(v2.x, s.ox), __fmul_rn(s.Sx, cz));
+    float Cy = __fsub_rn(__fsub_rn(v2.y, s.oy), __fmul_rn(s.Sy, cz));
     float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
     float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
     float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
@@ -360,7 +364,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& a, const uint32_t* pr
             const unsigned long long pn = ((unsigned long long)__float_as_uint(meta0.y) << 32) | __float_as_uint(meta0.x);
             const unsigned long long pt = ((unsigned long long)__float_as_uint(meta0.w) << 32) | __float_as_uint(meta0.z);
             nodes = reinterpret_cast<const float4*>(pn);
-            tris = reinterpret_cast<const float4*>(pt);
+            tris = reinterpret_cast<const float4*>(pt) + 3 * sh.order;  // the ray's axis order
             cur_id = meta1.y;
             cur_leaf = leaf;
             in_blas = true;
@@ -375,7 +379,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& a, const uint32_t* pr
         }
         // triangle leaf
         {
-            const float4* tp = tris + 3 * (size_t)leaf;
+            const float4* tp = tri_rec(tris, leaf);
             const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
             if (STATS) ++cnt.tris;
             TriResult h = tri_test(sh, v0, v1, v2, tmin, kAny ? tmax : best_t);
@@ -433,11 +437,13 @@ __global__ void __launch_bounds__(BLOCK) k_trace_warp(TraceArgs a) {
 // warps of 32) and then over the closest-hit rays, so warps that run out of
 // one kind take the other and the SMs stay busy until the last batch of both,
 // instead of idling through the tail of two separate launches.
-// Held to 64 registers (1024 threads per SM, as the single-mode kernels):
-// with both ray kinds inlined it would take 76 and fit 768, which measured
-// slower than the few spilled values cost.
+// Launched for 896 resident threads per SM (72 registers, 7 blocks of 128):
+// with both ray kinds inlined the kernel would take more and fit 768, and
+// held to 64 registers (1024 threads) it spills inside the traversal loop;
+// on the medium frame 896 measured fastest (2587 Mrays/s against 2550 at
+// 768 and 2381 at 1024).
 template <int SMODE, int CMODE, bool STATS, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_trace_pair(TraceArgs sa, TraceArgs ca) {
+__global__ void __launch_bounds__(BLOCK, 896 / BLOCK) k_trace_pair(TraceArgs sa, TraceArgs ca) {
     __shared__ uint32_t pre[kMaxLights + 1];
     const uint32_t ns = ray_count(sa, pre);
     const uint32_t nc = ca.d_count ? *ca.d_count : ca.n;
@@ -602,7 +608,8 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
                 nodes = reinterpret_cast<const float4*>(
                     ((unsigned long long)__float_as_uint(meta0.y) << 32) | __float_as_uint(meta0.x));
                 tris = reinterpret_cast<const float4*>(
-                    ((unsigned long long)__float_as_uint(meta0.w) << 32) | __float_as_uint(meta0.z));
+                           ((unsigned long long)__float_as_uint(meta0.w) << 32) | __float_as_uint(meta0.z)) +
+                       3 * sh.order;  // the ray's axis order
                 cur_id = meta1.y;
                 cur_leaf = leaf;
                 in_blas = true;
@@ -612,7 +619,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
         } else {
             // triangle
             const uint32_t leaf = ref & ~kLeaf;
-            const float4* tp = tris + 3 * (size_t)leaf;
+            const float4* tp = tri_rec(tris, leaf);
             const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
             if (STATS) ++c_tris;
             const TriResult h = tri_test(sh, v0, v1, v2, tmin, kAny ? tmax : best_t);
@@ -851,7 +858,7 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace8(TraceArgs a) {
                         const unsigned long long pt =
                             ((unsigned long long)__float_as_uint(meta0.w) << 32) | __float_as_uint(meta0.z);
                         nodes = reinterpret_cast<const float4*>(pn);
-                        tris = reinterpret_cast<const float4*>(pt);
+                        tris = reinterpret_cast<const float4*>(pt) + 3 * sh.order;  // the ray's axis order
                         cur_id = meta1.y;
                         cur_leaf = item;
                         in_blas = true;
@@ -861,7 +868,7 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace8(TraceArgs a) {
                         i_bits = 0;
                         continue;
                     }
-                    const float4* tp = tris + 3 * (size_t)item;
+                    const float4* tp = tri_rec(tris, item);
                     const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
                     if (STATS) ++c_tris;
                     TriResult h = tri_test(sh, v0, v1, v2, tmin, kAny ? tmax : best_t);

@@ -154,11 +154,10 @@ struct CollapseArgs {
 
 __device__ void copy_item(const CollapseArgs& a, uint32_t from, uint32_t to) {
     if (a.tris2) {
-        const float4* t = a.tris2 + 3 * (size_t)from;
-        float4* d = a.tris8 + 3 * (size_t)to;
-        d[0] = t[0];
-        d[1] = t[1];
-        d[2] = t[2];
+        const float4* t = a.tris2 + kTriStride * (size_t)from;
+        float4* d = a.tris8 + kTriStride * (size_t)to;
+#pragma unroll
+        for (uint32_t c = 0; c < kTriStride; ++c) d[c] = t[c];
     } else {
         InstDev I = a.inst2[from];
         const BlasDev& B = a.blas[I.blas];
