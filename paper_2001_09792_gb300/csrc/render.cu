@@ -87,9 +87,12 @@ __global__ void k_raygen(CameraDev cam, uint32_t w, uint32_t h, float4* __restri
     payload[i] = p;
 }
 
-// exclusive warp prefix of `c`; the warp total goes to one atomicAdd on *tail
-// (and, if `counter` is given, to a 64-bit statistics counter)
-__device__ __forceinline__ uint32_t warp_claim(uint32_t c, uint32_t* tail, unsigned long long* counter = nullptr) {
+// exclusive block prefix of `c`: warp totals meet in shared memory, and the
+// block total goes to one atomicAdd on *tail (every thread of the block calls
+// it; sm[0] starts at 0).  One global atomic per block and queue instead of
+// one per warp: the queue tails are single addresses that every block of a
+// level appends to, and per-warp claims measured 6 % of the frame slower.
+__device__ __forceinline__ uint32_t block_claim(uint32_t c, uint32_t* tail, uint32_t* sm) {
     const int lane = threadIdx.x & 31;
     uint32_t x = c;
 #pragma unroll
@@ -97,15 +100,20 @@ __device__ __forceinline__ uint32_t warp_claim(uint32_t c, uint32_t* tail, unsig
         uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
         if (lane >= off) x += y;
     }
-    uint32_t total = __shfl_sync(0xFFFFFFFFu, x, 31);
-    uint32_t base = 0;
-    if (lane == 31 && total) {
-        base = atomicAdd(tail, total);
-        if (counter) atomicAdd(counter, (unsigned long long)total);
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, x, 31);
+    uint32_t woff = 0;
+    if (lane == 31 && total) woff = atomicAdd(&sm[0], total);
+    woff = __shfl_sync(0xFFFFFFFFu, woff, 31);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t t = sm[0];
+        sm[1] = t ? atomicAdd(tail, t) : 0u;
+        sm[0] = 0u;
     }
-    base = __shfl_sync(0xFFFFFFFFu, base, 31);
-    return base + x - c;
+    __syncthreads();
+    return sm[1] + woff + x - c;
 }
+
 
 struct Surf {
     float3 p, nf, d;
@@ -163,12 +171,12 @@ __device__ __forceinline__ RayCtx ray_ctx(const ShadeArgs& a, const SlotDev* slo
     return c;
 }
 
-// Shade ray i (valid == false: take part in the warp's queue claims only).
+// Shade ray i (valid == false: take part in the block's queue claims only).
 // live_delta (batched only): per-slot sums of (path rays spawned - 1) of this
 // block, in shared memory.
 template <bool BATCH>
 __device__ __forceinline__ void shade_one(const ShadeArgs& a, uint32_t head, uint32_t next_base, uint32_t i,
-                                          bool valid, int* live_delta) {
+                                          bool valid, int* live_delta, uint32_t* sm) {
     uint32_t n_next = 0;
     bool lit = false;  // a diffuse hit: ambient term and shadow rays
     Surf s;
@@ -233,8 +241,8 @@ __device__ __forceinline__ void shade_one(const ShadeArgs& a, uint32_t head, uin
         }
     }
     // shadow rays: one sub-queue per light, so that a warp of shadow rays
-    // holds neighbouring surface points seen toward the same light (all lanes
-    // take part in every claim)
+    // holds neighbouring surface points seen toward the same light (every
+    // thread of the block takes part in every claim)
     {
         const uint32_t shadow_pw = BATCH ? pack_pixel(c.pixel, c.depth, c.slot) : c.pixel;
         const float3 os = lit ? s.p + s.eps * s.nf : f3(0.f, 0.f, 0.f);
@@ -248,7 +256,7 @@ __device__ __forceinline__ void shade_one(const ShadeArgs& a, uint32_t head, uin
                 lv = f3(L.pos[0], L.pos[1], L.pos[2]) - os;
                 want = dot3(s.nf, lv) > 0.0f;
             }
-            const uint32_t k = warp_claim(want ? 1u : 0u, a.shadow_count + l, &a.st->shadow_rays);
+            const uint32_t k = block_claim(want ? 1u : 0u, a.shadow_count + l, sm);
             if (!want) continue;
             const float dist = sqrtf(dot3(lv, lv));
             const float3 ld = (1.0f / dist) * lv;
@@ -264,8 +272,8 @@ __device__ __forceinline__ void shade_one(const ShadeArgs& a, uint32_t head, uin
             a.shadow_payload[slot] = sp;
         }
     }
-    // path rays (all lanes take part in the claim)
-    uint32_t nbase = warp_claim(n_next, a.next_count);
+    // path rays (every thread of the block takes part in the claim)
+    uint32_t nbase = block_claim(n_next, a.next_count, sm);
     // live path rays of the slot: this ray leaves, its spawns join
     if (BATCH && valid && n_next != 1) atomicAdd(live_delta + c.slot, (int)n_next - 1);
     if (!valid || !hit) return;
@@ -313,22 +321,27 @@ __device__ __forceinline__ void shade_one(const ShadeArgs& a, uint32_t head, uin
 }
 
 __global__ void __launch_bounds__(kShadeBlock) k_shade(ShadeArgs a, uint32_t n) {
+    __shared__ uint32_t sm[2];
+    if (threadIdx.x == 0) sm[0] = 0u;
+    __syncthreads();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    shade_one<false>(a, 0u, 0u, i, i < n, nullptr);
+    shade_one<false>(a, 0u, 0u, i, i < n, nullptr, sm);
 }
 
 // Mixed queue: the count is read on the device; whole blocks step together so
-// that every lane takes part in the warp claims.
+// that every thread takes part in the block claims.
 __global__ void __launch_bounds__(kShadeBlock) k_shade_batch(ShadeArgs a) {
     __shared__ int live_delta[kMaxSlots];
+    __shared__ uint32_t sm[2];
     static_assert(kShadeBlock >= kMaxSlots, "one thread per slot flushes the block's sums");
     if (threadIdx.x < kMaxSlots) live_delta[threadIdx.x] = 0;
+    if (threadIdx.x == 0) sm[0] = 0u;
     __syncthreads();
     const uint32_t n = *a.d_count;
     const uint32_t head = *a.ring_head, next_base = *a.next_base;
     for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         const uint32_t i = base + threadIdx.x;
-        shade_one<true>(a, head, next_base, i, i < n, live_delta);
+        shade_one<true>(a, head, next_base, i, i < n, live_delta, sm);
     }
     __syncthreads();
     if (threadIdx.x < kMaxSlots && live_delta[threadIdx.x] != 0)

@@ -205,6 +205,10 @@ __device__ __forceinline__ void emit(const TraceArgs& a, uint32_t i, uint32_t j,
 // Shadow rays in per-light sub-queues: the block's prefix of the sub-queue
 // counts goes to shared memory (pre[l] = rays before sub-queue l, pre[n_sub]
 // = all); returns the number of rays.  Without sub-queues: *d_count or n.
+// TOTAL: the first block adds the rays to the scene's shadow-ray statistic
+// (once per launch, instead of an atomic per warp and light in shading, which
+// serialised on the one counter).
+template <bool TOTAL>
 __device__ __forceinline__ uint32_t ray_count(const TraceArgs& a, uint32_t* pre) {
     if (!a.sub_counts) return a.d_count ? *a.d_count : a.n;
     if (threadIdx.x == 0) {
@@ -214,6 +218,7 @@ __device__ __forceinline__ uint32_t ray_count(const TraceArgs& a, uint32_t* pre)
             acc += a.sub_counts[l];
         }
         pre[a.n_sub] = acc;
+        if (TOTAL && blockIdx.x == 0) atomicAdd(&a.st->shadow_rays, (unsigned long long)acc);
     }
     __syncthreads();
     return pre[a.n_sub];
@@ -414,7 +419,7 @@ template <int MODE, bool BRUTE, bool STATS, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_trace_warp(TraceArgs a) {
     constexpr bool kAny = (MODE == kModeAnyAbi || MODE == kModeShadowRender || MODE == kModeShadowBatch);
     __shared__ uint32_t pre[kMaxLights + 1];
-    const uint32_t n = ray_count(a, pre);
+    const uint32_t n = ray_count<MODE == kModeShadowRender>(a, pre);
     const int lane = threadIdx.x & 31;
     // batched closest-hit rays sit in a ring of 2^k entries from *ring_head
     const uint32_t head = MODE == kModeClosestBatch ? *a.ring_head : 0u;
@@ -445,7 +450,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace_warp(TraceArgs a) {
 template <int SMODE, int CMODE, bool STATS, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 896 / BLOCK) k_trace_pair(TraceArgs sa, TraceArgs ca) {
     __shared__ uint32_t pre[kMaxLights + 1];
-    const uint32_t ns = ray_count(sa, pre);
+    const uint32_t ns = ray_count<SMODE == kModeShadowRender>(sa, pre);
     const uint32_t nc = ca.d_count ? *ca.d_count : ca.n;
     const uint32_t ns_pad = (ns + 31u) & ~31u;
     // batched closest-hit rays sit in a ring of 2^k entries from *ring_head
@@ -483,7 +488,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
     constexpr bool kAny = (MODE == kModeAnyAbi || MODE == kModeShadowRender || MODE == kModeShadowBatch);
     constexpr bool kBatch = (MODE == kModeClosestBatch || MODE == kModeShadowBatch);
     __shared__ uint32_t pre[kMaxLights + 1];
-    const uint32_t n = ray_count(a, pre);
+    const uint32_t n = ray_count<MODE == kModeShadowRender>(a, pre);
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t refill = a.refill;
     // batched closest-hit rays sit in a ring of 2^k entries from *ring_head
@@ -688,7 +693,7 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace8(TraceArgs a) {
     const uint32_t iter_cap = a.iter_cap;
     constexpr bool kAny = (MODE == kModeAnyAbi || MODE == kModeShadowRender);
     __shared__ uint32_t pre[kMaxLights + 1];
-    const uint32_t n = ray_count(a, pre);
+    const uint32_t n = ray_count<MODE == kModeShadowRender>(a, pre);
     const int lane = threadIdx.x & 31;
     unsigned long long c_nodes = 0, c_tris = 0, c_inst = 0;
     for (;;) {
