@@ -87,31 +87,21 @@ __global__ void k_raygen(CameraDev cam, uint32_t w, uint32_t h, float4* __restri
     payload[i] = p;
 }
 
-// exclusive block prefix of `c`: warp totals meet in shared memory, and the
-// block total goes to one atomicAdd on *tail (every thread of the block calls
-// it; sm[0] starts at 0).  One global atomic per block and queue instead of
-// one per warp: the queue tails are single addresses that every block of a
-// level appends to, and per-warp claims measured 6 % of the frame slower.
-__device__ __forceinline__ uint32_t block_claim(uint32_t c, uint32_t* tail, uint32_t* sm) {
-    const int lane = threadIdx.x & 31;
-    uint32_t x = c;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
-        if (lane >= off) x += y;
-    }
-    const uint32_t total = __shfl_sync(0xFFFFFFFFu, x, 31);
-    uint32_t woff = 0;
-    if (lane == 31 && total) woff = atomicAdd(&sm[0], total);
-    woff = __shfl_sync(0xFFFFFFFFu, woff, 31);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const uint32_t t = sm[0];
-        sm[1] = t ? atomicAdd(tail, t) : 0u;
-        sm[0] = 0u;
-    }
-    __syncthreads();
-    return sm[1] + woff + x - c;
+// Queue slots of one shading round, claimed per block: for each queue (one
+// per light, then the next level's path rays) every warp adds its count
+// (ballots: a ray wants 0 or 1 shadow rays per light and 0, 1 or 2 path rays)
+// to a shared-memory total, and the block makes one atomicAdd per queue on
+// its tail.  The tails are single addresses that every block of a level
+// appends to; claims per warp measured 6 % of the frame slower, and a round
+// per queue costs two barriers each.
+struct ClaimSmem {
+    uint32_t cnt[kMaxLights + 1];
+    uint32_t base[kMaxLights + 1];
+    uint32_t woff[kShadeBlock / 32][kMaxLights + 1];
+};
+
+__device__ __forceinline__ void claim_init(ClaimSmem* cs) {
+    for (uint32_t q = threadIdx.x; q <= kMaxLights; q += blockDim.x) cs->cnt[q] = 0u;
 }
 
 
@@ -176,7 +166,7 @@ __device__ __forceinline__ RayCtx ray_ctx(const ShadeArgs& a, const SlotDev* slo
 // block, in shared memory.
 template <bool BATCH>
 __device__ __forceinline__ void shade_one(const ShadeArgs& a, uint32_t head, uint32_t next_base, uint32_t i,
-                                          bool valid, int* live_delta, uint32_t* sm) {
+                                          bool valid, int* live_delta, ClaimSmem* cs) {
     uint32_t n_next = 0;
     bool lit = false;  // a diffuse hit: ambient term and shadow rays
     Surf s;
@@ -241,39 +231,56 @@ __device__ __forceinline__ void shade_one(const ShadeArgs& a, uint32_t head, uin
         }
     }
     // shadow rays: one sub-queue per light, so that a warp of shadow rays
-    // holds neighbouring surface points seen toward the same light (every
-    // thread of the block takes part in every claim)
-    {
-        const uint32_t shadow_pw = BATCH ? pack_pixel(c.pixel, c.depth, c.slot) : c.pixel;
-        const float3 os = lit ? s.p + s.eps * s.nf : f3(0.f, 0.f, 0.f);
-        const uint32_t n_loop = BATCH ? a.max_lights : a.n_lights;
-        for (uint32_t l = 0; l < n_loop; ++l) {
-            bool want = false;
-            rg_light L;
-            float3 lv = f3(0.f, 0.f, 0.f);
-            if (lit && l < c.n_lights) {
-                L = c.lights[l];
-                lv = f3(L.pos[0], L.pos[1], L.pos[2]) - os;
-                want = dot3(s.nf, lv) > 0.0f;
-            }
-            const uint32_t k = block_claim(want ? 1u : 0u, a.shadow_count + l, sm);
-            if (!want) continue;
-            const float dist = sqrtf(dot3(lv, lv));
-            const float3 ld = (1.0f / dist) * lv;
-            const float cl = dot3(s.nf, ld);
-            const size_t slot = (size_t)l * a.shadow_stride + k;
-            a.shadow_rays[2 * slot] = make_float4(os.x, os.y, os.z, 0.0f);
-            a.shadow_rays[2 * slot + 1] = make_float4(ld.x, ld.y, ld.z, dist - s.eps);
-            Payload sp;
-            sp.pixel = shadow_pw;
-            sp.r = thr.x * alb.x * L.intensity[0] * cl;
-            sp.g = thr.y * alb.y * L.intensity[1] * cl;
-            sp.b = thr.z * alb.z * L.intensity[2] * cl;
-            a.shadow_payload[slot] = sp;
-        }
+    // holds neighbouring surface points seen toward the same light; every
+    // thread of the block takes part in the claims
+    const uint32_t shadow_pw = BATCH ? pack_pixel(c.pixel, c.depth, c.slot) : c.pixel;
+    const float3 os = lit ? s.p + s.eps * s.nf : f3(0.f, 0.f, 0.f);
+    const uint32_t n_loop = BATCH ? a.max_lights : a.n_lights;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    // whether the surface point faces light l (lv: toward the light)
+    auto faces = [&](uint32_t l, rg_light* L, float3* lv) -> bool {
+        if (!lit || l >= c.n_lights) return false;
+        *L = c.lights[l];
+        *lv = f3(L->pos[0], L->pos[1], L->pos[2]) - os;
+        return dot3(s.nf, *lv) > 0.0f;
+    };
+    rg_light L;
+    float3 lv = f3(0.f, 0.f, 0.f);
+    for (uint32_t l = 0; l < n_loop; ++l) {
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, faces(l, &L, &lv));
+        if (lane == 0 && b) cs->woff[warp][l] = atomicAdd(&cs->cnt[l], (uint32_t)__popc(b));
     }
-    // path rays (every thread of the block takes part in the claim)
-    uint32_t nbase = block_claim(n_next, a.next_count, sm);
+    const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, n_next >= 1), b2 = __ballot_sync(0xFFFFFFFFu, n_next >= 2);
+    if (lane == 0 && b1) cs->woff[warp][n_loop] = atomicAdd(&cs->cnt[n_loop], (uint32_t)(__popc(b1) + __popc(b2)));
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q <= n_loop; q += blockDim.x) {
+        const uint32_t t = cs->cnt[q];
+        cs->base[q] = t ? atomicAdd(q < n_loop ? a.shadow_count + q : a.next_count, t) : 0u;
+        cs->cnt[q] = 0u;
+    }
+    __syncthreads();
+    for (uint32_t l = 0; l < n_loop; ++l) {
+        const bool want = faces(l, &L, &lv);
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, want);
+        if (!want) continue;
+        const uint32_t k = cs->base[l] + cs->woff[warp][l] + (uint32_t)__popc(b & lt);
+        const float dist = sqrtf(dot3(lv, lv));
+        const float3 ld = (1.0f / dist) * lv;
+        const float cl = dot3(s.nf, ld);
+        const size_t slot = (size_t)l * a.shadow_stride + k;
+        a.shadow_rays[2 * slot] = make_float4(os.x, os.y, os.z, 0.0f);
+        a.shadow_rays[2 * slot + 1] = make_float4(ld.x, ld.y, ld.z, dist - s.eps);
+        Payload sp;
+        sp.pixel = shadow_pw;
+        sp.r = thr.x * alb.x * L.intensity[0] * cl;
+        sp.g = thr.y * alb.y * L.intensity[1] * cl;
+        sp.b = thr.z * alb.z * L.intensity[2] * cl;
+        a.shadow_payload[slot] = sp;
+    }
+    // path rays
+    const uint32_t nbase =
+        cs->base[n_loop] + cs->woff[warp][n_loop] + (uint32_t)(__popc(b1 & lt) + __popc(b2 & lt));
     // live path rays of the slot: this ray leaves, its spawns join
     if (BATCH && valid && n_next != 1) atomicAdd(live_delta + c.slot, (int)n_next - 1);
     if (!valid || !hit) return;
@@ -321,27 +328,27 @@ __device__ __forceinline__ void shade_one(const ShadeArgs& a, uint32_t head, uin
 }
 
 __global__ void __launch_bounds__(kShadeBlock) k_shade(ShadeArgs a, uint32_t n) {
-    __shared__ uint32_t sm[2];
-    if (threadIdx.x == 0) sm[0] = 0u;
+    __shared__ ClaimSmem cs;
+    claim_init(&cs);
     __syncthreads();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    shade_one<false>(a, 0u, 0u, i, i < n, nullptr, sm);
+    shade_one<false>(a, 0u, 0u, i, i < n, nullptr, &cs);
 }
 
 // Mixed queue: the count is read on the device; whole blocks step together so
 // that every thread takes part in the block claims.
 __global__ void __launch_bounds__(kShadeBlock) k_shade_batch(ShadeArgs a) {
     __shared__ int live_delta[kMaxSlots];
-    __shared__ uint32_t sm[2];
+    __shared__ ClaimSmem cs;
     static_assert(kShadeBlock >= kMaxSlots, "one thread per slot flushes the block's sums");
     if (threadIdx.x < kMaxSlots) live_delta[threadIdx.x] = 0;
-    if (threadIdx.x == 0) sm[0] = 0u;
+    claim_init(&cs);
     __syncthreads();
     const uint32_t n = *a.d_count;
     const uint32_t head = *a.ring_head, next_base = *a.next_base;
     for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         const uint32_t i = base + threadIdx.x;
-        shade_one<true>(a, head, next_base, i, i < n, live_delta, sm);
+        shade_one<true>(a, head, next_base, i, i < n, live_delta, &cs);
     }
     __syncthreads();
     if (threadIdx.x < kMaxSlots && live_delta[threadIdx.x] != 0)
