@@ -154,14 +154,15 @@ def code_sha(*paths):
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
 
 
-TRAVERSAL_SOURCES = [os.path.join(ROOT, "paper_2001_09792_gb300", "csrc", f) for f in ("trace.cu", "api.cu")]
+TRAVERSAL_SOURCES = [os.path.join(ROOT, "paper_2001_09792_gb300", "csrc", f)
+                     for f in ("traverse.cuh", "trace.cu", "api.cu")]
 
 
 def traffic_record():
     """DRAM bytes per traversal launch of the medium frame (the frame's
     closest-hit, pair and shadow launches, averaged) from the committed ncu
-    summary, valid only while the traversal kernels (trace.cu) and the launch
-    sequence of a frame (api.cu) are unchanged."""
+    summary, valid only while the traversal code (traverse.cuh, trace.cu) and
+    the launch sequence of a frame (api.cu) are unchanged."""
     path = os.path.join(ROOT, "profiles", "trace_pair_medium.md")
     try:
         txt = open(path).read()

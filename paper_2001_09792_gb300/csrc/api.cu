@@ -659,6 +659,35 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
     std::memcpy(&cd, cam, sizeof cd);
     RG_CK(launch_raygen(cd, w, h, s->q_rays[0].p, s->q_pay[0].p, st));
 
+    // shading of depth level `depth` (its rays in queue q, spawns into 1 - q)
+    auto shade_args = [&](uint32_t depth, int q, uint32_t* c, bool last, uint32_t n_stride) {
+        ShadeArgs sa{};
+        sa.rays = s->q_rays[q].p;
+        sa.payload = s->q_pay[q].p;
+        sa.hits = s->hits.p;
+        sa.inst = s->wide ? s->inst8.p : s->inst.p;
+        sa.mats = s->mats.p;
+        sa.n_mats = s->n_mats;
+        sa.lights = s->lights.p;
+        sa.n_lights = L;
+        sa.bg[0] = s->desc.background[0];
+        sa.bg[1] = s->desc.background[1];
+        sa.bg[2] = s->desc.background[2];
+        sa.ambient = s->desc.ambient;
+        sa.depth = depth;
+        sa.max_depth = max_depth;
+        sa.image = d_rgba;
+        sa.next_rays = last ? nullptr : s->q_rays[1 - q].p;
+        sa.next_payload = last ? nullptr : s->q_pay[1 - q].p;
+        sa.next_count = c + 1;
+        sa.shadow_rays = s->s_rays.p;
+        sa.shadow_payload = s->s_pay.p;
+        sa.shadow_count = c + 4;
+        sa.shadow_stride = n_stride;
+        sa.st = s->st;
+        return sa;
+    };
+
     // closest-hit traversal of level d (count on the host, or on the device)
     auto trace_closest = [&](int q, uint32_t n_host, const uint32_t* d_count, uint32_t* c) -> rg_status {
         TraceArgs a = base_trace_args(s, true);
@@ -689,30 +718,7 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
             if ((r = s->q_pay[1 - cur].ensure(2 * (size_t)n, "payload queue"))) return r;
         }
 
-        ShadeArgs sa{};
-        sa.rays = s->q_rays[cur].p;
-        sa.payload = s->q_pay[cur].p;
-        sa.hits = s->hits.p;
-        sa.inst = s->wide ? s->inst8.p : s->inst.p;
-        sa.mats = s->mats.p;
-        sa.n_mats = s->n_mats;
-        sa.lights = s->lights.p;
-        sa.n_lights = L;
-        sa.bg[0] = s->desc.background[0];
-        sa.bg[1] = s->desc.background[1];
-        sa.bg[2] = s->desc.background[2];
-        sa.ambient = s->desc.ambient;
-        sa.depth = depth;
-        sa.max_depth = max_depth;
-        sa.image = d_rgba;
-        sa.next_rays = last ? nullptr : s->q_rays[1 - cur].p;
-        sa.next_payload = last ? nullptr : s->q_pay[1 - cur].p;
-        sa.next_count = c + 1;
-        sa.shadow_rays = s->s_rays.p;
-        sa.shadow_payload = s->s_pay.p;
-        sa.shadow_count = c + 4;
-        sa.shadow_stride = n;
-        sa.st = s->st;
+        const ShadeArgs sa = shade_args(depth, cur, c, last, n);
         RG_CK(launch_shade(sa, n, st));
         if (!last) {
             RG_CK(cudaMemcpyAsync(s->h_counts, c + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));

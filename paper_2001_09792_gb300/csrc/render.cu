@@ -161,96 +161,197 @@ __device__ __forceinline__ RayCtx ray_ctx(const ShadeArgs& a, const SlotDev* slo
     return c;
 }
 
-// Shade ray i (valid == false: take part in the block's queue claims only).
-// live_delta (batched only): per-slot sums of (path rays spawned - 1) of this
-// block, in shared memory.
+// What shading one ray decides (the closest-hit or miss shader's part that
+// does not depend on where its spawned rays go).
+struct ShadeEval {
+    RayCtx c;
+    Surf s;
+    float3 thr, alb;
+    float ior;
+    uint32_t type, n_next;
+    bool lit;  // a diffuse hit: ambient term and shadow rays
+    bool hit;
+};
+
+__device__ __forceinline__ ShadeEval shade_none() {
+    ShadeEval e;
+    e.c = RayCtx{};
+    e.thr = e.alb = f3(0.f, 0.f, 0.f);
+    e.ior = 1.0f;
+    e.type = 0;
+    e.n_next = 0;
+    e.lit = false;
+    e.hit = false;
+    return e;
+}
+
+// The ray (r0 = origin, tmin; r1 = direction, tmax), its payload and its hit:
+// the miss colour or the ambient term into the image, alpha for camera hits,
+// the surface, its material and how many path rays it spawns.
+template <bool BATCH>
+__device__ __forceinline__ ShadeEval shade_eval(const ShadeArgs& a, float4 r0, float4 r1, const Payload& pl,
+                                                const HitDev& hd) {
+    ShadeEval e = shade_none();
+    e.c = ray_ctx<BATCH>(a, a.slots, pl.pixel);
+    const RayCtx& c = e.c;
+    Surf& s = e.s;
+    const float3 thr = f3(pl.r, pl.g, pl.b);
+    e.thr = thr;
+    float* px = c.image + 4 * (size_t)c.pixel;
+    if (hd.inst_leaf == kMiss) {
+        atomicAdd(px + 0, thr.x * c.bg[0]);
+        atomicAdd(px + 1, thr.y * c.bg[1]);
+        atomicAdd(px + 2, thr.z * c.bg[2]);
+        return e;
+    }
+    e.hit = true;
+    if (c.depth == 1) px[3] = 1.0f;
+    const InstDev* I = c.inst + hd.inst_leaf;
+    const float4 i0 = I->inv[0], i1 = I->inv[1], i2 = I->inv[2];
+    const float4* tp = I->tris + kTriStride * (size_t)hd.tri_leaf;  // the (x, y, z) order
+    const float4 v0 = tp[0], v1 = tp[1], v2 = tp[2];
+    float3 e1 = f3(v1.x - v0.x, v1.y - v0.y, v1.z - v0.z);
+    float3 e2 = f3(v2.x - v0.x, v2.y - v0.y, v2.z - v0.z);
+    float3 no = cross3(e1, e2);
+    float3 nw = f3(i0.x * no.x + i1.x * no.y + i2.x * no.z, i0.y * no.x + i1.y * no.y + i2.y * no.z,
+                   i0.z * no.x + i1.z * no.y + i2.z * no.z);
+    nw = normalize3(nw);
+    s.d = f3(r1.x, r1.y, r1.z);
+    s.p = f3(fmaf(hd.t, r1.x, r0.x), fmaf(hd.t, r1.y, r0.y), fmaf(hd.t, r1.z, r0.z));
+    s.entering = dot3(s.d, nw) < 0.0f;
+    s.nf = s.entering ? nw : -1.0f * nw;
+    s.eps = 1e-4f * fmaxf(1.0f, fmaxf(fabsf(s.p.x), fmaxf(fabsf(s.p.y), fabsf(s.p.z))));
+    uint32_t mi = I->material;
+    if (mi >= c.n_mats) {
+        record_error(a.st, RG_ERR_INVALID_ARG);
+        mi = 0;
+    }
+    const rg_material M = c.mats[mi];
+    e.type = M.type;
+    e.alb = f3(M.albedo[0], M.albedo[1], M.albedo[2]);
+    e.ior = M.ior;
+    const float3 alb = e.alb;
+    if (e.type == RG_MAT_DIFFUSE) {
+        atomicAdd(px + 0, thr.x * alb.x * c.ambient);
+        atomicAdd(px + 1, thr.y * alb.y * c.ambient);
+        atomicAdd(px + 2, thr.z * alb.z * c.ambient);
+        e.lit = true;
+    } else if (c.depth < c.max_depth) {
+        e.n_next = 1;
+        if (e.type == RG_MAT_GLASS) {
+            float eta = s.entering ? 1.0f / e.ior : e.ior;
+            float ci = -dot3(s.d, s.nf);
+            float k = 1.0f - eta * eta * (1.0f - ci * ci);
+            if (k >= 0.0f) e.n_next = 2;
+        }
+    }
+    return e;
+}
+
+// Origin of the shadow rays of a lit surface point.
+__device__ __forceinline__ float3 shadow_origin(const ShadeEval& e) {
+    return e.lit ? e.s.p + e.s.eps * e.s.nf : f3(0.f, 0.f, 0.f);
+}
+
+// Whether the lit surface point faces light l (lv: from the shadow origin os
+// toward the light).
+__device__ __forceinline__ bool faces_light(const ShadeEval& e, float3 os, uint32_t l, rg_light* L, float3* lv) {
+    if (!e.lit || l >= e.c.n_lights) return false;
+    *L = e.c.lights[l];
+    *lv = f3(L->pos[0], L->pos[1], L->pos[2]) - os;
+    return dot3(e.s.nf, *lv) > 0.0f;
+}
+
+// The shadow ray toward a faced light: r0 = (os, 0), r1 = (direction, distance
+// - eps), and the Lambert contribution it adds if nothing occludes it
+// (ta = throughput * albedo).
+__device__ __forceinline__ void shadow_ray(float3 os, float3 nf, float eps, float3 ta, const rg_light& L, float3 lv,
+                                           float4* r0, float4* r1, float3* contrib) {
+    const float dist = sqrtf(dot3(lv, lv));
+    const float3 ld = (1.0f / dist) * lv;
+    const float cl = dot3(nf, ld);
+    *r0 = make_float4(os.x, os.y, os.z, 0.0f);
+    *r1 = make_float4(ld.x, ld.y, ld.z, dist - eps);
+    *contrib = f3(ta.x * L.intensity[0] * cl, ta.y * L.intensity[1] * cl, ta.z * L.intensity[2] * cl);
+}
+
+// The reflected (and, for glass, refracted) rays of a hit, at queue positions
+// nbase (and nbase + 1), ring-mapped from next_base in the batched mode.
+template <bool BATCH>
+__device__ __forceinline__ void write_path_rays(const ShadeArgs& a, const ShadeEval& e, uint32_t next_base,
+                                                uint32_t nbase) {
+    const Surf& s = e.s;
+    const float3 thr = e.thr, alb = e.alb;
+    const float ior = e.ior;
+    const uint32_t next_pw = BATCH ? pack_pixel(e.c.pixel, e.c.depth + 1, e.c.slot) : e.c.pixel;
+    float dn = dot3(s.d, s.nf);
+    float3 r = normalize3(s.d - (2.0f * dn) * s.nf);
+    float3 ro = s.p + s.eps * s.nf;
+    float3 w_r = thr;
+    if (e.type == RG_MAT_MIRROR) {
+        w_r = f3(thr.x * alb.x, thr.y * alb.y, thr.z * alb.z);
+    } else if (e.n_next == 2) {
+        float eta = s.entering ? 1.0f / ior : ior;
+        float ci = -dn;
+        float k = 1.0f - eta * eta * (1.0f - ci * ci);
+        float sk = sqrtf(k);
+        float3 T = normalize3(eta * s.d + (eta * ci - sk) * s.nf);
+        float R0 = (1.0f - ior) / (1.0f + ior);
+        R0 = R0 * R0;
+        float cc = s.entering ? ci : sk;
+        float m = 1.0f - cc;
+        float R = R0 + (1.0f - R0) * (m * m * m * m * m);
+        w_r = R * thr;
+        float3 to = s.p - s.eps * s.nf;
+        uint32_t slot = BATCH ? ((next_base + nbase + 1) & a.ring_mask) : nbase + 1;
+        a.next_rays[2 * (size_t)slot] = make_float4(to.x, to.y, to.z, 0.0f);
+        a.next_rays[2 * (size_t)slot + 1] = make_float4(T.x, T.y, T.z, __int_as_float(0x7F800000));
+        Payload tp;
+        tp.pixel = next_pw;
+        tp.r = (1.0f - R) * thr.x;
+        tp.g = (1.0f - R) * thr.y;
+        tp.b = (1.0f - R) * thr.z;
+        a.next_payload[slot] = tp;
+    }
+    const uint32_t rslot = BATCH ? ((next_base + nbase) & a.ring_mask) : nbase;
+    a.next_rays[2 * (size_t)rslot] = make_float4(ro.x, ro.y, ro.z, 0.0f);
+    a.next_rays[2 * (size_t)rslot + 1] = make_float4(r.x, r.y, r.z, __int_as_float(0x7F800000));
+    Payload rp;
+    rp.pixel = next_pw;
+    rp.r = w_r.x;
+    rp.g = w_r.y;
+    rp.b = w_r.z;
+    a.next_payload[rslot] = rp;
+}
+
+// Shade ray i into the queues (valid == false: take part in the block's queue
+// claims only).  live_delta (batched only): per-slot sums of (path rays
+// spawned - 1) of this block, in shared memory.
 template <bool BATCH>
 __device__ __forceinline__ void shade_one(const ShadeArgs& a, uint32_t head, uint32_t next_base, uint32_t i,
                                           bool valid, int* live_delta, ClaimSmem* cs) {
-    uint32_t n_next = 0;
-    bool lit = false;  // a diffuse hit: ambient term and shadow rays
-    Surf s;
-    uint32_t type = 0;
-    float3 alb = f3(0, 0, 0), thr = f3(0, 0, 0);
-    float ior = 1.0f;
-    bool hit = false;
-    RayCtx c{};
+    ShadeEval e = shade_none();
     if (valid) {
         const uint32_t j = BATCH ? ((head + i) & a.ring_mask) : i;
         const float4 r0 = a.rays[2 * (size_t)j], r1 = a.rays[2 * (size_t)j + 1];
-        const Payload pl = a.payload[j];
-        const HitDev hd = a.hits[i];
-        c = ray_ctx<BATCH>(a, a.slots, pl.pixel);
-        thr = f3(pl.r, pl.g, pl.b);
-        float* px = c.image + 4 * (size_t)c.pixel;
-        if (hd.inst_leaf == kMiss) {
-            atomicAdd(px + 0, thr.x * c.bg[0]);
-            atomicAdd(px + 1, thr.y * c.bg[1]);
-            atomicAdd(px + 2, thr.z * c.bg[2]);
-        } else {
-            hit = true;
-            if (c.depth == 1) px[3] = 1.0f;
-            const InstDev* I = c.inst + hd.inst_leaf;
-            const float4 i0 = I->inv[0], i1 = I->inv[1], i2 = I->inv[2];
-            const float4* tp = I->tris + kTriStride * (size_t)hd.tri_leaf;  // the (x, y, z) order
-            const float4 v0 = tp[0], v1 = tp[1], v2 = tp[2];
-            float3 e1 = f3(v1.x - v0.x, v1.y - v0.y, v1.z - v0.z);
-            float3 e2 = f3(v2.x - v0.x, v2.y - v0.y, v2.z - v0.z);
-            float3 no = cross3(e1, e2);
-            float3 nw = f3(i0.x * no.x + i1.x * no.y + i2.x * no.z, i0.y * no.x + i1.y * no.y + i2.y * no.z,
-                           i0.z * no.x + i1.z * no.y + i2.z * no.z);
-            nw = normalize3(nw);
-            s.d = f3(r1.x, r1.y, r1.z);
-            s.p = f3(fmaf(hd.t, r1.x, r0.x), fmaf(hd.t, r1.y, r0.y), fmaf(hd.t, r1.z, r0.z));
-            s.entering = dot3(s.d, nw) < 0.0f;
-            s.nf = s.entering ? nw : -1.0f * nw;
-            s.eps = 1e-4f * fmaxf(1.0f, fmaxf(fabsf(s.p.x), fmaxf(fabsf(s.p.y), fabsf(s.p.z))));
-            uint32_t mi = I->material;
-            if (mi >= c.n_mats) {
-                record_error(a.st, RG_ERR_INVALID_ARG);
-                mi = 0;
-            }
-            const rg_material M = c.mats[mi];
-            type = M.type;
-            alb = f3(M.albedo[0], M.albedo[1], M.albedo[2]);
-            ior = M.ior;
-            if (type == RG_MAT_DIFFUSE) {
-                atomicAdd(px + 0, thr.x * alb.x * c.ambient);
-                atomicAdd(px + 1, thr.y * alb.y * c.ambient);
-                atomicAdd(px + 2, thr.z * alb.z * c.ambient);
-                lit = true;
-            } else if (c.depth < c.max_depth) {
-                n_next = 1;
-                if (type == RG_MAT_GLASS) {
-                    float eta = s.entering ? 1.0f / ior : ior;
-                    float ci = -dot3(s.d, s.nf);
-                    float k = 1.0f - eta * eta * (1.0f - ci * ci);
-                    if (k >= 0.0f) n_next = 2;
-                }
-            }
-        }
+        e = shade_eval<BATCH>(a, r0, r1, a.payload[j], a.hits[i]);
     }
     // shadow rays: one sub-queue per light, so that a warp of shadow rays
     // holds neighbouring surface points seen toward the same light; every
     // thread of the block takes part in the claims
-    const uint32_t shadow_pw = BATCH ? pack_pixel(c.pixel, c.depth, c.slot) : c.pixel;
-    const float3 os = lit ? s.p + s.eps * s.nf : f3(0.f, 0.f, 0.f);
+    const uint32_t shadow_pw = BATCH ? pack_pixel(e.c.pixel, e.c.depth, e.c.slot) : e.c.pixel;
+    const float3 os = shadow_origin(e);
+    const float3 ta = f3(e.thr.x * e.alb.x, e.thr.y * e.alb.y, e.thr.z * e.alb.z);
     const uint32_t n_loop = BATCH ? a.max_lights : a.n_lights;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
-    // whether the surface point faces light l (lv: toward the light)
-    auto faces = [&](uint32_t l, rg_light* L, float3* lv) -> bool {
-        if (!lit || l >= c.n_lights) return false;
-        *L = c.lights[l];
-        *lv = f3(L->pos[0], L->pos[1], L->pos[2]) - os;
-        return dot3(s.nf, *lv) > 0.0f;
-    };
     rg_light L;
     float3 lv = f3(0.f, 0.f, 0.f);
     for (uint32_t l = 0; l < n_loop; ++l) {
-        const uint32_t b = __ballot_sync(0xFFFFFFFFu, faces(l, &L, &lv));
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, faces_light(e, os, l, &L, &lv));
         if (lane == 0 && b) cs->woff[warp][l] = atomicAdd(&cs->cnt[l], (uint32_t)__popc(b));
     }
+    const uint32_t n_next = e.n_next;
     const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, n_next >= 1), b2 = __ballot_sync(0xFFFFFFFFu, n_next >= 2);
     if (lane == 0 && b1) cs->woff[warp][n_loop] = atomicAdd(&cs->cnt[n_loop], (uint32_t)(__popc(b1) + __popc(b2)));
     __syncthreads();
@@ -261,70 +362,29 @@ __device__ __forceinline__ void shade_one(const ShadeArgs& a, uint32_t head, uin
     }
     __syncthreads();
     for (uint32_t l = 0; l < n_loop; ++l) {
-        const bool want = faces(l, &L, &lv);
+        const bool want = faces_light(e, os, l, &L, &lv);
         const uint32_t b = __ballot_sync(0xFFFFFFFFu, want);
         if (!want) continue;
         const uint32_t k = cs->base[l] + cs->woff[warp][l] + (uint32_t)__popc(b & lt);
-        const float dist = sqrtf(dot3(lv, lv));
-        const float3 ld = (1.0f / dist) * lv;
-        const float cl = dot3(s.nf, ld);
         const size_t slot = (size_t)l * a.shadow_stride + k;
-        a.shadow_rays[2 * slot] = make_float4(os.x, os.y, os.z, 0.0f);
-        a.shadow_rays[2 * slot + 1] = make_float4(ld.x, ld.y, ld.z, dist - s.eps);
+        float4 r0, r1;
+        float3 col;
+        shadow_ray(os, e.s.nf, e.s.eps, ta, L, lv, &r0, &r1, &col);
+        a.shadow_rays[2 * slot] = r0;
+        a.shadow_rays[2 * slot + 1] = r1;
         Payload sp;
         sp.pixel = shadow_pw;
-        sp.r = thr.x * alb.x * L.intensity[0] * cl;
-        sp.g = thr.y * alb.y * L.intensity[1] * cl;
-        sp.b = thr.z * alb.z * L.intensity[2] * cl;
+        sp.r = col.x;
+        sp.g = col.y;
+        sp.b = col.z;
         a.shadow_payload[slot] = sp;
     }
     // path rays
     const uint32_t nbase =
         cs->base[n_loop] + cs->woff[warp][n_loop] + (uint32_t)(__popc(b1 & lt) + __popc(b2 & lt));
     // live path rays of the slot: this ray leaves, its spawns join
-    if (BATCH && valid && n_next != 1) atomicAdd(live_delta + c.slot, (int)n_next - 1);
-    if (!valid || !hit) return;
-    const uint32_t next_pw = BATCH ? pack_pixel(c.pixel, c.depth + 1, c.slot) : c.pixel;
-    if (n_next) {
-        float dn = dot3(s.d, s.nf);
-        float3 r = normalize3(s.d - (2.0f * dn) * s.nf);
-        float3 ro = s.p + s.eps * s.nf;
-        float3 w_r = thr;
-        if (type == RG_MAT_MIRROR) {
-            w_r = f3(thr.x * alb.x, thr.y * alb.y, thr.z * alb.z);
-        } else if (n_next == 2) {
-            float eta = s.entering ? 1.0f / ior : ior;
-            float ci = -dn;
-            float k = 1.0f - eta * eta * (1.0f - ci * ci);
-            float sk = sqrtf(k);
-            float3 T = normalize3(eta * s.d + (eta * ci - sk) * s.nf);
-            float R0 = (1.0f - ior) / (1.0f + ior);
-            R0 = R0 * R0;
-            float cc = s.entering ? ci : sk;
-            float m = 1.0f - cc;
-            float R = R0 + (1.0f - R0) * (m * m * m * m * m);
-            w_r = R * thr;
-            float3 to = s.p - s.eps * s.nf;
-            uint32_t slot = BATCH ? ((next_base + nbase + 1) & a.ring_mask) : nbase + 1;
-            a.next_rays[2 * (size_t)slot] = make_float4(to.x, to.y, to.z, 0.0f);
-            a.next_rays[2 * (size_t)slot + 1] = make_float4(T.x, T.y, T.z, __int_as_float(0x7F800000));
-            Payload tp;
-            tp.pixel = next_pw;
-            tp.r = (1.0f - R) * thr.x;
-            tp.g = (1.0f - R) * thr.y;
-            tp.b = (1.0f - R) * thr.z;
-            a.next_payload[slot] = tp;
-        }
-        const uint32_t rslot = BATCH ? ((next_base + nbase) & a.ring_mask) : nbase;
-        a.next_rays[2 * (size_t)rslot] = make_float4(ro.x, ro.y, ro.z, 0.0f);
-        a.next_rays[2 * (size_t)rslot + 1] = make_float4(r.x, r.y, r.z, __int_as_float(0x7F800000));
-        Payload rp;
-        rp.pixel = next_pw;
-        rp.r = w_r.x;
-        rp.g = w_r.y;
-        rp.b = w_r.z;
-        a.next_payload[rslot] = rp;
-    }
+    if (BATCH && valid && n_next != 1) atomicAdd(live_delta + e.c.slot, (int)n_next - 1);
+    if (valid && e.hit && n_next) write_path_rays<BATCH>(a, e, next_base, nbase);
 }
 
 __global__ void __launch_bounds__(kShadeBlock) k_shade(ShadeArgs a, uint32_t n) {
@@ -567,5 +627,6 @@ cudaError_t launch_fxaa(const float4* in, uint32_t w, uint32_t h, float* lum, fl
     count_launches(2);
     return cudaGetLastError();
 }
+
 
 }  // namespace rg
