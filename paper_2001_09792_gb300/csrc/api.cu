@@ -129,6 +129,11 @@ void free_blas(BlasHost& b) {
     b = BlasHost();
 }
 
+// The last depth level's shadow rays, when at most kShadowSplitMax, are traced
+// as kShadowSplit segments each (the launch is then short of rays, and its
+// longest rays set its time).
+constexpr uint32_t kShadowSplit = 8, kShadowSplitMax = 32768;
+
 struct EventPair {
     cudaEvent_t a, b;
     int kind;  // 0 closest, 1 any, 2 shadow + closest pair
@@ -167,6 +172,7 @@ struct rg_scene {
     DevBuf<float4> q_rays[2], s_rays;
     DevBuf<Payload> q_pay[2], s_pay;
     DevBuf<HitDev> hits;
+    DevBuf<uint32_t> seg_count;    // per shadow ray of a split launch: segments finished / occluded (kept zero)
     DevBuf<uint32_t> counters;     // [0] closest work, [1] next count, [2] shadow work, [3] unused,
                                    // [4 + l] shadow rays toward light l
     uint32_t* h_counts = nullptr;  // pinned, 16 entries
@@ -352,6 +358,7 @@ rg_status rg_scene_destroy(rg_scene* s) {
     s->s_rays.release();
     s->s_pay.release();
     s->hits.release();
+    s->seg_count.release();
     s->counters.release();
     if (s->st) cudaFree(s->st);
     if (s->h_counts) cudaFreeHost(s->h_counts);
@@ -653,6 +660,10 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
     if ((r = s->q_rays[0].ensure(2 * (size_t)N, "ray queue"))) return r;
     if ((r = s->q_pay[0].ensure(N, "payload queue"))) return r;
     if ((r = s->hits.ensure(N, "hit queue"))) return r;
+    if (!s->seg_count.p) {
+        if ((r = s->seg_count.ensure(kShadowSplitMax, "shadow segment counts"))) return r;
+        RG_CK(cudaMemsetAsync(s->seg_count.p, 0, (size_t)kShadowSplitMax * sizeof(uint32_t), st));
+    }
     RG_CK(cudaMemsetAsync(s->counters.p, 0, CB * ((size_t)max_depth + 1) * sizeof(uint32_t), st));
     RG_CK(cudaMemsetAsync(d_rgba, 0, (size_t)N * 16, st));
     CameraDev cd;
@@ -737,6 +748,14 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
             b.work_counter = c + 2;
         }
         const bool pair = L && !last && !s->wide && !(s->desc.flags & RG_SCENE_NO_PAIR);
+        if (L && last && !s->wide) {
+            // the last level's shadow rays, traced on their own: when few, each
+            // as segments side by side (in a pair the closest-hit rays fill
+            // the lanes); the same rule with and without pairs
+            b.seg_count = s->seg_count.p;
+            b.split = kShadowSplit;
+            b.split_max = kShadowSplitMax;
+        }
         if (L && !pair) {
             EventPair* ev;
             if ((r = event_begin(s, 1, st, &ev))) return r;

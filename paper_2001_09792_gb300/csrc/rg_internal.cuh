@@ -253,6 +253,12 @@ struct TraceArgs {
     // sub_stride entries, sub_counts[l] rays in sub-queue l (then n, d_count unused)
     const uint32_t* sub_counts;
     uint32_t n_sub, sub_stride;
+    // kModeShadowRender: when the queue holds at most split_max rays, each
+    // ray is traced as `split` segments of its interval by `split` lanes, and
+    // seg_count[i] (zero before the launch) counts ray i's unoccluded
+    // segments; null: no splitting
+    uint32_t* seg_count;
+    uint32_t split, split_max;
 };
 constexpr uint32_t kMaxLights = 64;  // lights per scene (one shadow sub-queue each)
 cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a, cudaStream_t s,

@@ -20,14 +20,21 @@ __global__ void __launch_bounds__(BLOCK) k_trace_warp(TraceArgs a) {
     const int lane = threadIdx.x & 31;
     // batched closest-hit rays sit in a ring of 2^k entries from *ring_head
     const uint32_t head = MODE == kModeClosestBatch ? *a.ring_head : 0u;
+    const uint32_t k = shadow_split<MODE>(a, n);
+    const uint32_t items = n * k;
     TraceCounts cnt;
     for (;;) {
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(a.work_counter, 32u);
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
-        if (base >= n) break;
+        if (base >= items) break;
         const uint32_t i = base + lane;
-        if (i < n) trace_ray<MODE, BRUTE, STATS>(a, pre, head, i, cnt);
+        if (i < items) {
+            if (MODE == kModeShadowRender && k > 1)
+                trace_segment<BRUTE, STATS>(a, pre, i, k, cnt);
+            else
+                trace_ray<MODE, BRUTE, STATS>(a, pre, head, i, cnt);
+        }
     }
     flush_counts<kAny, STATS>(a, cnt.nodes, cnt.tris, cnt.inst);
 }
@@ -47,7 +54,9 @@ __global__ void __launch_bounds__(BLOCK) k_trace_warp(TraceArgs a) {
 template <int SMODE, int CMODE, bool STATS, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 896 / BLOCK) k_trace_pair(TraceArgs sa, TraceArgs ca) {
     __shared__ uint32_t pre[kMaxLights + 1];
-    const uint32_t ns = ray_count<SMODE == kModeShadowRender>(sa, pre);
+    const uint32_t ns_rays = ray_count<SMODE == kModeShadowRender>(sa, pre);
+    const uint32_t k = shadow_split<SMODE>(sa, ns_rays);
+    const uint32_t ns = ns_rays * k;  // shadow work items (segments)
     const uint32_t nc = ca.d_count ? *ca.d_count : ca.n;
     const uint32_t ns_pad = (ns + 31u) & ~31u;
     // batched closest-hit rays sit in a ring of 2^k entries from *ring_head
@@ -60,7 +69,12 @@ __global__ void __launch_bounds__(BLOCK, 896 / BLOCK) k_trace_pair(TraceArgs sa,
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
         if (base < ns_pad) {
             const uint32_t i = base + lane;
-            if (i < ns) trace_ray<SMODE, false, STATS>(sa, pre, 0u, i, cs);
+            if (i < ns) {
+                if (SMODE == kModeShadowRender && k > 1)
+                    trace_segment<false, STATS>(sa, pre, i, k, cs);
+                else
+                    trace_ray<SMODE, false, STATS>(sa, pre, 0u, i, cs);
+            }
         } else {
             const uint32_t b = base - ns_pad;
             if (b >= nc) break;

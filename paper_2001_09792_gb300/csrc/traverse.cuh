@@ -420,6 +420,46 @@ __device__ __forceinline__ RayHit trace_core(const TraceArgs& a, const float4* t
     return h;
 }
 
+// Segments per shadow ray in a launch of n rays: a.split when the queue is
+// small enough to leave lanes idle (its longest rays then set the launch
+// time, and segments of one ray run side by side), else 1.
+template <int MODE>
+__device__ __forceinline__ uint32_t shadow_split(const TraceArgs& a, uint32_t n) {
+    return (MODE == kModeShadowRender && a.seg_count && n <= a.split_max && a.split > 1) ? a.split : 1u;
+}
+
+// Work item w of a shadow launch split into k segments per ray: segment
+// w % k of ray w / k, over [b_s, b_s+1] with b_0 = tmin, b_k = tmax and the
+// inner bounds computed by one expression, so neighbouring segments share
+// their bound exactly and the closed intervals cover [tmin, tmax]; the ray is
+// unoccluded iff all its segments are.
+template <bool BRUTE, bool STATS>
+__device__ __forceinline__ void trace_segment(const TraceArgs& a, const uint32_t* pre, uint32_t w, uint32_t k,
+                                              TraceCounts& cnt) {
+    const uint32_t i = w / k, seg = w - i * k;
+    const uint32_t j = sub_entry(a, pre, i);
+    float4 r0 = __ldg(a.rays + 2 * (size_t)j), r1 = __ldg(a.rays + 2 * (size_t)j + 1);
+    const float t0 = r0.w, t1 = r1.w, len = __fsub_rn(t1, t0), inv_k = __frcp_rn((float)k);
+    auto bound = [&](uint32_t q) { return q == 0 ? t0 : (q == k ? t1 : __fmaf_rn(len, __fmul_rn((float)q, inv_k), t0)); };
+    r0.w = bound(seg);
+    r1.w = bound(seg + 1);
+    const RayHit h = trace_core<true, BRUTE, STATS>(a, a.tlas_nodes, a.inst, a.tlas_root, r0, r1, cnt);
+    // low 16 bits: segments finished, high 16 bits: segments occluded (or
+    // failed); the ray's last segment adds the contribution if none was, and
+    // clears the count for the next launch
+    const bool lit = !h.found && h.ok;
+    const uint32_t old = atomicAdd(a.seg_count + i, lit ? 1u : 0x10001u);
+    if ((old & 0xFFFFu) != k - 1) return;
+    a.seg_count[i] = 0u;
+    if (lit && (old >> 16) == 0u) {
+        const Payload p = a.payload[j];
+        float* px = a.image + 4 * (size_t)px_of(p.pixel);
+        atomicAdd(px + 0, p.r);
+        atomicAdd(px + 1, p.g);
+        atomicAdd(px + 2, p.b);
+    }
+}
+
 // Ray i of a queue (its entry via the sub-queues or the ring), traced and
 // written out.
 template <int MODE, bool BRUTE, bool STATS>
