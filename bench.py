@@ -64,6 +64,8 @@ def parse():
                         "serve: the continuous-batching render server alone")
     p.add_argument("--requests", type=int, default=400, help="serving: requests in the Poisson stream")
     p.add_argument("--no-serving", action="store_true", help="medium: skip the serving measurement")
+    p.add_argument("--inflight", type=int, default=2,
+                   help="medium: frames in flight (scene contexts sharing the BLAS, one stream each)")
     p.add_argument("--no-pair", action="store_true",
                    help="trace each level's (server: step's) shadow rays and the next one's closest-hit rays in separate launches")
     return p.parse_args()
@@ -230,12 +232,24 @@ def run_native(args, world, rank, local):
     cam = rg.make_camera(s.camera)
     stream = torch.cuda.current_stream()
 
-    def frame(k):
-        rg.rg_tlas_build(gs.h, inst_dev[k])
-        rg.rg_render(gs.h, cam, W, H, D, out=img)
+    # F frame contexts over the same BLAS (rg_scene_create_shared), one stream
+    # each: frame k renders on context k mod F, so the next frame's first,
+    # throughput-bound levels fill the latency-bound last levels of the one
+    # before it
+    F = max(1, args.inflight)
+    ctxs = [gs] + [gs.shared() for _ in range(F - 1)]
+    streams = [stream] + [torch.cuda.Stream() for _ in range(F - 1)]
+    imgs_f = [img] + [torch.empty_like(img) for _ in range(F - 1)]
+
+    def frame(q, k):
+        st_q = streams[q]
+        with torch.cuda.stream(st_q):
+            rg.rg_tlas_build(ctxs[q].h, inst_dev[k], stream=st_q)
+            rg.rg_render(ctxs[q].h, cam, W, H, D, out=imgs_f[q], stream=st_q)
 
     for k in range(args.warmup):
-        frame(k)
+        for q in range(F):
+            frame(q, k)
     torch.cuda.synchronize()
 
     # algorithmic work per closest-hit ray: one counting frame on a second scene
@@ -245,31 +259,56 @@ def run_native(args, world, rank, local):
         rg.rg_render(gc.h, cam, W, H, D)
         cst = rg.rg_get_stats(gc.h)
 
-    rg.rg_sync(gs.h)
-    rg.rg_reset_stats(gs.h)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
+    def timed(nf):
+        """args.steps frames, nf in flight; the L2 flush (on the frame's
+        stream) before each frame is inside the one timed region.  Returns
+        rays, wall seconds, per-frame ms (its stream, flush excluded) and the
+        contexts' statistics."""
+        for c in ctxs[:nf]:
+            rg.rg_sync(c.h)
+            rg.rg_reset_stats(c.h)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e_start = torch.cuda.Event(enable_timing=True)
+        e_end = torch.cuda.Event(enable_timing=True)
+        e_start.record(stream)
+        for q in range(1, nf):
+            streams[q].wait_event(e_start)
+        per = []
+        for k in range(args.warmup, n_frames):
+            q = (k - args.warmup) % nf
+            with torch.cuda.stream(streams[q]):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(streams[q])
+                frame(q, k)
+                e1.record(streams[q])
+            per.append((e0, e1))
+        for q in range(1, nf):
+            stream.wait_stream(streams[q])
+        e_end.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        stats = [rg.rg_get_stats(c.h) for c in ctxs[:nf]]
+        rays = sum(x["closest_rays"] + x["shadow_rays"] for x in stats)
+        return rays, e_start.elapsed_time(e_end) / 1e3, [a.elapsed_time(b) for a, b in per], stats
+
     clocks = ClockSampler(gpu_index(local))
     clocks.start()
-    times = []
-    for k in range(args.warmup, n_frames):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        frame(k)
-        e1.record(stream)
-        times.append((e0, e1))
+    for k in range(args.warmup):             # settle after the sampler starts
+        for q in range(F):
+            frame(q, k)
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    rays1, wall1, ms, stats1 = timed(1)      # one frame at a time: also the kernels' roofline
+    if F > 1:
+        rays, total_s, ms_f, stats_f = timed(F)
+    else:
+        rays, total_s, ms_f, stats_f = rays1, wall1, ms, stats1
     clk = clocks.stop()
-    ms = [a.elapsed_time(b) for a, b in times]
-    st = rg.rg_get_stats(gs.h)
-    rg.rg_sync(gs.h)
-    rays = st["closest_rays"] + st["shadow_rays"]
-    total_s = sum(ms) / 1e3
+    st = stats1[0]
 
     # FXAA of the frame (Sec. 2.1 post-processing), timed alone, L2 flushed before each launch
     fx_out = torch.empty_like(img)
@@ -293,36 +332,45 @@ def run_native(args, world, rank, local):
     e2e = None
     if not args.no_e2e:
         pin_in = [torch.from_numpy(x).pin_memory() for x in inst_host]
-        pin_out = [torch.empty((H, W, 4), dtype=torch.float32).pin_memory() for _ in range(2)]
-        imgs = [img, torch.empty_like(img)]
-        dev_in = torch.empty_like(inst_dev[0])
+        nb = max(F, 2)
+        pin_out = [torch.empty((H, W, 4), dtype=torch.float32).pin_memory() for _ in range(nb)]
+        out_dev = imgs_f + [torch.empty_like(img) for _ in range(nb - F)]
+        dev_in = [torch.empty_like(inst_dev[0]) for _ in range(F)]
         copy_stream = torch.cuda.Stream()
-        freed = [None, None]
-        rg.rg_reset_stats(gs.h)
+        freed = [None] * nb
+        for c in ctxs:
+            rg.rg_sync(c.h)
+            rg.rg_reset_stats(c.h)
         torch.cuda.synchronize()
         e_start = torch.cuda.Event(enable_timing=True)
         e_end = torch.cuda.Event(enable_timing=True)
         e_start.record(stream)
+        for q in range(1, F):
+            streams[q].wait_event(e_start)
         for k in range(args.warmup, n_frames):
-            b = k % 2
+            q = (k - args.warmup) % F          # context and stream
+            b = (k - args.warmup) % nb         # device image and pinned readback buffer
+            st_q = streams[q]
             if freed[b] is not None:
-                stream.wait_event(freed[b])          # image b's previous readback is done
-            flush.zero_()
-            dev_in.copy_(pin_in[k], non_blocking=True)
-            rg.rg_tlas_build(gs.h, dev_in)
-            rg.rg_render(gs.h, cam, W, H, D, out=imgs[b])
-            rendered = torch.cuda.Event()
-            rendered.record(stream)
+                st_q.wait_event(freed[b])      # image b's previous readback is done
+            with torch.cuda.stream(st_q):
+                flush.zero_()
+                dev_in[q].copy_(pin_in[k], non_blocking=True)
+                rg.rg_tlas_build(ctxs[q].h, dev_in[q], stream=st_q)
+                rg.rg_render(ctxs[q].h, cam, W, H, D, out=out_dev[b], stream=st_q)
+                rendered = torch.cuda.Event()
+                rendered.record(st_q)
             copy_stream.wait_event(rendered)
             with torch.cuda.stream(copy_stream):
-                pin_out[b].copy_(imgs[b], non_blocking=True)
+                pin_out[b].copy_(out_dev[b], non_blocking=True)
                 freed[b] = torch.cuda.Event()
                 freed[b].record(copy_stream)
+        for q in range(1, F):
+            stream.wait_stream(streams[q])
         stream.wait_stream(copy_stream)
         e_end.record(stream)
         torch.cuda.synchronize()
-        st2 = rg.rg_get_stats(gs.h)
-        e2e_rays = st2["closest_rays"] + st2["shadow_rays"]
+        e2e_rays = sum(rg.rg_get_stats(c.h)["closest_rays"] + rg.rg_get_stats(c.h)["shadow_rays"] for c in ctxs)
         e2e = (e2e_rays, e_start.elapsed_time(e_end) / 1e3, inst_host[0].nbytes, W * H * 16)
 
     # aggregate over ranks: the slowest rank's time, every rank's rays
@@ -365,7 +413,11 @@ def run_native(args, world, rank, local):
                     "shadow_nodes_per_ray": round(cst["any_node_visits"] / sr, 2),
                     "shadow_inst_per_ray": round(cst["any_inst_entries"] / sr, 3),
                     "shadow_tris_per_ray": round(cst["any_tri_tests"] / sr, 2)}
-        ms_sorted = sorted(ms)
+        def pcts(x):
+            xs = sorted(x)
+            return round(xs[len(xs) // 2], 3), round(xs[min(len(xs) - 1, math.ceil(0.99 * len(xs)) - 1)], 3)
+        p50, p99 = pcts(ms_f)
+        p50_1, p99_1 = pcts(ms)
         out = {
             "metric": METRIC,
             "value": round(rays_all / total_s_all / 1e6, 2),
@@ -383,24 +435,30 @@ def run_native(args, world, rank, local):
                        "instances": s.n_instances, "instanced_tris": s.instanced_tris(),
                        "rays_per_step": round(rays / args.steps), "closest_rays_per_step": round(st["closest_rays"] / args.steps),
                        "shadow_rays_per_step": round(st["shadow_rays"] / args.steps),
-                       "closest_mrays_s": round(st["closest_rays"] / total_s / 1e6, 2),
-                       "p50_ms": round(ms_sorted[len(ms) // 2], 3),
-                       "p99_ms": round(ms_sorted[min(len(ms) - 1, math.ceil(0.99 * len(ms)) - 1)], 3),
+                       "closest_mrays_s": round(st["closest_rays"] / max(rays1, 1) * rays / total_s / 1e6, 2),
+                       "frames_in_flight": F,
+                       "p50_ms": p50, "p99_ms": p99,
+                       "one_in_flight": {"value": round(rays1 / wall1 / 1e6, 2), "ms_per_step": round(wall1 * 1e3 / args.steps, 3),
+                                         "p50_ms": p50_1, "p99_ms": p99_1,
+                                         "note": "the same frames one at a time; the roofline's launch times are taken here"},
+                       "latency": "per frame, from its TLAS build to its image on its stream (with frames in flight, "
+                                  "the frames share the GPU)",
                        "blas_build_ms": round(blas_build_ms, 2), "blas_build": blas_build,
-                       "l2": "flushed before each step (256 MiB write)",
+                       "l2": "flushed before each frame (256 MiB write on the frame's stream, inside the timed region)",
                        "fxaa": {"ms": round(fxaa_ms, 4), "gbs": round(W * H * 32 / (fxaa_ms / 1e3) / 1e9, 1),
                                 "bytes_per_pixel": 32, "note": "k_fxaa_luma + k_fxaa on the frame, timed alone, not in the step"},
                        "parallelism": f"replicas x{world}", "bvh": "compressed 8-wide" if args.compressed else "binary float32"},
             "roofline": roofline,
-            "gpu_launches": int(st["kernel_launches"]),
+            "gpu_launches": int(stats_f[0]["kernel_launches"]),
         }
         if clk:
             out["clocks"] = clk
         if e2e:
             out["e2e"] = {"value": round(e2e[0] / e2e[1] / 1e6, 2), "unit": "Mrays/s",
                           "h2d_bytes_per_step": int(e2e[2]), "d2h_bytes_per_step": int(e2e[3]),
-                          "note": "frames back to back, image readback overlapped with the next frame "
-                                  "(two device images, a copy stream); one timed region incl. L2 flushes"}
+                          "note": f"frames back to back, {F} in flight (one scene context and stream each), "
+                                  "each image read back on a copy stream while later frames render; one timed "
+                                  "region incl. L2 flushes"}
         if world == 1 and not args.no_serving:
             out["serving"] = run_serving(args.requests, pair=not args.no_pair)
         if world == 1 and not args.no_cpu_baseline:

@@ -114,7 +114,16 @@ typedef struct {
 /* Create an empty scene on the current CUDA device.  desc may be NULL
  * (background (0.2,0.3,0.5), ambient 0.1, no flags). */
 rg_status rg_scene_create(rg_scene** out, const rg_scene_desc* desc);
-/* Free every device allocation of the scene (synchronises the device). */
+/* A new scene on src's device that shares src's BLAS (by reference: they
+ * stay allocated until the last scene holding them is destroyed) and starts
+ * with a copy of src's description, materials and lights; its TLAS, queues,
+ * counters and statistics are its own.  Renders of the two scenes on
+ * different streams may run at the same time, e.g. two frames in flight,
+ * each with its own instance transforms.  Once shared, neither scene can
+ * build another BLAS (RG_ERR_INVALID_ARG). */
+rg_status rg_scene_create_shared(rg_scene** out, rg_scene* src);
+/* Free every device allocation of the scene (synchronises the device); BLAS
+ * shared with another scene stay until the last of them is destroyed. */
 rg_status rg_scene_destroy(rg_scene* scene);
 
 /* ---- step 1 of the paper's model: the two-layered structure (Sec. 1) ---- */

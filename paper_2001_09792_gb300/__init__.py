@@ -34,7 +34,7 @@ RG_MAT_DIFFUSE, RG_MAT_MIRROR, RG_MAT_GLASS = 0, 1, 2
 MISS = 0xFFFFFFFF
 
 # exported symbols, in include/rg.h order
-SYMBOLS = ["rg_scene_create", "rg_scene_destroy", "rg_blas_build", "rg_tlas_build", "rg_tlas_refit",
+SYMBOLS = ["rg_scene_create", "rg_scene_create_shared", "rg_scene_destroy", "rg_blas_build", "rg_tlas_build", "rg_tlas_refit",
            "rg_scene_set_materials", "rg_scene_set_lights", "rg_trace_rays", "rg_render", "rg_sync", "rg_get_stats",
            "rg_reset_stats", "rg_last_error", "rg_tri_bounds", "rg_morton_codes", "rg_radix_sort_pairs", "rg_karras",
            "rg_blas_export", "rg_tlas_export", "rg_wide_export", "rg_radix_sort_pairs_noalloc",
@@ -127,6 +127,7 @@ def lib():
         P, u32, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32
         sig = {
             "rg_scene_create": [ctypes.POINTER(P), P],
+            "rg_scene_create_shared": [ctypes.POINTER(P), P],
             "rg_scene_destroy": [P],
             "rg_blas_build": [P, P, u32, P, u32, u32, ctypes.POINTER(u32), P],
             "rg_tlas_build": [P, P, u32, P],
@@ -207,6 +208,13 @@ def rg_scene_create(background=(0.2, 0.3, 0.5), ambient=0.1, flags=0):
     d = rg_scene_desc(f32x3(*background), float(ambient), int(flags))
     h = ctypes.c_void_p()
     _check(lib().rg_scene_create(ctypes.byref(h), ctypes.byref(d)))
+    return h
+
+
+def rg_scene_create_shared(src):
+    """A scene sharing src's BLAS, with copies of its materials and lights."""
+    h = ctypes.c_void_p()
+    _check(lib().rg_scene_create_shared(ctypes.byref(h), src))
     return h
 
 
@@ -557,6 +565,23 @@ class GpuScene:
         except Exception:
             self.close()
             raise
+
+    def shared(self, stream=None):
+        """Another GpuScene over the same BLAS (rg_scene_create_shared) with
+        this one's instances, materials and lights and a TLAS of its own."""
+        torch = _torch()
+        other = GpuScene.__new__(GpuScene)
+        other.h = rg_scene_create_shared(self.h)
+        try:
+            other.n_inst, other.nts, other.blas = self.n_inst, list(self.nts), list(self.blas)
+            other.inst_host = self.inst_host.copy()
+            other.inst = torch.from_numpy(other.inst_host).cuda()
+            rg_tlas_build(other.h, other.inst, stream)
+            rg_sync(other.h)
+        except Exception:
+            other.close()
+            raise
+        return other
 
     def refit(self, M, stream=None):
         torch = _torch()

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -134,6 +135,18 @@ void free_blas(BlasHost& b) {
 // longest rays set its time).
 constexpr uint32_t kShadowSplit = 8, kShadowSplitMax = 32768;
 
+// The BLAS of one or more scenes; freed with the last scene that holds it
+// (its destructor runs on that scene's device).
+struct BlasSet {
+    std::vector<BlasHost> blas;
+    DevBuf<BlasDev> d_blas;
+    uint32_t max_nt = 0;
+    ~BlasSet() {
+        for (BlasHost& b : blas) free_blas(b);
+        d_blas.release();
+    }
+};
+
 struct EventPair {
     cudaEvent_t a, b;
     int kind;  // 0 closest, 1 any, 2 shadow + closest pair
@@ -145,10 +158,8 @@ struct rg_scene {
     int device = 0;
     rg_scene_desc desc{};
     DevStatus* st = nullptr;
-    // BLAS
-    std::vector<BlasHost> blas;
-    DevBuf<BlasDev> d_blas;
-    uint32_t max_nt = 0;
+    // BLAS (shared with the scenes made by rg_scene_create_shared)
+    std::shared_ptr<BlasSet> B = std::make_shared<BlasSet>();
     // TLAS
     bool tlas_built = false;
     uint32_t n_inst = 0;
@@ -248,7 +259,7 @@ uint32_t iter_cap_for(const rg_scene* s, bool brute) {
     // brute force: every node and triangle of every instance once, with pops;
     // a BVH traversal visits a tiny fraction of that, and 2^22 steps per ray
     // bound it far above any valid traversal of the supported scene sizes
-    uint64_t per_inst = 4ull * (uint64_t)s->max_nt + 16;
+    uint64_t per_inst = 4ull * (uint64_t)s->B->max_nt + 16;
     uint64_t cap = 4ull * (uint64_t)s->n_inst + (uint64_t)s->n_inst * per_inst + 64;
     if (!brute && cap > (1ull << 22)) cap = 1ull << 22;
     return cap > 0xFFFFFFF0ull ? 0xFFFFFFF0u : (uint32_t)cap;
@@ -330,12 +341,48 @@ rg_status rg_scene_create(rg_scene** out, const rg_scene_desc* desc) {
     return RG_OK;
 }
 
+rg_status rg_scene_create_shared(rg_scene** out, rg_scene* src) {
+    if (!out) return fail(RG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    rg_status r;
+    if ((r = check_scene(src))) return r;
+    if ((r = set_device(src))) return r;
+    rg_scene* s = nullptr;
+    if ((r = rg_scene_create(&s, &src->desc))) return r;
+    s->B = src->B;
+    // materials and lights as the source has them now
+    if (src->n_mats) {
+        if ((r = s->mats.ensure(src->n_mats, "materials"))) {
+            rg_scene_destroy(s);
+            return r;
+        }
+        cudaError_t e = cudaMemcpy(s->mats.p, src->mats.p, src->n_mats * sizeof(rg_material), cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) {
+            rg_scene_destroy(s);
+            return cuda_fail(e, "copying materials");
+        }
+        s->n_mats = src->n_mats;
+    }
+    if ((r = s->lights.ensure(src->n_lights ? src->n_lights : 1, "lights"))) {
+        rg_scene_destroy(s);
+        return r;
+    }
+    if (src->n_lights) {
+        cudaError_t e = cudaMemcpy(s->lights.p, src->lights.p, src->n_lights * sizeof(rg_light), cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) {
+            rg_scene_destroy(s);
+            return cuda_fail(e, "copying lights");
+        }
+    }
+    s->n_lights = src->n_lights;
+    *out = s;
+    return RG_OK;
+}
+
 rg_status rg_scene_destroy(rg_scene* s) {
     if (!s) return RG_OK;
     set_device(s);
     cudaDeviceSynchronize();
-    for (BlasHost& b : s->blas) free_blas(b);
-    s->d_blas.release();
     s->tlas8.release();
     s->inst8.release();
     s->src8.release();
@@ -379,6 +426,7 @@ rg_status rg_blas_build(rg_scene* s, const float* d_vtx, uint32_t nv, const uint
                         uint32_t flags, uint32_t* blas_id, void* stream) {
     rg_status r;
     if ((r = check_scene(s))) return r;
+    if (s->B.use_count() > 1) return fail(RG_ERR_INVALID_ARG, "the scene's BLAS are shared with another scene");
     if (!d_vtx || !d_idx || !blas_id) return fail(RG_ERR_INVALID_ARG, "NULL geometry or id pointer");
     if (nt == 0 || nv == 0) return fail(RG_ERR_INVALID_ARG, "empty mesh");
     if (flags & ~(RG_MORTON63 | RG_COMPRESSED | RG_WIDE_LEAF(3))) return fail(RG_ERR_INVALID_ARG, "unknown BLAS flags");
@@ -408,21 +456,21 @@ rg_status rg_blas_build(rg_scene* s, const float* d_vtx, uint32_t nv, const uint
             return r;
         }
     }
-    uint32_t id = (uint32_t)s->blas.size();
+    uint32_t id = (uint32_t)s->B->blas.size();
     if ((r = [&]() -> rg_status {
              // grow the descriptor array, keeping the old entries
-             if (id + 1 > s->d_blas.cap) {
+             if (id + 1 > s->B->d_blas.cap) {
                  size_t ncap = (id + 1) * 2;
                  BlasDev* np = nullptr;
                  rg_status rr = dev_alloc(reinterpret_cast<void**>(&np), ncap * sizeof(BlasDev), "BLAS table");
                  if (rr) return rr;
-                 if (s->d_blas.p && id) RG_CK(cudaMemcpyAsync(np, s->d_blas.p, id * sizeof(BlasDev), cudaMemcpyDeviceToDevice, st));
-                 if (s->d_blas.p) {
+                 if (s->B->d_blas.p && id) RG_CK(cudaMemcpyAsync(np, s->B->d_blas.p, id * sizeof(BlasDev), cudaMemcpyDeviceToDevice, st));
+                 if (s->B->d_blas.p) {
                      RG_CK(cudaStreamSynchronize(st));
-                     cudaFree(s->d_blas.p);
+                     cudaFree(s->B->d_blas.p);
                  }
-                 s->d_blas.p = np;
-                 s->d_blas.cap = ncap;
+                 s->B->d_blas.p = np;
+                 s->B->d_blas.cap = ncap;
              }
              BlasDev hd{};
              hd.nodes = b.nodes;
@@ -431,7 +479,7 @@ rg_status rg_blas_build(rg_scene* s, const float* d_vtx, uint32_t nv, const uint
              hd.nt = nt;
              hd.nodes8 = b.nodes8;
              hd.tris8 = b.tris8;
-             RG_CK(cudaMemcpyAsync(s->d_blas.p + id, &hd, sizeof hd, cudaMemcpyHostToDevice, st));
+             RG_CK(cudaMemcpyAsync(s->B->d_blas.p + id, &hd, sizeof hd, cudaMemcpyHostToDevice, st));
              RG_CK(cudaStreamSynchronize(st));  // hd lives on this stack frame
 
              TempAlloc tmp(st);
@@ -459,14 +507,14 @@ rg_status rg_blas_build(rg_scene* s, const float* d_vtx, uint32_t nv, const uint
              }
              RG_CK(launch_blas_leaves_refit(d_vtx, d_idx, static_cast<uint32_t*>(perm), static_cast<float*>(lohi), nt,
                                             static_cast<uint32_t*>(parents), b.nodes, static_cast<uint32_t*>(fl), b.tris,
-                                            s->d_blas.p + id, s->st, st));
-             RG_CK(launch_bound_sphere(d_vtx, nv, s->d_blas.p + id, st));
+                                            s->B->d_blas.p + id, s->st, st));
+             RG_CK(launch_bound_sphere(d_vtx, nv, s->B->d_blas.p + id, st));
              if (wide) {
                  WideOut out{b.nodes8, b.src8, b.item_src8, b.counts8, static_cast<uint2*>(tasks)};
-                 const float* leaf_box = reinterpret_cast<const float*>(reinterpret_cast<const char*>(s->d_blas.p + id) +
+                 const float* leaf_box = reinterpret_cast<const float*>(reinterpret_cast<const char*>(s->B->d_blas.p + id) +
                                                                         offsetof(BlasDev, lo));
                  RG_CK(launch_collapse(b.nodes, static_cast<uint32_t*>(ranges), nt, leaf_box, b.tris, b.tris8, nullptr,
-                                       nullptr, s->d_blas.p, out, s->st, st, leaf_max));
+                                       nullptr, s->B->d_blas.p, out, s->st, st, leaf_max));
              }
              return RG_OK;
          }())) {
@@ -474,8 +522,8 @@ rg_status rg_blas_build(rg_scene* s, const float* d_vtx, uint32_t nv, const uint
         free_blas(b);
         return r;
     }
-    s->blas.push_back(b);
-    if (nt > s->max_nt) s->max_nt = nt;
+    s->B->blas.push_back(b);
+    if (nt > s->B->max_nt) s->B->max_nt = nt;
     *blas_id = id;
     return RG_OK;
 }
@@ -487,24 +535,24 @@ static rg_status tlas_common(rg_scene* s, const rg_instance* d_inst, uint32_t n,
         // one single-block launch for the whole build or refit
         void* ranges = nullptr;
         if (!refit && s->wide && n > 1 && (r = tmp.get(&ranges, (size_t)(n - 1) * 8, "ranges"))) return r;
-        RG_CK(launch_tlas_small(d_inst, n, s->d_blas.p, (uint32_t)s->blas.size(), s->inst_tmp.p, s->wbox.p, refit,
+        RG_CK(launch_tlas_small(d_inst, n, s->B->d_blas.p, (uint32_t)s->B->blas.size(), s->inst_tmp.p, s->wbox.p, refit,
                                 s->tlas_nodes.p, s->perm.p, s->parents.p, s->flags.p, static_cast<uint32_t*>(ranges),
                                 s->inst.p, s->st, st));
         if (s->wide) {
             WideOut out{s->tlas8.p, s->src8.p, s->item_src8.p, s->counts8.p, s->tasks8.p};
             if (refit)
-                RG_CK(launch_wide_refit(s->tlas_nodes.p, s->wbox.p, s->perm.p, n, s->inst.p, s->inst8.p, s->d_blas.p,
+                RG_CK(launch_wide_refit(s->tlas_nodes.p, s->wbox.p, s->perm.p, n, s->inst.p, s->inst8.p, s->B->d_blas.p,
                                         out, s->st, st));
             else
                 RG_CK(launch_collapse(s->tlas_nodes.p, static_cast<uint32_t*>(ranges), n, s->wbox.p, nullptr, nullptr,
-                                      s->inst.p, s->inst8.p, s->d_blas.p, out, s->st, st, 1u));
+                                      s->inst.p, s->inst8.p, s->B->d_blas.p, out, s->st, st, 1u));
         }
         return RG_OK;
     }
     void* cb;
     if ((r = tmp.get(&cb, 64, "centroid bounds"))) return r;
     if (!refit) RG_CK(launch_init_bounds(static_cast<int*>(cb), st));
-    RG_CK(launch_instance_prep(d_inst, n, s->d_blas.p, (uint32_t)s->blas.size(), s->inst_tmp.p, s->wbox.p,
+    RG_CK(launch_instance_prep(d_inst, n, s->B->d_blas.p, (uint32_t)s->B->blas.size(), s->inst_tmp.p, s->wbox.p,
                                refit ? nullptr : static_cast<int*>(cb), refit, s->st, st));
     void* ranges = nullptr;
     if (!refit) {
@@ -523,11 +571,11 @@ static rg_status tlas_common(rg_scene* s, const rg_instance* d_inst, uint32_t n,
     if (s->wide) {
         WideOut out{s->tlas8.p, s->src8.p, s->item_src8.p, s->counts8.p, s->tasks8.p};
         if (refit)
-            RG_CK(launch_wide_refit(s->tlas_nodes.p, s->wbox.p, s->perm.p, n, s->inst.p, s->inst8.p, s->d_blas.p, out,
+            RG_CK(launch_wide_refit(s->tlas_nodes.p, s->wbox.p, s->perm.p, n, s->inst.p, s->inst8.p, s->B->d_blas.p, out,
                                     s->st, st));
         else
             RG_CK(launch_collapse(s->tlas_nodes.p, static_cast<uint32_t*>(ranges), n, s->wbox.p, nullptr, nullptr,
-                                  s->inst.p, s->inst8.p, s->d_blas.p, out, s->st, st, 1u));
+                                  s->inst.p, s->inst8.p, s->B->d_blas.p, out, s->st, st, 1u));
     }
     return RG_OK;
 }
@@ -537,7 +585,7 @@ rg_status rg_tlas_build(rg_scene* s, const rg_instance* d_inst, uint32_t n, void
     if ((r = check_scene(s))) return r;
     if (!d_inst || n == 0) return fail(RG_ERR_INVALID_ARG, "no instances");
     if (n > (1u << 28)) return fail(RG_ERR_INVALID_ARG, "too many instances");
-    if (s->blas.empty()) return fail(RG_ERR_NOT_BUILT, "no BLAS built");
+    if (s->B->blas.empty()) return fail(RG_ERR_NOT_BUILT, "no BLAS built");
     if ((r = set_device(s))) return r;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     s->tlas_built = false;
@@ -550,7 +598,7 @@ rg_status rg_tlas_build(rg_scene* s, const rg_instance* d_inst, uint32_t n, void
     if ((r = s->flags.ensure(n, "TLAS flags"))) return r;
     s->wide = false;
     if (s->desc.flags & RG_SCENE_COMPRESSED) {
-        for (const BlasHost& b : s->blas)
+        for (const BlasHost& b : s->B->blas)
             if (!b.nodes8) return fail(RG_ERR_NOT_BUILT, "a BLAS of this compressed scene has no wide form");
         const size_t n_int = n > 1 ? n - 1 : 1;
         if ((r = s->tlas8.ensure(n_int * 5, "wide TLAS nodes"))) return r;
@@ -914,10 +962,10 @@ rg_status rg_karras(const void* d_sorted_keys, uint32_t n, uint32_t key_bits, ui
 rg_status rg_blas_export(rg_scene* s, uint32_t blas_id, void* h_nodes, void* h_tris, uint32_t* h_root) {
     rg_status r;
     if ((r = check_scene(s))) return r;
-    if (blas_id >= s->blas.size()) return fail(RG_ERR_INVALID_ARG, "no such BLAS");
+    if (blas_id >= s->B->blas.size()) return fail(RG_ERR_INVALID_ARG, "no such BLAS");
     if ((r = set_device(s))) return r;
     RG_CK(cudaDeviceSynchronize());
-    const BlasHost& b = s->blas[blas_id];
+    const BlasHost& b = s->B->blas[blas_id];
     if (h_nodes && b.nt > 1) RG_CK(cudaMemcpy(h_nodes, b.nodes, (size_t)(b.nt - 1) * 64, cudaMemcpyDeviceToHost));
     // the (x, y, z) order of each triangle record
     if (h_tris) RG_CK(cudaMemcpy2D(h_tris, 48, b.tris, kTriRecord, 48, b.nt, cudaMemcpyDeviceToHost));
@@ -939,8 +987,8 @@ rg_status rg_wide_export(rg_scene* s, uint32_t blas_id, void* h_nodes, uint32_t*
         item_src = s->item_src8.p;
         counts = s->counts8.p;
     } else {
-        if (blas_id >= s->blas.size()) return fail(RG_ERR_INVALID_ARG, "no such BLAS");
-        const BlasHost& b = s->blas[blas_id];
+        if (blas_id >= s->B->blas.size()) return fail(RG_ERR_INVALID_ARG, "no such BLAS");
+        const BlasHost& b = s->B->blas[blas_id];
         if (!b.nodes8) return fail(RG_ERR_NOT_BUILT, "this BLAS has no wide form");
         nodes = b.nodes8;
         src = b.src8;
@@ -998,8 +1046,8 @@ rg_status scene_view(rg_scene* s, SceneView* v) {
     if (!s->tlas_built) return fail(RG_ERR_NOT_BUILT, "scene has no TLAS");
     if (s->n_mats == 0) return fail(RG_ERR_NOT_BUILT, "scene has no materials");
     v->device = s->device;
-    v->d_blas = s->d_blas.p;
-    v->n_blas = (uint32_t)s->blas.size();
+    v->d_blas = s->B->d_blas.p;
+    v->n_blas = (uint32_t)s->B->blas.size();
     v->tlas_nodes = s->tlas_nodes.p;
     v->perm = s->perm.p;
     v->parents = s->parents.p;

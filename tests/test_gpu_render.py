@@ -193,3 +193,42 @@ def test_paired_launches_equal_separate_launches(lights):
     assert sa["trace_launches"] == 1 and sa["any_launches"] == 1
     assert sb["trace_launches"] == s.max_depth and sb["any_launches"] == s.max_depth
     assert sa["kernel_launches"] == sb["kernel_launches"] - (s.max_depth - 1)
+
+
+def test_shared_scenes_render_concurrently():
+    """Two scenes over the same BLAS (rg_scene_create_shared), each with its
+    own instance transforms, render on two streams at once; each image equals
+    the render of a fresh scene with those transforms.  The shared BLAS
+    outlive the scene that built them, and a shared set takes no new BLAS."""
+    s = g.medium_scene(width=320, height=180, max_depth=4)
+    Ms = [g.motion(s.M, 3), g.motion(s.M, 8)]
+    refs = []
+    for M in Ms:
+        s2 = g.medium_scene(width=320, height=180, max_depth=4)
+        s2.M = M
+        refs.append(render(s2))
+    a = rg.GpuScene(s)
+    b = a.shared()
+    try:
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        imgs = []
+        for gs, M, st in zip([a, b], Ms, streams):
+            with torch.cuda.stream(st):
+                inst = torch.from_numpy(rg.pack_instances(M, [gs.blas[m] for m in s.mesh_id], s.material_id)).cuda()
+                rg.rg_tlas_build(gs.h, inst, stream=st)
+                imgs.append(rg.rg_render(gs.h, s.camera, s.width, s.height, s.max_depth, stream=st))
+        torch.cuda.synchronize()
+        for img, ref in zip(imgs, refs):
+            np.testing.assert_allclose(img.cpu().numpy().reshape(-1, 4).astype(np.float64), ref, atol=1e-5)
+        v, i = g.cube_mesh(0.5)
+        with pytest.raises(rg.RgError) as e:
+            rg.rg_blas_build(b.h, torch.from_numpy(v).cuda(), torch.from_numpy(i.view(np.int32)).cuda())
+        assert e.value.status == rg.RG_ERR_INVALID_ARG
+        a.close()                                   # b keeps the BLAS
+        img = render(s, gs=b)
+        b_ref = g.medium_scene(width=320, height=180, max_depth=4)
+        b_ref.M = Ms[1]
+        np.testing.assert_allclose(img, render(b_ref), atol=1e-5)
+    finally:
+        a.close()
+        b.close()
