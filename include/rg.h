@@ -184,7 +184,13 @@ rg_status rg_trace_rays(rg_scene* scene, const rg_ray* d_rays, uint32_t n, uint3
  * reflection; glass: Schlick-weighted reflection + refraction (total internal
  * reflection beyond the critical angle); misses: background.  Reflection and
  * refraction rays are spawned while the ray depth (primary = 1) is below
- * max_depth.  Synchronises the stream once per depth level to size queues. */
+ * max_depth.  Asynchronous on `stream`: the scene's queues are sized once
+ * for the frame's worst case (level d holds at most w h 2^(d-1) rays) when
+ * that takes at most 16 GB, and every launch reads its ray count on the
+ * device, so the call returns without waiting for the GPU; beyond that size
+ * the host waits once per depth level to size the next queues.  Renders of
+ * one scene on different streams must not overlap (its queues are shared);
+ * scenes made with rg_scene_create_shared may render concurrently. */
 rg_status rg_render(rg_scene* scene, const rg_camera* h_cam, uint32_t w, uint32_t h, uint32_t max_depth,
                     float* d_rgba, void* stream);
 

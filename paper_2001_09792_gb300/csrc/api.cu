@@ -134,6 +134,9 @@ void free_blas(BlasHost& b) {
 // as kShadowSplit segments each (the launch is then short of rays, and its
 // longest rays set its time).
 constexpr uint32_t kShadowSplit = 8, kShadowSplitMax = 32768;
+// Queue bytes a render may take for its worst case to run without waiting
+// for the host (1080p at depth 4 with 4 lights takes 4.6 GB).
+constexpr uint64_t kAsyncQueueBudget = 16ull << 30;
 
 // The BLAS of one or more scenes; freed with the last scene that holds it
 // (its destructor runs on that scene's device).
@@ -697,14 +700,40 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
     // Per depth level: closest-hit traversal, shading, shadow traversal.  The
     // shadow rays of a level and the closest-hit rays of the next depend only
     // on the level's shading and share one launch (k_trace_pair) unless
-    // RG_SCENE_NO_PAIR is set or the BVH is the compressed one.  The host
-    // learns each level's ray count one step late: the count is copied back
-    // while the GPU traces, and the closest-hit traversal reads the count on
-    // the device, so the stream never waits for the host.  Counters: one block
-    // per level, [0] closest work, [1] rays of the next level, [2] shadow
-    // work (and the pair's), [4 + l] shadow rays toward light l.
+    // RG_SCENE_NO_PAIR is set or the BVH is the compressed one.  Every launch
+    // reads its ray count on the device.  Counters: one block per level, [0]
+    // closest work, [1] rays of the next level, [2] shadow work (and the
+    // pair's), [4 + l] shadow rays toward light l.
     const size_t CB = 4 + kMaxLights;
     if ((r = s->counters.ensure(CB * ((size_t)max_depth + 1), "counters"))) return r;
+    // Queue room (before anything is written to the queues: growing one
+    // frees its contents).  Level d holds at most N 2^(d-1) rays (a ray spawns at most
+    // two).  When that worst case for the whole frame fits the budget it is
+    // allocated once and the frame is enqueued without the host waiting:
+    // every count is read on the device.  Otherwise the host learns each
+    // level's count one level late (copied back while the GPU traces) and
+    // sizes the next queues from it.
+    auto cap_of = [&](uint32_t d) { return (uint64_t)N << (d - 1); };
+    bool async = !s->wide && max_depth <= 24;
+    uint64_t cap_q[2] = {0, 0}, cap_max = 0;
+    if (async) {
+        for (uint32_t d = 1; d <= max_depth; ++d) {
+            cap_q[(d - 1) & 1] = std::max(cap_q[(d - 1) & 1], cap_of(d));
+            cap_max = std::max(cap_max, cap_of(d));
+        }
+        const uint64_t bytes = (cap_q[0] + cap_q[1]) * 48 + cap_max * 16 + cap_max * L * 48;
+        async = cap_max <= 0xFFFFFFFFull && bytes <= kAsyncQueueBudget;
+    }
+    if (async) {
+        if ((r = s->q_rays[0].ensure(2 * cap_q[0], "ray queue")) || (r = s->q_pay[0].ensure(cap_q[0], "payload queue")) ||
+            (max_depth > 1 && ((r = s->q_rays[1].ensure(2 * cap_q[1], "ray queue")) ||
+                               (r = s->q_pay[1].ensure(cap_q[1], "payload queue")))) ||
+            (r = s->hits.ensure(cap_max, "hit queue")) ||
+            (L && ((r = s->s_rays.ensure(2 * cap_max * L, "shadow queue")) ||
+                   (r = s->s_pay.ensure(cap_max * L, "shadow payload")))))
+            return r;
+    }
+
     if ((r = s->q_rays[0].ensure(2 * (size_t)N, "ray queue"))) return r;
     if ((r = s->q_pay[0].ensure(N, "payload queue"))) return r;
     if ((r = s->hits.ensure(N, "hit queue"))) return r;
@@ -762,24 +791,28 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
         return event_end(s, st);
     };
 
-    uint32_t n = N;
+    uint32_t n = N;  // this level's rays (a bound on them when async)
     int cur = 0;
     if ((r = trace_closest(cur, N, nullptr, s->counters.p))) return r;
     for (uint32_t depth = 1; depth <= max_depth; ++depth) {
         const bool last = depth == max_depth;
         uint32_t* c = s->counters.p + CB * (depth - 1);
-        s->closest_rays += n;
-        // room for what this level's shading writes (growing a buffer waits for the device)
-        if (L && (r = s->s_rays.ensure(2 * (size_t)n * L, "shadow queue"))) return r;
-        if (L && (r = s->s_pay.ensure((size_t)n * L, "shadow payload"))) return r;
-        if (!last) {
-            if ((r = s->q_rays[1 - cur].ensure(4 * (size_t)n, "ray queue"))) return r;
-            if ((r = s->q_pay[1 - cur].ensure(2 * (size_t)n, "payload queue"))) return r;
+        if (async) {
+            n = (uint32_t)cap_of(depth);
+        } else {
+            // room for what this level's shading writes (growing a buffer waits for the device)
+            if (L && (r = s->s_rays.ensure(2 * (size_t)n * L, "shadow queue"))) return r;
+            if (L && (r = s->s_pay.ensure((size_t)n * L, "shadow payload"))) return r;
+            if (!last) {
+                if ((r = s->q_rays[1 - cur].ensure(4 * (size_t)n, "ray queue"))) return r;
+                if ((r = s->q_pay[1 - cur].ensure(2 * (size_t)n, "payload queue"))) return r;
+            }
         }
 
-        const ShadeArgs sa = shade_args(depth, cur, c, last, n);
+        ShadeArgs sa = shade_args(depth, cur, c, last, n);
+        if (async && depth > 1) sa.d_count = c - CB + 1;  // written by the previous level's shading
         RG_CK(launch_shade(sa, n, st));
-        if (!last) {
+        if (!last && !async) {
             RG_CK(cudaMemcpyAsync(s->h_counts, c + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
             RG_CK(cudaEventRecord(s->count_ev, st));
         }
@@ -813,7 +846,7 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
         if (last) break;
         // the next level's rays (at most 2 per ray of this level) are traced
         // before the host knows how many there are
-        if ((r = s->hits.ensure(2 * (size_t)n, "hit queue"))) return r;
+        if (!async && (r = s->hits.ensure(2 * (size_t)n, "hit queue"))) return r;
         if (pair) {
             TraceArgs a = base_trace_args(s, true);
             a.rays = s->q_rays[1 - cur].p;
@@ -826,10 +859,12 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
         } else if ((r = trace_closest(1 - cur, 0, c + 1, c + CB))) {
             return r;
         }
-        RG_CK(cudaEventSynchronize(s->count_ev));
-        n = s->h_counts[0];
         cur = 1 - cur;
-        if (n == 0) break;
+        if (!async) {
+            RG_CK(cudaEventSynchronize(s->count_ev));
+            n = s->h_counts[0];
+            if (n == 0) break;
+        }
     }
     return RG_OK;
 }
@@ -880,7 +915,7 @@ rg_status rg_get_stats(rg_scene* s, rg_stats* out) {
     if ((r = collect_events(s))) return r;
     DevStatus d;
     RG_CK(cudaMemcpy(&d, s->st, sizeof d, cudaMemcpyDeviceToHost));
-    out->closest_rays = s->closest_rays;
+    out->closest_rays = s->closest_rays + d.closest_rays;  // rg_trace_rays + the renderer's launches
     out->shadow_rays = s->shadow_rays_host + d.shadow_rays;
     out->trace_launches = s->trace_launches;
     out->trace_ms = s->trace_ms;

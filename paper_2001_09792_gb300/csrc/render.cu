@@ -387,12 +387,18 @@ __device__ __forceinline__ void shade_one(const ShadeArgs& a, uint32_t head, uin
     if (valid && e.hit && n_next) write_path_rays<BATCH>(a, e, next_base, nbase);
 }
 
-__global__ void __launch_bounds__(kShadeBlock) k_shade(ShadeArgs a, uint32_t n) {
+// One depth level's rays: n_host of them, or *a.d_count when the count is
+// only on the device; whole blocks step together through the queue so that
+// every thread takes part in the block claims.
+__global__ void __launch_bounds__(kShadeBlock) k_shade(ShadeArgs a, uint32_t n_host) {
     __shared__ ClaimSmem cs;
     claim_init(&cs);
     __syncthreads();
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    shade_one<false>(a, 0u, 0u, i, i < n, nullptr, &cs);
+    const uint32_t n = a.d_count ? *a.d_count : n_host;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        shade_one<false>(a, 0u, 0u, i, i < n, nullptr, &cs);
+    }
 }
 
 // Mixed queue: the count is read on the device; whole blocks step together so
@@ -598,7 +604,9 @@ cudaError_t launch_raygen(const CameraDev& cam, uint32_t w, uint32_t h, float4* 
 
 cudaError_t launch_shade(const ShadeArgs& a, uint32_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    k_shade<<<(n + kShadeBlock - 1) / kShadeBlock, kShadeBlock, 0, s>>>(a, n);
+    // n: the rays (a.d_count null) or a bound on them; blocks loop over the queue
+    const uint32_t blocks = min((n + kShadeBlock - 1) / kShadeBlock, (uint32_t)device_sm_count() * 8u);
+    k_shade<<<blocks, kShadeBlock, 0, s>>>(a, n);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -17,6 +17,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace_warp(TraceArgs a) {
     constexpr bool kAny = (MODE == kModeAnyAbi || MODE == kModeShadowRender || MODE == kModeShadowBatch);
     __shared__ uint32_t pre[kMaxLights + 1];
     const uint32_t n = ray_count<MODE == kModeShadowRender>(a, pre);
+    count_closest<MODE>(a, n);
     const int lane = threadIdx.x & 31;
     // batched closest-hit rays sit in a ring of 2^k entries from *ring_head
     const uint32_t head = MODE == kModeClosestBatch ? *a.ring_head : 0u;
@@ -58,6 +59,7 @@ __global__ void __launch_bounds__(BLOCK, 896 / BLOCK) k_trace_pair(TraceArgs sa,
     const uint32_t k = shadow_split<SMODE>(sa, ns_rays);
     const uint32_t ns = ns_rays * k;  // shadow work items (segments)
     const uint32_t nc = ca.d_count ? *ca.d_count : ca.n;
+    count_closest<CMODE>(ca, nc);
     const uint32_t ns_pad = (ns + 31u) & ~31u;
     // batched closest-hit rays sit in a ring of 2^k entries from *ring_head
     const uint32_t head = CMODE == kModeClosestBatch ? *ca.ring_head : 0u;
@@ -100,6 +102,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
     constexpr bool kBatch = (MODE == kModeClosestBatch || MODE == kModeShadowBatch);
     __shared__ uint32_t pre[kMaxLights + 1];
     const uint32_t n = ray_count<MODE == kModeShadowRender>(a, pre);
+    count_closest<MODE>(a, n);
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t refill = a.refill;
     // batched closest-hit rays sit in a ring of 2^k entries from *ring_head
@@ -305,6 +308,7 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace8(TraceArgs a) {
     constexpr bool kAny = (MODE == kModeAnyAbi || MODE == kModeShadowRender);
     __shared__ uint32_t pre[kMaxLights + 1];
     const uint32_t n = ray_count<MODE == kModeShadowRender>(a, pre);
+    count_closest<MODE>(a, n);
     const int lane = threadIdx.x & 31;
     unsigned long long c_nodes = 0, c_tris = 0, c_inst = 0;
     for (;;) {

@@ -228,6 +228,15 @@ __device__ __forceinline__ uint32_t ray_count(const TraceArgs& a, uint32_t* pre)
     return pre[a.n_sub];
 }
 
+// The renderer's closest-hit launches add their ray count to the scene's
+// statistic (first thread of the first block), so a render needs no count on
+// the host.
+template <int MODE>
+__device__ __forceinline__ void count_closest(const TraceArgs& a, uint32_t n) {
+    if (MODE == kModeClosestRender && blockIdx.x == 0 && threadIdx.x == 0 && n)
+        atomicAdd(&a.st->closest_rays, (unsigned long long)n);
+}
+
 // Queue entry of ray i: its place in its light's sub-queue.
 __device__ __forceinline__ uint32_t sub_entry(const TraceArgs& a, const uint32_t* pre, uint32_t i) {
     if (!a.sub_counts) return i;
