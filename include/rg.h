@@ -86,8 +86,10 @@ typedef struct { float pos[3]; float intensity[3]; } rg_light;
  * per 8 children instead of 64 B per 2), and traces and renders with it; hit
  * records are bit-identical to the binary float32 path.  rg_render traces
  * each depth level's shadow rays and the next level's closest-hit rays in one
- * launch (binary BVH); RG_SCENE_NO_PAIR makes them two launches. */
-enum { RG_SCENE_TIMING = 1u, RG_SCENE_COUNT = 2u, RG_SCENE_COMPRESSED = 4u, RG_SCENE_NO_PAIR = 8u };
+ * launch (binary BVH); RG_SCENE_NO_PAIR makes them two launches.
+ * RG_SCENE_FRUGAL sizes rg_render's queues from each depth level's ray count
+ * (the host waits once per level) instead of the frame's worst case. */
+enum { RG_SCENE_TIMING = 1u, RG_SCENE_COUNT = 2u, RG_SCENE_COMPRESSED = 4u, RG_SCENE_NO_PAIR = 8u, RG_SCENE_FRUGAL = 16u };
 typedef struct { float background[3]; float ambient; uint32_t flags; } rg_scene_desc;
 
 /* Counters since the last rg_reset_stats. */

@@ -232,3 +232,35 @@ def test_shared_scenes_render_concurrently():
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("lights", [4, 0])
+def test_frugal_queues_equal_worst_case_queues(lights):
+    """Queues sized from each level's ray count (the host waits per level,
+    RG_SCENE_FRUGAL) and queues sized once for the frame's worst case (no host
+    wait) render the same image from the same rays and traversal work."""
+    s = g.medium_scene(width=480, height=270, max_depth=6)
+    s.light_pos, s.light_I = s.light_pos[:lights], s.light_I[:lights]
+    out = {}
+    for name, flags in [("frugal", rg.RG_SCENE_FRUGAL), ("worst", 0)]:
+        with rg.GpuScene(s, flags=flags | rg.RG_SCENE_COUNT) as gs:
+            rg.rg_reset_stats(gs.h)
+            img = render(s, gs=gs)
+            out[name] = (img, rg.rg_get_stats(gs.h))
+    (a, sa), (b, sb) = out["frugal"], out["worst"]
+    np.testing.assert_allclose(a, b, atol=1e-5)
+    for k in ["closest_rays", "shadow_rays", "node_visits", "tri_tests", "inst_entries", "any_node_visits",
+              "any_tri_tests", "any_inst_entries"]:
+        assert sa[k] == sb[k], k
+    assert sa["closest_rays"] > s.width * s.height
+
+
+def test_deep_render_beyond_the_worst_case_budget():
+    """A render whose worst-case queues exceed the budget (960x540, depth 10:
+    up to 512 rays per pixel at the last level) takes the per-level path and
+    agrees with the oracle on sampled pixels."""
+    s = g.medium_scene(width=960, height=540, max_depth=10)
+    img = render(s)
+    pix = np.random.default_rng(10).choice(s.width * s.height, 10_000, replace=False).astype(np.uint32)
+    ref = oracle.OracleScene(s).render(s.camera, s.width, s.height, s.max_depth, pixels=pix, kappa=KAPPA, rel_t=REL_T)
+    compare(img, ref, pixels=pix, label="deep")
