@@ -295,6 +295,9 @@ __device__ __forceinline__ RayHit trace_core(const TraceArgs& a, const float4* t
     Shear sh;
 
     float best_t = tmax;
+    // culling distance of the box tests: the ray's end (any hit) or the best
+    // hit so far (closest hit), with the relative slack
+    float tlim = __fmul_rn(tmax, kCullSlack);
     uint32_t best_id = kMiss, best_prim = kMiss;
     uint32_t best_il = kMiss, best_tl = kMiss;
     float best_V = 0.f, best_W = 0.f, best_det = 1.f;
@@ -332,7 +335,6 @@ __device__ __forceinline__ RayHit trace_core(const TraceArgs& a, const float4* t
             const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2);
             const uint4 n3 = __ldg(reinterpret_cast<const uint4*>(nd + 3));
             if (STATS) ++cnt.nodes;
-            const float tlim = kAny ? __fmul_rn(tmax, kCullSlack) : __fmul_rn(best_t, kCullSlack);
             float tn0, tn1, tf0, tf1;
             bool h0 = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, cr, tmin, tlim, tn0, tf0);
             bool h1 = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, cr, tmin, tlim, tn1, tf1);
@@ -409,6 +411,7 @@ __device__ __forceinline__ RayHit trace_core(const TraceArgs& a, const float4* t
                 if (better) {
                     best_t = h.t; best_id = cur_id; best_prim = prim;
                     best_il = cur_leaf; best_tl = leaf;
+                    tlim = __fmul_rn(best_t, kCullSlack);
                     best_V = h.V; best_W = h.W; best_det = h.det;
                     found = true;
                 }
