@@ -264,3 +264,23 @@ def test_deep_render_beyond_the_worst_case_budget():
     pix = np.random.default_rng(10).choice(s.width * s.height, 10_000, replace=False).astype(np.uint32)
     ref = oracle.OracleScene(s).render(s.camera, s.width, s.height, s.max_depth, pixels=pix, kappa=KAPPA, rel_t=REL_T)
     compare(img, ref, pixels=pix, label="deep")
+
+
+def test_split_shadow_rays_see_an_occluder_near_the_light():
+    """Depth 1 with few shadow rays: each is traced as 8 segments.  A small
+    occluder at 90 % of the way to the light lies in the last segments only;
+    the pixels it shadows get the ambient term alone, the others the Lambert
+    term too, as the oracle renders them."""
+    v, i = g.quad_mesh(20.0, 0.0)
+    ov, oi = g.quad_mesh(0.4, 0.0)
+    a = 0.75
+    s = _scene([(v, i), (ov, oi)], [g.affine(np.eye(3), [0, 0, 0]), g.affine(np.eye(3), [0, 9.0, 0])],
+               [(0, (a, a, a), 1.0), (0, (a, a, a), 1.0)], (0.0, 10.0, 0.0))
+    cam = dict(eye=(0, 6, 14), target=(0, 0, 0), up=(0, 1, 0), vfov=50.0)
+    w = h = 96
+    img = render(s, w=w, h=h, depth=1, camera=cam)
+    ref = oracle.OracleScene(s).render(cam, w, h, 1, kappa=KAPPA, rel_t=REL_T)
+    compare(img, ref, label="occluder near the light")
+    ground = img[:, 3] == 1.0
+    shadowed = ground & (np.abs(img[:, 0] - a * AMB) < 1e-6)
+    assert shadowed.sum() > 100 and (ground & ~shadowed).sum() > 1000
