@@ -86,3 +86,94 @@ def test_t_and_barycentrics_do_not_depend_on_the_swap():
         inside2 = ~(((U2 < 0) | (V2 < 0) | (W2 < 0)) & ((U2 > 0) | (V2 > 0) | (W2 > 0)))
         np.testing.assert_array_equal(inside1, inside2)
         assert inside1.sum() > 1000
+
+
+# ---------------------------------------------------------------- box test
+
+K_IZE = f32(1.0) + f32(2.0) * (f32(3.0) * f32(2.0 ** -24)) / (f32(1.0) - f32(3.0) * f32(2.0 ** -24))
+CULL = f32(1.0) + f32(1.0 / 4096.0)
+
+
+def slab32(lo, hi, o, d, tmin, tlim):
+    """The float32 box test as the traversal runs it: t = (plane - o) * (1/d)
+    per axis, NaN-propagating min / max per axis, NaN-dropping max / min
+    across axes, far distance scaled by 1 + 2 gamma_3, then clipped to tlim."""
+    with np.errstate(all="ignore"):
+        ix = f32(1) / d
+        t0 = (lo - o) * ix
+        t1 = (hi - o) * ix
+        nmin = np.minimum(t0, t1)   # NaN if either is NaN
+        nmax = np.maximum(t0, t1)
+        tn = np.fmax(np.fmax(nmin[:, 0], nmin[:, 1]), np.fmax(nmin[:, 2], tmin))
+        tf = np.fmin(np.fmin(nmax[:, 0], nmax[:, 1]), nmax[:, 2])
+        tf = np.fmin(tf * K_IZE, tlim)
+        return tn <= tf
+
+
+def exact_hit(lo, hi, o, d, tmin, tmax):
+    """Whether the segment [tmin, tmax] of the ray meets the closed box, in
+    float64 (the float32 inputs are exact in it)."""
+    lo, hi, o, d = (np.asarray(x, np.float64) for x in (lo, hi, o, d))
+    tn = np.full(len(o), float(tmin))
+    tf = np.full(len(o), float(tmax))
+    with np.errstate(all="ignore"):
+        for a in range(3):
+            z = d[:, a] == 0
+            ta, tb = (lo[:, a] - o[:, a]) / d[:, a], (hi[:, a] - o[:, a]) / d[:, a]
+            tn = np.where(z, tn, np.maximum(tn, np.minimum(ta, tb)))
+            tf = np.where(z, tf, np.minimum(tf, np.maximum(ta, tb)))
+            inside = (lo[:, a] <= o[:, a]) & (o[:, a] <= hi[:, a])
+            tf = np.where(z & ~inside, -np.inf, tf)
+    return tn <= tf
+
+
+def box_cases(n, seed):
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-20, 20, (n, 3))
+    ext = rng.uniform(0, 3, (n, 3)) * (rng.random((n, 3)) > 0.1)   # some flat boxes
+    lo, hi = (c - ext).astype(f32), (c + ext).astype(f32)
+    o = rng.uniform(-30, 30, (n, 3)).astype(f32)
+    # aim most rays at a point of the box's closure (corners, edges, faces included)
+    target = lo + (hi - lo) * rng.choice([0.0, 0.5, 1.0, rng.random()], (n, 3)).astype(f32)
+    d = (target - o).astype(f32)
+    m = rng.random(n) < 0.2
+    d[m] = rng.normal(size=(m.sum(), 3)).astype(f32)
+    # axis-aligned rays, some with the origin on a slab plane (0 * inf = NaN)
+    k = rng.random(n) < 0.2
+    ax = rng.integers(0, 3, n)
+    for a in range(3):
+        sel = k & (ax == a)
+        keep = d[sel, a].copy()
+        d[sel] = 0
+        d[sel, a] = np.where(keep == 0, 1, keep)
+        on = sel & (rng.random(n) < 0.5)
+        o[on, (a + 1) % 3] = rng.choice([0, 1], on.sum()).astype(f32) * (hi[on, (a + 1) % 3] - lo[on, (a + 1) % 3]) + lo[on, (a + 1) % 3]
+    return lo, hi, o, d
+
+
+def test_box_test_never_rejects_a_box_the_segment_meets():
+    lo, hi, o, d = box_cases(400_000, 3)
+    for tmax in [np.inf, 5.0, 40.0]:
+        tlim = f32(tmax) * CULL if np.isfinite(tmax) else f32(np.inf)
+        got = slab32(lo, hi, o, d, f32(0), tlim)
+        want = exact_hit(lo, hi, o, d, 0.0, tmax)
+        missed = want & ~got
+        assert not missed.any(), f"tmax {tmax}: {missed.sum()} boxes rejected, e.g. case {np.nonzero(missed)[0][:3]}"
+        assert want.sum() > 100_000
+        # conservative, not permissive: a box the segment misses by more than
+        # a relative 1e-4 (its copy grown by that much is still missed) is
+        # rejected
+        grow = (1e-4 * (1.0 + np.maximum(np.abs(lo).max(1), np.abs(o).max(1))))[:, None]
+        far = ~exact_hit(lo - grow, hi + grow, o, d, 0.0, tmax)
+        assert far.sum() > 50_000
+        assert not (got & far).any()
+
+
+def test_zero_direction_origin_on_plane_leaves_the_axis_open():
+    # ray along +z, origin exactly on the box's x = lo plane: 0 * inf = NaN on x
+    lo = np.array([[0, -1, 5]], f32)
+    hi = np.array([[2, 1, 6]], f32)
+    d = np.array([[0, 0, 1]], f32)
+    for ox, want in [(0.0, True), (2.0, True), (1.0, True), (-1e-7, False), (2.0000002, False)]:
+        o = np.array([[ox, 0, 0]], f32)
+        assert slab32(lo, hi, o, d, f32(0), f32(np.inf))[0] == want, ox
