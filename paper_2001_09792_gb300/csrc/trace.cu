@@ -47,13 +47,12 @@ __global__ void __launch_bounds__(BLOCK) k_trace_warp(TraceArgs a) {
 // warps of 32) and then over the closest-hit rays, so warps that run out of
 // one kind take the other and the SMs stay busy until the last batch of both,
 // instead of idling through the tail of two separate launches.
-// Launched for 896 resident threads per SM (72 registers, 7 blocks of 128):
-// with both ray kinds inlined the kernel would take more and fit 768, and
-// held to 64 registers (1024 threads) it spills inside the traversal loop;
-// on the medium frame 896 measured fastest (2587 Mrays/s against 2550 at
-// 768 and 2381 at 1024).
+// Launched for 1024 resident threads per SM (64 registers, 8 blocks of 128)
+// at the cost of a few spilled values: with several frames in flight this
+// measured 2.8 % faster than 896 threads (72 registers, no spills), one frame
+// at a time the same, and 768 threads slower than both.
 template <int SMODE, int CMODE, bool STATS, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 896 / BLOCK) k_trace_pair(TraceArgs sa, TraceArgs ca) {
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_trace_pair(TraceArgs sa, TraceArgs ca) {
     __shared__ uint32_t pre[kMaxLights + 1];
     const uint32_t ns_rays = ray_count<SMODE == kModeShadowRender>(sa, pre);
     const uint32_t k = shadow_split<SMODE>(sa, ns_rays);
