@@ -27,7 +27,11 @@ namespace rg {
 
 namespace {
 
-constexpr int kShadeBlock = 256;
+// Shading blocks of 128 threads: the block-wide queue claims wait at two
+// barriers, and smaller blocks wait for fewer warps; with several frames in
+// flight 128 measured 1.9 % faster than 256 (one frame at a time 1.5 %
+// slower), 512 slower in both.
+constexpr int kShadeBlock = 128;
 
 __device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
 __device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
