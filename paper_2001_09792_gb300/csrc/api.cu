@@ -50,6 +50,16 @@ long fault_alloc_index() {
     return idx;
 }
 
+// Test limits for the failure paths (no GPU fault is involved): a smaller
+// traversal stack (RG_TEST_STACK=n) or iteration cap (RG_TEST_ITER_CAP=n) for
+// every traversal the library launches; 0 when unset.
+uint32_t test_limit(const char* name) {
+    const char* v = std::getenv(name);
+    if (!v) return 0;
+    const long x = std::atol(v);
+    return x > 0 && x < (1l << 30) ? (uint32_t)x : 0u;
+}
+
 rg_status dev_alloc(void** p, size_t bytes, const char* what) {
     *p = nullptr;
     long k = ++g_alloc_count;
@@ -265,6 +275,8 @@ uint32_t iter_cap_for(const rg_scene* s, bool brute) {
     uint64_t per_inst = 4ull * (uint64_t)s->B->max_nt + 16;
     uint64_t cap = 4ull * (uint64_t)s->n_inst + (uint64_t)s->n_inst * per_inst + 64;
     if (!brute && cap > (1ull << 22)) cap = 1ull << 22;
+    static const uint32_t test_cap = test_limit("RG_TEST_ITER_CAP");
+    if (test_cap) cap = test_cap;
     return cap > 0xFFFFFFF0ull ? 0xFFFFFFF0u : (uint32_t)cap;
 }
 
@@ -276,6 +288,8 @@ TraceArgs base_trace_args(rg_scene* s, bool wide) {
     a.n_inst = s->n_inst;
     a.st = s->st;
     a.iter_cap = iter_cap_for(s, false);
+    static const uint32_t test_stack = test_limit("RG_TEST_STACK");
+    a.stack_max = test_stack;
     if (wide && s->wide) {
         a.tlas_nodes8 = s->tlas8.p;
         a.inst8 = s->inst8.p;

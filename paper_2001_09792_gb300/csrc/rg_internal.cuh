@@ -259,7 +259,11 @@ struct TraceArgs {
     // segments; null: no splitting
     uint32_t* seg_count;
     uint32_t split, split_max;
+    // binary traversal: stack entries a ray may use (0: all kTraceStack); a
+    // smaller limit only makes failure-path tests reach RG_ERR_STACK
+    uint32_t stack_max;
 };
+constexpr uint32_t kTraceStack = 64;  // binary traversal stack entries per thread
 constexpr uint32_t kMaxLights = 64;  // lights per scene (one shadow sub-queue each)
 cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a, cudaStream_t s,
                          const TraceShape& shape = TraceShape());

@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
     bool found = false, ok = true, in_blas = false;
     uint32_t stack[kStack];
     int sp = 0;
+    const int smax = (a.stack_max >= 1 && a.stack_max < (uint32_t)kStack) ? (int)a.stack_max : kStack;
     uint32_t ref = kNone, iter = 0, cur_id = 0, cur_leaf = 0;
     const float4* nodes = nullptr;
     const float4* tris = nullptr;
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
             bool h1 = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, cr, tmin, tlim, tn1, tf1);
             if (BRUTE) h0 = h1 = true;
             if (h0 && h1) {
-                if (sp >= kStack) {
+                if (sp >= smax) {
                     record_error(a.st, RG_ERR_STACK);
                     ok = false;
                     finished = true;
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
             const float ddx = fmaf(m0.x, dx, fmaf(m0.y, dy, __fmul_rn(m0.z, dz)));
             const float ddy = fmaf(m1.x, dx, fmaf(m1.y, dy, __fmul_rn(m1.z, dz)));
             const float ddz = fmaf(m2.x, dx, fmaf(m2.y, dy, __fmul_rn(m2.z, dz)));
-            if (sp >= kStack) {
+            if (sp >= smax) {
                 record_error(a.st, RG_ERR_STACK);
                 ok = false;
                 finished = true;

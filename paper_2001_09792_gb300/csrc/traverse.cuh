@@ -33,7 +33,7 @@ namespace rg {
 
 namespace {
 
-constexpr int kStack = 64;
+constexpr int kStack = (int)kTraceStack;
 constexpr uint32_t kMarker = 0xFFFFFFFEu;
 constexpr int kTraceBlock = 128;
 // 1 + 2 * gamma_3, gamma_3 = 3u / (1 - 3u), u = 2^-24
@@ -305,6 +305,7 @@ __device__ __forceinline__ RayHit trace_core(const TraceArgs& a, const float4* t
 
     uint32_t stack[kStack];
     int sp = 0;
+    const int smax = (a.stack_max >= 1 && a.stack_max < (uint32_t)kStack) ? (int)a.stack_max : kStack;
     uint32_t ref = tlas_root;
     bool in_blas = false;
     const float4* nodes = tlas_nodes;
@@ -343,7 +344,7 @@ __device__ __forceinline__ RayHit trace_core(const TraceArgs& a, const float4* t
                 const bool f0 = visit_first0<kAny>(tn0, tf0, tn1, tf1);
                 uint32_t nearc = f0 ? n3.x : n3.y;
                 uint32_t farc = f0 ? n3.y : n3.x;
-                if (sp >= kStack) {
+                if (sp >= smax) {
                     record_error(a.st, RG_ERR_STACK);
                     ok = false;
                     break;
@@ -383,7 +384,7 @@ __device__ __forceinline__ RayHit trace_core(const TraceArgs& a, const float4* t
             cur_id = meta1.y;
             cur_leaf = leaf;
             in_blas = true;
-            if (sp >= kStack) {
+            if (sp >= smax) {
                 record_error(a.st, RG_ERR_STACK);
                 ok = false;
                 break;

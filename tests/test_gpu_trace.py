@@ -275,3 +275,43 @@ rg.rg_scene_destroy(h)
     p = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=300)
     assert p.returncode == 0, p.stderr
     assert f"STATUS {rg.RG_ERR_OOM}" in p.stdout and "AFTER 0" in p.stdout, p.stdout
+
+
+@pytest.mark.parametrize("env,status", [("RG_TEST_STACK=1", "RG_ERR_STACK"), ("RG_TEST_ITER_CAP=3", "RG_ERR_TIMEOUT")])
+def test_traversal_limits_report_errors(env, status):
+    """A traversal stack of one entry, or an iteration cap of three steps (test
+    limits set from the environment), is exceeded by most rays of the medium
+    scene: the rays come back as misses, the next rg_sync returns the error
+    (for rg_trace_rays and rg_render alike), and the scene stays usable.  No
+    GPU fault is involved: the kernels record the error and end the ray."""
+    code = r"""
+import numpy as np, torch, paper_2001_09792_gb300 as rg, scenegen as g
+s = g.medium_scene(width=160, height=90, max_depth=2)
+with rg.GpuScene(s) as gs:
+    lo, hi = s.world_aabb()
+    rays = torch.from_numpy(g.random_rays(20000, lo - 5, hi + 5, seed=9)).cuda()
+    hits = rg.split_hits(rg.rg_trace_rays(gs.h, rays))
+    try:
+        rg.rg_sync(gs.h)
+        print("NOERROR")
+    except rg.RgError as e:
+        print("TRACE", e.status)
+    print("MISSES", float((hits["inst"] == 0xFFFFFFFF).mean()))
+    rg.rg_render(gs.h, s.camera, s.width, s.height, s.max_depth)
+    try:
+        rg.rg_sync(gs.h)
+        print("NOERROR")
+    except rg.RgError as e:
+        print("RENDER", e.status)
+    rg.rg_sync(gs.h)
+    print("USABLE")
+"""
+    k, v = env.split("=")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    p = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, **{k: v}), cwd=root, capture_output=True,
+                       text=True, timeout=300)
+    assert p.returncode == 0, p.stderr
+    want = getattr(rg, status)
+    assert f"TRACE {want}" in p.stdout and f"RENDER {want}" in p.stdout and "USABLE" in p.stdout, p.stdout
+    misses = float(p.stdout.split("MISSES")[1].split()[0])
+    assert misses > 0.5, p.stdout
