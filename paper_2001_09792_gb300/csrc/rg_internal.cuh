@@ -259,8 +259,9 @@ struct TraceArgs {
     // segments; null: no splitting
     uint32_t* seg_count;
     uint32_t split, split_max;
-    // binary traversal: stack entries a ray may use (0: all kTraceStack); a
-    // smaller limit only makes failure-path tests reach RG_ERR_STACK
+    // binary traversal with counting (RG_TRACE_STATS, RG_SCENE_COUNT): stack
+    // entries a ray may use (0: all kTraceStack); a smaller limit only makes
+    // failure-path tests reach RG_ERR_STACK
     uint32_t stack_max;
 };
 constexpr uint32_t kTraceStack = 64;  // binary traversal stack entries per thread

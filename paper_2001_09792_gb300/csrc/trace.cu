@@ -120,7 +120,9 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
     bool found = false, ok = true, in_blas = false;
     uint32_t stack[kStack];
     int sp = 0;
-    const int smax = (a.stack_max >= 1 && a.stack_max < (uint32_t)kStack) ? (int)a.stack_max : kStack;
+    // the test limit on the stack applies to the counting instantiations only,
+    // so the timed kernels compare with the constant
+    const int smax = (STATS && a.stack_max >= 1 && a.stack_max < (uint32_t)kStack) ? (int)a.stack_max : kStack;
     uint32_t ref = kNone, iter = 0, cur_id = 0, cur_leaf = 0;
     const float4* nodes = nullptr;
     const float4* tris = nullptr;

