@@ -1,6 +1,6 @@
 """Closest-hit / any-hit / miss on the GPU vs the FP64 oracle.
 
-Tolerances (stated here; derived in the design doc):
+Tolerances (derived from the float32 arithmetic of the path):
   * hit ids equal on every ray the oracle does not flag as ambiguous;
   * t within 1e-5 relative, widened for grazing incidence by the float32
     position error eta / |cos| (eta = KAPPA * 2^-24 * the magnitudes entering
