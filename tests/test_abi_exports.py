@@ -88,3 +88,37 @@ def test_null_server_is_rejected_without_gpu():
     assert L.rg_server_step(None, None) == rg.RG_ERR_INVALID_ARG
     assert L.rg_server_destroy(None) == rg.RG_OK
     assert L.rg_server_create(None, None) == rg.RG_ERR_INVALID_ARG
+
+
+def header_signatures():
+    """name -> list of parameter declarations, from include/rg.h."""
+    txt = open(os.path.join(ROOT, "include", "rg.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(?:rg_status|const char\*)\s+(rg_[a-z_0-9]+)\s*\(([^)]*)\)\s*;", txt):
+        params = [p.strip() for p in m.group(2).replace("\n", " ").split(",") if p.strip() and p.strip() != "void"]
+        out[m.group(1)] = params
+    return out
+
+
+def test_binding_argument_types_match_the_header():
+    """Every function the binding declares takes as many arguments as the
+    header says, pointers where the header has pointers and 32-bit integers
+    where it has 32-bit integers."""
+    sigs = header_signatures()
+    L = rg.lib()
+    assert set(sigs) == set(declared_symbols())
+    ptr_types = (ctypes.c_void_p, ctypes.c_char_p)
+    for name, params in sigs.items():
+        if name == "rg_last_error":
+            assert params == [] and L.rg_last_error.argtypes == []
+            continue
+        args = getattr(L, name).argtypes
+        assert args is not None and len(args) == len(params), (name, params, args)
+        for decl, t in zip(params, args):
+            is_ptr = "*" in decl or "[" in decl  # an array parameter is a pointer
+            binding_ptr = t in ptr_types or (isinstance(t, type) and issubclass(t, ctypes._Pointer))
+            assert is_ptr == binding_ptr, (name, decl, t)
+            if not is_ptr:
+                assert t in (ctypes.c_uint32, ctypes.c_int32), (name, decl, t)
+                assert ("uint32_t" in decl) == (t is ctypes.c_uint32), (name, decl, t)
