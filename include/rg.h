@@ -386,9 +386,11 @@ rg_status rg_server_create(rg_server** out, const rg_server_desc* desc);
 rg_status rg_server_destroy(rg_server* server);
 /* Makes a built scene (rg_tlas_build and rg_scene_set_materials done)
  * available to requests; the scene must stay alive and must not be rebuilt
- * (rg_blas_build, rg_tlas_build) or destroyed while the server exists.
- * Returns RG_ERR_INVALID_ARG for a compressed-only or foreign-device scene or
- * one with more lights than max_lights. */
+ * (rg_blas_build, rg_tlas_build) or destroyed while the server exists.  The
+ * server traces the scene's binary float32 BVH, also for a scene made with
+ * RG_SCENE_COMPRESSED (its hit records are the same in both forms).  Returns
+ * RG_ERR_INVALID_ARG for a foreign-device scene or one with more lights than
+ * max_lights. */
 rg_status rg_server_add_scene(rg_server* server, rg_scene* scene, uint32_t* scene_id);
 /* Queues a request; validated here (RG_ERR_INVALID_ARG on a bad size, depth,
  * scene id or pointer). */

@@ -272,3 +272,19 @@ def test_single_request_completes_after_its_shadow_rays(scenes):
     imgs, done, st = run_server(gss, req)
     assert done[0]["admitted_step"] == 1 and done[0]["completed_step"] == 2 and st["steps"] == 2
     check_against_alone(descs, gss, req, imgs, st)
+
+
+def test_compressed_scene_served_from_its_binary_bvh(scenes):
+    """A scene made with RG_SCENE_COMPRESSED is served from its binary float32
+    BVH; since the two forms give bit-identical hit records, the served image
+    equals rg_render of the compressed scene alone and the ray counts agree."""
+    descs, _ = scenes
+    desc = descs[1]
+    gs = rg.GpuScene(desc, flags=rg.RG_SCENE_COMPRESSED)
+    try:
+        reqs = [dict(scene=0, w=320, h=180, depth=4, M=g.motion(desc.M, 5), camera=desc.camera)]
+        imgs, done, st = run_server([gs], reqs)
+        assert len(done) == 1
+        check_against_alone([desc], [gs], reqs, imgs, st)
+    finally:
+        gs.close()
