@@ -8,6 +8,11 @@ back-face culling).  Without culling the swap negates the edge functions U, V,
 W, their sum det and the scaled distance T together, so t = T/det and the
 barycentrics V/det, W/det come out bit for bit the same: the traversal uses
 the cyclic order (kz+1, kz+2, kz) and reads triangles stored in that order.
+
+The box tests are pinned the same way: the binary BVH's slab test and the
+compressed 8-wide node's dequantising FMA test with its widening never reject
+a box that the ray's segment meets (float64), and reject boxes it misses by a
+clear margin; the outward quantisation of child boxes contains each box.
 """
 import numpy as np
 
@@ -177,3 +182,152 @@ def test_zero_direction_origin_on_plane_leaves_the_axis_open():
     for ox, want in [(0.0, True), (2.0, True), (1.0, True), (-1e-7, False), (2.0000002, False)]:
         o = np.array([[ox, 0, 0]], f32)
         assert slab32(lo, hi, o, d, f32(0), f32(np.inf))[0] == want, ox
+
+
+# ---------------------------------------------------------------- compressed 8-wide node test
+#
+# A wide node stores its children's boxes as 8-bit integers against a float32
+# origin p and a per-axis power of two 2^e, rounded outward:
+#   qlo = floor(rd(lo - p) / 2^e),  qhi = ceil(ru(hi - p) / 2^e),
+# with e the smallest exponent such that 255 * 2^e >= ru(max hi - p).  The
+# traversal tests a child with one FMA per plane, t = q * (2^e / d) + (p - o) / d,
+# and widens every child interval of the node by
+#   E = 8 * 2^-24 * max over axes of (255 |2^e / d| + |(p - o) / d|).
+
+QERR = f32(8.0 * 2.0 ** -24)
+
+
+def round_dir(x, up):
+    """float64 -> float32, rounded down (up=False) or up."""
+    r = x.astype(f32)
+    if up:
+        return np.where(r.astype(np.float64) < x, np.nextafter(r, f32(np.inf)), r)
+    return np.where(r.astype(np.float64) > x, np.nextafter(r, f32(-np.inf)), r)
+
+
+def exact_diff(a, b):
+    """a - b of float32 arrays in float64, with a mask of the cases where that
+    difference is exact (TwoSum error zero)."""
+    a, b = a.astype(np.float64), b.astype(np.float64)
+    s = a - b
+    bb = s - a
+    err = (a - (s - bb)) + (-b - bb)
+    return s, err == 0
+
+
+def exp_for(ext):
+    """Smallest e in [-126, 127] with 255 * 2^e >= ext (ext >= 0)."""
+    with np.errstate(divide="ignore"):
+        e = np.where(ext > 0, np.ceil(np.log2(np.where(ext > 0, ext, 1.0) / 255.0)), -126).astype(np.int64)
+    e = np.clip(e, -126, 127)
+    for _ in range(3):
+        e = np.where((e > -126) & (np.ldexp(255.0, e - 1) >= ext), e - 1, e)
+        e = np.where((e < 127) & (np.ldexp(255.0, e) < ext), e + 1, e)
+    return e
+
+
+def quantize(lo, hi, p, e):
+    """The builder's outward rounding of float32 child boxes against p, 2^e."""
+    dlo, ok_lo = exact_diff(lo, p)
+    dhi, ok_hi = exact_diff(hi, p)
+    qlo = np.floor(round_dir(dlo, False).astype(np.float64) * np.ldexp(1.0, -e))
+    qhi = np.ceil(round_dir(dhi, True).astype(np.float64) * np.ldexp(1.0, -e))
+    return np.clip(qlo, 0, 255), np.clip(qhi, 0, 255), ok_lo & ok_hi
+
+
+def fma32(a, b, c):
+    """float32 fused multiply-add: the product is exact in float64 (8-bit by
+    24-bit operands), then the sum is rounded (to float64, then float32; the
+    double rounding can differ by an ulp, far inside the widening)."""
+    with np.errstate(all="ignore"):
+        return (np.asarray(a, np.float64) * np.asarray(b, np.float64) + np.asarray(c, np.float64)).astype(f32)
+
+
+def wide_child_test(p, e, qlo, qhi, o, d, tmin, tlim):
+    """The traversal's test of one child of a compressed node, in float32."""
+    with np.errstate(all="ignore"):
+        ix = f32(1) / d
+        S = np.ldexp(f32(1), e).astype(f32) * ix          # exact: a power of two times 1/d
+        B = (p - o) * ix
+        Ea = fma32(f32(255), np.abs(S), np.abs(B))
+        E = QERR * np.fmax(np.fmax(Ea[:, 0], Ea[:, 1]), Ea[:, 2])
+        Bn, Bf = B - E[:, None], B + E[:, None]
+        neg = np.signbit(ix)
+        qn = np.where(neg, qhi, qlo).astype(f32)
+        qf = np.where(neg, qlo, qhi).astype(f32)
+        tnear, tfar = fma32(qn, S, Bn), fma32(qf, S, Bf)
+        tn = np.fmax(np.fmax(tnear[:, 0], tnear[:, 1]), np.fmax(tnear[:, 2], tmin))
+        tf = np.fmin(np.fmin(tfar[:, 0], tfar[:, 1]), np.fmin(tfar[:, 2], tlim))
+    return tn <= tf
+
+
+def wide_cases(n, seed):
+    """Child boxes of random wide nodes at three scales (some flat, some
+    spanning the node), and rays aimed at points of their closure, random or
+    axis-aligned."""
+    rng = np.random.default_rng(seed)
+    scale = rng.choice([1e-3, 1.0, 1e3], n)[:, None]
+    p = (rng.uniform(-20, 20, (n, 3)) * scale).astype(f32)
+    ext = rng.uniform(0, 10, (n, 3)) * scale * (rng.random((n, 3)) > 0.05)
+    c0 = rng.random((n, 3)) * ext
+    c1 = c0 + rng.random((n, 3)) * (ext - c0) * (rng.random((n, 3)) > 0.1)
+    lo = round_dir(p + c0, True)
+    hi = np.maximum(round_dir(p + c1, False), lo)
+    mx = np.maximum(round_dir(p + ext, False), hi)
+    dmx, ok = exact_diff(mx, p)
+    e = exp_for(round_dir(dmx, True).astype(np.float64))
+    qlo, qhi, okq = quantize(lo, hi, p, e)
+    o = (rng.uniform(-30, 30, (n, 3)) * scale).astype(f32)
+    blo = p.astype(np.float64) + qlo * np.ldexp(1.0, e)
+    bhi = p.astype(np.float64) + qhi * np.ldexp(1.0, e)
+    target = blo + (bhi - blo) * rng.choice([0.0, 0.5, 1.0, rng.random()], (n, 3))
+    d = (target - o).astype(f32)
+    m = rng.random(n) < 0.2
+    d[m] = rng.normal(size=(m.sum(), 3)).astype(f32)
+    k = rng.random(n) < 0.1
+    ax = rng.integers(0, 3, n)
+    for a in range(3):
+        sel = k & (ax == a)
+        keep = d[sel, a].copy()
+        d[sel] = 0
+        d[sel, a] = np.where(keep == 0, 1, keep)
+    keep = (ok & okq).all(axis=1)
+    return [x[keep] for x in (lo, hi, p, e, qlo, qhi, blo, bhi, o, d)]
+
+
+def test_wide_quantisation_contains_the_box_and_is_tight():
+    lo, hi, p, e, qlo, qhi, blo, bhi, *_ = wide_cases(300_000, 5)
+    assert len(lo) > 290_000
+    assert ((qlo >= 0) & (qlo <= qhi) & (qhi <= 255)).all()
+    # outward: the dequantised box contains the float32 box, exactly
+    assert (blo <= lo.astype(np.float64)).all() and (bhi >= hi.astype(np.float64)).all()
+    # and at most one step looser on each side (the directed rounding of the
+    # difference may cross one multiple of 2^e)
+    step = np.ldexp(1.0, e)
+    assert (lo.astype(np.float64) - blo < 2 * step).all()
+    assert (bhi - hi.astype(np.float64) < 2 * step).all()
+    # the scale: the smallest power of two that spans an extent in 255 steps
+    ext = np.concatenate([np.ldexp(255.0, np.arange(-126, 128)), np.random.default_rng(9).uniform(0, 1e6, 10_000),
+                          np.ldexp(np.random.default_rng(10).random(10_000), -120), [0.0]])
+    ee = exp_for(ext)
+    assert (np.ldexp(255.0, ee) >= ext).all()
+    assert ((ee == -126) | (np.ldexp(255.0, ee - 1) < ext)).all()
+
+
+def test_wide_node_test_never_rejects_a_child_the_segment_meets():
+    lo, hi, p, e, qlo, qhi, blo, bhi, o, d = wide_cases(300_000, 6)
+    nonzero = (np.abs(d) >= 1e-2 * np.abs(d).max(axis=1, keepdims=True)).all(axis=1)
+    for tmax in [np.inf, 5.0, 40.0]:
+        tm = tmax * 1.0
+        tlim = f32(tm) * CULL if np.isfinite(tm) else f32(np.inf)
+        got = wide_child_test(p, e, qlo, qhi, o, d, f32(0), tlim)
+        want = exact_hit(blo, bhi, o, d, 0.0, tm)
+        missed = want & ~got
+        assert not missed.any(), f"tmax {tmax}: {missed.sum()} children rejected, e.g. case {np.nonzero(missed)[0][:3]}"
+        assert want.sum() > 100_000
+        # not permissive beyond the widening: with no near-zero direction
+        # component, a child missed by a relative 1e-3 is rejected
+        grow = (1e-3 * (np.abs(p).max(1) + np.abs(o).max(1) + np.abs(bhi - blo).max(1)))[:, None]
+        far = nonzero & ~exact_hit(blo - grow, bhi + grow, o, d, 0.0, tm)
+        assert far.sum() > 20_000
+        assert not (got & far).any(), f"tmax {tmax}: {(got & far).sum()} far misses accepted"
