@@ -728,7 +728,7 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, uint32_t w, uint32_t h, u
     // level's count one level late (copied back while the GPU traces) and
     // sizes the next queues from it.
     auto cap_of = [&](uint32_t d) { return (uint64_t)N << (d - 1); };
-    bool async = !s->wide && !(s->desc.flags & RG_SCENE_FRUGAL) && max_depth <= 24;
+    bool async = !(s->desc.flags & RG_SCENE_FRUGAL) && max_depth <= 24;
     uint64_t cap_q[2] = {0, 0}, cap_max = 0;
     if (async) {
         for (uint32_t d = 1; d <= max_depth; ++d) {

@@ -234,16 +234,17 @@ def test_shared_scenes_render_concurrently():
         b.close()
 
 
-@pytest.mark.parametrize("lights", [4, 0])
-def test_frugal_queues_equal_worst_case_queues(lights):
+@pytest.mark.parametrize("lights,bvh", [(4, 0), (0, 0), (4, rg.RG_SCENE_COMPRESSED)])
+def test_frugal_queues_equal_worst_case_queues(lights, bvh):
     """Queues sized from each level's ray count (the host waits per level,
     RG_SCENE_FRUGAL) and queues sized once for the frame's worst case (no host
-    wait) render the same image from the same rays and traversal work."""
+    wait) render the same image from the same rays and traversal work, on the
+    binary and on the compressed BVH."""
     s = g.medium_scene(width=480, height=270, max_depth=6)
     s.light_pos, s.light_I = s.light_pos[:lights], s.light_I[:lights]
     out = {}
     for name, flags in [("frugal", rg.RG_SCENE_FRUGAL), ("worst", 0)]:
-        with rg.GpuScene(s, flags=flags | rg.RG_SCENE_COUNT) as gs:
+        with rg.GpuScene(s, flags=flags | bvh | rg.RG_SCENE_COUNT) as gs:
             rg.rg_reset_stats(gs.h)
             img = render(s, gs=gs)
             out[name] = (img, rg.rg_get_stats(gs.h))
