@@ -284,24 +284,40 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
 // group (triangles or instances of the leaf slots hit at the last node: base
 // index, one bit per item).  Items are handled before the next node is
 // fetched; unfinished groups and the BLAS marker go on a short stack of
-// 8-byte entries.  Child boxes are tested with one FMA per plane,
-// t = q * (2^e / d) + (p - o) / d, which differs from the exact slab
-// distance by at most kQuantErr * (255 |2^e / d| + |(p - o) / d|) (a few
-// roundings of those magnitudes); widening every child interval of the node
-// by that bound E keeps the test conservative, so the wide path finds the same
-// hits as the binary one.
+// 8-byte entries.  Child boxes are tested with one FMA per plane on the
+// byte's float v = 1 + q 2^-15 (built by a byte permute, exact):
+// t = v * 2^15 S + (B - 2^15 S) with S = 2^e / d and B = (p - o) / d, which
+// is q S + B up to a few roundings of magnitude 255 |S| + |B| and two of
+// magnitude 2^15 |S| (at most 2^-9 |S| each).  Widening each axis' child
+// intervals by E = kQuantErr (255 |S| + |B|) + 2^-7 |S| keeps the test
+// conservative, so the wide path finds the same hits as the binary one.  A
+// plane offset that overflows (or a zero direction component) becomes NaN,
+// which leaves that axis open.
 constexpr int kStack8 = 48;
 constexpr uint32_t kKindNode = 0u, kKindItem = 1u << 30, kKindMarker = 2u << 30;
 constexpr float kQuantErr = 8.0f * 5.9604644775390625e-08f;
+constexpr float kPlaneErr = 0.0078125f;  // 2^-7
+constexpr float kBias = 32768.0f;        // 2^15
 
 __device__ __forceinline__ uint32_t oct_of(const SpaceRay& r) {
     return (__float_as_uint(r.ix) >> 31) | ((__float_as_uint(r.iy) >> 31) << 1) | ((__float_as_uint(r.iz) >> 31) << 2);
 }
 
-// Byte k of w as a float: one byte permute builds the bit pattern of 2^23 + q
-// (exponent byte 0x4B above the byte), then an exact subtraction of 2^23.
-__device__ __forceinline__ float byte_f(uint32_t w, int k) {
-    return __uint_as_float(__byte_perm(w, 0x4B000000u, (uint32_t)k | 0x7440u)) - 8388608.0f;
+// Byte k of w as the float 1 + q 2^-15: one byte permute puts q in the
+// second byte of the mantissa of 1.0 (bit pattern 0x3F80qq00).
+__device__ __forceinline__ float byte_v(uint32_t w, int k) {
+    return __uint_as_float(__byte_perm(w, 0x3F800000u, ((uint32_t)k << 4) | 0x7604u));
+}
+
+// Plane offset B - 2^15 S in one rounding; NaN where it overflows.
+__device__ __forceinline__ float plane_offset(float S, float B) {
+    const float c = fmaf(-kBias, S, B);
+    return fabsf(c) < INFINITY ? c : __int_as_float(0x7FFFFFFF);
+}
+
+// Per-axis widening of the child intervals (see above).
+__device__ __forceinline__ float plane_err(float S, float B) {
+    return fmaf(kQuantErr, fmaf(255.0f, fabsf(S), fabsf(B)), kPlaneErr * fabsf(S));
 }
 
 template <int MODE, bool STATS>
@@ -388,11 +404,12 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace8(TraceArgs a) {
                     const float Bx = __fmul_rn(__fsub_rn(w0.x, cr.ox), cr.ix);
                     const float By = __fmul_rn(__fsub_rn(w0.y, cr.oy), cr.iy);
                     const float Bz = __fmul_rn(__fsub_rn(w0.z, cr.oz), cr.iz);
-                    const float E = kQuantErr * fmaxf(fmaxf(fmaf(255.0f, fabsf(Sx), fabsf(Bx)), fmaf(255.0f, fabsf(Sy), fabsf(By))),
-                                                      fmaf(255.0f, fabsf(Sz), fabsf(Bz)));
+                    const float Ux = Sx * kBias, Uy = Sy * kBias, Uz = Sz * kBias;  // exact (or inf)
+                    const float Cx = plane_offset(Sx, Bx), Cy = plane_offset(Sy, By), Cz = plane_offset(Sz, Bz);
+                    const float Ex = plane_err(Sx, Bx), Ey = plane_err(Sy, By), Ez = plane_err(Sz, Bz);
                     // near planes shifted down by E, far planes up by E
-                    const float Bxn = Bx - E, Byn = By - E, Bzn = Bz - E;
-                    const float Bxf = Bx + E, Byf = By + E, Bzf = Bz + E;
+                    const float Bxn = Cx - Ex, Byn = Cy - Ey, Bzn = Cz - Ez;
+                    const float Bxf = Cx + Ex, Byf = Cy + Ey, Bzf = Cz + Ez;
                     // near/far planes per axis from the direction signs
                     const bool nx = oct & 1, ny = oct & 2, nz = oct & 4;
                     const uint32_t nx0 = nx ? w3.z : w2.x, nx1 = nx ? w3.w : w2.y, fx0 = nx ? w2.x : w3.z, fx1 = nx ? w2.y : w3.w;
@@ -404,12 +421,12 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace8(TraceArgs a) {
     #pragma unroll
                     for (int c = 0; c < 8; ++c) {
                         const int k = c & 3;
-                        const float tnx = fmaf(byte_f(c < 4 ? nx0 : nx1, k), Sx, Bxn);
-                        const float tfx = fmaf(byte_f(c < 4 ? fx0 : fx1, k), Sx, Bxf);
-                        const float tny = fmaf(byte_f(c < 4 ? ny0 : ny1, k), Sy, Byn);
-                        const float tfy = fmaf(byte_f(c < 4 ? fy0 : fy1, k), Sy, Byf);
-                        const float tnz = fmaf(byte_f(c < 4 ? nz0 : nz1, k), Sz, Bzn);
-                        const float tfz = fmaf(byte_f(c < 4 ? fz0 : fz1, k), Sz, Bzf);
+                        const float tnx = fmaf(byte_v(c < 4 ? nx0 : nx1, k), Ux, Bxn);
+                        const float tfx = fmaf(byte_v(c < 4 ? fx0 : fx1, k), Ux, Bxf);
+                        const float tny = fmaf(byte_v(c < 4 ? ny0 : ny1, k), Uy, Byn);
+                        const float tfy = fmaf(byte_v(c < 4 ? fy0 : fy1, k), Uy, Byf);
+                        const float tnz = fmaf(byte_v(c < 4 ? nz0 : nz1, k), Uz, Bzn);
+                        const float tfz = fmaf(byte_v(c < 4 ? fz0 : fz1, k), Uz, Bzf);
                         const float tn = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, tmin));
                         const float tf = fminf(fminf(tfx, tfy), fminf(tfz, tlim));
                         if (tn <= tf) hitmask |= 1u << c;

@@ -190,11 +190,17 @@ def test_zero_direction_origin_on_plane_leaves_the_axis_open():
 # origin p and a per-axis power of two 2^e, rounded outward:
 #   qlo = floor(rd(lo - p) / 2^e),  qhi = ceil(ru(hi - p) / 2^e),
 # with e the smallest exponent such that 255 * 2^e >= ru(max hi - p).  The
-# traversal tests a child with one FMA per plane, t = q * (2^e / d) + (p - o) / d,
-# and widens every child interval of the node by
-#   E = 8 * 2^-24 * max over axes of (255 |2^e / d| + |(p - o) / d|).
+# traversal tests a child with one FMA per plane on the byte's float 1 + q 2^-15
+# (a byte permute puts q in the mantissa under the exponent of 1; exact):
+#   t = (1 + q 2^-15) * 2^15 S + (B - 2^15 S),  S = 2^e / d,  B = (p - o) / d,
+# and widens the child intervals of each axis by
+#   E = 8 * 2^-24 * (255 |S| + |B|) + 2^-7 |S|
+# (the last term covers the roundings of B - 2^15 S and of the shifted
+# planes, each at most 2^-9 |S| beyond those of B itself).  A plane offset
+# B - 2^15 S that overflows is replaced by NaN, which leaves the axis open.
 
 QERR = f32(8.0 * 2.0 ** -24)
+PLANE_ERR = f32(2.0 ** -7)
 
 
 def round_dir(x, up):
@@ -236,9 +242,10 @@ def quantize(lo, hi, p, e):
 
 
 def fma32(a, b, c):
-    """float32 fused multiply-add: the product is exact in float64 (8-bit by
-    24-bit operands), then the sum is rounded (to float64, then float32; the
-    double rounding can differ by an ulp, far inside the widening)."""
+    """float32 fused multiply-add: the product of two float32 values is exact
+    in float64, then the sum is rounded (to float64, then float32; where the
+    exact sum needs more than 53 bits the double rounding can differ by an
+    ulp, far inside the widening)."""
     with np.errstate(all="ignore"):
         return (np.asarray(a, np.float64) * np.asarray(b, np.float64) + np.asarray(c, np.float64)).astype(f32)
 
@@ -249,13 +256,15 @@ def wide_child_test(p, e, qlo, qhi, o, d, tmin, tlim):
         ix = f32(1) / d
         S = np.ldexp(f32(1), e).astype(f32) * ix          # exact: a power of two times 1/d
         B = (p - o) * ix
-        Ea = fma32(f32(255), np.abs(S), np.abs(B))
-        E = QERR * np.fmax(np.fmax(Ea[:, 0], Ea[:, 1]), Ea[:, 2])
-        Bn, Bf = B - E[:, None], B + E[:, None]
+        U = S * f32(2.0 ** 15)                             # exact (or inf)
+        E = fma32(QERR, fma32(f32(255), np.abs(S), np.abs(B)), PLANE_ERR * np.abs(S))
+        C = fma32(f32(-(2.0 ** 15)), S, B)
+        C = np.where(np.isinf(C), f32(np.nan), C)
+        Cn, Cf = C - E, C + E
         neg = np.signbit(ix)
-        qn = np.where(neg, qhi, qlo).astype(f32)
-        qf = np.where(neg, qlo, qhi).astype(f32)
-        tnear, tfar = fma32(qn, S, Bn), fma32(qf, S, Bf)
+        vn = (1.0 + np.where(neg, qhi, qlo) * 2.0 ** -15).astype(f32)   # exact
+        vf = (1.0 + np.where(neg, qlo, qhi) * 2.0 ** -15).astype(f32)
+        tnear, tfar = fma32(vn, U, Cn), fma32(vf, U, Cf)
         tn = np.fmax(np.fmax(tnear[:, 0], tnear[:, 1]), np.fmax(tnear[:, 2], tmin))
         tf = np.fmin(np.fmin(tfar[:, 0], tfar[:, 1]), np.fmin(tfar[:, 2], tlim))
     return tn <= tf
