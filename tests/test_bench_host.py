@@ -1,0 +1,72 @@
+"""Host-side logic of bench.py, on the CPU: the clock summary that decides
+whether a run is kept, the nearest-rank percentiles of the latency figures,
+and the code hash that ties the committed DRAM traffic record to the
+traversal sources it was measured on."""
+import os
+
+import pytest
+
+import bench
+
+
+def test_clock_summary_median_max_and_active_reasons():
+    lines = [
+        "2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n",
+        "2070, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "[N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active\n",   # unreadable sample
+        "garbage\n",
+    ]
+    out = bench.summarize_clocks(lines)
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+
+
+def test_clock_summary_names_a_thermal_slowdown_and_a_low_clock():
+    lines = ["1200, 2070, 800, 0x40, Not Active, Active, Not Active, Not Active\n"] * 4
+    out = bench.summarize_clocks(lines)
+    assert out["reasons"] == ["hw_thermal_slowdown"]
+    assert out["sm_mhz"] == 1200.0 and out["sm_max_mhz"] == 2070.0
+
+
+def test_clock_summary_without_samples_is_none():
+    assert bench.summarize_clocks([]) is None
+    assert bench.summarize_clocks(["only, three, fields\n"]) is None
+
+
+def test_nearest_rank_percentiles():
+    xs = list(range(1, 101))
+    assert bench.pct(xs, 0.5) == 50
+    assert bench.pct(xs, 0.99) == 99
+    assert bench.pct(xs, 1.0) == 100
+    assert bench.pct([7.0], 0.99) == 7.0
+    assert bench.pct([4, 1, 3, 2], 0.5) == 2   # order of the input does not matter
+
+
+def test_code_hash_ignores_comments_and_blank_lines(tmp_path):
+    a = tmp_path / "a.cu"
+    b = tmp_path / "b.cu"
+    a.write_text("int f(int x) {\n    return x + 1;\n}\n")
+    b.write_text("// a comment\nint f(int x) {   \n\n    return x + 1;  // trailing comment\n}\n")
+    assert bench.code_sha(str(a)) == bench.code_sha(str(b))
+    b.write_text("int f(int x) {\n    return x + 2;\n}\n")
+    assert bench.code_sha(str(a)) != bench.code_sha(str(b))
+    # file order and boundaries count
+    assert bench.code_sha(str(a), str(b)) != bench.code_sha(str(b), str(a))
+
+
+def test_traffic_record_only_for_the_sources_it_was_measured_on(tmp_path, monkeypatch):
+    txt = open(os.path.join(bench.ROOT, "profiles", "trace_pair_medium.md")).read()
+    assert "traversal_code_sha256_16:" in txt and "dram_bytes_per_traversal_launch:" in txt
+    # a source set other than the measured one gives no record
+    other = tmp_path / "other.cu"
+    other.write_text("__global__ void k() {}\n")
+    monkeypatch.setattr(bench, "TRAVERSAL_SOURCES", [str(other)])
+    assert bench.traffic_record() is None
+
+
+def test_traffic_record_value_is_a_plausible_byte_count():
+    rec = bench.traffic_record()
+    if rec is None:
+        pytest.skip("traversal sources changed since the DRAM capture (the bench then reports traffic null)")
+    # per launch: more than the rays read, far less than the algorithmic bytes (the BVH is in L2)
+    assert 1e6 < rec < 1.33e9
