@@ -70,3 +70,26 @@ def test_traffic_record_value_is_a_plausible_byte_count():
         pytest.skip("traversal sources changed since the DRAM capture (the bench then reports traffic null)")
     # per launch: more than the rays read, far less than the algorithmic bytes (the BVH is in L2)
     assert 1e6 < rec < 1.33e9
+
+
+def test_clock_sampler_stop_reads_and_removes_its_file(tmp_path):
+    """The sampler's stop path: signal the sampling process, summarise its CSV
+    file, delete it (a stand-in process object replaces nvidia-smi)."""
+    class Proc:
+        signals = []
+
+        def send_signal(self, sig):
+            self.signals.append(sig)
+
+        def wait(self, timeout=None):
+            return 0
+
+    path = tmp_path / "clocks.csv"
+    path.write_text("2070, 2070, 1000, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                    "2055, 2070, 1300, 0x4, Not Active, Not Active, Not Active, Active\n")
+    cs = bench.ClockSampler(0)
+    cs.proc, cs.path = Proc(), str(path)
+    out = cs.stop()
+    assert out == {"sm_mhz": 2062.5, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 2}
+    assert Proc.signals and not path.exists()
+    assert bench.ClockSampler(0).stop() is None   # never started (no nvidia-smi): no clocks
