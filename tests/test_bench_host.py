@@ -1,7 +1,7 @@
 """Host-side logic of bench.py, on the CPU: the clock summary that decides
 whether a run is kept, the nearest-rank percentiles of the latency figures,
-and the code hash that ties the committed DRAM traffic record to the
-traversal sources it was measured on."""
+the code hash that ties the committed DRAM traffic record to the traversal
+sources it was measured on, and the reference (oracle) arm's JSON line."""
 import os
 
 import pytest
@@ -93,3 +93,37 @@ def test_clock_sampler_stop_reads_and_removes_its_file(tmp_path):
     assert out == {"sm_mhz": 2062.5, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 2}
     assert Proc.signals and not path.exists()
     assert bench.ClockSampler(0).stop() is None   # never started (no nvidia-smi): no clocks
+
+
+def _run_bench(args, env_extra=None, timeout=300):
+    import json
+    import subprocess
+    import sys
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    p = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), *args], capture_output=True, text=True,
+                       env=env, timeout=timeout)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [json.loads(l) for l in p.stdout.splitlines() if l.startswith("{")]
+    return lines
+
+
+def test_reference_arm_prints_one_contract_line():
+    """The oracle arm on the host cores: one JSON line with the metric of the
+    native arm, the oracle named as the baseline and an end-to-end figure
+    equal to the line's own (no host<->device copies)."""
+    lines = _run_bench(["--impl", "reference", "--steps", "2", "--warmup", "1"])
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "Mrays/s"
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["higher_is_better"] is True and d["vs_baseline"] is None and d["scaling"] == "weak"
+    assert d["config"]["workload"] == bench.WORKLOAD
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    assert _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"],
+                      {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
