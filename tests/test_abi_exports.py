@@ -122,3 +122,27 @@ def test_binding_argument_types_match_the_header():
             if not is_ptr:
                 assert t in (ctypes.c_uint32, ctypes.c_int32), (name, decl, t)
                 assert ("uint32_t" in decl) == (t is ctypes.c_uint32), (name, decl, t)
+
+
+def test_product_path_has_no_cpu_fallback():
+    """The package never imports the oracle, and without a usable GPU the
+    library's own calls fail with a CUDA status instead of computing on the
+    host."""
+    import subprocess
+    import sys
+    code = ("import sys, paper_2001_09792_gb300 as rg\n"
+            "assert not [m for m in sys.modules if m == 'oracle' or m.startswith('oracle.')]\n")
+    subprocess.run([sys.executable, "-c", code], check=True, cwd=ROOT)
+    pkg = os.path.join(ROOT, "paper_2001_09792_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", txt, flags=re.M), f
+                assert "oracle.cpp" not in txt and "liboracle" not in txt, f
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the failure path is not reachable")
+    with pytest.raises(rg.RgError) as e:
+        rg.rg_scene_create()
+    assert e.value.status == rg.RG_ERR_CUDA
