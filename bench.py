@@ -188,6 +188,26 @@ def traffic_record():
     return None
 
 
+def l2_record(compressed):
+    """L2 figures of one traversal launch of the medium frame, read from the
+    committed ncu summary (a capture, not measured by this run): L2 and L1
+    sector hit rates and, for the binary BVH, L2 throughput in % of peak."""
+    name = "trace8_medium.md" if compressed else "trace_pair_medium.md"
+    try:
+        txt = open(os.path.join(ROOT, "profiles", name)).read()
+    except OSError:
+        return None
+    m = re.search(r"^\| L2 / L1 sector hit rate \| ([0-9.]+) % / ([0-9.]+) %", txt, flags=re.M)
+    if not m:
+        return None
+    out = {"l2_sector_hit_pct": float(m.group(1)), "l1_sector_hit_pct": float(m.group(2))}
+    t = re.search(r"^\| L2 \(lts\) throughput, % of peak \| ([0-9.]+) %", txt, flags=re.M)
+    if t:
+        out["l2_throughput_pct_of_peak"] = float(t.group(1))
+    out["source"] = f"ncu capture of one traversal launch (profiles/{name}), not this run"
+    return out
+
+
 def path_flag(args):
     import paper_2001_09792_gb300 as rg
     return ((rg.RG_SCENE_COMPRESSED if args.compressed else 0)
@@ -425,7 +445,8 @@ def run_native(args, world, rank, local):
                                "shadow_alone": round(st["any_ms"] / sum(ms), 3)},
                     "shadow_nodes_per_ray": round(cst["any_node_visits"] / sr, 2),
                     "shadow_inst_per_ray": round(cst["any_inst_entries"] / sr, 3),
-                    "shadow_tris_per_ray": round(cst["any_tri_tests"] / sr, 2)}
+                    "shadow_tris_per_ray": round(cst["any_tri_tests"] / sr, 2),
+                    "l2": l2_record(args.compressed)}
         def pcts(x):
             xs = sorted(x)
             return round(xs[len(xs) // 2], 3), round(xs[min(len(xs) - 1, math.ceil(0.99 * len(xs)) - 1)], 3)

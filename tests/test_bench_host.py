@@ -127,3 +127,11 @@ def test_reference_arm_prints_one_contract_line():
 def test_reference_arm_runs_on_rank_zero_only():
     assert _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"],
                       {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_l2_figures_come_from_the_committed_captures():
+    b = bench.l2_record(False)
+    assert 0 < b["l2_sector_hit_pct"] <= 100 and 0 < b["l1_sector_hit_pct"] <= 100
+    assert 0 < b["l2_throughput_pct_of_peak"] <= 100 and "trace_pair_medium.md" in b["source"]
+    w = bench.l2_record(True)
+    assert 0 < w["l2_sector_hit_pct"] <= 100 and "trace8_medium.md" in w["source"]
