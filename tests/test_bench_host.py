@@ -135,3 +135,26 @@ def test_l2_figures_come_from_the_committed_captures():
     assert 0 < b["l2_throughput_pct_of_peak"] <= 100 and "trace_pair_medium.md" in b["source"]
     w = bench.l2_record(True)
     assert 0 < w["l2_sector_hit_pct"] <= 100 and "trace8_medium.md" in w["source"]
+
+
+def test_profile_summaries_name_committed_commands():
+    """Every ncu summary gives the command that made it: ncu with the clocks
+    left alone, run on committed files only."""
+    import glob
+    import re
+    files = sorted(glob.glob(os.path.join(bench.ROOT, "profiles", "*.md")))
+    assert len(files) >= 3
+    for path in files:
+        lines = open(path).read().splitlines()
+        cmds = []
+        for k, line in enumerate(lines):
+            if re.match(r"\s+ncu ", line):
+                c = line
+                while c.endswith("\\") and k + 1 < len(lines):
+                    k += 1
+                    c = c[:-1] + lines[k]
+                cmds.append(c)
+        assert cmds, path
+        for c in cmds:
+            assert "--clock-control none" in c, (path, c[:80])
+            assert "python bench.py" in c and "_work" not in c, (path, c[:80])
