@@ -211,6 +211,15 @@ rg_status rg_render(rg_scene* scene, const rg_camera* h_cam, uint32_t w, uint32_
  * temporary device memory (the luma image) for the duration of the call. */
 rg_status rg_fxaa(const float* d_in, uint32_t w, uint32_t h, float* d_out, void* stream);
 
+/* rg_sync waits for all of the device's work and returns the first error a
+ * kernel of this scene recorded since the last rg_sync (RG_ERR_STACK,
+ * RG_ERR_TIMEOUT, RG_ERR_SINGULAR, RG_ERR_INVALID_ARG for a bad index found on
+ * the device), clearing it; the rays concerned came back as misses and the
+ * scene stays usable.  rg_get_stats waits for the device and fills *out with
+ * the counters since the last rg_reset_stats (rays traced, timed launches and
+ * their device time with RG_SCENE_TIMING, node / triangle / instance counts of
+ * counting traversals); rg_reset_stats waits and zeroes them.  RG_ERR_INVALID_ARG
+ * for a NULL scene or output. */
 rg_status rg_sync(rg_scene* scene);
 rg_status rg_get_stats(rg_scene* scene, rg_stats* out);
 rg_status rg_reset_stats(rg_scene* scene);
