@@ -161,8 +161,11 @@ rg_status rg_tlas_build(rg_scene* scene, const rg_instance* d_inst, uint32_t n, 
  * and boxes and the node boxes; the topology is unchanged. */
 rg_status rg_tlas_refit(rg_scene* scene, const rg_instance* d_inst, uint32_t n, void* stream);
 
-/* Materials (host array, copied) and point lights (host array, copied; at
- * most 64, else RG_ERR_INVALID_ARG). */
+/* Shading tables of the renderer (Sec. 2.1: the render system shows multiple
+ * objects with shadow casting, reflection and refraction; the materials say
+ * which surface reflects or refracts, the lights which shadows are cast).
+ * Materials: host array, copied.  Point lights: host array, copied; at most
+ * 64, else RG_ERR_INVALID_ARG. */
 rg_status rg_scene_set_materials(rg_scene* scene, const rg_material* h_mat, uint32_t n);
 rg_status rg_scene_set_lights(rg_scene* scene, const rg_light* h_lights, uint32_t n);
 
@@ -196,8 +199,6 @@ rg_status rg_trace_rays(rg_scene* scene, const rg_ray* d_rays, uint32_t n, uint3
 rg_status rg_render(rg_scene* scene, const rg_camera* h_cam, uint32_t w, uint32_t h, uint32_t max_depth,
                     float* d_rgba, void* stream);
 
-/* Wait for the scene's stream work and return the first device-side error
- * recorded since the last rg_sync (then clear it). */
 /* FXAA (Sec. 2.1: the engine's compute passes include fast approximate
  * anti-aliasing; the method is Lottes' FXAA, 2009) of a w x h RGBA32F image,
  * row 0 at the top, into d_out (same layout, must not alias d_in; both
@@ -284,14 +285,16 @@ rg_status rg_wide_export(rg_scene* scene, uint32_t blas_id, void* h_nodes, uint3
  * makes no device allocation: its temporaries live in one fixed array inside
  * librg.so, sized for RG_NOALLOC_SORT_MAX_PAIRS pairs of 64-bit keys (about
  * 3.2 MB, held on every GPU that loads the library until the process exits).
- * It is meant for callers that cannot allocate device memory: code that runs
- * while a stream is captured into a CUDA graph (cudaMalloc is refused during
- * capture), code whose device memory is owned by a caching allocator that
- * holds what the GPU has free, and frame loops that must not stall on an
- * allocation.  The caller still provides inputs and outputs.
+ * It is meant for callers that cannot allocate device memory: code whose
+ * device memory is owned by a caching allocator that has already reserved
+ * what the GPU has free, and frame loops that must not stall on an
+ * allocation.  The caller still provides inputs and outputs (d_keys_out and
+ * d_vals_out hold n elements each, on the current device).
  *  - n > RG_NOALLOC_SORT_MAX_PAIRS returns RG_ERR_INVALID_ARG.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    (cudaGetSymbolAddress) and keeps it for the process; make that first
+ *    call before any stream capture.  The address is not looked up again
+ *    after cudaDeviceReset.
  *  - All calls share the array and it keeps the last call's contents (every
  *    byte a call reads there it wrote first): calls whose GPU work overlaps
  *    (other streams, other host threads) race and must be serialised. */

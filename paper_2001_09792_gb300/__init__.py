@@ -369,15 +369,35 @@ def rg_morton_codes(lohi, bits, stream=None):
     return codes, cb
 
 
+def _sort_args(keys, vals, keys_out=None, vals_out=None):
+    """Checks shared by the two sorts: n = len(keys) pairs; vals holds n
+    values; outputs (when given) hold at least n elements of the right type;
+    every tensor is on keys' device.  Returns (n, key_bits)."""
+    torch = _torch()
+    if keys.dim() != 1 or vals.dim() != 1:
+        raise ValueError("keys and vals must be 1-D")
+    n = keys.shape[0]
+    if vals.numel() != n:
+        raise ValueError(f"vals holds {vals.numel()} values for {n} keys")
+    for name, t in (("vals", vals), ("keys_out", keys_out), ("vals_out", vals_out)):
+        if t is not None and t.device != keys.device:
+            raise ValueError(f"{name} is on {t.device}, keys on {keys.device}")
+    for name, t in (("keys_out", keys_out), ("vals_out", vals_out)):
+        if t is not None and t.numel() < n:
+            raise ValueError(f"{name} holds {t.numel()} elements, fewer than n = {n}")
+    return n, (64 if keys.dtype == torch.int64 else 32)
+
+
 def rg_radix_sort_pairs(keys, vals, stream=None):
     """Stable sort of (keys int32/int64 as unsigned, vals int32); returns (keys, vals)."""
     torch = _torch()
-    key_bits = 64 if keys.dtype == torch.int64 else 32
-    ko = torch.empty_like(keys)
-    vo = torch.empty_like(vals)
-    _check(lib().rg_radix_sort_pairs(_dev(keys, keys.dtype, None, "keys"), _dev(vals, torch.int32, None, "vals"),
-                                     keys.shape[0], key_bits, ctypes.c_void_p(ko.data_ptr()),
-                                     ctypes.c_void_p(vo.data_ptr()), _stream(stream)))
+    n, key_bits = _sort_args(keys, vals)
+    with torch.cuda.device(keys.device):
+        ko = torch.empty_like(keys)
+        vo = torch.empty_like(vals)
+        _check(lib().rg_radix_sort_pairs(_dev(keys, keys.dtype, None, "keys"), _dev(vals, torch.int32, None, "vals"),
+                                         n, key_bits, ctypes.c_void_p(ko.data_ptr()),
+                                         ctypes.c_void_p(vo.data_ptr()), _stream(stream)))
     return ko, vo
 
 
@@ -387,12 +407,14 @@ def rg_radix_sort_pairs_noalloc(keys, vals, keys_out=None, vals_out=None, stream
     most RG_NOALLOC_SORT_MAX_PAIRS pairs).  Outputs are caller buffers; they
     are allocated here only when not given."""
     torch = _torch()
-    key_bits = 64 if keys.dtype == torch.int64 else 32
-    ko = torch.empty_like(keys) if keys_out is None else keys_out
-    vo = torch.empty_like(vals) if vals_out is None else vals_out
-    _check(lib().rg_radix_sort_pairs_noalloc(_dev(keys, keys.dtype, None, "keys"), _dev(vals, torch.int32, None, "vals"),
-                                             keys.shape[0], key_bits, _dev(ko, keys.dtype, None, "keys_out"),
-                                             _dev(vo, torch.int32, None, "vals_out"), _stream(stream)))
+    n, key_bits = _sort_args(keys, vals, keys_out, vals_out)
+    with torch.cuda.device(keys.device):
+        ko = torch.empty_like(keys) if keys_out is None else keys_out
+        vo = torch.empty_like(vals) if vals_out is None else vals_out
+        _check(lib().rg_radix_sort_pairs_noalloc(_dev(keys, keys.dtype, None, "keys"),
+                                                 _dev(vals, torch.int32, None, "vals"), n, key_bits,
+                                                 _dev(ko, keys.dtype, None, "keys_out"),
+                                                 _dev(vo, torch.int32, None, "vals_out"), _stream(stream)))
     return ko, vo
 
 

@@ -1126,12 +1126,15 @@ void set_capturing(bool on) { g_capturing = on; }
 unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 int device_sm_count() {
-    static int sms = 0;
+    // looked up once per process; concurrent first callers store the same value
+    static std::atomic<int> cached{0};
+    int sms = cached.load(std::memory_order_relaxed);
     if (sms == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 1;
+        cached.store(sms, std::memory_order_relaxed);
     }
     return sms;
 }

@@ -706,12 +706,7 @@ cudaError_t launch_morton(const float* lohi, uint32_t n, const int* cb_ord, int 
     return cudaGetLastError();
 }
 
-size_t radix_sort_scratch_bytes(uint32_t n, int key_bits) {
-    size_t nb = (n + kSortTile - 1) / kSortTile;
-    size_t kb = key_bits == 64 ? 8 : 4;
-    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    return al(n * kb) + al(n * 4) + al(256 * nb * 4);
-}
+static_assert(kSortTile == (int)kSortTilePairs, "sort tile size and scratch layout disagree");
 
 template <class K>
 static cudaError_t radix_sort_impl(const K* keys_in, const uint32_t* vals_in, uint32_t n, K* keys_out,

@@ -169,8 +169,14 @@ cudaError_t launch_init_bounds(int* cb_ord, cudaStream_t s);
 cudaError_t launch_centroid_bounds(const float* lohi, uint32_t n, int* cb_ord, cudaStream_t s);
 cudaError_t launch_morton(const float* lohi, uint32_t n, const int* cb_ord, int bits, void* codes, uint32_t* vals,
                           float* cb_out, cudaStream_t s);
-// Radix sort; scratch must hold radix_sort_scratch_bytes(n, key_bits) bytes.
-size_t radix_sort_scratch_bytes(uint32_t n, int key_bits);
+// Radix sort; scratch must hold radix_sort_scratch_bytes(n, key_bits) bytes:
+// ping-pong keys and values, and 256 digit counts per tile of kSortTilePairs
+// pairs, each part 256-byte aligned.
+constexpr uint32_t kSortTilePairs = 2048;
+constexpr size_t radix_sort_scratch_bytes(uint32_t n, int key_bits) {
+    return ((((size_t)n * (key_bits == 64 ? 8 : 4)) + 255) & ~(size_t)255) + ((((size_t)n * 4) + 255) & ~(size_t)255) +
+           ((((size_t)256 * ((n + kSortTilePairs - 1) / kSortTilePairs) * 4) + 255) & ~(size_t)255);
+}
 cudaError_t radix_sort_pairs(const void* keys_in, const uint32_t* vals_in, uint32_t n, int key_bits, void* keys_out,
                              uint32_t* vals_out, void* scratch, cudaStream_t s);
 // ranges (optional, 2 per internal node): first and last leaf of node i.

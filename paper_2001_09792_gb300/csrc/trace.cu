@@ -2,6 +2,8 @@
 // traverse.cuh): persistent warps pull rays from a global counter, 32 at a
 // time (k_trace_warp), as lanes fall idle (k_trace_lane), or from two queues
 // in one launch (k_trace_pair); k_trace8 walks the compressed 8-wide BVH.
+#include <atomic>
+
 #include "traverse.cuh"
 
 namespace rg {
@@ -555,12 +557,14 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace8(TraceArgs a) {
 
 template <int MODE, bool STATS>
 cudaError_t launch_mode8(const TraceArgs& a, cudaStream_t s) {
-    static int blocks = 0;
+    static std::atomic<int> cached{0};  // per process; concurrent first callers store the same value
+    int blocks = cached.load(std::memory_order_relaxed);
     if (blocks == 0) {
         int per_sm = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace8<MODE, STATS>, kTraceBlock, 0);
         if (e != cudaSuccess) return e;
         blocks = device_sm_count() * (per_sm > 0 ? per_sm : 1);
+        cached.store(blocks, std::memory_order_relaxed);
     }
     k_trace8<MODE, STATS><<<blocks, kTraceBlock, 0, s>>>(a);
     count_launches(1);
@@ -569,7 +573,8 @@ cudaError_t launch_mode8(const TraceArgs& a, cudaStream_t s) {
 
 template <int MODE, bool BRUTE, bool STATS, int BLOCK, bool LANE>
 cudaError_t launch_block(const TraceArgs& a, int blocks_per_sm, cudaStream_t s) {
-    static int per_sm = 0;
+    static std::atomic<int> cached{0};  // per process; concurrent first callers store the same value
+    int per_sm = cached.load(std::memory_order_relaxed);
     if (per_sm == 0) {
         cudaError_t e = LANE ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_lane<MODE, BRUTE, STATS, BLOCK>,
                                                                              BLOCK, 0)
@@ -577,6 +582,7 @@ cudaError_t launch_block(const TraceArgs& a, int blocks_per_sm, cudaStream_t s) 
                                                                              BLOCK, 0);
         if (e != cudaSuccess) return e;
         if (per_sm <= 0) per_sm = 1;
+        cached.store(per_sm, std::memory_order_relaxed);
     }
     const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
     if (LANE)
@@ -589,12 +595,14 @@ cudaError_t launch_block(const TraceArgs& a, int blocks_per_sm, cudaStream_t s) 
 
 template <int SMODE, int CMODE, bool STATS, int BLOCK>
 cudaError_t launch_pair_t(const TraceArgs& sa, const TraceArgs& ca, int blocks_per_sm, cudaStream_t s) {
-    static int per_sm = 0;
+    static std::atomic<int> cached{0};  // per process; concurrent first callers store the same value
+    int per_sm = cached.load(std::memory_order_relaxed);
     if (per_sm == 0) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_pair<SMODE, CMODE, STATS, BLOCK>,
                                                                       BLOCK, 0);
         if (e != cudaSuccess) return e;
         if (per_sm <= 0) per_sm = 1;
+        cached.store(per_sm, std::memory_order_relaxed);
     }
     const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
     k_trace_pair<SMODE, CMODE, STATS, BLOCK><<<device_sm_count() * b, BLOCK, 0, s>>>(sa, ca);
