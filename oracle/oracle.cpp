@@ -25,7 +25,11 @@
 //        box with directed rounding, emulated with fesetround.
 //  * Ray queries (paper Sec. 1: closest-hit, any-hit and miss per ray), in
 //    float64 on an independent object-median BVH (or brute force), using the
-//    watertight ray/triangle test of Woop, Benthin & Wald (JCGT 2013).  Each
+//    watertight ray/triangle test of Woop, Benthin & Wald (JCGT 2013).  The
+//    nearest hit is chosen on the exact distances rounded to float32, the
+//    precision of the hit records (equal float32 t: smaller instance, then
+//    smaller primitive), so exact ties such as coplanar surfaces have one
+//    answer that does not depend on how float64 rounds them.  Each
 //    ray also gets an "ambiguous" flag: the float32 path may legitimately
 //    differ from the exact answer when another triangle lies within the
 //    float32 error bound (see orc_trace).
@@ -428,8 +432,12 @@ struct Query {
             if (c.t < tmin - c.tau || c.t > tmax + c.tau || c.t < t_lo || c.t > cull) return;
             cands.push_back(c);
             if (c.strict && c.t <= tmax) {
-                bool better = !have || c.t < best.t ||
-                              (c.t == best.t && (c.inst < best.inst || (c.inst == best.inst && c.prim < best.prim)));
+                // the nearest hit, with distances compared as float32 values
+                // (the precision the hit records carry): equal float32 t is a
+                // tie, decided by the smaller instance, then the smaller prim
+                const float ct = (float)c.t, bt = (float)best.t;
+                bool better = !have || ct < bt ||
+                              (ct == bt && (c.inst < best.inst || (c.inst == best.inst && c.prim < best.prim)));
                 if (better) {
                     best = c;
                     have = true;

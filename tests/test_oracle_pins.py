@@ -127,6 +127,29 @@ def test_tie_break_smaller_instance_then_prim():
     assert h["ambiguous"][0]  # coincident candidates are a near tie
 
 
+def test_tie_between_coplanar_triangles_is_decided_in_float32():
+    """Two different triangles in one tilted plane (x + 2y + 4z = 2, every
+    vertex exactly on it), the small one inside the large one: their exact
+    distances are equal on every ray through the small one.  The nearest hit
+    is decided on distances rounded to float32, so the tie rule (smaller
+    prim) picks prim 0 on every ray; comparing the float64 distances, which
+    round differently for the two vertex sets, picks prim 1 on about a
+    quarter of them."""
+    v = np.array([[1.0, 0.25, 0.125], [0.5, 0.5, 0.125], [0.75, 0.125, 0.25], [2, 0, 0], [0, 1, 0], [0, 0, 0.5]],
+                 np.float32)
+    assert np.all(v[:, 0] + 2 * v[:, 1] + 4 * v[:, 2] == 2)
+    i = np.array([[0, 1, 2], [3, 4, 5]], np.uint32)
+    O = one_mesh_scene(v, i)
+    rng = np.random.default_rng(5)
+    n = 4000
+    p = rng.dirichlet([4, 4, 4], n) @ v[0:3].astype(np.float64)
+    o = rng.uniform(1.5, 4.0, (n, 3))
+    rays = np.c_[o, np.zeros(n), p - o, np.full(n, np.inf)].astype(np.float32)
+    h = O.trace(rays)
+    assert np.all(h["inst"] == 0) and np.all(h["prim"] == 0)
+    assert np.all(h["ambiguous"])  # an exact tie is always flagged as one
+
+
 # ----------------------------------------------------------- transforms
 
 def test_instance_transform_matches_pretransformed_mesh():
