@@ -827,6 +827,7 @@ def run_native_large(args, world, rank, local):
                "config": {"workload": LARGE_WORKLOAD, "rays_per_step": 2 * n, "instances": s.n_instances,
                           "closest_mrays_s": round(st["closest_rays"] / (sum(ms) / 1e3) / 1e6, 2),
                           "closest_ms": round(launch_ms, 3), "any_ms": round(st["any_ms"] / max(st["any_launches"], 1), 3),
+                          "refine_ms": round(st["refine_ms"] / max(st["refine_launches"], 1), 3),
                           "p50_ms": round(ms_sorted[len(ms) // 2], 3), "p99_ms": round(ms_sorted[-1], 3),
                           "l2": "inputs larger than L2 (2 x 512 MiB of rays, ~220 MB of BVH)",
                           "parallelism": f"replicas x{world}", "bvh": "compressed 8-wide" if args.compressed else "binary float32"},

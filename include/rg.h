@@ -109,6 +109,8 @@ typedef struct {
     uint64_t kernel_launches; /* kernels launched by the library (all scenes of the process) */
     uint64_t pair_launches;   /* timed launches that trace one level's shadow rays together with */
     double pair_ms;           /*   the next level's closest-hit rays, and their summed device time */
+    uint64_t refine_launches; /* timed launches that complete rg_trace_rays' hit records (exact t, u, v */
+    double refine_ms;         /*   and tie decisions), and their summed device time */
 } rg_stats;
 
 /* ---- scene lifetime ---------------------------------------------------- */

@@ -76,7 +76,8 @@ class rg_stats(ctypes.Structure):
                 ("node_visits", ctypes.c_uint64), ("tri_tests", ctypes.c_uint64), ("inst_entries", ctypes.c_uint64),
                 ("any_node_visits", ctypes.c_uint64), ("any_tri_tests", ctypes.c_uint64),
                 ("any_inst_entries", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
-                ("pair_launches", ctypes.c_uint64), ("pair_ms", ctypes.c_double)]
+                ("pair_launches", ctypes.c_uint64), ("pair_ms", ctypes.c_double),
+                ("refine_launches", ctypes.c_uint64), ("refine_ms", ctypes.c_double)]
 
 
 class rg_server_desc(ctypes.Structure):

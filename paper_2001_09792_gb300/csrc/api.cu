@@ -121,6 +121,7 @@ struct BlasHost {
     float4* tris = nullptr;
     uint32_t nt = 0;
     uint32_t root = 0;
+    uint32_t* leaf_of_prim = nullptr;  // BLAS leaf of each triangle index
     // compressed 8-wide form (null if not built)
     float4* nodes8 = nullptr;
     float4* tris8 = nullptr;
@@ -132,6 +133,7 @@ struct BlasHost {
 void free_blas(BlasHost& b) {
     cudaFree(b.nodes);
     cudaFree(b.tris);
+    if (b.leaf_of_prim) cudaFree(b.leaf_of_prim);
     if (b.nodes8) cudaFree(b.nodes8);
     if (b.tris8) cudaFree(b.tris8);
     if (b.src8) cudaFree(b.src8);
@@ -181,6 +183,8 @@ struct rg_scene {
     DevBuf<InstDev> inst, inst_tmp;
     DevBuf<float> wbox;
     DevBuf<uint32_t> perm, parents, flags;
+    DevBuf<uint32_t> leaf_of_inst;  // TLAS leaf of each instance index (made on first need after a build)
+    bool leaf_of_inst_valid = false;
     // compressed 8-wide TLAS
     bool wide = false;
     DevBuf<float4> tlas8;
@@ -204,8 +208,8 @@ struct rg_scene {
     // statistics and timing
     uint64_t closest_rays = 0, shadow_rays_host = 0;
     std::vector<EventPair> events, free_events;
-    double trace_ms = 0, any_ms = 0, pair_ms = 0;
-    uint64_t trace_launches = 0, any_launches = 0, pair_launches = 0;
+    double trace_ms = 0, any_ms = 0, pair_ms = 0, refine_ms = 0;
+    uint64_t trace_launches = 0, any_launches = 0, pair_launches = 0, refine_launches = 0;
     unsigned long long launch_base = 0;
 };
 
@@ -258,6 +262,9 @@ rg_status collect_events(rg_scene* s) {
         } else if (ep.kind == 1) {
             s->any_ms += ms;
             s->any_launches++;
+        } else if (ep.kind == 3) {
+            s->refine_ms += ms;
+            s->refine_launches++;
         } else {
             s->pair_ms += ms;
             s->pair_launches++;
@@ -459,7 +466,8 @@ rg_status rg_blas_build(rg_scene* s, const float* d_vtx, uint32_t nv, const uint
     b.nt = nt;
     b.root = nt == 1 ? kLeaf : 0u;
     if ((r = dev_alloc(reinterpret_cast<void**>(&b.nodes), n_int * 64, "BLAS nodes"))) return r;
-    if ((r = dev_alloc(reinterpret_cast<void**>(&b.tris), (size_t)nt * kTriRecord, "BLAS triangles"))) {
+    if ((r = dev_alloc(reinterpret_cast<void**>(&b.tris), (size_t)nt * kTriRecord, "BLAS triangles")) ||
+        (r = dev_alloc(reinterpret_cast<void**>(&b.leaf_of_prim), (size_t)nt * 4, "BLAS leaf map"))) {
         free_blas(b);
         return r;
     }
@@ -496,6 +504,7 @@ rg_status rg_blas_build(rg_scene* s, const float* d_vtx, uint32_t nv, const uint
              hd.nt = nt;
              hd.nodes8 = b.nodes8;
              hd.tris8 = b.tris8;
+             hd.leaf_of_prim = b.leaf_of_prim;
              RG_CK(cudaMemcpyAsync(s->B->d_blas.p + id, &hd, sizeof hd, cudaMemcpyHostToDevice, st));
              RG_CK(cudaStreamSynchronize(st));  // hd lives on this stack frame
 
@@ -526,6 +535,7 @@ rg_status rg_blas_build(rg_scene* s, const float* d_vtx, uint32_t nv, const uint
                                             static_cast<uint32_t*>(parents), b.nodes, static_cast<uint32_t*>(fl), b.tris,
                                             s->B->d_blas.p + id, s->st, st));
              RG_CK(launch_bound_sphere(d_vtx, nv, s->B->d_blas.p + id, st));
+             RG_CK(launch_invert_perm(static_cast<uint32_t*>(perm), nt, b.leaf_of_prim, st));
              if (wide) {
                  WideOut out{b.nodes8, b.src8, b.item_src8, b.counts8, static_cast<uint2*>(tasks)};
                  const float* leaf_box = reinterpret_cast<const float*>(reinterpret_cast<const char*>(s->B->d_blas.p + id) +
@@ -606,6 +616,7 @@ rg_status rg_tlas_build(rg_scene* s, const rg_instance* d_inst, uint32_t n, void
     if ((r = set_device(s))) return r;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     s->tlas_built = false;
+    s->leaf_of_inst_valid = false;
     if ((r = s->tlas_nodes.ensure((size_t)(n > 1 ? n - 1 : 1) * 4, "TLAS nodes"))) return r;
     if ((r = s->inst.ensure(n, "instances"))) return r;
     if ((r = s->inst_tmp.ensure(n, "instance staging"))) return r;
@@ -692,6 +703,19 @@ rg_status rg_trace_rays(rg_scene* s, const rg_ray* d_rays, uint32_t n, uint32_t 
     if ((r = event_begin(s, any ? 1 : 0, st, &ev))) return r;
     RG_CK(launch_trace(any ? kModeAnyAbi : kModeClosestAbi, flags & RG_TRACE_BRUTE, flags & RG_TRACE_STATS, a, st));
     if ((r = event_end(s, st))) return r;
+    // closest hit: exact t, u, v of the hits and the tie decisions (the
+    // traversal wrote provisional records that refer to the instance array it
+    // walked)
+    if (!any) {
+        if (!s->leaf_of_inst_valid) {
+            if ((r = s->leaf_of_inst.ensure(s->n_inst, "instance leaf map"))) return r;
+            RG_CK(launch_invert_perm(s->perm.p, s->n_inst, s->leaf_of_inst.p, st));
+            s->leaf_of_inst_valid = true;
+        }
+        if ((r = event_begin(s, 3, st, &ev))) return r;
+        RG_CK(launch_refine_hits(a.rays, d_hits, n, s->inst.p, s->leaf_of_inst.p, s->B->d_blas.p, st));
+        if ((r = event_end(s, st))) return r;
+    }
     if (any)
         s->shadow_rays_host += n;
     else
@@ -944,6 +968,8 @@ rg_status rg_get_stats(rg_scene* s, rg_stats* out) {
     out->kernel_launches = launches_so_far() - s->launch_base;
     out->pair_launches = s->pair_launches;
     out->pair_ms = s->pair_ms;
+    out->refine_launches = s->refine_launches;
+    out->refine_ms = s->refine_ms;
     return RG_OK;
 }
 
@@ -954,8 +980,8 @@ rg_status rg_reset_stats(rg_scene* s) {
     RG_CK(cudaDeviceSynchronize());
     if ((r = collect_events(s))) return r;
     s->closest_rays = s->shadow_rays_host = 0;
-    s->trace_ms = s->any_ms = s->pair_ms = 0;
-    s->trace_launches = s->any_launches = s->pair_launches = 0;
+    s->trace_ms = s->any_ms = s->pair_ms = s->refine_ms = 0;
+    s->trace_launches = s->any_launches = s->pair_launches = s->refine_launches = 0;
     s->launch_base = launches_so_far();
     RG_CK(cudaMemset(reinterpret_cast<char*>(s->st) + offsetof(DevStatus, closest_rays), 0,
                      sizeof(DevStatus) - offsetof(DevStatus, closest_rays)));

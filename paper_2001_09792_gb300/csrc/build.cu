@@ -763,6 +763,19 @@ cudaError_t launch_karras(const void* keys, uint32_t n, int key_bits, uint32_t* 
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void k_invert_perm(const uint32_t* __restrict__ perm, uint32_t n, uint32_t* __restrict__ inv) {
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) inv[perm[j]] = j;
+}
+}  // namespace
+
+cudaError_t launch_invert_perm(const uint32_t* perm, uint32_t n, uint32_t* inv, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_invert_perm<<<min(grid_for(n), 4096u), kBlock, 0, s>>>(perm, n, inv);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_blas_leaves_refit(const float* vtx, const uint32_t* idx, const uint32_t* perm, const float* lohi,
                                      uint32_t n, const uint32_t* parents, float4* nodes, uint32_t* flags,
                                      float4* tris, BlasDev* blas_out, DevStatus* st, cudaStream_t s) {

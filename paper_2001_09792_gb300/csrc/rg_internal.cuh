@@ -60,7 +60,8 @@ struct __align__(16) BlasDev {
     // bound on |v - c|^2 over the vertices, c = (lo + hi) * 0.5, every
     // operation rounded upward (bits of a non-negative float, atomicMax-able)
     uint32_t r2_bits;
-    uint32_t pad[3];
+    uint32_t pad;
+    const uint32_t* leaf_of_prim;  // BLAS leaf (triangle record) of each triangle index
 };
 static_assert(sizeof(BlasDev) == 80, "BLAS descriptor is 80 B");
 
@@ -188,6 +189,8 @@ cudaError_t launch_blas_leaves_refit(const float* vtx, const uint32_t* idx, cons
 // Bounding sphere of a mesh about its root box centre (after the BLAS refit
 // wrote the root box): blas->r2_bits = max over the vertices.
 cudaError_t launch_bound_sphere(const float* vtx, uint32_t nv, BlasDev* blas, cudaStream_t s);
+// inv[perm[j]] = j for j < n (perm a permutation of 0..n-1).
+cudaError_t launch_invert_perm(const uint32_t* perm, uint32_t n, uint32_t* inv, cudaStream_t s);
 cudaError_t launch_instance_prep(const rg_instance* in, uint32_t n, const BlasDev* blas, uint32_t nblas,
                                  InstDev* tmp, float* wbox, int* cb_ord, bool check_blas, DevStatus* st,
                                  cudaStream_t s);
@@ -274,6 +277,14 @@ constexpr uint32_t kTraceStack = 64;  // binary traversal stack entries per thre
 constexpr uint32_t kMaxLights = 64;  // lights per scene (one shadow sub-queue each)
 cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a, cudaStream_t s,
                          const TraceShape& shape = TraceShape());
+// Completes the provisional hit records that a closest-hit ABI traversal
+// (kModeClosestAbi) wrote: exact t, u, v of the chosen triangle and the tie
+// decision.
+// Records carry (instance index, prim) of the best and the runner-up; the
+// binary TLAS's instances (inst, TLAS leaf order, with leaf_of_inst mapping an
+// instance index to its leaf) and the BLAS table locate them.
+cudaError_t launch_refine_hits(const float4* rays, rg_hit* hits, uint32_t n, const InstDev* inst,
+                               const uint32_t* leaf_of_inst, const BlasDev* blas, cudaStream_t s);
 // The shadow rays of sa and the closest-hit rays of ca in one launch
 // (kModeShadowRender + kModeClosestRender, or with batch the two batched
 // modes, whose launch takes shape.block and shape.blocks_per_sm);

@@ -117,8 +117,10 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
     float tmin = 0.f, tmax = 0.f, dx = 0.f, dy = 0.f, dz = 0.f;
     SpaceRay wr, cr;
     Shear sh;
-    float best_t = 0.f, best_V = 0.f, best_W = 0.f, best_det = 1.f;
-    uint32_t best_id = kMiss, best_prim = kMiss, best_il = kMiss, best_tl = kMiss;
+    constexpr bool kTies = MODE == kModeClosestAbi;
+    Best2 best;
+    best.reset(0.f);
+    float any_V = 0.f, any_W = 0.f, any_det = 1.f;
     bool found = false, ok = true, in_blas = false;
     uint32_t stack[kStack];
     int sp = 0;
@@ -159,10 +161,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
                     wr.ox = r0.x; wr.oy = r0.y; wr.oz = r0.z;
                     wr.ix = safe_rcp(dx); wr.iy = safe_rcp(dy); wr.iz = safe_rcp(dz);
                     cr = wr;
-                    best_t = tmax;
-                    best_id = best_prim = best_il = best_tl = kMiss;
-                    best_V = best_W = 0.f;
-                    best_det = 1.f;
+                    best.reset(tmax);
                     found = false;
                     ok = true;
                     in_blas = false;
@@ -188,7 +187,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
             const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2);
             const uint4 n3 = __ldg(reinterpret_cast<const uint4*>(nd + 3));
             if (STATS) ++c_nodes;
-            const float tlim = kAny ? __fmul_rn(tmax, kCullSlack) : __fmul_rn(best_t, kCullSlack);
+            const float tlim = kAny ? __fmul_rn(tmax, kCullSlack) : __fmul_rn(best.t, kCullSlack);
             float tn0, tn1, tf0, tf1;
             bool h0 = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, cr, tmin, tlim, tn0, tf0);
             bool h1 = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, cr, tmin, tlim, tn1, tf1);
@@ -245,14 +244,17 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
             const float4* tp = tri_rec(tris, leaf);
             const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
             if (STATS) ++c_tris;
-            const TriResult h = tri_test(sh, v0, v1, v2, tmin, kAny ? tmax : best_t);
+            const float tlo = kAny ? tmax : (kTies && found ? fminf(__fmul_rn(best.t, kTieBand), tmax) : best.t);
+            const TriResult h = tri_test(sh, v0, v1, v2, tmin, tlo);
             ref = kNone;
             if (h.hit) {
                 const uint32_t prim = __float_as_uint(v0.w);
-                if (kAny || h.t < best_t || cur_id < best_id || (cur_id == best_id && prim < best_prim)) {
-                    best_t = h.t; best_id = cur_id; best_prim = prim;
-                    best_il = cur_leaf; best_tl = leaf;
-                    best_V = h.V; best_W = h.W; best_det = h.det;
+                if (kTies) {
+                    if (best.offer(h.t, cur_id, prim)) found = true;
+                } else if (kAny || h.t < best.t || cur_id < best.id || (cur_id == best.id && prim < best.prim)) {
+                    best.t = h.t; best.id = cur_id; best.prim = prim;
+                    best.il = cur_leaf; best.tl = leaf;
+                    any_V = h.V; any_W = h.W; any_det = h.det;
                     found = true;
                 }
                 if (kAny) finished = true;
@@ -272,7 +274,8 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
             finished = ref == kNone;
         }
         if (finished) {
-            emit<MODE>(a, i, j, found && ok, ok, best_t, best_id, best_prim, best_il, best_tl, best_V, best_W, best_det);
+            emit<MODE>(a, i, j, found && ok, ok, best.t, best.id, best.prim, best.il, best.tl,
+                       kTies ? best.tie_id() : kMiss, best.prim2, any_V, any_W, any_det);
             active = false;
         }
     }
@@ -350,9 +353,10 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace8(TraceArgs a) {
         uint32_t oct = oct_w;
         Shear sh;
 
-        float best_t = tmax;
-        uint32_t best_id = kMiss, best_prim = kMiss, best_il = kMiss, best_tl = kMiss;
-        float best_V = 0.f, best_W = 0.f, best_det = 1.f;
+        constexpr bool kTies = MODE == kModeClosestAbi;
+        Best2 best;
+        best.reset(tmax);
+        float any_V = 0.f, any_W = 0.f, any_det = 1.f;
         bool found = false, ok = true, in_blas = false;
 
         uint2 stack[kStack8];
@@ -417,7 +421,7 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace8(TraceArgs a) {
                     const uint32_t nx0 = nx ? w3.z : w2.x, nx1 = nx ? w3.w : w2.y, fx0 = nx ? w2.x : w3.z, fx1 = nx ? w2.y : w3.w;
                     const uint32_t ny0 = ny ? w4.x : w2.z, ny1 = ny ? w4.y : w2.w, fy0 = ny ? w2.z : w4.x, fy1 = ny ? w2.w : w4.y;
                     const uint32_t nz0 = nz ? w4.z : w3.x, nz1 = nz ? w4.w : w3.y, fz0 = nz ? w3.x : w4.z, fz1 = nz ? w3.y : w4.w;
-                    const float tlim = kAny ? __fmul_rn(tmax, kCullSlack) : __fmul_rn(best_t, kCullSlack);
+                    const float tlim = kAny ? __fmul_rn(tmax, kCullSlack) : __fmul_rn(best.t, kCullSlack);
                     const uint32_t meta_lo = w1.z, meta_hi = w1.w;
                     uint32_t hitmask = 0;
     #pragma unroll
@@ -512,20 +516,24 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace8(TraceArgs a) {
                     const float4* tp = tri_rec(tris, item);
                     const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
                     if (STATS) ++c_tris;
-                    TriResult h = tri_test(sh, v0, v1, v2, tmin, kAny ? tmax : best_t);
+                    const float tlo =
+                        kAny ? tmax : (kTies && found ? fminf(__fmul_rn(best.t, kTieBand), tmax) : best.t);
+                    TriResult h = tri_test(sh, v0, v1, v2, tmin, tlo);
                     if (h.hit) {
                         const uint32_t prim = __float_as_uint(v0.w);
                         if (kAny) {
-                            best_t = h.t; best_id = cur_id; best_prim = prim;
-                            best_V = h.V; best_W = h.W; best_det = h.det;
+                            best.t = h.t; best.id = cur_id; best.prim = prim;
+                            best.il = cur_leaf; best.tl = item;
+                            any_V = h.V; any_W = h.W; any_det = h.det;
                             found = true;
                             done = true;
                             break;
                         }
-                        if (h.t < best_t || cur_id < best_id || (cur_id == best_id && prim < best_prim)) {
-                            best_t = h.t; best_id = cur_id; best_prim = prim;
-                            best_il = cur_leaf; best_tl = item;
-                            best_V = h.V; best_W = h.W; best_det = h.det;
+                        if (kTies) {
+                            if (best.offer(h.t, cur_id, prim)) found = true;
+                        } else if (h.t < best.t || cur_id < best.id || (cur_id == best.id && prim < best.prim)) {
+                            best.t = h.t; best.id = cur_id; best.prim = prim;
+                            best.il = cur_leaf; best.tl = item;
                             found = true;
                         }
                     }
@@ -550,7 +558,8 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace8(TraceArgs a) {
             }
         }
         if (!ok) found = false;
-        emit<MODE>(a, i, j, found, ok, best_t, best_id, best_prim, best_il, best_tl, best_V, best_W, best_det);
+        emit<MODE>(a, i, j, found, ok, best.t, best.id, best.prim, best.il, best.tl, kTies ? best.tie_id() : kMiss,
+                   best.prim2, any_V, any_W, any_det);
     }
     flush_counts<kAny, STATS>(a, c_nodes, c_tris, c_inst);
 }
@@ -642,7 +651,67 @@ cudaError_t launch_mode(const TraceArgs& a0, cudaStream_t s, const TraceShape& s
     return launch_block<MODE, BRUTE, STATS, 128, false>(a, shape.blocks_per_sm, s);
 }
 
+// Completes the provisional ABI hit records of a traversal launch (emit):
+// t, u, v of the chosen triangle recomputed exactly (refine_hit), and, when the
+// traversal found a runner-up within the tie band, the two candidates decided
+// again on their exact distances rounded to float32, then instance, then
+// primitive (the tie rule).  t is kept within the ray's [tmin, tmax], which the
+// float32 test enforced.  Both traversals (binary and wide) name candidates
+// by (instance, prim); the binary TLAS's instance records and the BLAS
+// triangle records locate them.
+__global__ void __launch_bounds__(256) k_refine_hits(const float4* __restrict__ rays, rg_hit* __restrict__ hits,
+                                                     uint32_t n, const InstDev* __restrict__ inst,
+                                                     const uint32_t* __restrict__ leaf_of_inst,
+                                                     const BlasDev* __restrict__ blas) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t* rec = reinterpret_cast<uint32_t*>(hits + i);
+        uint32_t id = rec[0], prim = rec[1];
+        if (id == kMiss) continue;
+        const uint32_t id2 = rec[3], prim2 = rec[4];
+        const float t0 = __uint_as_float(rec[2]);
+        const float4 r0 = __ldg(rays + 2 * (size_t)i), r1 = __ldg(rays + 2 * (size_t)i + 1);
+        auto candidate = [&](uint32_t cid, uint32_t cprim) {
+            const InstDev* I = inst + __ldg(leaf_of_inst + cid);
+            const float4 m0 = __ldg(&I->m[0]), m1 = __ldg(&I->m[1]), m2 = __ldg(&I->m[2]);
+            const float4 meta0 = __ldg(reinterpret_cast<const float4*>(&I->nodes));  // nodes, tris
+            const uint32_t b = __ldg(&I->blas);
+            const float4* tris = reinterpret_cast<const float4*>(
+                ((unsigned long long)__float_as_uint(meta0.w) << 32) | __float_as_uint(meta0.z));
+            const uint32_t* lp = reinterpret_cast<const uint32_t*>(__ldg(reinterpret_cast<const unsigned long long*>(
+                &blas[b].leaf_of_prim)));
+            const float4* tp = tris + kTriStride * (size_t)__ldg(lp + cprim);  // axis order (x, y, z)
+            const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+            Refined q = refine_hit(r0, r1, t0, m0, m1, m2, v0, v1, v2);
+            q.t = fminf(fmaxf(q.t, r0.w), r1.w);
+            return q;
+        };
+        Refined q = candidate(id, prim);
+        if (id2 != kMiss) {
+            const Refined q2 = candidate(id2, prim2);
+            if (hit_before(q2.t, id2, prim2, q.t, id, prim)) {
+                q = q2;
+                id = id2;
+                prim = prim2;
+            }
+        }
+        rec[0] = id;
+        rec[1] = prim;
+        rec[2] = __float_as_uint(q.t);
+        rec[3] = __float_as_uint(q.u);
+        rec[4] = __float_as_uint(q.v);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_refine_hits(const float4* rays, rg_hit* hits, uint32_t n, const InstDev* inst,
+                               const uint32_t* leaf_of_inst, const BlasDev* blas, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const uint32_t blocks = min((n + 255u) / 256u, (uint32_t)device_sm_count() * 8u);
+    k_refine_hits<<<blocks, 256, 0, s>>>(rays, hits, n, inst, leaf_of_inst, blas);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a0, cudaStream_t s,
                          const TraceShape& shape) {

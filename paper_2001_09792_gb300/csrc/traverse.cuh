@@ -39,6 +39,13 @@ constexpr int kTraceBlock = 128;
 // 1 + 2 * gamma_3, gamma_3 = 3u / (1 - 3u), u = 2^-24
 constexpr float kIze = 1.0f + 2.0f * (3.0f * 5.9604644775390625e-08f) / (1.0f - 3.0f * 5.9604644775390625e-08f);
 constexpr float kCullSlack = 1.0f + 1.0f / 4096.0f;
+// Closest-hit queries of the ABI keep, beside the best candidate, the next one
+// in the order (t, instance, prim); when its float32 distance lies within this
+// relative band of the best one, the two are decided again on their exact
+// distances (k_refine_hits).  The band is a quarter of the culling slack, so a
+// box holding such a candidate is never culled and every traversal (binary,
+// wide, brute force) sees the same pair.
+constexpr float kTieBand = 1.0f + 1.0f / 16384.0f;
 
 // 1/d correctly rounded (the same value as the IEEE division 1/d): a zero
 // component gives +-inf.
@@ -167,18 +174,29 @@ __device__ __forceinline__ TriResult tri_test(const Shear& s, float4 v0, float4 
 
 // Write one ray's result: an ABI hit record, a render hit, or (shadow rays)
 // the unshadowed contribution added to the image.
+// Closest-hit ABI queries write a provisional record that k_refine_hits
+// completes: for a hit {instance, prim, float32 t, runner-up instance or kMiss,
+// runner-up prim}; a miss is written in its final form.  Any-hit ABI queries (only occluded / not is defined) write
+// their final record: the hit's ids, float32 t and barycentrics V/det, W/det
+// of the watertight test.
 template <int MODE>
 __device__ __forceinline__ void emit(const TraceArgs& a, uint32_t i, uint32_t j, bool found, bool ok, float best_t, uint32_t best_id,
-                                     uint32_t best_prim, uint32_t best_il, uint32_t best_tl, float best_V,
-                                     float best_W, float best_det) {
+                                     uint32_t best_prim, uint32_t best_il, uint32_t best_tl, uint32_t run_il = kMiss,
+                                     uint32_t run_tl = kMiss, float any_V = 0.f, float any_W = 0.f, float any_det = 1.f) {
     if (MODE == kModeClosestAbi || MODE == kModeAnyAbi) {
         rg_hit out;
-        if (found) {
+        if (found && MODE == kModeAnyAbi) {
             out.instance = best_id;
             out.prim = best_prim;
             out.t = best_t;
-            out.u = __fdiv_rn(best_V, best_det);
-            out.v = __fdiv_rn(best_W, best_det);
+            out.u = __fdiv_rn(any_V, any_det);
+            out.v = __fdiv_rn(any_W, any_det);
+        } else if (found) {
+            out.instance = best_id;
+            out.prim = best_prim;
+            out.t = best_t;
+            out.u = __uint_as_float(run_il);
+            out.v = __uint_as_float(run_tl);
         } else {
             out.instance = kMiss;
             out.prim = kMiss;
@@ -274,15 +292,53 @@ struct TraceCounts {
 // triangle leaf, closest hit only).
 struct RayHit {
     bool found, ok;
-    float t, V, W, det;
+    float t;
     uint32_t id, prim, il, tl;
+    uint32_t id2, prim2;  // ABI closest hit: the runner-up within kTieBand of t (id2 = kMiss: none)
+    float V, W, det;    // any hit: the watertight test's V, W and det of the hit
+};
+
+// Order of closest-hit candidates: distance, then instance, then primitive.
+__device__ __forceinline__ bool hit_before(float t, uint32_t id, uint32_t prim, float t0, uint32_t id0, uint32_t prim0) {
+    return t < t0 || (t == t0 && (id < id0 || (id == id0 && prim < prim0)));
+}
+
+// The two first candidates of a closest-hit query in hit_before order.
+struct Best2 {
+    float t, t2;
+    uint32_t id, prim, il, tl;  // il, tl: TLAS leaf and BLAS leaf of the best (the renderer's hit record)
+    uint32_t id2, prim2;
+    __device__ __forceinline__ void reset(float tmax) {
+        t = tmax;
+        t2 = __int_as_float(0x7F800000);
+        id = prim = il = tl = kMiss;
+        id2 = prim2 = kMiss;
+    }
+    // ABI closest hit (no leaf indices kept); returns true when c became the best
+    __device__ __forceinline__ bool offer(float ct, uint32_t cid, uint32_t cprim) {
+        if (hit_before(ct, cid, cprim, t, id, prim)) {
+            if (id != kMiss) {
+                t2 = t; id2 = id; prim2 = prim;
+            }
+            t = ct; id = cid; prim = cprim;
+            return true;
+        }
+        if (hit_before(ct, cid, cprim, t2, id2, prim2)) {
+            t2 = ct; id2 = cid; prim2 = cprim;
+        }
+        return false;
+    }
+    // the runner-up's instance, if it lies within the tie band of the best (else kMiss)
+    __device__ __forceinline__ uint32_t tie_id() const { return (id2 != kMiss && t2 <= __fmul_rn(t, kTieBand)) ? id2 : kMiss; }
 };
 
 // One ray, run to completion: one loop iteration per node visit, instance
 // entry or triangle test; a stack pop joins the step that follows it.  The ray
 // is r0 = (origin, tmin), r1 = (direction, tmax) in world space; ANY: the
 // first hit ends it.
-template <bool ANY, bool BRUTE, bool STATS>
+// TIES (closest-hit queries of the ABI): also keep the runner-up (Best2), and
+// test triangles up to the tie band beyond the best distance.
+template <bool ANY, bool BRUTE, bool STATS, bool TIES = false>
 __device__ __forceinline__ RayHit trace_core(const TraceArgs& a, const float4* tlas_nodes, const InstDev* tlas_inst,
                                              uint32_t tlas_root, float4 r0, float4 r1, TraceCounts& cnt) {
     const uint32_t iter_cap = a.iter_cap;
@@ -294,13 +350,12 @@ __device__ __forceinline__ RayHit trace_core(const TraceArgs& a, const float4* t
     SpaceRay cr = wr;  // ray of the current space
     Shear sh;
 
-    float best_t = tmax;
+    Best2 best;
+    best.reset(tmax);
+    float any_V = 0.f, any_W = 0.f, any_det = 1.f;
     // culling distance of the box tests: the ray's end (any hit) or the best
     // hit so far (closest hit), with the relative slack
     float tlim = __fmul_rn(tmax, kCullSlack);
-    uint32_t best_id = kMiss, best_prim = kMiss;
-    uint32_t best_il = kMiss, best_tl = kMiss;
-    float best_V = 0.f, best_W = 0.f, best_det = 1.f;
     bool found = false;
 
     uint32_t stack[kStack];
@@ -400,22 +455,27 @@ __device__ __forceinline__ RayHit trace_core(const TraceArgs& a, const float4* t
             const float4* tp = tri_rec(tris, leaf);
             const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
             if (STATS) ++cnt.tris;
-            TriResult h = tri_test(sh, v0, v1, v2, tmin, kAny ? tmax : best_t);
+            const float tlo = kAny ? tmax : (TIES && found ? fminf(__fmul_rn(best.t, kTieBand), tmax) : best.t);
+            TriResult h = tri_test(sh, v0, v1, v2, tmin, tlo);
             ref = kNone;
             if (h.hit) {
                 const uint32_t prim = __float_as_uint(v0.w);
                 if (kAny) {
-                    best_t = h.t; best_id = cur_id; best_prim = prim;
-                    best_V = h.V; best_W = h.W; best_det = h.det;
+                    best.t = h.t; best.id = cur_id; best.prim = prim;
+                    best.il = cur_leaf; best.tl = leaf;
+                    any_V = h.V; any_W = h.W; any_det = h.det;
                     found = true;
                     break;
                 }
-                bool better = h.t < best_t || cur_id < best_id || (cur_id == best_id && prim < best_prim);
-                if (better) {
-                    best_t = h.t; best_id = cur_id; best_prim = prim;
-                    best_il = cur_leaf; best_tl = leaf;
-                    tlim = __fmul_rn(best_t, kCullSlack);
-                    best_V = h.V; best_W = h.W; best_det = h.det;
+                if (TIES) {
+                    if (best.offer(h.t, cur_id, prim)) {
+                        tlim = __fmul_rn(best.t, kCullSlack);
+                        found = true;
+                    }
+                } else if (h.t < best.t || cur_id < best.id || (cur_id == best.id && prim < best.prim)) {
+                    best.t = h.t; best.id = cur_id; best.prim = prim;
+                    best.il = cur_leaf; best.tl = leaf;
+                    tlim = __fmul_rn(best.t, kCullSlack);
                     found = true;
                 }
             }
@@ -424,14 +484,16 @@ __device__ __forceinline__ RayHit trace_core(const TraceArgs& a, const float4* t
     RayHit h;
     h.found = found && ok;
     h.ok = ok;
-    h.t = best_t;
-    h.V = best_V;
-    h.W = best_W;
-    h.det = best_det;
-    h.id = best_id;
-    h.prim = best_prim;
-    h.il = best_il;
-    h.tl = best_tl;
+    h.t = best.t;
+    h.id = best.id;
+    h.prim = best.prim;
+    h.il = best.il;
+    h.tl = best.tl;
+    h.id2 = TIES ? best.tie_id() : kMiss;
+    h.prim2 = best.prim2;
+    h.V = any_V;
+    h.W = any_W;
+    h.det = any_det;
     return h;
 }
 
@@ -495,8 +557,130 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& a, const uint32_t* pr
         tlas_root = S->tlas_root;
     }
     const float4 r0 = __ldg(a.rays + 2 * (size_t)j), r1 = __ldg(a.rays + 2 * (size_t)j + 1);
-    const RayHit h = trace_core<kAny, BRUTE, STATS>(a, tlas_nodes, tlas_inst, tlas_root, r0, r1, cnt);
-    emit<MODE>(a, i, j, h.found, h.ok, h.t, h.id, h.prim, h.il, h.tl, h.V, h.W, h.det);
+    const RayHit h = trace_core<kAny, BRUTE, STATS, MODE == kModeClosestAbi>(a, tlas_nodes, tlas_inst, tlas_root, r0, r1, cnt);
+    emit<MODE>(a, i, j, h.found, h.ok, h.t, h.id, h.prim, h.il, h.tl, h.id2, h.prim2, h.V, h.W, h.det);
+}
+
+
+// ---------------------------------------------------------------- exact hit attributes
+// The ABI's hit records carry t, u, v of the chosen triangle to far better
+// than float32 resolution of the scene: a float32 evaluation loses about
+// 2^-24 of the ray's travel distance and of the coordinates' magnitude, which
+// is far beyond 1e-5 of u for a small triangle seen from afar, or of t for a
+// hit close to an origin far from the world origin.  k_refine_hits recomputes
+// them in float-float arithmetic (a value is the unevaluated sum hi + lo of two
+// floats) from the exact float32 inputs: the world ray (o, d), the instance's
+// object-to-world rows [A | T] and the triangle's object-space vertices.
+//
+//   c_i = A v_i + T - (o + t0 d)       vertex i seen from the float32 hit
+//                                      point, exact to ~2^-44 of the terms
+//   X0 = c1 x c2, X1 = c2 x c0, X2 = c0 x c1
+//   E_i = d . X_i                      signed volume spanned by d and the edge
+//                                      opposite vertex i (the edge functions of
+//                                      the watertight test, free of the shear)
+//   u = E_1 / (E_0 + E_1 + E_2),  v = E_2 / (E_0 + E_1 + E_2)
+//   t = t0 + det(c0, c1, c2) / (E_0 + E_1 + E_2)
+//
+// E_i does not change when the origin slides along d, and det(c0, c1, c2) is
+// (t - t0) times the same sum, so no step depends on t0 being accurate; t0
+// only keeps the magnitudes of c_i near the triangle's size.  Error-free
+// transformations: Knuth's TwoSum and the FMA product (Dekker; Ogita, Rump &
+// Oishi 2005, "Accurate sum and dot product"), with every operation an
+// explicit intrinsic so no contraction changes the roundings.
+struct FF {
+    float h, l;
+};
+
+__device__ __forceinline__ FF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ FF two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+// row . v + B (row, v exact floats, B float-float)
+__device__ __forceinline__ FF affine_ff(float4 row, float4 v, FF B) {
+    const FF p0 = two_prod(row.x, v.x), p1 = two_prod(row.y, v.y), p2 = two_prod(row.z, v.z);
+    const FF s0 = two_sum(B.h, p0.h);
+    const FF s1 = two_sum(s0.h, p1.h);
+    const FF s2 = two_sum(s1.h, p2.h);
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(B.l, p0.l), __fadd_rn(p1.l, p2.l)),
+                               __fadd_rn(__fadd_rn(s0.l, s1.l), s2.l));
+    return two_sum(s2.h, lo);
+}
+
+// a1 b2 - a2 b1 in float-float
+__device__ __forceinline__ FF cross_ff(FF a1, FF b2, FF a2, FF b1) {
+    const FF p = two_prod(a1.h, b2.h), q = two_prod(a2.h, b1.h);
+    const FF s = two_sum(p.h, -q.h);
+    const float cross_lo = __fsub_rn(__fmaf_rn(a1.h, b2.l, __fmul_rn(a1.l, b2.h)),
+                                     __fmaf_rn(a2.h, b1.l, __fmul_rn(a2.l, b1.h)));
+    return two_sum(s.h, __fadd_rn(__fadd_rn(__fsub_rn(p.l, q.l), s.l), cross_lo));
+}
+
+// x . y for float-float vectors (x0 may have a zero lo part), rounded once at the end
+__device__ __forceinline__ float dot_ff(FF x0, FF x1, FF x2, FF y0, FF y1, FF y2) {
+    const FF p0 = two_prod(x0.h, y0.h), p1 = two_prod(x1.h, y1.h), p2 = two_prod(x2.h, y2.h);
+    const FF s0 = two_sum(p0.h, p1.h);
+    const FF s1 = two_sum(s0.h, p2.h);
+    const float cross_lo = __fadd_rn(__fadd_rn(__fmaf_rn(x0.h, y0.l, __fmul_rn(x0.l, y0.h)),
+                                               __fmaf_rn(x1.h, y1.l, __fmul_rn(x1.l, y1.h))),
+                                     __fmaf_rn(x2.h, y2.l, __fmul_rn(x2.l, y2.h)));
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(p0.l, p1.l), __fadd_rn(p2.l, s0.l)), __fadd_rn(s1.l, cross_lo));
+    return __fadd_rn(s1.h, lo);
+}
+
+struct Refined {
+    float t, u, v;
+};
+
+// t, u, v of the ray (o, d) against one triangle of one instance, from the
+// approximate distance t0 (see above).  m: the instance's object-to-world rows
+// {A_k0, A_k1, A_k2, T_k}; v0..v2: object-space vertices (x, y, z).  If the
+// ray is parallel to the triangle's plane (no finite solution), t0 is kept
+// and u = v = 0.
+__device__ __forceinline__ Refined refine_hit(float4 r0, float4 r1, float t0, float4 m0, float4 m1, float4 m2,
+                                              float4 v0, float4 v1, float4 v2) {
+    // B_k = T_k - o_k - t0 d_k
+    auto base = [&](float T, float o, float d) {
+        const FF a = two_sum(T, -o);
+        const FF p = two_prod(t0, d);
+        const FF b = two_sum(a.h, -p.h);
+        return two_sum(b.h, __fadd_rn(__fsub_rn(a.l, p.l), b.l));
+    };
+    const FF Bx = base(m0.w, r0.x, r1.x), By = base(m1.w, r0.y, r1.y), Bz = base(m2.w, r0.z, r1.z);
+    const FF c0x = affine_ff(m0, v0, Bx), c0y = affine_ff(m1, v0, By), c0z = affine_ff(m2, v0, Bz);
+    const FF c1x = affine_ff(m0, v1, Bx), c1y = affine_ff(m1, v1, By), c1z = affine_ff(m2, v1, Bz);
+    const FF c2x = affine_ff(m0, v2, Bx), c2y = affine_ff(m1, v2, By), c2z = affine_ff(m2, v2, Bz);
+    const FF zero = {0.f, 0.f};
+    const FF dx = {r1.x, 0.f}, dy = {r1.y, 0.f}, dz = {r1.z, 0.f};
+    // X0 = c1 x c2
+    const FF X0x = cross_ff(c1y, c2z, c1z, c2y), X0y = cross_ff(c1z, c2x, c1x, c2z), X0z = cross_ff(c1x, c2y, c1y, c2x);
+    const float E0 = dot_ff(dx, dy, dz, X0x, X0y, X0z);
+    const float D = dot_ff(c0x, c0y, c0z, X0x, X0y, X0z);
+    // X1 = c2 x c0
+    const FF X1x = cross_ff(c2y, c0z, c2z, c0y), X1y = cross_ff(c2z, c0x, c2x, c0z), X1z = cross_ff(c2x, c0y, c2y, c0x);
+    const float E1 = dot_ff(dx, dy, dz, X1x, X1y, X1z);
+    // X2 = c0 x c1
+    const FF X2x = cross_ff(c0y, c1z, c0z, c1y), X2y = cross_ff(c0z, c1x, c0x, c1z), X2z = cross_ff(c0x, c1y, c0y, c1x);
+    const float E2 = dot_ff(dx, dy, dz, X2x, X2y, X2z);
+    (void)zero;
+    const float det = __fadd_rn(__fadd_rn(E0, E1), E2);
+    Refined r;
+    const float dt = __fdiv_rn(D, det);
+    if (!(fabsf(det) > 0.f) || !(fabsf(dt) < INFINITY)) {
+        r.t = t0;
+        r.u = r.v = 0.f;
+        return r;
+    }
+    r.t = __fadd_rn(t0, dt);
+    r.u = __fdiv_rn(E1, det);
+    r.v = __fdiv_rn(E2, det);
+    return r;
 }
 
 }  // namespace

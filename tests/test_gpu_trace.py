@@ -1,12 +1,16 @@
 """Closest-hit / any-hit / miss on the GPU vs the FP64 oracle.
 
-Tolerances (derived from the float32 arithmetic of the path):
-  * hit ids equal on every ray the oracle does not flag as ambiguous;
-  * t within 1e-5 relative, widened for grazing incidence by the float32
-    position error eta / |cos| (eta = KAPPA * 2^-24 * the magnitudes entering
-    the object-space ray), as computed per ray by the oracle (tol_t);
-  * u, v within 1e-5 + eta / (smallest altitude of the hit triangle) (tol_b);
-  * ambiguous (exempt) rays counted and bounded.
+Tolerances are the plain ones of the method's statement:
+  * t within 1e-5 relative: |t - t_ref| <= 1e-5 t_ref;
+  * barycentrics within 1e-5 relative: |u - u_ref| <= 1e-5 max(|u_ref|, 1e-3),
+    the same for v (a floor of 1e-3 keeps the bound finite at an edge);
+  * hit ids equal.
+A ray that fails any of these "differs".  Every differing ray must be one the
+oracle flags as ambiguous (its exact winner lies within the float32 error band
+of an edge, another candidate lies within that band of its distance, or it
+grazes), and the differing rays number at most 1e-4 of the set.  The float32
+error band (eta / |cos|, from the magnitudes that enter the object-space ray)
+only decides which rays are flagged; it widens no comparison.
 BVH traversal must equal brute force bit for bit.
 """
 import os
@@ -24,8 +28,10 @@ import scenegen as g
 pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("librg")]
 MISS = 0xFFFFFFFF
 KAPPA = 16.0
-REL_T = 1e-5
-MAX_EXEMPT = 1e-4
+REL_T = 1e-5       # t within 1e-5 relative
+REL_B = 1e-5       # barycentrics within 1e-5 relative ...
+B_FLOOR = 1e-3     # ... to max(|u|, 1e-3)
+MAX_EXEMPT = 1e-4  # differing (flagged) rays, at most this fraction of a set
 
 
 def trace(gs, rays, flags=0):
@@ -34,28 +40,44 @@ def trace(gs, rays, flags=0):
     return rg.split_hits(hits)
 
 
+def plain_differ(h, ref):
+    """Per ray: True where the GPU record differs from the oracle's under the
+    plain tolerances (ids, t, u, v; a miss must be the exact miss record)."""
+    id_diff = (h["inst"] != ref["inst"]) | (h["prim"] != ref["prim"])
+    hit = ~id_diff & (ref["inst"] != MISS)
+    t_ref = ref["t"]
+    dt = np.abs(h["t"].astype(np.float64) - t_ref)
+    du = np.abs(h["u"].astype(np.float64) - ref["u"])
+    dv = np.abs(h["v"].astype(np.float64) - ref["v"])
+    with np.errstate(invalid="ignore"):
+        bad_t = hit & ~(dt <= REL_T * np.abs(t_ref))
+        bad_u = hit & ~(du <= REL_B * np.maximum(np.abs(ref["u"]), B_FLOOR))
+        bad_v = hit & ~(dv <= REL_B * np.maximum(np.abs(ref["v"]), B_FLOOR))
+    miss = ~id_diff & (ref["inst"] == MISS)
+    bad_miss = miss & ~(np.isinf(h["t"]) & (h["u"] == 0) & (h["v"] == 0))
+    return id_diff | bad_t | bad_u | bad_v | bad_miss
+
+
 def compare_closest(h, ref, max_exempt=MAX_EXEMPT, label=""):
-    """Every ray the oracle does not flag ambiguous must match; rays that do
-    differ (ids, or t/u/v beyond tolerance) must all be flagged, and their
-    count is bounded by max_exempt of the rays.  Returns that fraction."""
+    """Every ray that differs under the plain tolerances must be flagged
+    ambiguous by the oracle, and at most max_exempt of the rays may differ.
+    Prints the counts and the worst errors of the agreeing hits; returns the
+    differing fraction."""
     amb = ref["ambiguous"]
-    ok = ~amb
-    bad_id = ok & ((h["inst"] != ref["inst"]) | (h["prim"] != ref["prim"]))
-    assert not bad_id.any(), f"{label}: {bad_id.sum()} id mismatches, e.g. ray {np.nonzero(bad_id)[0][:5]}"
-    hit = ok & (ref["inst"] != MISS)
-    dt = np.abs(h["t"][hit].astype(np.float64) - ref["t"][hit])
-    assert np.all(dt <= ref["tol_t"][hit]), f"{label}: t error {np.max(dt / ref['tol_t'][hit]):.2f} x tol"
-    du = np.abs(h["u"][hit] - ref["u"][hit])
-    dv = np.abs(h["v"][hit] - ref["v"][hit])
-    assert np.all(du <= ref["tol_b"][hit]) and np.all(dv <= ref["tol_b"][hit]), f"{label}: barycentric error"
-    miss = ok & (ref["inst"] == MISS)
-    assert np.all(np.isinf(h["t"][miss])) and np.all(h["u"][miss] == 0) and np.all(h["prim"][miss] == MISS)
-    differ = (h["inst"] != ref["inst"]) | (h["prim"] != ref["prim"])
-    both = ~differ & (ref["inst"] != MISS)
-    differ[both] |= (np.abs(h["t"][both] - ref["t"][both]) > ref["tol_t"][both])
-    frac = differ.mean()
-    assert frac <= max_exempt, f"{label}: {differ.sum()} exempt rays differ ({frac:.2e} > {max_exempt:.0e})"
-    return frac
+    differ = plain_differ(h, ref)
+    unflagged = differ & ~amb
+    assert not unflagged.any(), (
+        f"{label}: {unflagged.sum()} differing rays are not flagged, e.g. ray {np.nonzero(unflagged)[0][:5]}")
+    n = len(differ)
+    allowed = int(np.floor(max_exempt * n))
+    assert differ.sum() <= allowed, f"{label}: {differ.sum()} rays differ (flagged), more than {allowed} of {n}"
+    agree = ~differ & (ref["inst"] != MISS)
+    rt = (np.abs(h["t"][agree] - ref["t"][agree]) / np.abs(ref["t"][agree])).max(initial=0.0)
+    ru = (np.abs(h["u"][agree] - ref["u"][agree]) / np.maximum(np.abs(ref["u"][agree]), B_FLOOR)).max(initial=0.0)
+    rv = (np.abs(h["v"][agree] - ref["v"][agree]) / np.maximum(np.abs(ref["v"][agree]), B_FLOOR)).max(initial=0.0)
+    print(f"{label}: {differ.sum()} of {n} rays differ (all flagged; allowed {allowed}), {amb.sum()} flagged; "
+          f"worst relative error t {rt:.2e}, u {ru:.2e}, v {rv:.2e}")
+    return differ.mean()
 
 
 def camera_rays(scene, pixels=None):
@@ -98,16 +120,35 @@ def test_tiny_camera_and_random_rays(tiny):
 
 
 def test_tiny_coplanar_contact_from_below(tiny):
-    """The cubes rest on the ground: their bottom faces are coplanar with it.
-    Rays from below meet both surfaces at the same t, a near tie that the
-    tie rule decides from float32 rounding; every ray that differs from the
-    oracle must be one the oracle flags as a near tie."""
+    """The cubes rest on the ground: their bottom faces are coplanar with it,
+    so rays from below meet both surfaces at exactly the same t.  Both sides
+    decide that tie on the exact distance rounded to float32, then by the
+    smaller instance (the ground), so the contact is bounded like any other
+    ray set."""
     s, gs, O = tiny
     rays = g.random_rays(50_000, np.array([-6, -3, -6]), np.array([6, -0.5, 6]), seed=13)
     h = trace(gs, rays)
     ref = O.trace(rays, kappa=KAPPA, rel_t=REL_T)
-    frac = compare_closest(h, ref, max_exempt=1.0, label="tiny-below")
-    print(f"coplanar contact: {frac:.2e} of rays differ (all flagged)")
+    # rays that meet a cube's bottom face inside the ground's footprint: exact ties
+    ties = (ref["inst"] == 0) & ref["ambiguous"]
+    assert ties.sum() > 100
+    compare_closest(h, ref, label="tiny-below")
+
+
+def test_tiny_rays_from_all_directions(tiny):
+    """The tiny scene from every direction: origins uniform in a box around it
+    (above, beside and below the ground), directions uniform on the sphere;
+    the coplanar contact of the cubes and the ground is met from below."""
+    s, gs, O = tiny
+    rng = np.random.default_rng(17)
+    n = 200_000
+    o = rng.uniform([-7, -4, -7], [7, 6, 7], (n, 3))
+    d = rng.normal(size=(n, 3))
+    rays = np.c_[o, np.zeros(n), d / np.linalg.norm(d, axis=1, keepdims=True), np.full(n, np.inf)].astype(np.float32)
+    h = trace(gs, rays)
+    ref = O.trace(rays, kappa=KAPPA, rel_t=REL_T)
+    assert (ref["inst"] != MISS).mean() > 0.1
+    compare_closest(h, ref, label="tiny all directions")
 
 
 def test_tiny_any_hit(tiny):
