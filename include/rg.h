@@ -181,7 +181,17 @@ enum {
     RG_TRACE_PLAIN = 8u    /* in an RG_SCENE_COMPRESSED scene: use the binary float32 BVH */
 };
 /* Trace n rays (device array d_rays) and write n hit records to d_hits.
- * n may be 0. */
+ * n may be 0.  Closest hit: the nearest triangle is chosen by a float32
+ * traversal; a second pass then recomputes t, u, v of that triangle in
+ * float-float arithmetic (about 44 bits) from the float32 inputs, so they are
+ * the exact values rounded to float32 up to a few units in the last place
+ * (far inside 1e-5 relative, also for small triangles seen from afar), and
+ * t is kept within [tmin, tmax].  When the float32 distances of the two
+ * nearest candidates lie within a relative 2^-14, the two are decided again
+ * on their exact distances rounded to float32 (then instance, then prim), so
+ * exact ties such as coplanar surfaces have one answer.  Any hit: only
+ * occluded / not is defined; the record of some hit carries the float32 t,
+ * u, v of the watertight test. */
 rg_status rg_trace_rays(rg_scene* scene, const rg_ray* d_rays, uint32_t n, uint32_t flags, rg_hit* d_hits,
                         void* stream);
 
