@@ -1,24 +1,26 @@
 #!/usr/bin/env python
-"""Frame benchmark of the GB300 ray tracer.
+"""Benchmark of the GB300 ray tracer.
 
-One step = one frame of the medium workload (64 instances of 4 procedural
-meshes, 157,964 unique triangles, 1920x1080, 4 point lights, max depth 4):
-seeded per-instance motion, a full TLAS rebuild (float64 instance inverses,
-Arvo boxes, Morton codes, radix sort, Karras hierarchy, refit), then the
-Whitted render (ray generation, closest-hit traversal, shading and queue
-compaction, any-hit shadow traversal with accumulation) into an RGBA32F
-image.  The four BLAS are built once per scene (their build time is reported
-in config.blas_build_ms).
+Default (--workload large): one step = the large query workload (4,096
+instances of 16 procedural meshes, 1,938,944 unique / about 60M instanced
+triangles): seeded per-instance motion, a full TLAS rebuild (float64 instance
+inverses, Arvo boxes, Morton codes, sort, Karras hierarchy, refit), then
+16,777,216 closest-hit rays (one rg_trace_rays launch: float32 traversal, then
+the exact t, u, v of each hit) and 16,777,216 any-hit rays (one launch).
+Inputs are larger than L2 (1 GiB of rays, about 400 MB of BVH).
 
-value  = traced rays (closest-hit + shadow) per second over all ranks, inputs
-         resident in HBM, L2 flushed (256 MiB write) before every timed frame.
-e2e    = the same frames with the instance transforms copied host->device from
-         pinned memory and the image copied back to pinned memory, inside the
-         timed region.
---impl reference runs the float64 CPU oracle on the same frames.
+value  = closest-hit rays per step / ms_per_step (the whole step: rebuild,
+         closest-hit and any-hit launches), over all ranks.
+e2e    = the same steps through rg_trace_rays with the rays in pinned host
+         memory and the hit records copied back to it, copies inside the
+         timed region (overlapped with tracing in chunks of 4M rays).
+The line also carries the any-hit rate, the medium render frame (64
+instances, 1920x1080, depth 4) and the serving stream as extra keys.
+--impl reference runs the float64 CPU oracle on a seeded sample of each
+step's rays.
 
-Multi-GPU (torchrun): replicas, each rank renders its own frames; value is
-the sum of all ranks' rays over the slowest rank's time.
+Multi-GPU (torchrun): replicas, each rank runs its own steps; value is the
+sum of all ranks' rays over the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -43,15 +45,21 @@ sys.path.insert(0, ROOT)
 import scenegen as g  # noqa: E402
 
 METRIC = "Mrays/s closest-hit at 1 GB300 vs plain path & oracle; p50/p99 frame latency"
-WORKLOAD = ("medium: 64 instances of 4 procedural meshes (UV sphere 80x40, icosphere s5, cube, 256^2 heightfield; "
-            "157,964 unique tris) with seeded affine transforms in a 100^3 box, materials diffuse/mirror/glass "
-            "60/20/20%, 4 point lights, 1920x1080, max_depth 4; per frame seeded motion + full TLAS rebuild + render")
+LARGE_WORKLOAD = ("large: 4096 instances of 16 procedural meshes (1,938,944 unique / ~60M instanced tris), per step "
+                  "seeded motion + full TLAS rebuild + 16,777,216 closest-hit and 16,777,216 any-hit rays "
+                  "(origins uniform in the scene box, directions uniform, any-hit length U(1,50))")
+MEDIUM_WORKLOAD = ("medium: 64 instances of 4 procedural meshes (UV sphere 80x40, icosphere s5, cube, 256^2 heightfield; "
+                   "157,964 unique tris) with seeded affine transforms in a 100^3 box, materials diffuse/mirror/glass "
+                   "60/20/20%, 4 point lights, 1920x1080, max_depth 4; per frame seeded motion + full TLAS rebuild + render")
+WORKLOAD = LARGE_WORKLOAD
+N_LARGE = 1 << 24
+E2E_CHUNK = 1 << 22
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--steps", type=int, default=None, help="timed steps (default: large 20, medium 200)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU baseline budget (wall seconds)")
@@ -59,16 +67,21 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--compressed", action="store_true",
                    help="trace with the compressed 8-wide BVH (default: the float32 binary BVH, faster here)")
-    p.add_argument("--workload", default="medium", choices=["medium", "large", "serve"],
-                   help="medium: the render frame (default); large: incoherent closest/any-hit queries; "
+    p.add_argument("--workload", default="large", choices=["large", "medium", "serve"],
+                   help="large: incoherent closest/any-hit queries (default); medium: the render frame; "
                         "serve: the continuous-batching render server alone")
     p.add_argument("--requests", type=int, default=400, help="serving: requests in the Poisson stream")
-    p.add_argument("--no-serving", action="store_true", help="medium: skip the serving measurement")
+    p.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    p.add_argument("--no-medium", action="store_true", help="large: skip the medium render frame")
+    p.add_argument("--rays", type=int, default=N_LARGE, help="large: rays of each kind per step")
     p.add_argument("--inflight", type=int, default=4,
                    help="medium: frames in flight (scene contexts sharing the BLAS, one stream each)")
     p.add_argument("--no-pair", action="store_true",
                    help="trace each level's (server: step's) shadow rays and the next one's closest-hit rays in separate launches")
-    return p.parse_args()
+    a = p.parse_args(argv)
+    if a.steps is None:
+        a.steps = 200 if a.workload == "medium" else 20
+    return a
 
 
 def dist_env():
@@ -153,6 +166,15 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def sm_max_mhz():
+    """The maximum SM clock (MEASURED_PEAKS.json, else GB300's 2070 MHz)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except (OSError, KeyError, ValueError):
+        return 2070.0
+
+
 def code_sha(*paths):
     """Hash of source files' code: // comments, trailing spaces and blank
     lines removed (a comment edit leaves the kernels, and their counters, as
@@ -170,22 +192,34 @@ TRAVERSAL_SOURCES = [os.path.join(ROOT, "paper_2001_09792_gb300", "csrc", f)
                      for f in ("traverse.cuh", "trace.cu", "api.cu")]
 
 
-def traffic_record():
-    """DRAM bytes per traversal launch of the medium frame (the frame's
-    closest-hit, pair and shadow launches, averaged) from the committed ncu
-    summary, valid only while the traversal code (traverse.cuh, trace.cu) and
-    the launch sequence of a frame (api.cu) are unchanged."""
-    path = os.path.join(ROOT, "profiles", "trace_pair_medium.md")
+def traffic_record(profile="trace_pair_medium.md", key="dram_bytes_per_traversal_launch"):
+    """DRAM bytes per launch of a traversal kernel, from a committed ncu
+    summary under profiles/ (default: the medium frame's five traversal
+    launches, averaged), valid only while the traversal code (traverse.cuh,
+    trace.cu) and the launch sequence (api.cu) are unchanged: the summary
+    carries the hash of that code."""
+    path = os.path.join(ROOT, "profiles", profile)
     try:
         txt = open(path).read()
         sha = code_sha(*TRAVERSAL_SOURCES)
-        m = re.search(r"dram_bytes_per_traversal_launch:\s*([0-9.]+)", txt)
+        m = re.search(key + r":\s*([0-9.]+)", txt)
         s = re.search(r"traversal_code_sha256_16:\s*([0-9a-f]+)", txt)
         if m and s and s.group(1) == sha:
             return float(m.group(1))
     except OSError:
         pass
     return None
+
+
+def profile_figure(profile, label):
+    """A percentage from a table row '| label | x % ...' of a committed ncu
+    summary (a capture, not measured by this run); None if absent."""
+    try:
+        txt = open(os.path.join(ROOT, "profiles", profile)).read()
+    except OSError:
+        return None
+    m = re.search(r"^\| " + re.escape(label) + r" \| ([0-9.]+) %", txt, flags=re.M)
+    return float(m.group(1)) if m else None
 
 
 def l2_record(compressed):
@@ -230,18 +264,16 @@ def frame_motions(scene, n):
     return [g.motion(scene.M, k) for k in range(n)]
 
 
-# ---------------------------------------------------------------- native arm
+# ---------------------------------------------------------------- medium render frame
 
-def run_native(args, world, rank, local):
+def run_medium(args, world, rank, local, embedded=False):
+    """The medium render frame (--workload medium, or a key of the large
+    line when embedded): frames with per-frame motion, TLAS rebuild and
+    render, four in flight; also one at a time (the roofline's launch times
+    come from that pass, where launches do not overlap).  Returns the line on
+    rank 0."""
     import torch
     import paper_2001_09792_gb300 as rg
-    from paper_2001_09792_gb300 import _build
-
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    _build.build()
 
     s = g.medium_scene()
     W, H, D = s.width, s.height, s.max_depth
@@ -336,6 +368,7 @@ def run_native(args, world, rank, local):
     # process has measured slow at times, so it runs twice and the second counts
     timed(1)
     rays1, wall1, ms, stats1 = timed(1)
+    closest1 = stats1[0]["closest_rays"]
     if F > 1:
         rays, total_s, ms_f, stats_f = timed(F)
     else:
@@ -357,6 +390,8 @@ def run_native(args, world, rank, local):
             fx_ms.append((e0, e1))
     torch.cuda.synchronize()
     fxaa_ms = statistics.median(a.elapsed_time(b) for a, b in fx_ms)
+
+    closest_f = sum(x["closest_rays"] for x in stats_f)
 
     # e2e: host instance transforms in, host image out, through the same calls;
     # frames back to back with the readback of frame k overlapping frame k+1
@@ -403,12 +438,16 @@ def run_native(args, world, rank, local):
         stream.wait_stream(copy_stream)
         e_end.record(stream)
         torch.cuda.synchronize()
-        e2e_rays = sum(rg.rg_get_stats(c.h)["closest_rays"] + rg.rg_get_stats(c.h)["shadow_rays"] for c in ctxs)
+        e2e_rays = sum(rg.rg_get_stats(c.h)["closest_rays"] for c in ctxs)
         e2e = (e2e_rays, e_start.elapsed_time(e_end) / 1e3, inst_host[0].nbytes, W * H * 16)
 
     # aggregate over ranks: the slowest rank's time, every rank's rays
-    (total_s_all, e2e_s_all), (rays_all, e2e_rays_all) = reduce_over_ranks(
-        [total_s, e2e[1] if e2e else 0.0], [float(rays), float(e2e[0]) if e2e else 0.0], "cuda")
+    if embedded:
+        total_s_all, e2e_s_all, rays_all, closest_all = total_s, (e2e[1] if e2e else 0.0), rays, closest_f
+        e2e_rays_all = e2e[0] if e2e else 0.0
+    else:
+        (total_s_all, e2e_s_all), (rays_all, closest_all, e2e_rays_all) = reduce_over_ranks(
+            [total_s, e2e[1] if e2e else 0.0], [float(rays), float(closest_f), float(e2e[0]) if e2e else 0.0], "cuda")
     if e2e:
         e2e = (e2e_rays_all, e2e_s_all, e2e[2], e2e[3])
 
@@ -430,8 +469,18 @@ def run_native(args, world, rank, local):
         rays_per_launch = (st["closest_rays"] + st["shadow_rays"]) / trav_launches
         achieved = trav_bytes / trav_launches / (launch_ms / 1e3) / 1e9
         tr = None if args.compressed else traffic_record()
-        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+        prof = "trace8_medium.md" if args.compressed else "trace_pair_medium.md"
+        # the BVH lives in L2: the traversal is bound by instruction issue, so the
+        # counted bytes (mostly L1/L2 hits) over the HBM peak is no DRAM fraction;
+        # the DRAM fraction is the captured traffic over the same launch time
+        roofline = {"bound": "issue", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(achieved / peak, 4), "traffic": None if tr is None else round(tr),
+                    "dram_frac": None if tr is None else round(tr / (launch_ms / 1e3) / 1e9 / peak, 4),
+                    "issue_slots_active_pct": profile_figure(prof, "issue slots active"),
+                    "bound_note": "achieved and frac: algorithmic (counted) bytes per launch over the launch time, "
+                                  "served mostly by L1/L2; dram_frac: the captured DRAM bytes over the same time; "
+                                  "issue_slots_active_pct from the committed capture",
+                    "timed_region": "the one-in-flight pass (config.one_in_flight.ms_per_step)",
                     "kernel": kernel_name(args, "render"), "peak_kind": peak_kind,
                     "algorithmic_bytes_per_launch": round(trav_bytes / trav_launches),
                     "algorithmic_bytes_per_closest_ray": round(bytes_per_ray, 1),
@@ -454,7 +503,7 @@ def run_native(args, world, rank, local):
         p50_1, p99_1 = pcts(ms)
         out = {
             "metric": METRIC,
-            "value": round(rays_all / total_s_all / 1e6, 2),
+            "value": round(closest_all / total_s_all / 1e6, 2),
             "unit": "Mrays/s",
             "n_gpus": world,
             "steps": args.steps,
@@ -465,14 +514,18 @@ def run_native(args, world, rank, local):
             "vs_baseline": None,
             "dtype": "f32",
             "data": "synthetic (seeded procedural scene, random-free shading)",
-            "config": {"workload": WORKLOAD, "width": W, "height": H, "max_depth": D, "lights": 4,
+            "config": {"workload": MEDIUM_WORKLOAD, "width": W, "height": H, "max_depth": D, "lights": 4,
                        "instances": s.n_instances, "instanced_tris": s.instanced_tris(),
                        "rays_per_step": round(rays / args.steps), "closest_rays_per_step": round(st["closest_rays"] / args.steps),
                        "shadow_rays_per_step": round(st["shadow_rays"] / args.steps),
-                       "closest_mrays_s": round(st["closest_rays"] / max(rays1, 1) * rays / total_s / 1e6, 2),
+                       "all_rays_mrays_s": round(rays_all / total_s_all / 1e6, 2),
+                       "value_is": "closest-hit rays (camera, reflected, refracted) per second; shadow (any-hit) "
+                                   "rays are counted in all_rays_mrays_s",
                        "frames_in_flight": F,
                        "p50_ms": p50, "p99_ms": p99,
-                       "one_in_flight": {"value": round(rays1 / wall1 / 1e6, 2), "ms_per_step": round(wall1 * 1e3 / args.steps, 3),
+                       "one_in_flight": {"value": round(closest1 / wall1 / 1e6, 2),
+                                         "all_rays_mrays_s": round(rays1 / wall1 / 1e6, 2),
+                                         "ms_per_step": round(wall1 * 1e3 / args.steps, 3),
                                          "p50_ms": p50_1, "p99_ms": p99_1,
                                          "note": "the same frames one at a time; the roofline's launch times are taken here"},
                        "latency": "per frame, from its TLAS build to its image on its stream (with frames in flight, "
@@ -488,20 +541,385 @@ def run_native(args, world, rank, local):
         if clk:
             out["clocks"] = clk
         if e2e:
-            out["e2e"] = {"value": round(e2e[0] / e2e[1] / 1e6, 2), "unit": "Mrays/s",
+            out["e2e"] = {"value": round(e2e[0] / e2e[1] / 1e6, 2), "unit": "Mrays/s (closest-hit)",
                           "h2d_bytes_per_step": int(e2e[2]), "d2h_bytes_per_step": int(e2e[3]),
                           "note": f"frames back to back, {F} in flight (one scene context and stream each), "
                                   "each image read back on a copy stream while later frames render; one timed "
                                   "region incl. L2 flushes"}
-        if world == 1 and not args.no_serving:
+        if not embedded and world == 1 and not args.no_serving:
             out["serving"] = run_serving(args.requests, pair=not args.no_pair)
-        if world == 1 and not args.no_cpu_baseline:
+        if not embedded and world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(s, motions[args.warmup:], args.cpu_seconds)
-        print(json.dumps(out), flush=True)
+    for c in ctxs[1:]:
+        c.close()
     gs.close()
+    return out if rank == 0 else None
+
+
+def run_native_medium(args, world, rank, local):
+    import torch
+    from paper_2001_09792_gb300 import _build
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    out = run_medium(args, world, rank, local)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- large queries (default)
+
+def ray_bytes(cst, node_b, any_hit):
+    """Algorithmic bytes per ray of a counting pass: the ray (32 B), its hit
+    record (20 B), node_b per BVH node fetched, 48 B per triangle tested (one
+    axis order of the record) and 80 B per instance entered (the float32
+    inverse rows and the BLAS pointers, root and ids)."""
+    pre = "any_" if any_hit else ""
+    r = max(cst["shadow_rays" if any_hit else "closest_rays"], 1)
+    return (32 + 20 + node_b * cst[pre + "node_visits"] / r + 48 * cst[pre + "tri_tests"] / r
+            + 80 * cst[pre + "inst_entries"] / r)
+
+
+def large_counts(s, rg, torch, args, motion, d_c, d_a):
+    """Node, triangle and instance counts per ray of the large query (a
+    counting traversal on a second scene with the same motion)."""
+    with rg.GpuScene(s, flags=rg.RG_SCENE_COUNT | path_flag(args)) as gc:
+        rg.rg_tlas_build(gc.h, torch.from_numpy(rg.pack_instances(motion, [gc.blas[m] for m in s.mesh_id],
+                                                                  s.material_id)).cuda())
+        rg.rg_reset_stats(gc.h)
+        rg.rg_trace_rays(gc.h, d_c, rg.RG_CLOSEST | rg.RG_TRACE_STATS)
+        rg.rg_trace_rays(gc.h, d_a, rg.RG_ANY | rg.RG_TRACE_STATS)
+        return rg.rg_get_stats(gc.h)
+
+
+def large_e2e(rg, torch, gs, inst_host, closest, anyhit, steps, first):
+    """The large steps end to end: per step the instance transforms, the
+    closest-hit rays and the any-hit rays are copied from pinned host memory
+    and the hit records copied back to it, in chunks of E2E_CHUNK rays
+    pipelined over a copy-in stream, the tracing stream and a copy-out stream
+    (two device buffers per kind).  One timed region over all steps.  Returns
+    (closest rays, seconds, H2D bytes per step, D2H bytes per step)."""
+    n = closest.shape[0]
+    pin_c = torch.from_numpy(closest).pin_memory()
+    pin_a = torch.from_numpy(anyhit).pin_memory()
+    pin_inst = [torch.from_numpy(x).pin_memory() for x in inst_host]
+    out_c = torch.empty((n, 5), dtype=torch.int32).pin_memory()
+    out_a = torch.empty((n, 5), dtype=torch.int32).pin_memory()
+    C = min(E2E_CHUNK, n)
+    d_rays = [torch.empty((C, 8), dtype=torch.float32, device="cuda") for _ in range(2)]
+    d_hits = [torch.empty((C, 5), dtype=torch.int32, device="cuda") for _ in range(2)]
+    d_inst = torch.empty_like(torch.from_numpy(inst_host[0])).cuda()
+    s_in, s_run, s_out = torch.cuda.Stream(), torch.cuda.current_stream(), torch.cuda.Stream()
+    traced = [None, None]   # buffer b's rays have been traced (its ray buffer may be refilled)
+    copied = [None, None]   # buffer b's hits have been copied out (its hit buffer may be rewritten)
+    rg.rg_sync(gs.h)
+    rg.rg_reset_stats(gs.h)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s_run)
+    s_in.wait_event(e0)
+    s_out.wait_event(e0)
+    b = 0
+    for k in range(first, first + steps):
+        with torch.cuda.stream(s_in):
+            d_inst.copy_(pin_inst[k % len(pin_inst)], non_blocking=True)
+            ready = torch.cuda.Event()
+            ready.record(s_in)
+        s_run.wait_event(ready)
+        rg.rg_tlas_build(gs.h, d_inst, stream=s_run)
+        inst_used = torch.cuda.Event()
+        inst_used.record(s_run)
+        for host_in, host_out, flags in ((pin_c, out_c, rg.RG_CLOSEST), (pin_a, out_a, rg.RG_ANY)):
+            for c0 in range(0, n, C):
+                m = min(C, n - c0)
+                with torch.cuda.stream(s_in):
+                    if traced[b] is not None:
+                        s_in.wait_event(traced[b])
+                    d_rays[b][:m].copy_(host_in[c0:c0 + m], non_blocking=True)
+                    loaded = torch.cuda.Event()
+                    loaded.record(s_in)
+                s_run.wait_event(loaded)
+                if copied[b] is not None:
+                    s_run.wait_event(copied[b])
+                rg.rg_trace_rays(gs.h, d_rays[b][:m], flags, d_hits[b], stream=s_run)
+                traced[b] = torch.cuda.Event()
+                traced[b].record(s_run)
+                with torch.cuda.stream(s_out):
+                    s_out.wait_event(traced[b])
+                    host_out[c0:c0 + m].copy_(d_hits[b][:m], non_blocking=True)
+                    copied[b] = torch.cuda.Event()
+                    copied[b].record(s_out)
+                b ^= 1
+        s_in.wait_event(inst_used)  # the next step's transforms overwrite d_inst
+    s_run.wait_stream(s_out)
+    s_run.wait_stream(s_in)
+    e1.record(s_run)
+    torch.cuda.synchronize()
+    closest_rays = rg.rg_get_stats(gs.h)["closest_rays"]
+    h2d = inst_host[0].nbytes + closest.nbytes + anyhit.nbytes
+    d2h = out_c.numel() * 4 + out_a.numel() * 4
+    return closest_rays, e0.elapsed_time(e1) / 1e3, h2d, d2h
+
+
+def hit_error_vs_oracle(h, ref):
+    """Per-output error of closest-hit records against the float64 oracle:
+    ids that differ (and how many of those the oracle flags), and for the hits
+    whose ids agree the largest and 99th-percentile relative errors of t and of
+    u, v (relative to max(|u|, 1e-3))."""
+    miss = 0xFFFFFFFF
+    id_diff = (h["inst"] != ref["inst"]) | (h["prim"] != ref["prim"])
+    agree = ~id_diff & (ref["inst"] != miss)
+    et = np.abs(h["t"][agree] - ref["t"][agree]) / np.abs(ref["t"][agree])
+    eu = np.abs(h["u"][agree] - ref["u"][agree]) / np.maximum(np.abs(ref["u"][agree]), 1e-3)
+    ev = np.abs(h["v"][agree] - ref["v"][agree]) / np.maximum(np.abs(ref["v"][agree]), 1e-3)
+    q = lambda x, p: float(np.quantile(x, p)) if x.size else 0.0  # noqa: E731
+    return {"rays": int(len(id_diff)), "hits": int(agree.sum()), "id_differ": int(id_diff.sum()),
+            "id_differ_flagged": int((id_diff & ref["ambiguous"]).sum()), "flagged": int(ref["ambiguous"].sum()),
+            "t_rel": {"max": q(et, 1.0), "p99": q(et, 0.99)}, "u_rel": {"max": q(eu, 1.0), "p99": q(eu, 0.99)},
+            "v_rel": {"max": q(ev, 1.0), "p99": q(ev, 0.99)},
+            "tolerance": "t 1e-5 relative; u, v 1e-5 relative to max(|u|, 1e-3); differing ids flagged, <= 1e-4"}
+
+
+def oracle_prefix(O, rays, budget_s, chunk=65536, any_hit=False):
+    """The oracle on a prefix of the rays, chunk by chunk until the budget is
+    spent (at least one chunk); returns (rays traced, seconds, its records)."""
+    outs, done, t0 = [], 0, time.perf_counter()
+    while done < len(rays):
+        outs.append(O.trace(rays[done:done + chunk], any_hit=any_hit))
+        done = min(len(rays), done + chunk)
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    secs = time.perf_counter() - t0
+    rec = {k: np.concatenate([o[k] for o in outs]) for k in outs[0]}
+    return done, secs, rec
+
+
+def run_native_large(args, world, rank, local):
+    """The default benchmark line (see the module docstring)."""
+    import torch
+    import paper_2001_09792_gb300 as rg
+    from paper_2001_09792_gb300 import _build
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    s = g.large_scene()
+    n = args.rays
+    closest, anyhit = g.large_rays(s, n)
+    n_frames = args.warmup + args.steps
+    motions = [g.motion(s.M, k) for k in range(min(n_frames, 8))]
+    gs = rg.GpuScene(s, flags=rg.RG_SCENE_TIMING | path_flag(args))
+    blas_ids = [gs.blas[m] for m in s.mesh_id]
+    inst_host = [rg.pack_instances(M, blas_ids, s.material_id) for M in motions]
+    inst_dev = [torch.from_numpy(x).cuda() for x in inst_host]
+    d_c, d_a = torch.from_numpy(closest).cuda(), torch.from_numpy(anyhit).cuda()
+    h_c = torch.empty((n, 5), dtype=torch.int32, device="cuda")
+    h_a = torch.empty((n, 5), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(k):
+        rg.rg_tlas_build(gs.h, inst_dev[k % len(inst_dev)])
+        rg.rg_trace_rays(gs.h, d_c, rg.RG_CLOSEST, h_c)
+        rg.rg_trace_rays(gs.h, d_a, rg.RG_ANY, h_a)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    cst = large_counts(s, rg, torch, args, motions[0], d_c, d_a)
+    rg.rg_sync(gs.h)
+    rg.rg_reset_stats(gs.h)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(gpu_index(local))
+    clocks.start()
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = []
+    e_start.record(stream)
+    for k in range(args.warmup, n_frames):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(k)
+        e1.record(stream)
+        ev.append((e0, e1))
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    wall = e_start.elapsed_time(e_end) / 1e3
+    ms = [a.elapsed_time(b) for a, b in ev]
+    st = rg.rg_get_stats(gs.h)
+    rg.rg_sync(gs.h)
+    last_motion = (n_frames - 1) % len(motions)
+    gpu_hits = rg.split_hits(h_c[: min(n, 1 << 20)]) if rank == 0 else None
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = large_e2e(rg, torch, gs, inst_host, closest, anyhit, args.steps, args.warmup)
+    (wall_all, e2e_s_all), (closest_all, any_all, e2e_rays_all) = reduce_over_ranks(
+        [wall, e2e[1] if e2e else 0.0], [float(st["closest_rays"]), float(st["shadow_rays"]),
+                                         float(e2e[0]) if e2e else 0.0], "cuda")
+
+    out = None
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        nb = node_bytes(args)
+        bpr = ray_bytes(cst, nb, False)
+        bpa = ray_bytes(cst, nb, True)
+        c_launches = max(st["trace_launches"], 1)
+        c_ms = st["trace_ms"] / c_launches
+        a_ms = st["any_ms"] / max(st["any_launches"], 1)
+        r_ms = st["refine_ms"] / max(st["refine_launches"], 1)
+        c_bytes = bpr * n
+        counted_gbs = c_bytes / (c_ms / 1e3) / 1e9
+        prof = "trace_large_compressed.md" if args.compressed else "trace_large.md"
+        tr = traffic_record(prof, "dram_bytes_per_closest_launch")
+        ipr = traffic_record(prof, "warp_inst_per_closest_ray")
+        ms_sorted = sorted(ms)
+        step_ms = wall_all * 1e3 / args.steps
+        # The traversal is bound by instruction issue and the latency of its
+        # dependent loads, not by HBM (the captured DRAM traffic is a few % of
+        # the counted bytes): achieved = warp instructions per launch (the
+        # captured count per ray times the rays) over the event-timed launch;
+        # peak = SMs x 4 schedulers x 1 warp instruction per cycle at the
+        # maximum SM clock.
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        issue_peak = sms * 4 * sm_max_mhz() * 1e6 / 1e9
+        achieved = None if ipr is None else ipr * n / (c_ms / 1e3) / 1e9
+        roofline = {
+            "bound": "issue", "achieved": None if achieved is None else round(achieved, 1), "peak": round(issue_peak, 1),
+            "unit": "G warp-instructions/s", "frac": None if achieved is None else round(achieved / issue_peak, 4),
+            "traffic": None if tr is None else round(tr),
+            "dram_frac": None if tr is None else round(tr / (c_ms / 1e3) / 1e9 / peak, 4),
+            "counted_bytes": {"gbs": round(counted_gbs, 1), "frac_of_hbm": round(counted_gbs / peak, 4),
+                              "hbm_peak_gbs": peak, "hbm_peak_kind": peak_kind,
+                              "note": "algorithmic bytes (nodes, triangles, instances, ray, hit) per launch over the "
+                                      "launch time; served mostly from L1/L2"},
+            "peak_derivation": f"{sms} SMs x 4 warp schedulers x 1 instruction/cycle x {sm_max_mhz():.0f} MHz",
+            "warp_inst_per_ray": ipr, "kernel": kernel_name(args, "rg_trace_rays"),
+            "per_launch": "one closest-hit traversal launch of 16,777,216 rays, timed by CUDA events around each "
+                          "launch inside the timed steps; instructions per ray and DRAM bytes from the committed "
+                          f"ncu capture (profiles/{prof}, valid for the traversal code it hashes)",
+            "avg_launch_ms": round(c_ms, 4), "algorithmic_bytes_per_launch": round(c_bytes),
+            "algorithmic_bytes_per_ray": round(bpr, 1),
+            "nodes_per_ray": round(cst["node_visits"] / max(cst["closest_rays"], 1), 2),
+            "tris_per_ray": round(cst["tri_tests"] / max(cst["closest_rays"], 1), 2),
+            "inst_per_ray": round(cst["inst_entries"] / max(cst["closest_rays"], 1), 3),
+            "any_hit": {"algorithmic_bytes_per_ray": round(bpa, 1), "avg_launch_ms": round(a_ms, 4),
+                        "achieved_gbs": round(bpa * n / (a_ms / 1e3) / 1e9, 1),
+                        "nodes_per_ray": round(cst["any_node_visits"] / max(cst["shadow_rays"], 1), 2)},
+            "step_check": {"algorithmic_bytes_per_step": round(c_bytes + bpa * n),
+                           "gbs_over_ms_per_step": round((c_bytes + bpa * n) / (step_ms / 1e3) / 1e9, 1)},
+            "l2": profile_l2(prof)}
+        out = {
+            "metric": METRIC,
+            "value": round(closest_all / wall_all / 1e6, 2),
+            "unit": "Mrays/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(step_ms, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded procedural scene and rays)",
+            "config": {
+                "workload": LARGE_WORKLOAD, "instances": s.n_instances, "instanced_tris": s.instanced_tris(),
+                "closest_rays_per_step": n, "any_hit_rays_per_step": n,
+                "value_is": "closest-hit rays per step / ms_per_step (the step: TLAS rebuild + closest-hit launch "
+                            "+ exact-attribute pass + any-hit launch)",
+                "closest_launch_ms": round(c_ms, 3), "refine_ms": round(r_ms, 3), "any_launch_ms": round(a_ms, 3),
+                "closest_query_mrays_s": round(n / ((c_ms + r_ms) / 1e3) / 1e6, 2),
+                "any_hit_mrays_s": round(n / (a_ms / 1e3) / 1e6, 2),
+                "all_rays_mrays_s": round((closest_all + any_all) / wall_all / 1e6, 2),
+                "tlas_rebuild_and_rest_ms": round(step_ms - c_ms - r_ms - a_ms, 3),
+                "p50_ms": round(ms_sorted[len(ms) // 2], 3), "p99_ms": round(pct(ms, 0.99), 3),
+                "latency": "per step (TLAS rebuild + both queries), CUDA events on the stream",
+                "l2": "inputs larger than L2 (2 x 512 MiB of rays, about 400 MB of BVH and triangle records); "
+                      "no flush",
+                "parallelism": f"replicas x{world}", "bvh": "compressed 8-wide" if args.compressed else "binary float32"},
+            "roofline": roofline,
+            "gpu_launches": int(st["kernel_launches"]),
+        }
+        if clk:
+            out["clocks"] = clk
+        if e2e:
+            out["e2e"] = {"value": round(e2e_rays_all / e2e_s_all / 1e6, 2), "unit": "Mrays/s",
+                          "h2d_bytes_per_step": int(e2e[2]), "d2h_bytes_per_step": int(e2e[3]),
+                          "note": "rays in pinned host memory, hit records back to pinned host memory, copies of 4M-ray "
+                                  "chunks overlapped with tracing (copy-in, trace, copy-out streams), one timed region"}
+    if world == 1 and rank == 0:
+        if not args.no_cpu_baseline:
+            import oracle
+            O = oracle.OracleScene(s)
+            O.set_instances(motions[last_motion], s.mesh_id, s.material_id)
+            k, secs, ref = oracle_prefix(O, closest, args.cpu_seconds)
+            ka, secs_a, _ = oracle_prefix(O, anyhit, max(1.0, args.cpu_seconds / 4), any_hit=True)
+            cores = len(os.sched_getaffinity(0))
+            out["cpu_baseline"] = {
+                "value": round(k / secs / 1e6, 4), "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+                "sample": f"the first {k:,} closest-hit rays of the step (float64, {cores} threads, {secs:.1f} s)",
+                "any_hit": {"value": round(ka / secs_a / 1e6, 4), "unit": "Mrays/s",
+                            "sample": f"the first {ka:,} any-hit rays ({secs_a:.1f} s)"}}
+            m = min(k, len(gpu_hits["inst"]))
+            out["error_vs_oracle"] = hit_error_vs_oracle({kk: v[:m] for kk, v in gpu_hits.items()},
+                                                         {kk: v[:m] for kk, v in ref.items()})
+            out["error_vs_oracle"]["sample"] = f"closest-hit records of the first {m:,} rays of the last timed step"
+        gs.close()
+        if not args.no_medium:
+            out["medium"] = medium_summary(run_medium(args_for_medium(args), 1, 0, local, embedded=True))
+        if not args.no_serving:
+            out["serving"] = run_serving(args.requests, pair=not args.no_pair)
+    else:
+        gs.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def args_for_medium(args):
+    a = argparse.Namespace(**vars(args))
+    a.steps = 60
+    a.no_cpu_baseline = True
+    a.no_serving = True
+    return a
+
+
+def medium_summary(line):
+    """The medium frame's line, kept as a key of the large line."""
+    keep = ("value", "unit", "ms_per_step", "config", "roofline", "e2e", "clocks", "gpu_launches", "steps", "warmup")
+    out = {k: line[k] for k in keep if k in line}
+    out["workload"] = MEDIUM_WORKLOAD
+    out["value_is"] = "closest-hit rays per second of the frames (four in flight)"
+    return out
+
+
+def profile_l2(profile):
+    """L2 / L1 hit rates and L2 throughput of a captured traversal launch."""
+    try:
+        txt = open(os.path.join(ROOT, "profiles", profile)).read()
+    except OSError:
+        return None
+    m = re.search(r"^\| L2 / L1 sector hit rate \| ([0-9.]+) % / ([0-9.]+) %", txt, flags=re.M)
+    if not m:
+        return None
+    out = {"l2_sector_hit_pct": float(m.group(1)), "l1_sector_hit_pct": float(m.group(2)),
+           "source": f"ncu capture (profiles/{profile}), not this run"}
+    for label, key in (("L2 (lts) throughput, % of peak", "l2_throughput_pct_of_peak"),
+                       ("DRAM throughput, % of peak", "dram_throughput_pct_of_peak"),
+                       ("issue slots active", "issue_slots_active_pct")):
+        v = profile_figure(profile, label)
+        if v is not None:
+            out[key] = v
+    return out
 
 
 SERVE_WORKLOAD = ("serve: Poisson arrivals at 200 req/s over 8 resident scenes (the tiny scene + 7 medium-style "
@@ -704,7 +1122,7 @@ def cpu_baseline(scene, motions, budget_s):
                            "sample": f"a seeded eighth of one frame's pixels, 1 thread, {t1:.1f} s"}}
 
 
-def run_reference(args, world, rank, local):
+def run_reference_medium(args, world, rank, local):
     if rank != 0:
         return
     s = g.medium_scene()
@@ -716,7 +1134,7 @@ def run_reference(args, world, rank, local):
     n_pix = s.width * s.height
     sample = max(1, n_pix // 8)
     rng = np.random.default_rng(7)
-    times, rays = [], 0
+    times, rays, closest = [], 0, 0
     for k in range(n_frames):
         pix = np.sort(rng.choice(n_pix, sample, replace=False)).astype(np.uint32)
         t0 = time.perf_counter()
@@ -726,16 +1144,17 @@ def run_reference(args, world, rank, local):
         if k >= args.warmup:
             times.append(dt)
             rays += r["closest_rays"] + r["shadow_rays"]
+            closest += r["closest_rays"]
     total = sum(times)
     cores = len(os.sched_getaffinity(0))
-    value = round(rays / total / 1e6, 3)
+    value = round(closest / total / 1e6, 3)
     ts = sorted(times)
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total * 1e3 / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded procedural scene)",
-        "config": {"workload": WORKLOAD, "width": s.width, "height": s.height, "max_depth": s.max_depth,
+        "config": {"workload": MEDIUM_WORKLOAD, "width": s.width, "height": s.height, "max_depth": s.max_depth,
                    "sample_pixels_per_step": sample, "p50_ms": round(ts[len(ts) // 2] * 1e3, 3),
                    "p99_ms": round(ts[-1] * 1e3, 3), "parallelism": "host threads"},
         "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": "Mrays/s",
@@ -745,103 +1164,60 @@ def run_reference(args, world, rank, local):
     print(json.dumps(out), flush=True)
 
 
-LARGE_WORKLOAD = ("large: 4096 instances of 16 procedural meshes (1,938,944 unique / ~60M instanced tris), per step "
-                  "seeded motion + full TLAS rebuild + 16,777,216 closest-hit and 16,777,216 any-hit rays "
-                  "(origins uniform in the scene box, directions uniform, any-hit length U(1,50))")
+
+REF_SAMPLE = 65536
 
 
-def run_native_large(args, world, rank, local):
-    """Incoherent ray queries: per step a TLAS rebuild and one closest-hit and
-    one any-hit launch of 2^24 rays each (inputs larger than L2)."""
-    import torch
-    import paper_2001_09792_gb300 as rg
-    from paper_2001_09792_gb300 import _build
-
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    _build.build()
+def run_reference_large(args, world, rank, local):
+    """The oracle on the large workload, on the host cores: per step the
+    step's motion (the oracle's instance BVH rebuilt), then a seeded sample of
+    REF_SAMPLE closest-hit and REF_SAMPLE any-hit rays of the step's ray sets;
+    value = closest-hit rays per second of the steps, as in the native arm."""
+    if rank != 0:
+        return
+    import oracle
     s = g.large_scene()
-    n = 1 << 24
+    n = args.rays
     closest, anyhit = g.large_rays(s, n)
     n_frames = args.warmup + args.steps
-    gs = rg.GpuScene(s, flags=rg.RG_SCENE_TIMING | path_flag(args))
-    blas_ids = [gs.blas[m] for m in s.mesh_id]
-    inst_dev = [torch.from_numpy(rg.pack_instances(g.motion(s.M, k), blas_ids, s.material_id)).cuda()
-                for k in range(min(n_frames, 8))]
-    d_c, d_a = torch.from_numpy(closest).cuda(), torch.from_numpy(anyhit).cuda()
-    h_c = torch.empty((n, 5), dtype=torch.int32, device="cuda")
-    h_a = torch.empty((n, 5), dtype=torch.int32, device="cuda")
-    stream = torch.cuda.current_stream()
+    motions = [g.motion(s.M, k) for k in range(min(n_frames, 8))]
+    O = oracle.OracleScene(s)
+    rng = np.random.default_rng(7)
+    times = []
+    for k in range(n_frames):
+        ic = np.sort(rng.choice(n, REF_SAMPLE, replace=False))
+        ia = np.sort(rng.choice(n, REF_SAMPLE, replace=False))
+        t0 = time.perf_counter()
+        O.set_instances(motions[k % len(motions)], s.mesh_id, s.material_id)
+        O.trace(closest[ic])
+        O.trace(anyhit[ia], any_hit=True)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    cores = len(os.sched_getaffinity(0))
+    value = round(REF_SAMPLE * len(times) / total / 1e6, 4)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total * 1e3 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded procedural scene and rays)",
+        "config": {"workload": LARGE_WORKLOAD, "sample_closest_rays_per_step": REF_SAMPLE,
+                   "sample_any_hit_rays_per_step": REF_SAMPLE, "p50_ms": round(pct(times, 0.5) * 1e3, 3),
+                   "p99_ms": round(pct(times, 0.99) * 1e3, 3), "parallelism": "host threads"},
+        "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": "Mrays/s",
+                         "sample": f"per step: instance BVH rebuild, then {REF_SAMPLE} seeded closest-hit and "
+                                   f"{REF_SAMPLE} any-hit rays of the 16,777,216 of each kind, float64, {cores} threads"},
+        "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
 
-    def step(k):
-        rg.rg_tlas_build(gs.h, inst_dev[k % len(inst_dev)])
-        rg.rg_trace_rays(gs.h, d_c, rg.RG_CLOSEST, h_c)
-        rg.rg_trace_rays(gs.h, d_a, rg.RG_ANY, h_a)
 
-    for k in range(args.warmup):
-        step(k)
-    torch.cuda.synchronize()
-    with rg.GpuScene(s, flags=rg.RG_SCENE_COUNT | path_flag(args)) as gc:
-        rg.rg_tlas_build(gc.h, torch.from_numpy(rg.pack_instances(g.motion(s.M, 0), [gc.blas[m] for m in s.mesh_id],
-                                                                  s.material_id)).cuda())
-        rg.rg_reset_stats(gc.h)
-        rg.rg_trace_rays(gc.h, d_c, rg.RG_CLOSEST | rg.RG_TRACE_STATS, h_c)
-        cst = rg.rg_get_stats(gc.h)
-    rg.rg_sync(gs.h)
-    rg.rg_reset_stats(gs.h)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(gpu_index(local))
-    clocks.start()
-    ev = []
-    for k in range(args.warmup, n_frames):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step(k)
-        e1.record(stream)
-        ev.append((e0, e1))
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
-    ms = [a.elapsed_time(b) for a, b in ev]
-    st = rg.rg_get_stats(gs.h)
-    rg.rg_sync(gs.h)
-    rays = st["closest_rays"] + st["shadow_rays"]
-    (total_s_all,), (rays_all,) = reduce_over_ranks([sum(ms) / 1e3], [float(rays)], "cuda")
-    if rank == 0:
-        peak, peak_kind = measured_peaks()
-        cr = max(cst["closest_rays"], 1)
-        bpr = 32 + 20 + node_bytes(args) * cst["node_visits"] / cr + 48 * cst["tri_tests"] / cr + 80 * cst["inst_entries"] / cr
-        launch_ms = st["trace_ms"] / max(st["trace_launches"], 1)
-        achieved = bpr * (st["closest_rays"] / max(st["trace_launches"], 1)) / (launch_ms / 1e3) / 1e9
-        ms_sorted = sorted(ms)
-        out = {"metric": METRIC, "value": round(rays_all / total_s_all / 1e6, 2), "unit": "Mrays/s", "n_gpus": world,
-               "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_s_all * 1e3 / args.steps, 3),
-               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-               "data": "synthetic (seeded procedural scene and rays)",
-               "config": {"workload": LARGE_WORKLOAD, "rays_per_step": 2 * n, "instances": s.n_instances,
-                          "closest_mrays_s": round(st["closest_rays"] / (sum(ms) / 1e3) / 1e6, 2),
-                          "closest_ms": round(launch_ms, 3), "any_ms": round(st["any_ms"] / max(st["any_launches"], 1), 3),
-                          "refine_ms": round(st["refine_ms"] / max(st["refine_launches"], 1), 3),
-                          "p50_ms": round(ms_sorted[len(ms) // 2], 3), "p99_ms": round(ms_sorted[-1], 3),
-                          "l2": "inputs larger than L2 (2 x 512 MiB of rays, ~220 MB of BVH)",
-                          "parallelism": f"replicas x{world}", "bvh": "compressed 8-wide" if args.compressed else "binary float32"},
-               "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                            "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
-                            "kernel": kernel_name(args, "rg_trace_rays"), "algorithmic_bytes_per_ray": round(bpr, 1),
-                            "nodes_per_ray": round(cst["node_visits"] / cr, 2),
-                            "tris_per_ray": round(cst["tri_tests"] / cr, 2),
-                            "inst_per_ray": round(cst["inst_entries"] / cr, 3)},
-               "gpu_launches": int(st["kernel_launches"])}
-        if clk:
-            out["clocks"] = clk
-        print(json.dumps(out), flush=True)
-    gs.close()
+def run_reference(args, world, rank, local):
+    if args.workload == "medium":
+        run_reference_medium(args, world, rank, local)
+    else:
+        run_reference_large(args, world, rank, local)
 
 
 def run_native_serve(args, world, rank, local):
@@ -871,7 +1247,7 @@ def main():
     elif args.workload == "serve":
         run_native_serve(args, world, rank, local)
     else:
-        run_native(args, world, rank, local)
+        run_native_medium(args, world, rank, local)
 
 
 if __name__ == "__main__":

@@ -158,3 +158,36 @@ def test_profile_summaries_name_committed_commands():
         for c in cmds:
             assert "--clock-control none" in c, (path, c[:80])
             assert "python bench.py" in c and "_work" not in c, (path, c[:80])
+
+
+def test_large_profile_carries_the_values_the_bench_reads():
+    txt = open(os.path.join(bench.ROOT, "profiles", "trace_large.md")).read()
+    for key in ("traversal_code_sha256_16:", "dram_bytes_per_closest_launch:", "warp_inst_per_closest_ray:"):
+        assert key in txt, key
+    rec = bench.traffic_record("trace_large.md", "dram_bytes_per_closest_launch")
+    if rec is None:
+        pytest.skip("traversal sources changed since the capture (the bench then reports traffic null)")
+    # more than the rays read and the hit records written, far less than the counted bytes
+    assert (1 << 24) * (32 + 20) < rec < 51.7e9
+
+
+def test_ray_bytes_counts_ray_hit_nodes_triangles_and_instances():
+    cst = {"closest_rays": 10, "node_visits": 30, "tri_tests": 20, "inst_entries": 10,
+           "shadow_rays": 5, "any_node_visits": 5, "any_tri_tests": 0, "any_inst_entries": 5}
+    assert bench.ray_bytes(cst, 64, False) == 32 + 20 + 64 * 3 + 48 * 2 + 80 * 1
+    assert bench.ray_bytes(cst, 80, True) == 32 + 20 + 80 * 1 + 0 + 80 * 1
+
+
+def test_hit_error_summary_counts_differing_ids_and_relative_errors():
+    import numpy as np
+    miss = np.uint32(0xFFFFFFFF)
+    ref = {"inst": np.array([0, 1, 2, miss], np.uint32), "prim": np.array([5, 6, 7, miss], np.uint32),
+           "t": np.array([10.0, 20.0, 30.0, np.inf]), "u": np.array([0.5, 0.0001, 0.2, 0.0]),
+           "v": np.array([0.25, 0.5, 0.3, 0.0]), "ambiguous": np.array([False, False, True, False])}
+    h = {"inst": np.array([0, 1, 3, miss], np.uint32), "prim": np.array([5, 6, 7, miss], np.uint32),
+         "t": np.array([10.0001, 20.0, 31.0, np.inf], np.float32), "u": np.array([0.5, 0.0001 + 1e-9, 0.2, 0.0], np.float32),
+         "v": np.array([0.25, 0.5, 0.3, 0.0], np.float32)}
+    e = bench.hit_error_vs_oracle(h, ref)
+    assert e["rays"] == 4 and e["hits"] == 2 and e["id_differ"] == 1 and e["id_differ_flagged"] == 1
+    assert abs(e["t_rel"]["max"] - 1e-5) < 1e-7          # 10.0001 vs 10 (float32 rounding of 10.0001)
+    assert e["u_rel"]["max"] < 2e-6                        # 1e-9 against max(1e-4, 1e-3)
