@@ -433,14 +433,17 @@ rg_status rg_server_get_stats(rg_server* server, rg_server_stats* out);
 
 /* Launch shapes of the server's two traversals (which: 0 closest hit,
  * 1 shadow): threads per block 64 / 128 / 256, resident blocks per SM
- * (0 = as many as fit) and how many of a warp's 32 lanes must have finished
+ * (0 = as many as fit), how many of a warp's 32 lanes must have finished
  * their rays before the warp fetches new ones (1..32; 32 = only when all
- * have, a leaner loop; 0 = the default, 32). */
-typedef struct { uint32_t block, blocks_per_sm, refill; float ms; } rg_trace_shape;
+ * have, a leaner loop; 0 = the default, 32), and the short traversal stack:
+ * how many of a thread's stack entries live in shared memory, the rest in
+ * local memory (the benchmark spec's short stack; 0, or 8 or 16 with 128 threads per
+ * block; else RG_ERR_INVALID_ARG). */
+typedef struct { uint32_t block, blocks_per_sm, refill, stack; float ms; } rg_trace_shape;
 rg_status rg_server_set_shape(rg_server* server, uint32_t which, const rg_trace_shape* shape);
 rg_status rg_server_get_shape(rg_server* server, uint32_t which, rg_trace_shape* out);
 /* Autotuner: picks both shapes by timing every candidate (block x blocks per
- * SM x refill) on the sample request's rays (its primary rays for the closest
+ * SM x refill x short-stack depth) on the sample request's rays (its primary rays for the closest
  * traversal, the shadow rays their shading spawns for the shadow traversal),
  * sets them, and reports them in out[0..1] (ms = best time of that
  * traversal).  cache_path (may be NULL): a JSON file; if it holds shapes for

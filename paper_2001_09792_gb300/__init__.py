@@ -107,7 +107,7 @@ class rg_server_stats(ctypes.Structure):
 
 class rg_trace_shape(ctypes.Structure):
     _fields_ = [("block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32), ("refill", ctypes.c_uint32),
-                ("ms", ctypes.c_float)]
+                ("stack", ctypes.c_uint32), ("ms", ctypes.c_float)]
 
 
 class RgError(RuntimeError):
@@ -543,15 +543,15 @@ def rg_server_get_stats(server):
     return {k: getattr(st, k) for k, _ in rg_server_stats._fields_}
 
 
-def rg_server_set_shape(server, which, block, blocks_per_sm, refill):
-    sh = rg_trace_shape(int(block), int(blocks_per_sm), int(refill), 0.0)
+def rg_server_set_shape(server, which, block, blocks_per_sm, refill, stack=0):
+    sh = rg_trace_shape(int(block), int(blocks_per_sm), int(refill), int(stack), 0.0)
     _check(lib().rg_server_set_shape(server, int(which), ctypes.byref(sh)))
 
 
 def rg_server_get_shape(server, which):
     sh = rg_trace_shape()
     _check(lib().rg_server_get_shape(server, int(which), ctypes.byref(sh)))
-    return dict(block=sh.block, blocks_per_sm=sh.blocks_per_sm, refill=sh.refill)
+    return dict(block=sh.block, blocks_per_sm=sh.blocks_per_sm, refill=sh.refill, stack=sh.stack)
 
 
 def rg_server_autotune(server, scene_id, camera, width, height, max_depth, image, cache_path=None, force=False):
@@ -559,7 +559,7 @@ def rg_server_autotune(server, scene_id, camera, width, height, max_depth, image
     out = (rg_trace_shape * 2)()
     path = cache_path.encode() if cache_path else None
     _check(lib().rg_server_autotune(server, ctypes.byref(q), path, RG_TUNE_FORCE if force else 0, out))
-    return [dict(block=o.block, blocks_per_sm=o.blocks_per_sm, refill=o.refill, ms=o.ms) for o in out]
+    return [dict(block=o.block, blocks_per_sm=o.blocks_per_sm, refill=o.refill, stack=o.stack, ms=o.ms) for o in out]
 
 
 # ---------------------------------------------------------------- convenience

@@ -236,6 +236,7 @@ struct TraceShape {
     int block = 128;
     int blocks_per_sm = 0;
     int refill = 0;
+    int stack = 0;  // batched modes at 128 threads: short-stack entries in shared memory (0, 8 or 16)
 };
 struct TraceArgs {
     const float4* rays;          // n x 2 float4 {o, tmin}, {d, tmax}
@@ -274,6 +275,7 @@ struct TraceArgs {
     uint32_t stack_max;
 };
 constexpr uint32_t kTraceStack = 64;  // binary traversal stack entries per thread
+
 constexpr uint32_t kMaxLights = 64;  // lights per scene (one shadow sub-queue each)
 cudaError_t launch_trace(int mode, bool brute, bool stats, const TraceArgs& a, cudaStream_t s,
                          const TraceShape& shape = TraceShape());

@@ -601,12 +601,15 @@ bool read_num(const std::string& line, const std::string& key, long* v) {
 }
 
 bool parse_shape(const std::string& obj, TraceShape* sh) {
-    long b, bps, g;
+    long b, bps, g, st = 0;
     if (!read_num(obj, "block", &b) || !read_num(obj, "blocks_per_sm", &bps) || !read_num(obj, "refill", &g)) return false;
+    read_num(obj, "stack", &st);  // absent in caches written before the short stack: 0
     if ((b != 64 && b != 128 && b != 256) || bps < 0 || bps > 64 || g < 0 || g > 32) return false;
+    if (!(st == 0 || (b == 128 && (st == 8 || st == 16)))) return false;
     sh->block = (int)b;
     sh->blocks_per_sm = (int)bps;
     sh->refill = (int)g;
+    sh->stack = (int)st;
     return true;
 }
 
@@ -647,8 +650,8 @@ bool cache_lookup(const char* path, const std::string& dev, int sms, TraceShape 
 
 std::string shape_json(const TraceShape& t, float ms) {
     char buf[160];
-    std::snprintf(buf, sizeof buf, "{\"block\": %d, \"blocks_per_sm\": %d, \"refill\": %d, \"ms\": %.4f}", t.block,
-                  t.blocks_per_sm, t.refill, ms);
+    std::snprintf(buf, sizeof buf, "{\"block\": %d, \"blocks_per_sm\": %d, \"refill\": %d, \"stack\": %d, \"ms\": %.4f}",
+                  t.block, t.blocks_per_sm, t.refill, t.stack, ms);
     return buf;
 }
 
@@ -889,9 +892,12 @@ rg_status rg_server_set_shape(rg_server* s, uint32_t which, const rg_trace_shape
     if (which > 1 || !sh) return sfail(RG_ERR_INVALID_ARG, "bad shape selector");
     if ((sh->block != 64 && sh->block != 128 && sh->block != 256) || sh->blocks_per_sm > 64 || sh->refill > 32)
         return sfail(RG_ERR_INVALID_ARG, "bad launch shape");
+    if (!(sh->stack == 0 || (sh->block == 128 && (sh->stack == 8 || sh->stack == 16))))
+        return sfail(RG_ERR_INVALID_ARG, "short stack: 0, or 8 or 16 entries with 128 threads per block");
     s->shape[which].block = (int)sh->block;
     s->shape[which].blocks_per_sm = (int)sh->blocks_per_sm;
     s->shape[which].refill = (int)sh->refill;
+    s->shape[which].stack = (int)sh->stack;
     drop_step_graph(s);
     return RG_OK;
 }
@@ -903,6 +909,7 @@ rg_status rg_server_get_shape(rg_server* s, uint32_t which, rg_trace_shape* out)
     out->block = (uint32_t)s->shape[which].block;
     out->blocks_per_sm = (uint32_t)s->shape[which].blocks_per_sm;
     out->refill = (uint32_t)s->shape[which].refill;
+    out->stack = (uint32_t)s->shape[which].stack;
     out->ms = -1.0f;
     return RG_OK;
 }
@@ -936,7 +943,7 @@ rg_status rg_server_autotune(rg_server* s, const rg_request* sample, const char*
         if (r) return r;
         SV_CK(cudaMemcpyAsync(s->d_tune_count, &m, 4, cudaMemcpyHostToDevice, s->stream));
         SV_CK(cudaStreamSynchronize(s->stream));
-        const int blocks[3] = {64, 128, 256}, bps[3] = {0, 4, 8}, refills[4] = {8, 16, 24, 32};
+        const int blocks[3] = {64, 128, 256}, bps[3] = {0, 4, 8}, refills[4] = {8, 16, 24, 32}, stacks[3] = {0, 8, 16};
         auto time_one = [&](int which, const TraceShape& t, float* ms) -> rg_status {
             float best_t = 1e30f;
             for (int rep = 0; rep < 4; ++rep) {
@@ -968,18 +975,21 @@ rg_status rg_server_autotune(rg_server* s, const rg_request* sample, const char*
             best_ms[which] = 1e30f;
             for (int b : blocks)
                 for (int q : bps)
-                    for (int g : refills) {
-                        TraceShape t;
-                        t.block = b;
-                        t.blocks_per_sm = q;
-                        t.refill = g;
-                        float ms;
-                        if ((r = time_one(which, t, &ms))) return r;
-                        if (ms < best_ms[which]) {
-                            best_ms[which] = ms;
-                            best[which] = t;
+                    for (int g : refills)
+                        for (int sd : stacks) {
+                            if (sd && b != 128) continue;  // short stacks are compiled for 128 threads
+                            TraceShape t;
+                            t.block = b;
+                            t.blocks_per_sm = q;
+                            t.refill = g;
+                            t.stack = sd;
+                            float ms;
+                            if ((r = time_one(which, t, &ms))) return r;
+                            if (ms < best_ms[which]) {
+                                best_ms[which] = ms;
+                                best[which] = t;
+                            }
                         }
-                    }
         }
         // back to an empty ring and a free slot
         SV_CK(cudaStreamSynchronize(s->stream));
@@ -1002,6 +1012,7 @@ rg_status rg_server_autotune(rg_server* s, const rg_request* sample, const char*
             out[w].block = (uint32_t)best[w].block;
             out[w].blocks_per_sm = (uint32_t)best[w].blocks_per_sm;
             out[w].refill = (uint32_t)best[w].refill;
+            out[w].stack = (uint32_t)best[w].stack;
             out[w].ms = best_ms[w];
         }
     return RG_OK;

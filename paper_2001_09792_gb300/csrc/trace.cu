@@ -14,7 +14,7 @@ namespace {
 // counter, each lane runs its ray to completion, and the warp takes the next
 // 32 when all its lanes are done.  Best when the rays of a warp take similar
 // work (camera and secondary rays).
-template <int MODE, bool BRUTE, bool STATS, int BLOCK>
+template <int MODE, bool BRUTE, bool STATS, int BLOCK, int SD>
 __global__ void __launch_bounds__(BLOCK) k_trace_warp(TraceArgs a) {
     constexpr bool kAny = (MODE == kModeAnyAbi || MODE == kModeShadowRender || MODE == kModeShadowBatch);
     __shared__ uint32_t pre[kMaxLights + 1];
@@ -34,9 +34,9 @@ __global__ void __launch_bounds__(BLOCK) k_trace_warp(TraceArgs a) {
         const uint32_t i = base + lane;
         if (i < items) {
             if (MODE == kModeShadowRender && k > 1)
-                trace_segment<BRUTE, STATS>(a, pre, i, k, cnt);
+                trace_segment<BRUTE, STATS, BLOCK, SD>(a, pre, i, k, cnt);
             else
-                trace_ray<MODE, BRUTE, STATS>(a, pre, head, i, cnt);
+                trace_ray<MODE, BRUTE, STATS, BLOCK, SD>(a, pre, head, i, cnt);
         }
     }
     flush_counts<kAny, STATS>(a, cnt.nodes, cnt.tris, cnt.inst);
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace_warp(TraceArgs a) {
 // at the cost of a few spilled values: with several frames in flight this
 // measured 2.8 % faster than 896 threads (72 registers, no spills), one frame
 // at a time the same, and 768 threads slower than both.
-template <int SMODE, int CMODE, bool STATS, int BLOCK>
+template <int SMODE, int CMODE, bool STATS, int BLOCK, int SD>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_trace_pair(TraceArgs sa, TraceArgs ca) {
     __shared__ uint32_t pre[kMaxLights + 1];
     const uint32_t ns_rays = ray_count<SMODE == kModeShadowRender>(sa, pre);
@@ -74,15 +74,15 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_trace_pair(TraceArgs sa
             const uint32_t i = base + lane;
             if (i < ns) {
                 if (SMODE == kModeShadowRender && k > 1)
-                    trace_segment<false, STATS>(sa, pre, i, k, cs);
+                    trace_segment<false, STATS, BLOCK, SD>(sa, pre, i, k, cs);
                 else
-                    trace_ray<SMODE, false, STATS>(sa, pre, 0u, i, cs);
+                    trace_ray<SMODE, false, STATS, BLOCK, SD>(sa, pre, 0u, i, cs);
             }
         } else {
             const uint32_t b = base - ns_pad;
             if (b >= nc) break;
             const uint32_t i = b + lane;
-            if (i < nc) trace_ray<CMODE, false, STATS>(ca, nullptr, head, i, cc);
+            if (i < nc) trace_ray<CMODE, false, STATS, BLOCK, SD>(ca, nullptr, head, i, cc);
         }
     }
     flush_counts<true, STATS>(sa, cs.nodes, cs.tris, cs.inst);
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_trace_pair(TraceArgs sa
 // `refill` of them are idle, so lanes do not wait for the slowest ray of the
 // warp; that pays when ray lengths vary widely (incoherent queries) and costs
 // a warp vote per step otherwise.
-template <int MODE, bool BRUTE, bool STATS, int BLOCK>
+template <int MODE, bool BRUTE, bool STATS, int BLOCK, int SD>
 __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
     const uint32_t iter_cap = a.iter_cap;
     constexpr bool kAny = (MODE == kModeAnyAbi || MODE == kModeShadowRender || MODE == kModeShadowBatch);
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
     best.reset(0.f);
     float any_V = 0.f, any_W = 0.f, any_det = 1.f;
     bool found = false, ok = true, in_blas = false;
-    uint32_t stack[kStack];
+    ShortStack<BLOCK, SD> stack;
     int sp = 0;
     // the test limit on the stack applies to the counting instantiations only,
     // so the timed kernels compare with the constant
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
                     finished = true;
                 } else {
                     const bool first0 = visit_first0<kAny>(tn0, tf0, tn1, tf1);
-                    stack[sp++] = first0 ? n3.y : n3.x;
+                    stack.put(sp++, first0 ? n3.y : n3.x);
                     ref = first0 ? n3.x : n3.y;
                 }
             } else {
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
                 cur_id = meta1.y;
                 cur_leaf = leaf;
                 in_blas = true;
-                stack[sp++] = kMarker;
+                stack.put(sp++, kMarker);
                 ref = meta1.x;
             }
         } else {
@@ -263,12 +263,12 @@ __global__ void __launch_bounds__(BLOCK) k_trace_lane(TraceArgs a) {
         // pop what the step left (the BLAS marker brings back the world-space ray)
         if (!finished && ref == kNone) {
             if (sp > 0) {
-                ref = stack[--sp];
+                ref = stack.get(--sp);
                 if (ref == kMarker) {
                     in_blas = false;
                     nodes = tlas_nodes;
                     cr = wr;
-                    ref = sp > 0 ? stack[--sp] : kNone;
+                    ref = sp > 0 ? stack.get(--sp) : kNone;
                 }
             }
             finished = ref == kNone;
@@ -580,41 +580,48 @@ cudaError_t launch_mode8(const TraceArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int MODE, bool BRUTE, bool STATS, int BLOCK, bool LANE>
-cudaError_t launch_block(const TraceArgs& a, int blocks_per_sm, cudaStream_t s) {
-    static std::atomic<int> cached{0};  // per process; concurrent first callers store the same value
-    int per_sm = cached.load(std::memory_order_relaxed);
+// Resident blocks per SM of `kernel` with `smem` bytes of dynamic shared
+// memory (the short stack), looked up once per process and instantiation
+// (concurrent first callers store the same value).
+template <class K>
+cudaError_t resident_blocks(K kernel, int block, size_t smem, std::atomic<int>& cache, int* out) {
+    int per_sm = cache.load(std::memory_order_relaxed);
     if (per_sm == 0) {
-        cudaError_t e = LANE ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_lane<MODE, BRUTE, STATS, BLOCK>,
-                                                                             BLOCK, 0)
-                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_warp<MODE, BRUTE, STATS, BLOCK>,
-                                                                             BLOCK, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
         if (e != cudaSuccess) return e;
         if (per_sm <= 0) per_sm = 1;
-        cached.store(per_sm, std::memory_order_relaxed);
+        cache.store(per_sm, std::memory_order_relaxed);
     }
+    *out = per_sm;
+    return cudaSuccess;
+}
+
+template <int MODE, bool BRUTE, bool STATS, int BLOCK, bool LANE, int SD>
+cudaError_t launch_block(const TraceArgs& a, int blocks_per_sm, cudaStream_t s) {
+    static std::atomic<int> cached{0};
+    constexpr size_t smem = (size_t)SD * BLOCK * sizeof(uint32_t);
+    int per_sm = 0;
+    cudaError_t e = LANE ? resident_blocks(k_trace_lane<MODE, BRUTE, STATS, BLOCK, SD>, BLOCK, smem, cached, &per_sm)
+                         : resident_blocks(k_trace_warp<MODE, BRUTE, STATS, BLOCK, SD>, BLOCK, smem, cached, &per_sm);
+    if (e != cudaSuccess) return e;
     const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
     if (LANE)
-        k_trace_lane<MODE, BRUTE, STATS, BLOCK><<<device_sm_count() * b, BLOCK, 0, s>>>(a);
+        k_trace_lane<MODE, BRUTE, STATS, BLOCK, SD><<<device_sm_count() * b, BLOCK, smem, s>>>(a);
     else
-        k_trace_warp<MODE, BRUTE, STATS, BLOCK><<<device_sm_count() * b, BLOCK, 0, s>>>(a);
+        k_trace_warp<MODE, BRUTE, STATS, BLOCK, SD><<<device_sm_count() * b, BLOCK, smem, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
 
-template <int SMODE, int CMODE, bool STATS, int BLOCK>
+template <int SMODE, int CMODE, bool STATS, int BLOCK, int SD>
 cudaError_t launch_pair_t(const TraceArgs& sa, const TraceArgs& ca, int blocks_per_sm, cudaStream_t s) {
-    static std::atomic<int> cached{0};  // per process; concurrent first callers store the same value
-    int per_sm = cached.load(std::memory_order_relaxed);
-    if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_pair<SMODE, CMODE, STATS, BLOCK>,
-                                                                      BLOCK, 0);
-        if (e != cudaSuccess) return e;
-        if (per_sm <= 0) per_sm = 1;
-        cached.store(per_sm, std::memory_order_relaxed);
-    }
+    static std::atomic<int> cached{0};
+    constexpr size_t smem = (size_t)SD * BLOCK * sizeof(uint32_t);
+    int per_sm = 0;
+    cudaError_t e = resident_blocks(k_trace_pair<SMODE, CMODE, STATS, BLOCK, SD>, BLOCK, smem, cached, &per_sm);
+    if (e != cudaSuccess) return e;
     const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
-    k_trace_pair<SMODE, CMODE, STATS, BLOCK><<<device_sm_count() * b, BLOCK, 0, s>>>(sa, ca);
+    k_trace_pair<SMODE, CMODE, STATS, BLOCK, SD><<<device_sm_count() * b, BLOCK, smem, s>>>(sa, ca);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -628,9 +635,23 @@ constexpr int default_refill() {
     return MODE == kModeClosestAbi ? 8 : 32;
 }
 
-// Shapes other than 128 threads are compiled for the render and batched modes
-// (the ones the autotuner sets); the rest run with 128.  refill < 32 selects
-// the per-lane-refill kernel, 32 the whole-warp one.
+// Launch of one binary-traversal mode.  Shapes other than 128 threads are
+// compiled for the render and batched modes (the ones the autotuner sets);
+// the rest run with 128.  refill < 32 selects the per-lane-refill kernel, 32
+// the whole-warp one.  The batched modes at 128 threads are also compiled with
+// a short stack of 8 or 16 entries in shared memory (shape.stack), which the
+// autotuner chooses among; everything else keeps the whole stack in local
+// memory (measured fastest for the render and query kernels).
+template <int MODE, bool BRUTE, bool STATS, bool LANE>
+cudaError_t launch_block_128(const TraceArgs& a, const TraceShape& shape, cudaStream_t s) {
+    constexpr bool kBatch = MODE == kModeClosestBatch || MODE == kModeShadowBatch;
+    if constexpr (kBatch && !BRUTE && !STATS) {
+        if (shape.stack == 8) return launch_block<MODE, BRUTE, STATS, 128, LANE, 8>(a, shape.blocks_per_sm, s);
+        if (shape.stack == 16) return launch_block<MODE, BRUTE, STATS, 128, LANE, 16>(a, shape.blocks_per_sm, s);
+    }
+    return launch_block<MODE, BRUTE, STATS, 128, LANE, 0>(a, shape.blocks_per_sm, s);
+}
+
 template <int MODE, bool BRUTE, bool STATS>
 cudaError_t launch_mode(const TraceArgs& a0, cudaStream_t s, const TraceShape& shape = TraceShape()) {
     TraceArgs a = a0;
@@ -639,16 +660,16 @@ cudaError_t launch_mode(const TraceArgs& a0, cudaStream_t s, const TraceShape& s
     constexpr bool kTunable = !BRUTE && !STATS && MODE >= kModeClosestRender;
     if (refill < 32) {
         if constexpr (kTunable) {
-            if (shape.block == 64) return launch_block<MODE, BRUTE, STATS, 64, true>(a, shape.blocks_per_sm, s);
-            if (shape.block == 256) return launch_block<MODE, BRUTE, STATS, 256, true>(a, shape.blocks_per_sm, s);
+            if (shape.block == 64) return launch_block<MODE, BRUTE, STATS, 64, true, 0>(a, shape.blocks_per_sm, s);
+            if (shape.block == 256) return launch_block<MODE, BRUTE, STATS, 256, true, 0>(a, shape.blocks_per_sm, s);
         }
-        return launch_block<MODE, BRUTE, STATS, 128, true>(a, shape.blocks_per_sm, s);
+        return launch_block_128<MODE, BRUTE, STATS, true>(a, shape, s);
     }
     if constexpr (kTunable) {
-        if (shape.block == 64) return launch_block<MODE, BRUTE, STATS, 64, false>(a, shape.blocks_per_sm, s);
-        if (shape.block == 256) return launch_block<MODE, BRUTE, STATS, 256, false>(a, shape.blocks_per_sm, s);
+        if (shape.block == 64) return launch_block<MODE, BRUTE, STATS, 64, false, 0>(a, shape.blocks_per_sm, s);
+        if (shape.block == 256) return launch_block<MODE, BRUTE, STATS, 256, false, 0>(a, shape.blocks_per_sm, s);
     }
-    return launch_block<MODE, BRUTE, STATS, 128, false>(a, shape.blocks_per_sm, s);
+    return launch_block_128<MODE, BRUTE, STATS, false>(a, shape, s);
 }
 
 // Completes the provisional ABI hit records of a traversal launch (emit):
@@ -758,13 +779,17 @@ cudaError_t launch_trace_pair(bool batch, bool stats, const TraceArgs& sa, const
     if (batch) {
         if (stats) return cudaErrorInvalidValue;
         if (shape.block == 64)
-            return launch_pair_t<kModeShadowBatch, kModeClosestBatch, false, 64>(sa, ca, shape.blocks_per_sm, s);
+            return launch_pair_t<kModeShadowBatch, kModeClosestBatch, false, 64, 0>(sa, ca, shape.blocks_per_sm, s);
         if (shape.block == 256)
-            return launch_pair_t<kModeShadowBatch, kModeClosestBatch, false, 256>(sa, ca, shape.blocks_per_sm, s);
-        return launch_pair_t<kModeShadowBatch, kModeClosestBatch, false, 128>(sa, ca, shape.blocks_per_sm, s);
+            return launch_pair_t<kModeShadowBatch, kModeClosestBatch, false, 256, 0>(sa, ca, shape.blocks_per_sm, s);
+        if (shape.stack == 8)
+            return launch_pair_t<kModeShadowBatch, kModeClosestBatch, false, 128, 8>(sa, ca, shape.blocks_per_sm, s);
+        if (shape.stack == 16)
+            return launch_pair_t<kModeShadowBatch, kModeClosestBatch, false, 128, 16>(sa, ca, shape.blocks_per_sm, s);
+        return launch_pair_t<kModeShadowBatch, kModeClosestBatch, false, 128, 0>(sa, ca, shape.blocks_per_sm, s);
     }
-    return stats ? launch_pair_t<kModeShadowRender, kModeClosestRender, true, kTraceBlock>(sa, ca, 0, s)
-                 : launch_pair_t<kModeShadowRender, kModeClosestRender, false, kTraceBlock>(sa, ca, 0, s);
+    return stats ? launch_pair_t<kModeShadowRender, kModeClosestRender, true, kTraceBlock, 0>(sa, ca, 0, s)
+                 : launch_pair_t<kModeShadowRender, kModeClosestRender, false, kTraceBlock, 0>(sa, ca, 0, s);
 }
 
 }  // namespace rg

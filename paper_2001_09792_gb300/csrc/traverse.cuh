@@ -35,6 +35,27 @@ namespace {
 
 constexpr int kStack = (int)kTraceStack;
 constexpr uint32_t kMarker = 0xFFFFFFFEu;
+
+// Short traversal stack: the first SD entries of each thread's stack live in
+// the block's dynamic shared memory, the deeper ones in the thread's local
+// array (cached in L1).  Column layout: entry k of thread t is
+// rg_sstack[k * BLOCK + t], so the lanes of a warp touch 32 different banks
+// whatever depths they are at.  SD = 0 is the plain local-memory stack.
+extern __shared__ uint32_t rg_sstack[];
+
+template <int BLOCK, int SD>
+struct ShortStack {
+    uint32_t lo[kTraceStack];
+    __device__ __forceinline__ void put(int i, uint32_t v) {
+        if (SD > 0 && i < SD)
+            rg_sstack[i * BLOCK + threadIdx.x] = v;
+        else
+            lo[i] = v;
+    }
+    __device__ __forceinline__ uint32_t get(int i) const {
+        return (SD > 0 && i < SD) ? rg_sstack[i * BLOCK + threadIdx.x] : lo[i];
+    }
+};
 constexpr int kTraceBlock = 128;
 // 1 + 2 * gamma_3, gamma_3 = 3u / (1 - 3u), u = 2^-24
 constexpr float kIze = 1.0f + 2.0f * (3.0f * 5.9604644775390625e-08f) / (1.0f - 3.0f * 5.9604644775390625e-08f);
@@ -337,8 +358,9 @@ struct Best2 {
 // is r0 = (origin, tmin), r1 = (direction, tmax) in world space; ANY: the
 // first hit ends it.
 // TIES (closest-hit queries of the ABI): also keep the runner-up (Best2), and
-// test triangles up to the tie band beyond the best distance.
-template <bool ANY, bool BRUTE, bool STATS, bool TIES = false>
+// test triangles up to the tie band beyond the best distance.  BLOCK: the
+// launch's threads per block (the short stack's column stride).
+template <bool ANY, bool BRUTE, bool STATS, int BLOCK, int SD, bool TIES = false>
 __device__ __forceinline__ RayHit trace_core(const TraceArgs& a, const float4* tlas_nodes, const InstDev* tlas_inst,
                                              uint32_t tlas_root, float4 r0, float4 r1, TraceCounts& cnt) {
     const uint32_t iter_cap = a.iter_cap;
@@ -358,7 +380,7 @@ __device__ __forceinline__ RayHit trace_core(const TraceArgs& a, const float4* t
     float tlim = __fmul_rn(tmax, kCullSlack);
     bool found = false;
 
-    uint32_t stack[kStack];
+    ShortStack<BLOCK, SD> stack;
     int sp = 0;
     // the test limit on the stack applies to the counting instantiations only,
     // so the timed kernels compare with the constant
@@ -379,13 +401,13 @@ __device__ __forceinline__ RayHit trace_core(const TraceArgs& a, const float4* t
         if (ref == kNone) {
             // pop, and go on with the popped entry in this iteration
             if (sp == 0) break;
-            ref = stack[--sp];
+            ref = stack.get(--sp);
             if (ref == kMarker) {
                 in_blas = false;
                 nodes = tlas_nodes;
                 cr = wr;
                 if (sp == 0) break;
-                ref = stack[--sp];  // a TLAS entry: markers never follow each other
+                ref = stack.get(--sp);  // a TLAS entry: markers never follow each other
             }
         }
         if (!(ref & kLeaf)) {
@@ -406,7 +428,7 @@ __device__ __forceinline__ RayHit trace_core(const TraceArgs& a, const float4* t
                     ok = false;
                     break;
                 }
-                stack[sp++] = farc;
+                stack.put(sp++, farc);
                 ref = nearc;
             } else if (h0) {
                 ref = n3.x;
@@ -446,7 +468,7 @@ __device__ __forceinline__ RayHit trace_core(const TraceArgs& a, const float4* t
                 ok = false;
                 break;
             }
-            stack[sp++] = kMarker;
+            stack.put(sp++, kMarker);
             ref = meta1.x;
             continue;
         }
@@ -510,7 +532,7 @@ __device__ __forceinline__ uint32_t shadow_split(const TraceArgs& a, uint32_t n)
 // inner bounds computed by one expression, so neighbouring segments share
 // their bound exactly and the closed intervals cover [tmin, tmax]; the ray is
 // unoccluded iff all its segments are.
-template <bool BRUTE, bool STATS>
+template <bool BRUTE, bool STATS, int BLOCK, int SD>
 __device__ __forceinline__ void trace_segment(const TraceArgs& a, const uint32_t* pre, uint32_t w, uint32_t k,
                                               TraceCounts& cnt) {
     const uint32_t i = w / k, seg = w - i * k;
@@ -520,7 +542,7 @@ __device__ __forceinline__ void trace_segment(const TraceArgs& a, const uint32_t
     auto bound = [&](uint32_t q) { return q == 0 ? t0 : (q == k ? t1 : __fmaf_rn(len, __fmul_rn((float)q, inv_k), t0)); };
     r0.w = bound(seg);
     r1.w = bound(seg + 1);
-    const RayHit h = trace_core<true, BRUTE, STATS>(a, a.tlas_nodes, a.inst, a.tlas_root, r0, r1, cnt);
+    const RayHit h = trace_core<true, BRUTE, STATS, BLOCK, SD>(a, a.tlas_nodes, a.inst, a.tlas_root, r0, r1, cnt);
     // low 16 bits: segments finished, high 16 bits: segments occluded (or
     // failed); the ray's last segment adds the contribution if none was, and
     // clears the count for the next launch
@@ -539,7 +561,7 @@ __device__ __forceinline__ void trace_segment(const TraceArgs& a, const uint32_t
 
 // Ray i of a queue (its entry via the sub-queues or the ring), traced and
 // written out.
-template <int MODE, bool BRUTE, bool STATS>
+template <int MODE, bool BRUTE, bool STATS, int BLOCK, int SD>
 __device__ __forceinline__ void trace_ray(const TraceArgs& a, const uint32_t* pre, uint32_t head, uint32_t i,
                                           TraceCounts& cnt) {
     constexpr bool kAny = (MODE == kModeAnyAbi || MODE == kModeShadowRender || MODE == kModeShadowBatch);
@@ -557,7 +579,8 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& a, const uint32_t* pr
         tlas_root = S->tlas_root;
     }
     const float4 r0 = __ldg(a.rays + 2 * (size_t)j), r1 = __ldg(a.rays + 2 * (size_t)j + 1);
-    const RayHit h = trace_core<kAny, BRUTE, STATS, MODE == kModeClosestAbi>(a, tlas_nodes, tlas_inst, tlas_root, r0, r1, cnt);
+    const RayHit h =
+        trace_core<kAny, BRUTE, STATS, BLOCK, SD, MODE == kModeClosestAbi>(a, tlas_nodes, tlas_inst, tlas_root, r0, r1, cnt);
     emit<MODE>(a, i, j, h.found, h.ok, h.t, h.id, h.prim, h.il, h.tl, h.id2, h.prim2, h.V, h.W, h.det);
 }
 

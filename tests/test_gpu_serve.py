@@ -178,7 +178,8 @@ def test_autotune_sets_valid_shapes_and_caches(scenes, tmp_path):
         out = rg.rg_server_autotune(srv, sid, s.camera, 480, 270, 4, scratch, cache_path=str(cache))
         for o in out:
             assert o["block"] in (64, 128, 256) and 1 <= o["refill"] <= 32 and o["ms"] > 0
-        assert rg.rg_server_get_shape(srv, 0) == {k: out[0][k] for k in ("block", "blocks_per_sm", "refill")}
+            assert o["stack"] in (0, 8, 16) and (o["stack"] == 0 or o["block"] == 128)
+        assert rg.rg_server_get_shape(srv, 0) == {k: out[0][k] for k in ("block", "blocks_per_sm", "refill", "stack")}
         st = rg.rg_server_get_stats(srv)
         assert st["active"] == 0 and st["ring_rays"] == 0
         # the tuned server still renders correctly
@@ -197,9 +198,39 @@ def test_autotune_sets_valid_shapes_and_caches(scenes, tmp_path):
     try:
         sid = rg.rg_server_add_scene(srv, gss[1].h)
         again = rg.rg_server_autotune(srv, sid, s.camera, 480, 270, 4, scratch, cache_path=str(cache))
-        assert [{k: a[k] for k in ("block", "blocks_per_sm", "refill")} for a in again] == \
-               [{k: o[k] for k in ("block", "blocks_per_sm", "refill")} for o in out]
+        assert [{k: a[k] for k in ("block", "blocks_per_sm", "refill", "stack")} for a in again] == \
+               [{k: o[k] for k in ("block", "blocks_per_sm", "refill", "stack")} for o in out]
         assert again[0]["ms"] < 0
+    finally:
+        rg.rg_server_destroy(srv)
+
+
+@pytest.mark.parametrize("stack", [8, 16])
+def test_short_stack_shapes_serve_the_same_image(scenes, stack):
+    """Both traversals with a short stack of 8 or 16 entries in shared memory
+    (the rest in local memory) give the image of the default shapes: where a
+    stack entry lives does not change the traversal."""
+    descs, gss = scenes
+    s = descs[1]
+    imgs = []
+    for sd in (0, stack):
+        srv = rg.rg_server_create(batch_rays=1 << 18)
+        try:
+            sid = rg.rg_server_add_scene(srv, gss[1].h)
+            for which in (0, 1):
+                rg.rg_server_set_shape(srv, which, 128, 0, 32, sd)
+                assert rg.rg_server_get_shape(srv, which)["stack"] == sd
+            img = torch.empty((180, 240, 4), device="cuda")
+            rg.rg_server_submit(srv, sid, s.camera, 240, 180, 6, img, s.M)
+            rg.rg_server_drain(srv)
+            imgs.append(img.cpu().numpy())
+        finally:
+            rg.rg_server_destroy(srv)
+    np.testing.assert_allclose(imgs[1], imgs[0], atol=ATOL, rtol=0)
+    srv = rg.rg_server_create()
+    try:
+        with pytest.raises(rg.RgError):
+            rg.rg_server_set_shape(srv, 0, 256, 0, 32, 8)  # short stacks only with 128 threads
     finally:
         rg.rg_server_destroy(srv)
 
