@@ -473,13 +473,29 @@ def run_medium(args, world, rank, local, embedded=False):
         # the BVH lives in L2: the traversal is bound by instruction issue, so the
         # counted bytes (mostly L1/L2 hits) over the HBM peak is no DRAM fraction;
         # the DRAM fraction is the captured traffic over the same launch time
-        roofline = {"bound": "issue", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                    "frac": round(achieved / peak, 4), "traffic": None if tr is None else round(tr),
+        # issue-bound (the BVH lives in L2): warp instructions of a frame's
+        # traversal launches (the committed capture, valid for the code it
+        # hashes) over their event-timed duration, against SMs x 4 schedulers x
+        # the maximum SM clock; the counted bytes and the captured DRAM bytes
+        # over the same time are reported beside it
+        ipf = None if args.compressed else traffic_record(prof, "warp_inst_per_frame")
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        issue_peak = sms * 4 * sm_max_mhz() * 1e6 / 1e9
+        frame_trav_ms = trav_ms / args.steps
+        ach_i = None if ipf is None else ipf / (frame_trav_ms / 1e3) / 1e9
+        roofline = {"bound": "issue", "achieved": None if ach_i is None else round(ach_i, 1),
+                    "peak": round(issue_peak, 1), "unit": "G warp-instructions/s",
+                    "frac": None if ach_i is None else round(ach_i / issue_peak, 4),
+                    "traffic": None if tr is None else round(tr),
                     "dram_frac": None if tr is None else round(tr / (launch_ms / 1e3) / 1e9 / peak, 4),
+                    "counted_bytes": {"gbs": round(achieved, 1), "frac_of_hbm": round(achieved / peak, 4),
+                                      "hbm_peak_gbs": peak, "hbm_peak_kind": peak_kind},
+                    "peak_derivation": f"{sms} SMs x 4 warp schedulers x 1 instruction/cycle x {sm_max_mhz():.0f} MHz",
+                    "warp_inst_per_frame": ipf,
                     "issue_slots_active_pct": profile_figure(prof, "issue slots active"),
-                    "bound_note": "achieved and frac: algorithmic (counted) bytes per launch over the launch time, "
-                                  "served mostly by L1/L2; dram_frac: the captured DRAM bytes over the same time; "
-                                  "issue_slots_active_pct from the committed capture",
+                    "bound_note": "achieved: warp instructions of a frame's traversal launches (committed capture) over "
+                                  "their event-timed time; counted_bytes: algorithmic bytes per launch over the launch "
+                                  "time, served mostly by L1/L2; dram_frac: the captured DRAM bytes over the same time",
                     "timed_region": "the one-in-flight pass (config.one_in_flight.ms_per_step)",
                     "kernel": kernel_name(args, "render"), "peak_kind": peak_kind,
                     "algorithmic_bytes_per_launch": round(trav_bytes / trav_launches),
@@ -549,7 +565,18 @@ def run_medium(args, world, rank, local, embedded=False):
         if not embedded and world == 1 and not args.no_serving:
             out["serving"] = run_serving(args.requests, pair=not args.no_pair)
         if not embedded and world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(s, motions[args.warmup:], args.cpu_seconds)
+            out["cpu_baseline"], ref = cpu_baseline(s, motions[args.warmup:], args.cpu_seconds)
+            # the GPU's render and camera-ray records of the oracle's first frame
+            rg.rg_tlas_build(gs.h, inst_dev[args.warmup])
+            img0 = rg.rg_render(gs.h, cam, W, H, D)
+            hits0 = rg.rg_trace_rays(gs.h, torch.from_numpy(ref["rays"]).cuda())
+            rg.rg_sync(gs.h)
+            out["error_vs_oracle"] = {
+                "pixels": pixel_error_vs_oracle(img0.cpu().numpy(), ref["frame"]),
+                "rays": hit_error_vs_oracle(rg.split_hits(hits0), ref["ray_ref"]),
+                "bvh": "compressed 8-wide" if args.compressed else "binary float32",
+                "sample": f"the whole frame of the first timed motion, and {len(ref['rays']):,} seeded camera rays of "
+                          "it traced as closest-hit queries (rg_trace_rays)"}
     for c in ctxs[1:]:
         c.close()
     gs.close()
@@ -1084,13 +1111,15 @@ def blas_build_rate(scene, reps=3):
 
 
 def oracle_frames(scene, motions, budget_s, min_frames=1):
-    """Render whole frames with the float64 oracle until the budget is spent."""
+    """Render whole frames with the float64 oracle until the budget is spent;
+    also returns the first frame's result (rgba, ambiguous flags)."""
     import oracle
     O = oracle.OracleScene(scene)
     rays = 0
     frames = 0
     t0 = time.perf_counter()
     per_frame = []
+    first = None
     for M in motions:
         f0 = time.perf_counter()
         O.set_instances(M, scene.mesh_id, scene.material_id)
@@ -1098,15 +1127,21 @@ def oracle_frames(scene, motions, budget_s, min_frames=1):
         per_frame.append(time.perf_counter() - f0)
         rays += r["closest_rays"] + r["shadow_rays"]
         frames += 1
+        if first is None:
+            first = r
         if frames >= min_frames and time.perf_counter() - t0 >= budget_s:
             break
-    return rays, time.perf_counter() - t0, frames, per_frame
+    return rays, time.perf_counter() - t0, frames, per_frame, first
 
 
-def cpu_baseline(scene, motions, budget_s):
+def cpu_baseline(scene, motions, budget_s, n_sample_rays=50_000):
+    """The oracle on the medium frames (whole frames, all host cores; one
+    thread on an eighth of a frame).  Also returns, for the error of the GPU
+    path, the first frame's oracle image and the oracle's records of a seeded
+    sample of that frame's camera rays (traced as closest-hit queries)."""
     import oracle
     cores = len(os.sched_getaffinity(0))
-    rays, secs, frames, _ = oracle_frames(scene, motions, budget_s)
+    rays, secs, frames, _, first = oracle_frames(scene, motions, budget_s)
     # one thread, on a seeded eighth of one frame's pixels
     O = oracle.OracleScene(scene)
     O.set_instances(motions[0], scene.mesh_id, scene.material_id)
@@ -1116,10 +1151,32 @@ def cpu_baseline(scene, motions, budget_s):
     r = O.render(scene.camera, scene.width, scene.height, scene.max_depth, pixels=pix, threads=1)
     t1 = time.perf_counter() - t0
     one = (r["closest_rays"] + r["shadow_rays"]) / t1 / 1e6
-    return {"value": round(rays / secs / 1e6, 3), "unit": "Mrays/s", "cores": cores, "kind": "oracle",
-            "sample": f"{frames} whole frame(s) of the same workload (float64, {cores} threads), {secs:.1f} s",
-            "one_thread": {"value": round(one, 3), "unit": "Mrays/s",
-                           "sample": f"a seeded eighth of one frame's pixels, 1 thread, {t1:.1f} s"}}
+    spix = np.sort(np.random.default_rng(8).choice(n_px, min(n_sample_rays, n_px), replace=False)).astype(np.uint32)
+    cam_rays = np.zeros((len(spix), 8), np.float32)
+    cam_rays[:, 0:3] = scene.camera["eye"]
+    cam_rays[:, 4:7] = oracle.camera_dirs(scene.camera, scene.width, scene.height, spix)
+    cam_rays[:, 7] = np.inf
+    ray_ref = O.trace(cam_rays)
+    out = {"value": round(rays / secs / 1e6, 3), "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+           "sample": f"{frames} whole frame(s) of the same workload (float64, {cores} threads), {secs:.1f} s",
+           "one_thread": {"value": round(one, 3), "unit": "Mrays/s",
+                          "sample": f"a seeded eighth of one frame's pixels, 1 thread, {t1:.1f} s"}}
+    return out, {"frame": first, "rays": cam_rays, "ray_ref": ray_ref}
+
+
+def pixel_error_vs_oracle(img, ref, tol=2e-3):
+    """Per-pixel error of an RGBA32F image against the oracle's render: the
+    largest and 99th-percentile absolute channel error over the pixels the
+    oracle does not flag, and how many pixels exceed the tolerance (all must
+    be flagged)."""
+    img = np.asarray(img, np.float64).reshape(-1, 4)
+    err = np.abs(img - ref["rgba"]).max(1)
+    ok = ~ref["ambiguous"]
+    over = err > tol
+    return {"pixels": int(len(err)), "max": float(err[ok].max(initial=0.0)),
+            "p99": float(np.quantile(err[ok], 0.99)) if ok.any() else 0.0,
+            "over_tolerance": int(over.sum()), "over_tolerance_flagged": int((over & ~ok).sum()),
+            "flagged": int((~ok).sum()), "tolerance": f"{tol} absolute per channel"}
 
 
 def run_reference_medium(args, world, rank, local):

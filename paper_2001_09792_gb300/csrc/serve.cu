@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <string>
@@ -132,6 +133,23 @@ __global__ void k_step_end(const StepHdr* __restrict__ hdr, RingState* __restric
 
 rg_status sfail(rg_status code, const std::string& msg) { return report_error(code, msg.c_str()); }
 
+// An empty ring whose positions (head, tail) start at `start`.  Positions are
+// free-running 32-bit counters (ring entries are positions masked by the
+// capacity, sizes are differences of positions), so any start is valid; the
+// tests start near 2^32 to make a run wrap the counters (RG_TEST_RING_START,
+// read when a server is created; 0 otherwise).
+cudaError_t reset_ring(RingState* d_rs, uint32_t start) {
+    RingState rs;
+    std::memset(&rs, 0, sizeof rs);
+    rs.head = rs.tail = rs.gen_base = rs.next_base = rs.cons = start;
+    return cudaMemcpy(d_rs, &rs, sizeof rs, cudaMemcpyHostToDevice);
+}
+
+uint32_t ring_start_for_tests() {
+    const char* v = std::getenv("RG_TEST_RING_START");
+    return (v && *v) ? (uint32_t)std::strtoul(v, nullptr, 0) : 0u;
+}
+
 rg_status scuda(cudaError_t e, const char* what) {
     cudaGetLastError();
     return sfail(e == cudaErrorMemoryAllocation ? RG_ERR_OOM : RG_ERR_CUDA,
@@ -221,6 +239,7 @@ struct rg_server {
     std::deque<rg_completion> done;
     uint64_t next_id = 1;
     uint32_t ring_rays_now = 0;  // tail - head after the last step
+    uint32_t ring_start = 0;     // ring position of an empty ring at creation (a test hook; 0)
     TraceShape shape[2];
     cudaGraphExec_t step_exec = nullptr;
     rg_server_stats stats{};
@@ -730,7 +749,8 @@ rg_status rg_server_create(rg_server** out, const rg_server_desc* desc) {
         return bail(sfail(RG_ERR_OOM, "pinned host buffers"));
     std::memset(s->h_hdr, 0, sizeof(StepHdr));
     std::memset(s->h_out, 0, sizeof(StepOut));
-    if (cudaMemset(s->st, 0, sizeof(DevStatus)) != cudaSuccess || cudaMemset(s->d_rs, 0, sizeof(RingState)) != cudaSuccess ||
+    s->ring_start = ring_start_for_tests();
+    if (cudaMemset(s->st, 0, sizeof(DevStatus)) != cudaSuccess || reset_ring(s->d_rs, s->ring_start) != cudaSuccess ||
         cudaMemset(s->d_hdr, 0, sizeof(StepHdr)) != cudaSuccess)
         return bail(scuda(cudaGetLastError(), "cudaMemset"));
     *out = s;
@@ -995,7 +1015,7 @@ rg_status rg_server_autotune(rg_server* s, const rg_request* sample, const char*
         SV_CK(cudaStreamSynchronize(s->stream));
         int err = 0;
         SV_CK(cudaMemcpy(&err, &s->st->error, sizeof(int), cudaMemcpyDeviceToHost));
-        SV_CK(cudaMemset(s->d_rs, 0, sizeof(RingState)));
+        SV_CK(reset_ring(s->d_rs, s->ring_start));
         SV_CK(cudaMemset(&s->st->error, 0, sizeof(int)));
         s->ring_rays_now = 0;
         for (Active& a : s->active) a = Active();

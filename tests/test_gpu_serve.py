@@ -126,6 +126,21 @@ def test_mix_equals_alone(scenes):
     check_against_alone(descs, gss, reqs, imgs, st)
 
 
+def test_ring_counters_wrap_past_2_32(scenes, monkeypatch):
+    """The ring positions are free-running 32-bit counters, so a long-running
+    server wraps them after 2^32 path rays.  A server whose empty ring starts
+    100,000 positions below 2^32 (test hook RG_TEST_RING_START, read when the
+    server is created) runs a mixed request set across the wrap: every image
+    equals its render alone, and the server traces the same rays."""
+    monkeypatch.setenv("RG_TEST_RING_START", str(2 ** 32 - 100_000))
+    descs, gss = scenes
+    reqs = make_requests(descs, 12, seed=21, sizes=[(160, 120), (320, 240), (97, 33)])
+    imgs, done, st = run_server(gss, reqs, ring_log2=20, batch_rays=1 << 16)
+    assert sorted(d["tag"] for d in done) == list(range(len(reqs)))
+    assert st["closest_rays"] > 100_000   # the head passed 2^32
+    check_against_alone(descs, gss, reqs, imgs, st)
+
+
 def test_small_ring_wraps_and_admits_mid_flight(scenes):
     descs, gss = scenes
     reqs = make_requests(descs, 20, seed=11, sizes=[(128, 96), (160, 120), (61, 17)], depths=[2, 4, 8])
