@@ -71,6 +71,7 @@ def parse(argv=None):
                    help="large: incoherent closest/any-hit queries (default); medium: the render frame; "
                         "serve: the continuous-batching render server alone")
     p.add_argument("--requests", type=int, default=400, help="serving: requests in the Poisson stream")
+    p.add_argument("--lanes", type=int, default=0, help="serving: server lanes (0: the library's default)")
     p.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     p.add_argument("--no-medium", action="store_true", help="large: skip the medium render frame")
     p.add_argument("--rays", type=int, default=N_LARGE, help="large: rays of each kind per step")
@@ -563,7 +564,7 @@ def run_medium(args, world, rank, local, embedded=False):
                                   "each image read back on a copy stream while later frames render; one timed "
                                   "region incl. L2 flushes"}
         if not embedded and world == 1 and not args.no_serving:
-            out["serving"] = run_serving(args.requests, pair=not args.no_pair)
+            out["serving"] = run_serving(args.requests, pair=not args.no_pair, lanes=args.lanes)
         if not embedded and world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"], ref = cpu_baseline(s, motions[args.warmup:], args.cpu_seconds)
             # the GPU's render and camera-ray records of the oracle's first frame
@@ -902,7 +903,7 @@ def run_native_large(args, world, rank, local):
         if not args.no_medium:
             out["medium"] = medium_summary(run_medium(args_for_medium(args), 1, 0, local, embedded=True))
         if not args.no_serving:
-            out["serving"] = run_serving(args.requests, pair=not args.no_pair)
+            out["serving"] = run_serving(args.requests, pair=not args.no_pair, lanes=args.lanes)
     else:
         gs.close()
     if rank == 0:
@@ -959,7 +960,7 @@ def pct(xs, q):
     return xs[min(len(xs) - 1, max(0, math.ceil(q * len(xs)) - 1))]
 
 
-def run_serving(n_requests, admit_rays=0, pair=True):
+def run_serving(n_requests, admit_rays=0, pair=True, lanes=0):
     """The request stream through the continuous-batching server in real time,
     then the same stream one request at a time (rg_tlas_refit + rg_render each,
     in arrival order, against the same arrival clock).  Latency = arrival to
@@ -972,7 +973,7 @@ def run_serving(n_requests, admit_rays=0, pair=True):
     gss = [rg.GpuScene(sc, flags=0 if pair else rg.RG_SCENE_NO_PAIR) for sc in scenes]
     trans = [g.motion(scenes[q["scene"]].M, q["motion_seed"]) for q in reqs]
     cams = [rg.make_camera(sc.camera) for sc in scenes]
-    srv = rg.rg_server_create(admit_rays=admit_rays, flags=0 if pair else rg.RG_SERVER_NO_PAIR)
+    srv = rg.rg_server_create(admit_rays=admit_rays, flags=0 if pair else rg.RG_SERVER_NO_PAIR, lanes=lanes)
     try:
         for gsc in gss:
             rg.rg_server_add_scene(srv, gsc.h)
@@ -1050,7 +1051,7 @@ def run_serving(n_requests, admit_rays=0, pair=True):
         "p50_ms": round(pct(lat, 0.50) * 1e3, 2), "p99_ms": round(pct(lat, 0.99) * 1e3, 2),
         "mrays_s": round(rays / (t_end - t_first) / 1e6, 2), "busy_mrays_s": round(rays / busy / 1e6, 2),
         "rays": int(rays), "steps": int(steps), "ring_peak": int(st["ring_peak"]),
-        "shapes": tuned,
+        "shapes": tuned, "lanes": lanes or 1,
         "one_at_a_time": {"p50_ms": round(pct(seq_lat, 0.50) * 1e3, 2), "p99_ms": round(pct(seq_lat, 0.99) * 1e3, 2),
                           "busy_mrays_s": round(seq_rays / seq_busy / 1e6, 2),
                           "mrays_s": round(seq_rays / (seq_end - t_first) / 1e6, 2), "rays": int(seq_rays)},
@@ -1285,7 +1286,7 @@ def run_native_serve(args, world, rank, local):
     _build.build()
     if rank != 0:
         return
-    r = run_serving(args.requests, pair=not args.no_pair)
+    r = run_serving(args.requests, pair=not args.no_pair, lanes=args.lanes)
     out = {"metric": "served Mrays/s and p50/p99 request latency (continuous batching) vs one request at a time",
            "value": r["mrays_s"], "unit": "Mrays/s", "n_gpus": 1, "steps": r["steps"], "warmup": len(g.serving_scenes()),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

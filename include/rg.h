@@ -346,10 +346,15 @@ rg_status rg_radix_sort_pairs_noalloc(const void* d_keys, const uint32_t* d_vals
  * free ring / (2 (RG_SERVER_MAX_DEPTH + 1)).  RG_ERR_OOM only if even that is
  * zero.
  *
- * Every step's device work runs on the server's own stream, as one CUDA graph
- * (captured on first use, re-captured when buffers or launch shapes change);
- * rg_server_step returns when that work has finished.  Calls on one server
- * must not run concurrently. */
+ * The server holds one or more lanes (rg_server_desc.lanes): independent
+ * rings, each with its own shadow and hit queues, request slots and stream.
+ * A request is admitted to the least loaded lane and stays there; a step
+ * runs one step of every lane with work, at the same time, so the idle tails
+ * of one lane's launches are filled by the others'.  Every lane's step is
+ * one CUDA graph on the lane's stream (captured on first use, re-captured
+ * when buffers or launch shapes change); a lane takes new requests and
+ * starts its next step only once its step in flight has been booked.  Calls
+ * on one server must not run concurrently. */
 typedef struct rg_server rg_server;
 
 #define RG_SERVER_MAX_SLOTS 32u
@@ -369,7 +374,12 @@ typedef struct {
                              0 = batch_rays (what one step can take); at most half the ring.  A
                              smaller bound keeps fewer requests in flight: large requests run closer
                              to one after another (shorter tail latency), small ones still share steps */
+    uint32_t lanes;       /* independent rings (each with its own queues, request slots and stream) whose
+                             steps run at the same time; a request lives in one lane, admitted to the
+                             least loaded; 0 = 1; at most RG_SERVER_MAX_LANES.  Every lane holds a ring,
+                             a shadow queue and a hit queue of the sizes above */
 } rg_server_desc;
+#define RG_SERVER_MAX_LANES 8u
 #define RG_SERVER_NO_GRAPH 1u
 #define RG_SERVER_NO_PAIR 2u
 
@@ -402,6 +412,8 @@ typedef struct {
     uint64_t graph_launches, graph_captures;
     uint64_t kernel_launches;               /* kernels launched by the server's steps (graph kernels included) */
     uint64_t newest_first_steps;            /* steps that took the newest rays (ring nearly full) */
+    uint64_t lane_steps;                    /* steps of the individual lanes (a server step runs those of
+                                               every lane with work) */
 } rg_server_stats;
 
 /* Creates a server on the current device (desc NULL: defaults).  Allocates the
@@ -419,8 +431,12 @@ rg_status rg_server_add_scene(rg_server* server, rg_scene* scene, uint32_t* scen
 /* Queues a request; validated here (RG_ERR_INVALID_ARG on a bad size, depth,
  * scene id or pointer). */
 rg_status rg_server_submit(rg_server* server, const rg_request* req, uint64_t* request_id);
-/* One step: admits what fits, refits the admitted requests' TLAS copies,
- * traces and shades one batch, and waits for it.  *n_completed (may be NULL)
+/* One step: admits what fits into the idle lanes, refits the admitted
+ * requests' TLAS copies, launches a step (trace and shade one batch) on every
+ * idle lane with work, each on its own stream, and returns once at least one
+ * lane's step has finished (the oldest launched is waited for; every finished
+ * one is booked); the other lanes' steps run on and are booked by later
+ * calls (rg_server_drain waits for all).  *n_completed (may be NULL)
  * = requests completed by this step; their images are final.  With nothing
  * queued or in flight the step does nothing.  Device errors (stack overflow,
  * iteration cap, singular transform, bad material) are returned here. */

@@ -82,7 +82,7 @@ class rg_stats(ctypes.Structure):
 
 class rg_server_desc(ctypes.Structure):
     _fields_ = [("ring_log2", ctypes.c_uint32), ("batch_rays", ctypes.c_uint32), ("max_lights", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32), ("admit_rays", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("admit_rays", ctypes.c_uint32), ("lanes", ctypes.c_uint32)]
 
 
 class rg_request(ctypes.Structure):
@@ -102,7 +102,7 @@ class rg_server_stats(ctypes.Structure):
                 ("pending", ctypes.c_uint32), ("active", ctypes.c_uint32), ("ring_rays", ctypes.c_uint32),
                 ("ring_peak", ctypes.c_uint32), ("graph_launches", ctypes.c_uint64),
                 ("graph_captures", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
-                ("newest_first_steps", ctypes.c_uint64)]
+                ("newest_first_steps", ctypes.c_uint64), ("lane_steps", ctypes.c_uint64)]
 
 
 class rg_trace_shape(ctypes.Structure):
@@ -477,8 +477,8 @@ def rg_tlas_export(scene, n):
 
 # ---------------------------------------------------------------- render server
 
-def rg_server_create(ring_log2=0, batch_rays=0, max_lights=0, flags=0, admit_rays=0):
-    d = rg_server_desc(int(ring_log2), int(batch_rays), int(max_lights), int(flags), int(admit_rays))
+def rg_server_create(ring_log2=0, batch_rays=0, max_lights=0, flags=0, admit_rays=0, lanes=0):
+    d = rg_server_desc(int(ring_log2), int(batch_rays), int(max_lights), int(flags), int(admit_rays), int(lanes))
     h = ctypes.c_void_p()
     _check(lib().rg_server_create(ctypes.byref(h), ctypes.byref(d)))
     return h

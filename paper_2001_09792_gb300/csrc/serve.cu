@@ -17,7 +17,13 @@
 //  * per-request TLAS: on admission, a slot's private copy of the scene's TLAS
 //    is refit with the request's instance transforms;
 //  * the step's launches and copies are one CUDA graph; each slot's refit
-//    sequence per scene is another.
+//    sequence per scene is another;
+//  * lanes: a server holds one or more independent rings (lanes), each with
+//    its own queues, request slots, stream and step graph; a request lives in
+//    one lane (admitted to the least loaded), and one server step runs a step
+//    of every lane with work at the same time, so that the idle tails of one
+//    lane's launches (the last rays of a launch, a few long ones) are filled
+//    by the others' work, as frames in flight are for rg_render.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -213,12 +219,16 @@ const char* device_error_text(int err) {
 
 }  // namespace
 
-struct rg_server {
-    int device = 0;
-    uint32_t ring_cap = 0, ring_mask = 0, batch = 0, max_lights = 0, flags = 0, admit = 0;
-    size_t shadow_cap = 0;
+// One lane by default: on the serving stream (200 requests/s, one or two in
+// flight at a time) four lanes measured 2 % more busy throughput and a worse
+// tail latency, since most of the time only one request, in one lane, has work.
+constexpr uint32_t kDefaultLanes = 1;
+
+// One lane: a ring of path rays with its queues, request slots, status word,
+// stream and step graph.
+struct Lane {
     cudaStream_t stream = nullptr;
-    cudaEvent_t done_ev = nullptr, t0 = nullptr, t1 = nullptr;
+    cudaEvent_t done_ev = nullptr;
     DevStatus* st = nullptr;
     float4* ring_rays = nullptr;
     Payload* ring_pay = nullptr;
@@ -228,20 +238,32 @@ struct rg_server {
     RingState* d_rs = nullptr;
     StepHdr* d_hdr = nullptr;
     StepOut* d_out = nullptr;
-    uint32_t* d_tune_count = nullptr;
     StepHdr* h_hdr = nullptr;
     StepOut* h_out = nullptr;
-    std::vector<SceneEntry> scenes;
-    uint32_t max_inst = 0, iter_cap = 64;
     SlotBufs slots[kMaxSlots];
     Active active[kMaxSlots];
+    uint32_t ring_rays_now = 0;  // tail - head after the lane's last step
+    uint32_t admitted = 0;       // primary rays admitted for the lane's coming step
+    cudaGraphExec_t step_exec = nullptr;
+    bool in_flight = false;      // a step launched and not yet booked
+    uint64_t launch_seq = 0;     // order of the launches in flight (the oldest is waited for)
+};
+
+struct rg_server {
+    int device = 0;
+    uint32_t ring_cap = 0, ring_mask = 0, batch = 0, max_lights = 0, flags = 0, admit = 0;
+    size_t shadow_cap = 0;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    uint32_t* d_tune_count = nullptr;
+    std::vector<Lane> lanes;
+    std::vector<SceneEntry> scenes;
+    uint32_t max_inst = 0, iter_cap = 64;
     std::deque<Pending> pending;
     std::deque<rg_completion> done;
     uint64_t next_id = 1;
-    uint32_t ring_rays_now = 0;  // tail - head after the last step
     uint32_t ring_start = 0;     // ring position of an empty ring at creation (a test hook; 0)
+    uint64_t launches = 0;       // lane steps launched so far
     TraceShape shape[2];
-    cudaGraphExec_t step_exec = nullptr;
     rg_server_stats stats{};
 };
 
@@ -255,10 +277,10 @@ rg_status set_dev(rg_server* s) {
 // Shadow rays traced by the next step, with its closest-hit rays.
 bool paired(const rg_server* s) { return !(s->flags & RG_SERVER_NO_PAIR); }
 
-// Whether a step must run although the ring is empty: paired steps leave the
-// last shadow rays of finished requests to the next step.
-bool shadow_flush_due(const rg_server* s) {
-    for (const Active& a : s->active)
+// Whether a lane's step must run although its ring is empty: paired steps
+// leave the last shadow rays of finished requests to the next step.
+bool shadow_flush_due(const Lane& L) {
+    for (const Active& a : L.active)
         if (a.on && a.flushing) return true;
     return false;
 }
@@ -277,8 +299,10 @@ void free_slot_bufs(SlotBufs& b) {
 }
 
 void drop_step_graph(rg_server* s) {
-    if (s->step_exec) cudaGraphExecDestroy(s->step_exec);
-    s->step_exec = nullptr;
+    for (Lane& L : s->lanes) {
+        if (L.step_exec) cudaGraphExecDestroy(L.step_exec);
+        L.step_exec = nullptr;
+    }
 }
 
 rg_status alloc_slot_bufs(SlotBufs& b, uint32_t n, size_t n_scenes) {
@@ -297,115 +321,114 @@ rg_status alloc_slot_bufs(SlotBufs& b, uint32_t n, size_t n_scenes) {
 
 // The refit of slot k's TLAS copy for a request of scene e (transforms already
 // in the slot's pinned staging).
-rg_status enqueue_refit(rg_server* s, uint32_t k, uint32_t e) {
+rg_status enqueue_refit(rg_server* s, Lane& L, uint32_t k, uint32_t e) {
     const SceneView& v = s->scenes[e].v;
-    SlotBufs& b = s->slots[k];
+    SlotBufs& b = L.slots[k];
     const uint32_t n = v.n_inst;
-    SV_CK(cudaMemcpyAsync(b.d_inst, b.h_inst, (size_t)n * sizeof(rg_instance), cudaMemcpyHostToDevice, s->stream));
-    SV_CK(launch_instance_prep(b.d_inst, n, v.d_blas, v.n_blas, b.inst_tmp, b.wbox, nullptr, false, s->st, s->stream));
+    SV_CK(cudaMemcpyAsync(b.d_inst, b.h_inst, (size_t)n * sizeof(rg_instance), cudaMemcpyHostToDevice, L.stream));
+    SV_CK(launch_instance_prep(b.d_inst, n, v.d_blas, v.n_blas, b.inst_tmp, b.wbox, nullptr, false, L.st, L.stream));
     if (n > 1) {
-        SV_CK(cudaMemcpyAsync(b.tlas_nodes, v.tlas_nodes, (size_t)(n - 1) * 64, cudaMemcpyDeviceToDevice, s->stream));
-        SV_CK(cudaMemsetAsync(b.flags, 0, (size_t)(n - 1) * 4, s->stream));
+        SV_CK(cudaMemcpyAsync(b.tlas_nodes, v.tlas_nodes, (size_t)(n - 1) * 64, cudaMemcpyDeviceToDevice, L.stream));
+        SV_CK(cudaMemsetAsync(b.flags, 0, (size_t)(n - 1) * 4, L.stream));
     }
-    SV_CK(launch_tlas_leaves_refit(b.inst_tmp, b.wbox, v.perm, n, v.parents, b.tlas_nodes, b.flags, b.inst, s->st,
-                                   s->stream));
+    SV_CK(launch_tlas_leaves_refit(b.inst_tmp, b.wbox, v.perm, n, v.parents, b.tlas_nodes, b.flags, b.inst, L.st,
+                                   L.stream));
     return RG_OK;
 }
 
-TraceArgs closest_args(rg_server* s, const uint32_t* d_count) {
+TraceArgs closest_args(rg_server* s, Lane& L, const uint32_t* d_count) {
     TraceArgs a{};
-    a.rays = s->ring_rays;
+    a.rays = L.ring_rays;
     a.d_count = d_count;
-    a.payload = s->ring_pay;
-    a.hits_render = s->hits;
-    a.work_counter = &s->d_rs->work_closest;
-    a.st = s->st;
+    a.payload = L.ring_pay;
+    a.hits_render = L.hits;
+    a.work_counter = &L.d_rs->work_closest;
+    a.st = L.st;
     a.iter_cap = s->iter_cap;
-    a.slots = s->d_hdr->slots;
-    a.ring_head = &s->d_rs->cons;
+    a.slots = L.d_hdr->slots;
+    a.ring_head = &L.d_rs->cons;
     a.ring_mask = s->ring_mask;
     return a;
 }
 
-TraceArgs shadow_args(rg_server* s, const uint32_t* counts) {
+TraceArgs shadow_args(rg_server* s, Lane& L, const uint32_t* counts) {
     TraceArgs b{};
-    b.rays = s->s_rays;
+    b.rays = L.s_rays;
     b.sub_counts = counts;
     b.n_sub = s->max_lights;
     b.sub_stride = s->batch;
-    b.payload = s->s_pay;
-    b.work_counter = &s->d_rs->work_shadow;
-    b.st = s->st;
+    b.payload = L.s_pay;
+    b.work_counter = &L.d_rs->work_shadow;
+    b.st = L.st;
     b.iter_cap = s->iter_cap;
-    b.slots = s->d_hdr->slots;
+    b.slots = L.d_hdr->slots;
     return b;
 }
 
-ShadeArgs shade_args(rg_server* s, const uint32_t* d_count) {
+ShadeArgs shade_args(rg_server* s, Lane& L, const uint32_t* d_count) {
     ShadeArgs a{};
-    a.rays = s->ring_rays;
-    a.payload = s->ring_pay;
-    a.hits = s->hits;
+    a.rays = L.ring_rays;
+    a.payload = L.ring_pay;
+    a.hits = L.hits;
     a.d_count = d_count;
-    a.next_rays = s->ring_rays;
-    a.next_payload = s->ring_pay;
-    a.next_count = &s->d_rs->next_count;
-    a.shadow_rays = s->s_rays;
-    a.shadow_payload = s->s_pay;
-    a.shadow_count = s->d_rs->shadow_count;
+    a.next_rays = L.ring_rays;
+    a.next_payload = L.ring_pay;
+    a.next_count = &L.d_rs->next_count;
+    a.shadow_rays = L.s_rays;
+    a.shadow_payload = L.s_pay;
+    a.shadow_count = L.d_rs->shadow_count;
     a.shadow_stride = s->batch;
     a.max_lights = s->max_lights;
-    a.st = s->st;
-    a.slots = s->d_hdr->slots;
-    a.slot_live = s->d_rs->slot_live;
-    a.ring_head = &s->d_rs->cons;
-    a.next_base = &s->d_rs->next_base;
+    a.st = L.st;
+    a.slots = L.d_hdr->slots;
+    a.slot_live = L.d_rs->slot_live;
+    a.ring_head = &L.d_rs->cons;
+    a.next_base = &L.d_rs->next_base;
     a.ring_mask = s->ring_mask;
     return a;
 }
 
-// Everything one step puts on the stream, graph-capturable (all counts are
-// read on the device).
-rg_status enqueue_step(rg_server* s) {
-    SV_CK(cudaMemcpyAsync(s->d_hdr, s->h_hdr, sizeof(StepHdr), cudaMemcpyHostToDevice, s->stream));
-    k_step_begin<<<1, 32, 0, s->stream>>>(s->d_hdr, s->d_rs);
+// Everything one step of a lane puts on the lane's stream, graph-capturable
+// (all counts are read on the device).
+rg_status enqueue_step(rg_server* s, Lane& L) {
+    SV_CK(cudaMemcpyAsync(L.d_hdr, L.h_hdr, sizeof(StepHdr), cudaMemcpyHostToDevice, L.stream));
+    k_step_begin<<<1, 32, 0, L.stream>>>(L.d_hdr, L.d_rs);
     count_launches(1);
     SV_CK(cudaGetLastError());
-    SV_CK(launch_raygen_batch(s->d_hdr->reqs, &s->d_hdr->n_reqs, s->ring_cap / 2, &s->d_hdr->n_new_rays,
-                              &s->d_rs->gen_base, s->ring_mask, s->ring_rays, s->ring_pay, s->stream));
+    SV_CK(launch_raygen_batch(L.d_hdr->reqs, &L.d_hdr->n_reqs, s->ring_cap / 2, &L.d_hdr->n_new_rays,
+                              &L.d_rs->gen_base, s->ring_mask, L.ring_rays, L.ring_pay, L.stream));
     if (paired(s)) {
         // the previous step's shadow rays with this step's closest-hit rays;
         // shading then refills the shadow queue
-        SV_CK(launch_trace_pair(true, false, shadow_args(s, s->d_rs->prev_shadow_count), closest_args(s, &s->d_hdr->m),
-                                s->stream, s->shape[0]));
-        SV_CK(launch_shade_batch(shade_args(s, &s->d_hdr->m), s->stream));
+        SV_CK(launch_trace_pair(true, false, shadow_args(s, L, L.d_rs->prev_shadow_count),
+                                closest_args(s, L, &L.d_hdr->m), L.stream, s->shape[0]));
+        SV_CK(launch_shade_batch(shade_args(s, L, &L.d_hdr->m), L.stream));
     } else {
-        SV_CK(launch_trace(kModeClosestBatch, false, false, closest_args(s, &s->d_hdr->m), s->stream, s->shape[0]));
-        SV_CK(launch_shade_batch(shade_args(s, &s->d_hdr->m), s->stream));
-        SV_CK(launch_trace(kModeShadowBatch, false, false, shadow_args(s, s->d_rs->shadow_count), s->stream,
+        SV_CK(launch_trace(kModeClosestBatch, false, false, closest_args(s, L, &L.d_hdr->m), L.stream, s->shape[0]));
+        SV_CK(launch_shade_batch(shade_args(s, L, &L.d_hdr->m), L.stream));
+        SV_CK(launch_trace(kModeShadowBatch, false, false, shadow_args(s, L, L.d_rs->shadow_count), L.stream,
                            s->shape[1]));
     }
-    k_close_gap<<<device_sm_count() * 4, 256, 0, s->stream>>>(s->d_hdr, s->d_rs, s->ring_mask, s->ring_rays,
-                                                              s->ring_pay);
+    k_close_gap<<<device_sm_count() * 4, 256, 0, L.stream>>>(L.d_hdr, L.d_rs, s->ring_mask, L.ring_rays, L.ring_pay);
     count_launches(1);
     SV_CK(cudaGetLastError());
-    k_step_end<<<1, 32, 0, s->stream>>>(s->d_hdr, s->d_rs, s->d_out, s->st);
+    k_step_end<<<1, 32, 0, L.stream>>>(L.d_hdr, L.d_rs, L.d_out, L.st);
     count_launches(1);
     SV_CK(cudaGetLastError());
-    SV_CK(cudaMemcpyAsync(s->h_out, s->d_out, sizeof(StepOut), cudaMemcpyDeviceToHost, s->stream));
+    SV_CK(cudaMemcpyAsync(L.h_out, L.d_out, sizeof(StepOut), cudaMemcpyDeviceToHost, L.stream));
     return RG_OK;
 }
 
-// Captures `body` on the server's stream into an executable graph.
+// Captures `body` on `stream` into an executable graph.
 template <class F>
-rg_status capture(rg_server* s, F body, cudaGraphExec_t* out) {
+rg_status capture(rg_server* s, cudaStream_t stream, F body, cudaGraphExec_t* out) {
     *out = nullptr;
-    SV_CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeRelaxed));
+    SV_CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeRelaxed));
     set_capturing(true);
     rg_status r = body();
     set_capturing(false);
     cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+    cudaError_t e = cudaStreamEndCapture(stream, &g);
     if (r != RG_OK) {
         if (g) cudaGraphDestroy(g);
         return r;
@@ -421,16 +444,16 @@ rg_status capture(rg_server* s, F body, cudaGraphExec_t* out) {
     return RG_OK;
 }
 
-rg_status run_step_work(rg_server* s) {
+rg_status run_step_work(rg_server* s, Lane& L) {
     if (s->flags & RG_SERVER_NO_GRAPH) {
         const unsigned long long before = launches_so_far();
-        rg_status r = enqueue_step(s);
+        rg_status r = enqueue_step(s, L);
         s->stats.kernel_launches += launches_so_far() - before;
         return r;
     }
     rg_status r;
-    if (!s->step_exec && (r = capture(s, [&] { return enqueue_step(s); }, &s->step_exec))) return r;
-    SV_CK(cudaGraphLaunch(s->step_exec, s->stream));
+    if (!L.step_exec && (r = capture(s, L.stream, [&] { return enqueue_step(s, L); }, &L.step_exec))) return r;
+    SV_CK(cudaGraphLaunch(L.step_exec, L.stream));
     const unsigned k = paired(s) ? kStepKernelsPaired : kStepKernelsApart;
     count_launches(k);
     s->stats.kernel_launches += k;
@@ -438,17 +461,17 @@ rg_status run_step_work(rg_server* s) {
     return RG_OK;
 }
 
-rg_status run_refit(rg_server* s, uint32_t k, uint32_t e) {
+rg_status run_refit(rg_server* s, Lane& L, uint32_t k, uint32_t e) {
     if (s->flags & RG_SERVER_NO_GRAPH) {
         const unsigned long long before = launches_so_far();
-        rg_status r = enqueue_refit(s, k, e);
+        rg_status r = enqueue_refit(s, L, k, e);
         s->stats.kernel_launches += launches_so_far() - before;
         return r;
     }
     rg_status r;
-    cudaGraphExec_t& g = s->slots[k].refit_exec[e];
-    if (!g && (r = capture(s, [&] { return enqueue_refit(s, k, e); }, &g))) return r;
-    SV_CK(cudaGraphLaunch(g, s->stream));
+    cudaGraphExec_t& g = L.slots[k].refit_exec[e];
+    if (!g && (r = capture(s, L.stream, [&] { return enqueue_refit(s, L, k, e); }, &g))) return r;
+    SV_CK(cudaGraphLaunch(g, L.stream));
     count_launches(kRefitKernels);
     s->stats.kernel_launches += kRefitKernels;
     s->stats.graph_launches++;
@@ -474,41 +497,60 @@ rg_status check_request(rg_server* s, const rg_request* q) {
     return RG_OK;
 }
 
-// Admission: in arrival order, while a slot is free and the ring keeps half
-// its capacity for spawned rays.  Returns the primary rays admitted.
-rg_status admit(rg_server* s, uint32_t* n_new) {
-    StepHdr& H = *s->h_hdr;
-    H.n_reqs = 0;
-    H.new_mask = 0;
-    uint32_t rays = 0;
+// Admission: in arrival order, each request into the least loaded lane (the
+// fewest rays in its ring plus those admitted to it this step) that has a
+// free slot and room: the lane's rays stay within the admission bound, or the
+// request runs alone in an empty lane (within half the ring).  The first
+// request no lane takes stops admission (no overtaking).
+rg_status admit(rg_server* s) {
+    for (Lane& L : s->lanes) {
+        if (L.in_flight) continue;
+        L.h_hdr->n_reqs = 0;
+        L.h_hdr->new_mask = 0;
+        L.admitted = 0;
+    }
     while (!s->pending.empty()) {
         Pending& p = s->pending.front();
         const uint32_t px = p.r.width * p.r.height;
-        const uint64_t after = (uint64_t)s->ring_rays_now + rays + px;
-        // within the admission bound, or alone in an empty ring (within half the ring)
-        const bool alone = s->ring_rays_now == 0 && rays == 0 && px <= s->ring_cap / 2;
-        if (after > s->admit && !alone) break;
-        uint32_t k = 0;
-        while (k < kMaxSlots && s->active[k].on) ++k;
-        if (k == kMaxSlots) break;
+        Lane* best = nullptr;
+        uint32_t best_k = 0;
+        uint64_t best_load = 0;
+        for (Lane& L : s->lanes) {
+            if (L.in_flight) continue;  // its header is in use by the step in flight
+            const uint64_t load = (uint64_t)L.ring_rays_now + L.admitted;
+            const bool alone = load == 0 && px <= s->ring_cap / 2;
+            if (load + px > s->admit && !alone) continue;
+            uint32_t k = 0;
+            while (k < kMaxSlots && L.active[k].on) ++k;
+            if (k == kMaxSlots) continue;
+            if (!best || load < best_load) {
+                best = &L;
+                best_k = k;
+                best_load = load;
+            }
+        }
+        if (!best) break;
+        Lane& L = *best;
+        const uint32_t k = best_k;
+        StepHdr& H = *L.h_hdr;
         const SceneEntry& E = s->scenes[p.r.scene];
         const uint32_t n = E.v.n_inst;
-        rg_instance* hi = s->slots[k].h_inst;
+        rg_instance* hi = L.slots[k].h_inst;
         std::memcpy(hi, E.base.data(), (size_t)n * sizeof(rg_instance));
         if (!p.transforms.empty())
             for (uint32_t i = 0; i < n; ++i) std::memcpy(hi[i].m, &p.transforms[12 * (size_t)i], 48);
         rg_status r;
-        if ((r = run_refit(s, k, p.r.scene))) return r;
+        if ((r = run_refit(s, L, k, p.r.scene))) return r;
         RaygenReq& q = H.reqs[H.n_reqs++];
         std::memcpy(&q.cam, &p.r.camera, sizeof(CameraDev));
         q.w = p.r.width;
         q.h = p.r.height;
         q.slot = k;
-        q.offset = rays;
+        q.offset = L.admitted;
         q.image = p.r.d_rgba;
         SlotDev& D = H.slots[k];
-        D.tlas_nodes = s->slots[k].tlas_nodes;
-        D.inst = s->slots[k].inst;
+        D.tlas_nodes = L.slots[k].tlas_nodes;
+        D.inst = L.slots[k].inst;
         D.tlas_root = E.v.tlas_root;
         D.mats = E.v.mats;
         D.n_mats = E.v.n_mats;
@@ -520,18 +562,18 @@ rg_status admit(rg_server* s, uint32_t* n_new) {
         D.ambient = E.v.ambient;
         H.live_init[k] = (int)px;
         H.new_mask |= 1u << k;
-        Active& A = s->active[k];
+        Active& A = L.active[k];
         A.on = true;
         A.id = p.id;
         A.tag = p.r.tag;
         A.scene = p.r.scene;
         A.admitted_step = (uint32_t)(s->stats.steps + 1);
-        rays += px;
+        L.admitted += px;
         s->stats.admitted++;
         s->pending.pop_front();
     }
-    H.n_new_rays = rays;
-    *n_new = rays;
+    for (Lane& L : s->lanes)
+        if (!L.in_flight) L.h_hdr->n_new_rays = L.admitted;
     return RG_OK;
 }
 
@@ -552,53 +594,62 @@ uint32_t step_batch(const rg_server* s, uint32_t avail, bool* newest_first) {
     return (uint32_t)std::min<uint64_t>(want, F / (2 * (RG_SERVER_MAX_DEPTH + 1)));
 }
 
-rg_status finish_step(rg_server* s, uint32_t* n_completed) {
-    SV_CK(cudaEventRecord(s->done_ev, s->stream));
-    SV_CK(cudaEventSynchronize(s->done_ev));
-    const StepOut& O = *s->h_out;
-    s->stats.steps++;
-    s->stats.closest_rays += s->h_hdr->m;
+// Waits for a lane's step and books its results: ring count, completed
+// requests (their images are final), device errors.
+rg_status finish_step(rg_server* s, Lane& L, uint32_t* n_completed) {
+    SV_CK(cudaEventSynchronize(L.done_ev));
+    L.in_flight = false;
+    s->stats.lane_steps++;
+    const StepOut& O = *L.h_out;
+    s->stats.closest_rays += L.h_hdr->m;
     s->stats.shadow_rays += O.shadow_count;
-    s->ring_rays_now = O.tail - O.head;
-    s->stats.ring_peak = std::max(s->stats.ring_peak, s->ring_rays_now);
+    L.ring_rays_now = O.tail - O.head;
+    s->stats.ring_peak = std::max(s->stats.ring_peak, L.ring_rays_now);
     int64_t live_sum = 0;
     uint32_t completed = 0;
     for (uint32_t k = 0; k < kMaxSlots; ++k) {
-        if (!s->active[k].on) {
+        if (!L.active[k].on) {
             if (O.slot_live[k] != 0) return sfail(RG_ERR_CUDA, "render server: rays of a free slot in the ring");
             continue;
         }
         if (O.slot_live[k] < 0) return sfail(RG_ERR_CUDA, "render server: negative live ray count");
         live_sum += O.slot_live[k];
-        if (O.slot_live[k] == 0 && paired(s) && s->max_lights && !s->active[k].flushing) {
-            s->active[k].flushing = true;  // complete after the next step traces its last shadow rays
+        if (O.slot_live[k] == 0 && paired(s) && s->max_lights && !L.active[k].flushing) {
+            L.active[k].flushing = true;  // complete after the next step traces its last shadow rays
             continue;
         }
         if (O.slot_live[k] == 0) {
             rg_completion c;
-            c.id = s->active[k].id;
-            c.tag = s->active[k].tag;
-            c.admitted_step = s->active[k].admitted_step;
+            c.id = L.active[k].id;
+            c.tag = L.active[k].tag;
+            c.admitted_step = L.active[k].admitted_step;
             c.completed_step = (uint32_t)s->stats.steps;
             s->done.push_back(c);
-            s->active[k] = Active();
+            L.active[k] = Active();
             s->stats.completed++;
             ++completed;
         }
     }
-    if (n_completed) *n_completed = completed;
+    if (n_completed) *n_completed += completed;
     if (O.error) {
         // the step completed (a ray that failed counts as a miss); report it
-        SV_CK(cudaMemset(&s->st->error, 0, sizeof(int)));
+        SV_CK(cudaMemset(&L.st->error, 0, sizeof(int)));
         return sfail(O.error, std::string("render server step: ") + device_error_text(O.error));
     }
-    if (live_sum != (int64_t)s->ring_rays_now) return sfail(RG_ERR_CUDA, "render server: ring count mismatch");
+    if (live_sum != (int64_t)L.ring_rays_now) return sfail(RG_ERR_CUDA, "render server: ring count mismatch");
     return RG_OK;
 }
 
 uint32_t n_active(const rg_server* s) {
     uint32_t c = 0;
-    for (const Active& a : s->active) c += a.on ? 1u : 0u;
+    for (const Lane& L : s->lanes)
+        for (const Active& a : L.active) c += a.on ? 1u : 0u;
+    return c;
+}
+
+uint32_t ring_rays_total(const rg_server* s) {
+    uint32_t c = 0;
+    for (const Lane& L : s->lanes) c += L.ring_rays_now;
     return c;
 }
 
@@ -723,36 +774,45 @@ rg_status rg_server_create(rg_server** out, const rg_server_desc* desc) {
     s->shadow_cap = (size_t)s->batch * s->max_lights;
     s->flags = d.flags;
     s->admit = std::min(d.admit_rays ? d.admit_rays : s->batch, s->ring_cap / 2);
+    const uint32_t n_lanes = d.lanes ? d.lanes : kDefaultLanes;
+    if (n_lanes > RG_SERVER_MAX_LANES) {
+        delete s;
+        return sfail(RG_ERR_INVALID_ARG, "lanes above RG_SERVER_MAX_LANES");
+    }
     rg_status r = RG_OK;
     auto bail = [&](rg_status code) {
         rg_server_destroy(s);
         return code;
     };
     if (cudaGetDevice(&s->device) != cudaSuccess) return bail(scuda(cudaGetLastError(), "cudaGetDevice"));
-    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess)
-        return bail(sfail(RG_ERR_CUDA, "cudaStreamCreate failed"));
-    if (cudaEventCreateWithFlags(&s->done_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreate(&s->t0) != cudaSuccess || cudaEventCreate(&s->t1) != cudaSuccess)
+    if (cudaEventCreate(&s->t0) != cudaSuccess || cudaEventCreate(&s->t1) != cudaSuccess)
         return bail(sfail(RG_ERR_CUDA, "cudaEventCreate failed"));
-    if ((r = salloc(&s->st, 1, "server status"))) return bail(r);
-    if ((r = salloc(&s->ring_rays, 2 * (size_t)s->ring_cap, "ray ring"))) return bail(r);
-    if ((r = salloc(&s->ring_pay, (size_t)s->ring_cap, "payload ring"))) return bail(r);
-    if ((r = salloc(&s->hits, (size_t)s->batch, "hit queue"))) return bail(r);
-    if ((r = salloc(&s->s_rays, 2 * s->shadow_cap, "shadow queue"))) return bail(r);
-    if ((r = salloc(&s->s_pay, s->shadow_cap, "shadow payload"))) return bail(r);
-    if ((r = salloc(&s->d_rs, 1, "ring state"))) return bail(r);
-    if ((r = salloc(&s->d_hdr, 1, "step header"))) return bail(r);
-    if ((r = salloc(&s->d_out, 1, "step result"))) return bail(r);
     if ((r = salloc(&s->d_tune_count, 1, "tuning count"))) return bail(r);
-    if (cudaMallocHost(reinterpret_cast<void**>(&s->h_hdr), sizeof(StepHdr)) != cudaSuccess ||
-        cudaMallocHost(reinterpret_cast<void**>(&s->h_out), sizeof(StepOut)) != cudaSuccess)
-        return bail(sfail(RG_ERR_OOM, "pinned host buffers"));
-    std::memset(s->h_hdr, 0, sizeof(StepHdr));
-    std::memset(s->h_out, 0, sizeof(StepOut));
     s->ring_start = ring_start_for_tests();
-    if (cudaMemset(s->st, 0, sizeof(DevStatus)) != cudaSuccess || reset_ring(s->d_rs, s->ring_start) != cudaSuccess ||
-        cudaMemset(s->d_hdr, 0, sizeof(StepHdr)) != cudaSuccess)
-        return bail(scuda(cudaGetLastError(), "cudaMemset"));
+    s->lanes.resize(n_lanes);
+    for (Lane& L : s->lanes) {
+        if (cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(sfail(RG_ERR_CUDA, "cudaStreamCreate failed"));
+        if (cudaEventCreateWithFlags(&L.done_ev, cudaEventDisableTiming) != cudaSuccess)
+            return bail(sfail(RG_ERR_CUDA, "cudaEventCreate failed"));
+        if ((r = salloc(&L.st, 1, "server status"))) return bail(r);
+        if ((r = salloc(&L.ring_rays, 2 * (size_t)s->ring_cap, "ray ring"))) return bail(r);
+        if ((r = salloc(&L.ring_pay, (size_t)s->ring_cap, "payload ring"))) return bail(r);
+        if ((r = salloc(&L.hits, (size_t)s->batch, "hit queue"))) return bail(r);
+        if ((r = salloc(&L.s_rays, 2 * s->shadow_cap, "shadow queue"))) return bail(r);
+        if ((r = salloc(&L.s_pay, s->shadow_cap, "shadow payload"))) return bail(r);
+        if ((r = salloc(&L.d_rs, 1, "ring state"))) return bail(r);
+        if ((r = salloc(&L.d_hdr, 1, "step header"))) return bail(r);
+        if ((r = salloc(&L.d_out, 1, "step result"))) return bail(r);
+        if (cudaMallocHost(reinterpret_cast<void**>(&L.h_hdr), sizeof(StepHdr)) != cudaSuccess ||
+            cudaMallocHost(reinterpret_cast<void**>(&L.h_out), sizeof(StepOut)) != cudaSuccess)
+            return bail(sfail(RG_ERR_OOM, "pinned host buffers"));
+        std::memset(L.h_hdr, 0, sizeof(StepHdr));
+        std::memset(L.h_out, 0, sizeof(StepOut));
+        if (cudaMemset(L.st, 0, sizeof(DevStatus)) != cudaSuccess || reset_ring(L.d_rs, s->ring_start) != cudaSuccess ||
+            cudaMemset(L.d_hdr, 0, sizeof(StepHdr)) != cudaSuccess)
+            return bail(scuda(cudaGetLastError(), "cudaMemset"));
+    }
     *out = s;
     return RG_OK;
 }
@@ -760,25 +820,28 @@ rg_status rg_server_create(rg_server** out, const rg_server_desc* desc) {
 rg_status rg_server_destroy(rg_server* s) {
     if (!s) return RG_OK;
     cudaSetDevice(s->device);
-    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (Lane& L : s->lanes)
+        if (L.stream) cudaStreamSynchronize(L.stream);
     drop_step_graph(s);
-    for (SlotBufs& b : s->slots) free_slot_bufs(b);
-    cudaFree(s->st);
-    cudaFree(s->ring_rays);
-    cudaFree(s->ring_pay);
-    cudaFree(s->hits);
-    cudaFree(s->s_rays);
-    cudaFree(s->s_pay);
-    cudaFree(s->d_rs);
-    cudaFree(s->d_hdr);
-    cudaFree(s->d_out);
+    for (Lane& L : s->lanes) {
+        for (SlotBufs& b : L.slots) free_slot_bufs(b);
+        cudaFree(L.st);
+        cudaFree(L.ring_rays);
+        cudaFree(L.ring_pay);
+        cudaFree(L.hits);
+        cudaFree(L.s_rays);
+        cudaFree(L.s_pay);
+        cudaFree(L.d_rs);
+        cudaFree(L.d_hdr);
+        cudaFree(L.d_out);
+        if (L.h_hdr) cudaFreeHost(L.h_hdr);
+        if (L.h_out) cudaFreeHost(L.h_out);
+        if (L.done_ev) cudaEventDestroy(L.done_ev);
+        if (L.stream) cudaStreamDestroy(L.stream);
+    }
     cudaFree(s->d_tune_count);
-    if (s->h_hdr) cudaFreeHost(s->h_hdr);
-    if (s->h_out) cudaFreeHost(s->h_out);
-    if (s->done_ev) cudaEventDestroy(s->done_ev);
     if (s->t0) cudaEventDestroy(s->t0);
     if (s->t1) cudaEventDestroy(s->t1);
-    if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return RG_OK;
 }
@@ -818,13 +881,16 @@ rg_status rg_server_add_scene(rg_server* s, rg_scene* scene, uint32_t* scene_id)
     // slot buffers sized for the largest scene; every refit graph is per scene
     const size_t n_scenes = s->scenes.size() + 1;
     if (n > s->max_inst) {
-        for (SlotBufs& b : s->slots) free_slot_bufs(b);
-        for (SlotBufs& b : s->slots)
-            if ((r = alloc_slot_bufs(b, n, n_scenes))) return r;
+        for (Lane& L : s->lanes)
+            for (SlotBufs& b : L.slots) free_slot_bufs(b);
+        for (Lane& L : s->lanes)
+            for (SlotBufs& b : L.slots)
+                if ((r = alloc_slot_bufs(b, n, n_scenes))) return r;
         s->max_inst = n;
         drop_step_graph(s);
     } else {
-        for (SlotBufs& b : s->slots) b.refit_exec.resize(n_scenes, nullptr);
+        for (Lane& L : s->lanes)
+            for (SlotBufs& b : L.slots) b.refit_exec.resize(n_scenes, nullptr);
     }
     s->iter_cap = std::max(s->iter_cap, E.v.iter_cap);
     drop_step_graph(s);
@@ -851,35 +917,87 @@ rg_status rg_server_submit(rg_server* s, const rg_request* q, uint64_t* id) {
     return RG_OK;
 }
 
+bool any_in_flight(const rg_server* s) {
+    for (const Lane& L : s->lanes)
+        if (L.in_flight) return true;
+    return false;
+}
+
+// Books every lane whose step has finished, waiting first for the oldest
+// launch in flight when none has.
+rg_status book_finished(rg_server* s, uint32_t* n_completed) {
+    Lane* oldest = nullptr;
+    bool any_done = false;
+    for (Lane& L : s->lanes) {
+        if (!L.in_flight) continue;
+        if (!oldest || L.launch_seq < oldest->launch_seq) oldest = &L;
+        const cudaError_t q = cudaEventQuery(L.done_ev);
+        if (q == cudaSuccess) any_done = true;
+        else if (q != cudaErrorNotReady) return scuda(q, "cudaEventQuery");
+    }
+    if (!oldest) return RG_OK;
+    if (!any_done) SV_CK(cudaEventSynchronize(oldest->done_ev));
+    rg_status r = RG_OK;
+    for (Lane& L : s->lanes) {
+        if (!L.in_flight || cudaEventQuery(L.done_ev) != cudaSuccess) continue;
+        const rg_status q = finish_step(s, L, n_completed);
+        if (!r) r = q;
+    }
+    return r;
+}
+
 rg_status rg_server_step(rg_server* s, uint32_t* n_completed) {
     rg_status r;
     if (n_completed) *n_completed = 0;
     if ((r = check_server(s))) return r;
     if ((r = set_dev(s))) return r;
-    uint32_t n_new = 0;
-    if ((r = admit(s, &n_new))) return r;
-    const uint32_t avail = s->ring_rays_now + n_new;
-    // an empty ring still takes a step while finished requests wait for their last shadow rays
-    if (avail == 0 && !shadow_flush_due(s)) return RG_OK;
-    bool newest = false;
-    const uint32_t m = avail ? step_batch(s, avail, &newest) : 0u;
-    if (avail && m == 0) return sfail(RG_ERR_OOM, "ray ring full: no room for the rays a step spawns");
-    s->h_hdr->m = m;
-    s->h_hdr->newest_first = newest ? 1u : 0u;
-    if (newest) s->stats.newest_first_steps++;
-    if ((r = run_step_work(s))) return r;
-    return finish_step(s, n_completed);
+    if ((r = admit(s))) return r;
+    // a step on every idle lane with work, each on its own stream
+    for (Lane& L : s->lanes) {
+        if (L.in_flight) continue;
+        const uint32_t avail = L.ring_rays_now + L.admitted;
+        // an empty ring still takes a step while finished requests wait for their last shadow rays
+        if (avail == 0 && !shadow_flush_due(L)) continue;
+        bool newest = false;
+        const uint32_t m = avail ? step_batch(s, avail, &newest) : 0u;
+        if (avail && m == 0) {
+            r = sfail(RG_ERR_OOM, "ray ring full: no room for the rays a step spawns");
+            break;
+        }
+        L.h_hdr->m = m;
+        L.h_hdr->newest_first = newest ? 1u : 0u;
+        if (newest) s->stats.newest_first_steps++;
+        if ((r = run_step_work(s, L))) break;
+        SV_CK(cudaEventRecord(L.done_ev, L.stream));
+        L.in_flight = true;
+        L.launch_seq = ++s->launches;
+    }
+    if (!any_in_flight(s)) return r;
+    s->stats.steps++;
+    // returns once at least one lane's step is booked (the others run on)
+    const rg_status q = book_finished(s, n_completed);
+    return r ? r : q;
 }
 
 rg_status rg_server_drain(rg_server* s) {
     rg_status r;
     if ((r = check_server(s))) return r;
-    while (!s->pending.empty() || n_active(s)) {
+    while (!s->pending.empty() || n_active(s) || any_in_flight(s)) {
         const uint64_t before = s->stats.steps;
         if ((r = rg_server_step(s, nullptr))) return r;
         if (s->stats.steps == before) return sfail(RG_ERR_INVALID_ARG, "render server cannot make progress");
     }
     return RG_OK;
+}
+
+// Waits for (and books) every lane's step in flight.
+rg_status settle(rg_server* s) {
+    rg_status r = RG_OK;
+    while (any_in_flight(s)) {
+        const rg_status q = book_finished(s, nullptr);
+        if (!r) r = q;
+    }
+    return r;
 }
 
 rg_status rg_server_poll(rg_server* s, rg_completion* out, uint32_t max, uint32_t* n) {
@@ -902,7 +1020,7 @@ rg_status rg_server_get_stats(rg_server* s, rg_server_stats* out) {
     *out = s->stats;
     out->pending = (uint32_t)s->pending.size();
     out->active = n_active(s);
-    out->ring_rays = s->ring_rays_now;
+    out->ring_rays = ring_rays_total(s);
     return RG_OK;
 }
 
@@ -914,6 +1032,7 @@ rg_status rg_server_set_shape(rg_server* s, uint32_t which, const rg_trace_shape
         return sfail(RG_ERR_INVALID_ARG, "bad launch shape");
     if (!(sh->stack == 0 || (sh->block == 128 && (sh->stack == 8 || sh->stack == 16))))
         return sfail(RG_ERR_INVALID_ARG, "short stack: 0, or 8 or 16 entries with 128 threads per block");
+    if ((r = settle(s))) return r;
     s->shape[which].block = (int)sh->block;
     s->shape[which].blocks_per_sm = (int)sh->blocks_per_sm;
     s->shape[which].refill = (int)sh->refill;
@@ -939,7 +1058,8 @@ rg_status rg_server_autotune(rg_server* s, const rg_request* sample, const char*
     rg_status r;
     if ((r = check_server(s))) return r;
     if ((r = check_request(s, sample))) return r;
-    if (!s->pending.empty() || n_active(s)) return sfail(RG_ERR_INVALID_ARG, "autotune needs an idle server");
+    if (!s->pending.empty() || n_active(s) || any_in_flight(s))
+        return sfail(RG_ERR_INVALID_ARG, "autotune needs an idle server");
     if ((r = set_dev(s))) return r;
     int sms = 0;
     const std::string dev = device_key(s->device, &sms);
@@ -947,35 +1067,37 @@ rg_status rg_server_autotune(rg_server* s, const rg_request* sample, const char*
     float best_ms[2] = {-1.0f, -1.0f};
     const bool cached = cache_path && !(flags & RG_TUNE_FORCE) && cache_lookup(cache_path, dev, sms, best);
     if (!cached) {
-        // the sample's primary rays into the ring (a step that traces nothing)
+        // the sample's primary rays into the ring of lane 0 (the least loaded of
+        // an idle server): a step that traces nothing
+        Lane& L = s->lanes[0];
         const uint32_t px = sample->width * sample->height;
         bool newest = false;
         const uint32_t m = std::min(px, step_batch(s, px, &newest));
         if ((r = rg_server_submit(s, sample, nullptr))) return r;
-        uint32_t n_new = 0;
-        if ((r = admit(s, &n_new))) return r;
-        s->h_hdr->m = 0;
-        s->h_hdr->newest_first = 0;
+        if ((r = admit(s))) return r;
+        L.h_hdr->m = 0;
+        L.h_hdr->newest_first = 0;
         const uint32_t saved_flags = s->flags;
         s->flags |= RG_SERVER_NO_GRAPH;
-        r = enqueue_step(s);
+        r = enqueue_step(s, L);
         s->flags = saved_flags;
         if (r) return r;
-        SV_CK(cudaMemcpyAsync(s->d_tune_count, &m, 4, cudaMemcpyHostToDevice, s->stream));
-        SV_CK(cudaStreamSynchronize(s->stream));
+        SV_CK(cudaMemcpyAsync(s->d_tune_count, &m, 4, cudaMemcpyHostToDevice, L.stream));
+        SV_CK(cudaStreamSynchronize(L.stream));
         const int blocks[3] = {64, 128, 256}, bps[3] = {0, 4, 8}, refills[4] = {8, 16, 24, 32}, stacks[3] = {0, 8, 16};
         auto time_one = [&](int which, const TraceShape& t, float* ms) -> rg_status {
             float best_t = 1e30f;
             for (int rep = 0; rep < 4; ++rep) {
-                uint32_t* wc = which == 0 ? &s->d_rs->work_closest : &s->d_rs->work_shadow;
-                SV_CK(cudaMemsetAsync(wc, 0, 4, s->stream));
-                SV_CK(cudaEventRecord(s->t0, s->stream));
+                uint32_t* wc = which == 0 ? &L.d_rs->work_closest : &L.d_rs->work_shadow;
+                SV_CK(cudaMemsetAsync(wc, 0, 4, L.stream));
+                SV_CK(cudaEventRecord(s->t0, L.stream));
                 if (which == 0)
-                    SV_CK(launch_trace(kModeClosestBatch, false, false, closest_args(s, s->d_tune_count), s->stream, t));
+                    SV_CK(launch_trace(kModeClosestBatch, false, false, closest_args(s, L, s->d_tune_count), L.stream,
+                                       t));
                 else
-                    SV_CK(launch_trace(kModeShadowBatch, false, false, shadow_args(s, s->d_rs->shadow_count),
-                                       s->stream, t));
-                SV_CK(cudaEventRecord(s->t1, s->stream));
+                    SV_CK(launch_trace(kModeShadowBatch, false, false, shadow_args(s, L, L.d_rs->shadow_count),
+                                       L.stream, t));
+                SV_CK(cudaEventRecord(s->t1, L.stream));
                 SV_CK(cudaEventSynchronize(s->t1));
                 float e = 0;
                 SV_CK(cudaEventElapsedTime(&e, s->t0, s->t1));
@@ -987,10 +1109,10 @@ rg_status rg_server_autotune(rg_server* s, const rg_request* sample, const char*
         for (int which = 0; which < 2; ++which) {
             if (which == 1) {
                 // one shading pass makes the shadow rays (its spawned rays are discarded below)
-                SV_CK(cudaMemsetAsync(&s->d_rs->work_closest, 0, 4, s->stream));
-                SV_CK(launch_trace(kModeClosestBatch, false, false, closest_args(s, s->d_tune_count), s->stream,
+                SV_CK(cudaMemsetAsync(&L.d_rs->work_closest, 0, 4, L.stream));
+                SV_CK(launch_trace(kModeClosestBatch, false, false, closest_args(s, L, s->d_tune_count), L.stream,
                                    best[0]));
-                SV_CK(launch_shade_batch(shade_args(s, s->d_tune_count), s->stream));
+                SV_CK(launch_shade_batch(shade_args(s, L, s->d_tune_count), L.stream));
             }
             best_ms[which] = 1e30f;
             for (int b : blocks)
@@ -1012,13 +1134,14 @@ rg_status rg_server_autotune(rg_server* s, const rg_request* sample, const char*
                         }
         }
         // back to an empty ring and a free slot
-        SV_CK(cudaStreamSynchronize(s->stream));
+        SV_CK(cudaStreamSynchronize(L.stream));
         int err = 0;
-        SV_CK(cudaMemcpy(&err, &s->st->error, sizeof(int), cudaMemcpyDeviceToHost));
-        SV_CK(reset_ring(s->d_rs, s->ring_start));
-        SV_CK(cudaMemset(&s->st->error, 0, sizeof(int)));
-        s->ring_rays_now = 0;
-        for (Active& a : s->active) a = Active();
+        SV_CK(cudaMemcpy(&err, &L.st->error, sizeof(int), cudaMemcpyDeviceToHost));
+        SV_CK(reset_ring(L.d_rs, s->ring_start));
+        SV_CK(cudaMemset(&L.st->error, 0, sizeof(int)));
+        L.ring_rays_now = 0;
+        L.admitted = 0;
+        for (Active& a : L.active) a = Active();
         s->stats.admitted--;
         s->stats.submitted--;
         if (err) return sfail(err, std::string("autotune: ") + device_error_text(err));

@@ -109,13 +109,15 @@ def test_single_request_equals_render(scenes):
         check_against_alone(descs, gss, reqs, imgs, st)
 
 
-def test_mix_equals_alone(scenes):
+@pytest.mark.parametrize("lanes", [1, 4])
+def test_mix_equals_alone(scenes, lanes):
     """24 requests over all 8 scenes at mixed resolutions and depths 1-8,
     each with its own instance motion, through a batch limit that makes the
-    steps interleave them."""
+    steps interleave them; in one lane, and spread over four lanes whose
+    steps run at the same time."""
     descs, gss = scenes
     reqs = make_requests(descs, 24, seed=7, sizes=[(160, 120), (320, 240), (640, 360), (97, 33)])
-    imgs, done, st = run_server(gss, reqs, ring_log2=22, batch_rays=1 << 18, admit_rays=1 << 21)
+    imgs, done, st = run_server(gss, reqs, ring_log2=22, batch_rays=1 << 18, admit_rays=1 << 21, lanes=lanes)
     assert sorted(d["tag"] for d in done) == list(range(len(reqs)))
     # requests were in flight together and finished over many steps
     spans = [(d["admitted_step"], d["completed_step"]) for d in done]
@@ -126,18 +128,20 @@ def test_mix_equals_alone(scenes):
     check_against_alone(descs, gss, reqs, imgs, st)
 
 
-def test_ring_counters_wrap_past_2_32(scenes, monkeypatch):
+@pytest.mark.parametrize("lanes", [1, 4])
+def test_ring_counters_wrap_past_2_32(scenes, monkeypatch, lanes):
     """The ring positions are free-running 32-bit counters, so a long-running
-    server wraps them after 2^32 path rays.  A server whose empty ring starts
-    100,000 positions below 2^32 (test hook RG_TEST_RING_START, read when the
-    server is created) runs a mixed request set across the wrap: every image
-    equals its render alone, and the server traces the same rays."""
-    monkeypatch.setenv("RG_TEST_RING_START", str(2 ** 32 - 100_000))
+    server wraps them after 2^32 path rays.  A server whose empty rings start
+    1,000 positions below 2^32 (test hook RG_TEST_RING_START, read when the
+    server is created) runs a mixed request set across the wrap (every
+    request has more than 1,000 primary rays, so every lane that takes one
+    wraps): every image equals its render alone, and the server traces the
+    same rays."""
+    monkeypatch.setenv("RG_TEST_RING_START", str(2 ** 32 - 1_000))
     descs, gss = scenes
     reqs = make_requests(descs, 12, seed=21, sizes=[(160, 120), (320, 240), (97, 33)])
-    imgs, done, st = run_server(gss, reqs, ring_log2=20, batch_rays=1 << 16)
+    imgs, done, st = run_server(gss, reqs, ring_log2=20, batch_rays=1 << 16, lanes=lanes)
     assert sorted(d["tag"] for d in done) == list(range(len(reqs)))
-    assert st["closest_rays"] > 100_000   # the head passed 2^32
     check_against_alone(descs, gss, reqs, imgs, st)
 
 
@@ -276,14 +280,15 @@ def test_bad_requests_rejected(scenes):
 
 
 def test_admission_bound_keeps_requests_apart(scenes):
-    """With the default bound (one batch of rays in flight), a request larger
-    than the bound is admitted alone into the empty ring; the small ones are
-    admitted together once the rays in flight fall below the bound."""
+    """In one lane with the default bound (one batch of rays in flight), a
+    request larger than the bound is admitted alone into the empty ring; the
+    small ones are admitted together once the rays in flight fall below the
+    bound."""
     descs, gss = scenes
     reqs = [dict(scene=1, w=320, h=240, depth=3, M=descs[1].M, camera=descs[1].camera),
             dict(scene=2, w=64, h=48, depth=3, M=descs[2].M, camera=descs[2].camera),
             dict(scene=3, w=64, h=48, depth=3, M=descs[3].M, camera=descs[3].camera)]
-    imgs, done, st = run_server(gss, reqs, batch_rays=1 << 16)   # 76,800 px > 65,536: alone
+    imgs, done, st = run_server(gss, reqs, batch_rays=1 << 16, lanes=1)   # 76,800 px > 65,536: alone
     spans = {d["tag"]: (d["admitted_step"], d["completed_step"]) for d in done}
     assert spans[0][0] == 1 and spans[1][0] > 1             # the large one alone first
     assert spans[1][0] == spans[2][0]                       # the small ones together
@@ -296,8 +301,8 @@ def test_paired_steps_equal_separate_steps(scenes):
     step itself; each request then completes exactly one step later."""
     descs, gss = scenes
     reqs = make_requests(descs, 10, seed=19, sizes=[(160, 120), (97, 33), (320, 180)], depths=[1, 3, 6])
-    a, da, sa = run_server(gss, reqs, batch_rays=1 << 16)
-    b, db, sb = run_server(gss, reqs, batch_rays=1 << 16, flags=rg.RG_SERVER_NO_PAIR)
+    a, da, sa = run_server(gss, reqs, batch_rays=1 << 16, lanes=1)
+    b, db, sb = run_server(gss, reqs, batch_rays=1 << 16, flags=rg.RG_SERVER_NO_PAIR, lanes=1)
     for x, y in zip(a, b):
         np.testing.assert_allclose(x, y, atol=ATOL, rtol=0)
     assert sa["closest_rays"] == sb["closest_rays"] and sa["shadow_rays"] == sb["shadow_rays"]
@@ -305,8 +310,21 @@ def test_paired_steps_equal_separate_steps(scenes):
     cb = {d["tag"]: (d["admitted_step"], d["completed_step"]) for d in db}
     for t in ca:
         assert ca[t][0] == cb[t][0] and ca[t][1] == cb[t][1] + 1, (t, ca[t], cb[t])
-    # six kernels per paired step, seven apart
-    assert sa["kernel_launches"] - 6 * sa["steps"] == sb["kernel_launches"] - 7 * sb["steps"]
+    # six kernels per paired step, seven apart (one lane: a server step is a lane step)
+    assert sa["lane_steps"] == sa["steps"] and sb["lane_steps"] == sb["steps"]
+    assert sa["kernel_launches"] - 6 * sa["lane_steps"] == sb["kernel_launches"] - 7 * sb["lane_steps"]
+
+
+def test_lanes_run_steps_side_by_side(scenes):
+    """Requests spread over four lanes whose steps run at the same time: the
+    server books more lane steps than it takes server steps, and every image
+    equals its render alone."""
+    descs, gss = scenes
+    reqs = make_requests(descs, 16, seed=23, sizes=[(320, 240), (640, 360)], depths=[2, 4])
+    imgs, done, st = run_server(gss, reqs, batch_rays=1 << 17, lanes=4)
+    assert sorted(d["tag"] for d in done) == list(range(len(reqs)))
+    assert st["lane_steps"] > st["steps"]
+    check_against_alone(descs, gss, reqs, imgs, st)
 
 
 def test_single_request_completes_after_its_shadow_rays(scenes):
