@@ -415,6 +415,7 @@ rg_status rg_scene_destroy(rg_scene* s) {
     s->tasks8.release();
     s->tlas_nodes.release();
     s->inst.release();
+    s->leaf_of_inst.release();
     s->inst_tmp.release();
     s->wbox.release();
     s->perm.release();
