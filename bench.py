@@ -13,7 +13,7 @@ value  = closest-hit rays per step / ms_per_step (the whole step: rebuild,
          closest-hit and any-hit launches), over all ranks.
 e2e    = the same steps through rg_trace_rays with the rays in pinned host
          memory and the hit records copied back to it, copies inside the
-         timed region (overlapped with tracing in chunks of 4M rays).
+         timed region (each kind's rays copied in while the other kind traces).
 The line also carries the any-hit rate, the medium render frame (64
 instances, 1920x1080, depth 4) and the serving stream as extra keys.
 --impl reference runs the float64 CPU oracle on a seeded sample of each
@@ -53,7 +53,10 @@ MEDIUM_WORKLOAD = ("medium: 64 instances of 4 procedural meshes (UV sphere 80x40
                    "60/20/20%, 4 point lights, 1920x1080, max_depth 4; per frame seeded motion + full TLAS rebuild + render")
 WORKLOAD = LARGE_WORKLOAD
 N_LARGE = 1 << 24
-E2E_CHUNK = 1 << 22
+# e2e copy granularity: the step's rays of one kind (measured against 4M- and
+# 8M-ray chunks: 1,043-1,080 against 1,020-1,027 and 951-1,062 Mrays/s; every
+# chunk is a traversal launch with its own tail)
+E2E_CHUNK = 1 << 24
 
 
 def parse(argv=None):
@@ -629,9 +632,9 @@ def large_counts(s, rg, torch, args, motion, d_c, d_a):
 def large_e2e(rg, torch, gs, inst_host, closest, anyhit, steps, first):
     """The large steps end to end: per step the instance transforms, the
     closest-hit rays and the any-hit rays are copied from pinned host memory
-    and the hit records copied back to it, in chunks of E2E_CHUNK rays
-    pipelined over a copy-in stream, the tracing stream and a copy-out stream
-    (two device buffers per kind).  One timed region over all steps.  Returns
+    and the hit records copied back to it, in chunks of E2E_CHUNK rays (by
+    default one per kind) pipelined over a copy-in stream, the tracing stream
+    and a copy-out stream (two device buffers, used by the kinds in turn).  One timed region over all steps.  Returns
     (closest rays, seconds, H2D bytes per step, D2H bytes per step)."""
     n = closest.shape[0]
     pin_c = torch.from_numpy(closest).pin_memory()
@@ -880,8 +883,9 @@ def run_native_large(args, world, rank, local):
         if e2e:
             out["e2e"] = {"value": round(e2e_rays_all / e2e_s_all / 1e6, 2), "unit": "Mrays/s",
                           "h2d_bytes_per_step": int(e2e[2]), "d2h_bytes_per_step": int(e2e[3]),
-                          "note": "rays in pinned host memory, hit records back to pinned host memory, copies of 4M-ray "
-                                  "chunks overlapped with tracing (copy-in, trace, copy-out streams), one timed region"}
+                          "note": "rays in pinned host memory, hit records back to pinned host memory, each kind's rays "
+                                  "copied in while the other kind traces and its hits copied out while the next kind "
+                                  "traces (copy-in, trace, copy-out streams), one timed region"}
     if world == 1 and rank == 0:
         if not args.no_cpu_baseline:
             import oracle
