@@ -76,6 +76,8 @@ def parse(argv=None):
     p.add_argument("--requests", type=int, default=400, help="serving: requests in the Poisson stream")
     p.add_argument("--lanes", type=int, default=0, help="serving: server lanes (0: the library's default)")
     p.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    p.add_argument("--blas", default="sah", choices=["sah", "lbvh"],
+                   help="BLAS build of every scene: binned SAH (RG_BLAS_SAH, for trace speed) or LBVH (for build speed)")
     p.add_argument("--no-medium", action="store_true", help="large: skip the medium render frame")
     p.add_argument("--rays", type=int, default=N_LARGE, help="large: rays of each kind per step")
     p.add_argument("--inflight", type=int, default=4,
@@ -252,6 +254,16 @@ def path_flag(args):
             | (rg.RG_SCENE_NO_PAIR if getattr(args, "no_pair", False) else 0))
 
 
+def blas_flag(args):
+    import paper_2001_09792_gb300 as rg
+    return rg.RG_BLAS_SAH if getattr(args, "blas", "sah") == "sah" else rg.RG_MORTON30
+
+
+def bvh_label(args):
+    return (("compressed 8-wide" if args.compressed else "binary float32") + ", BLAS "
+            + ("binned SAH" if getattr(args, "blas", "sah") == "sah" else "LBVH"))
+
+
 def node_bytes(args):
     return 80 if args.compressed else 64
 
@@ -286,10 +298,11 @@ def run_medium(args, world, rank, local, embedded=False):
 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    gs = rg.GpuScene(s, flags=rg.RG_SCENE_TIMING | path_flag(args))
+    gs = rg.GpuScene(s, flags=rg.RG_SCENE_TIMING | path_flag(args), morton_flags=blas_flag(args))
     torch.cuda.synchronize()
     blas_build_ms = (time.perf_counter() - t0) * 1e3  # four BLAS + first TLAS, host-timed incl. uploads
     blas_build = blas_build_rate(s)
+    blas_build["sah"] = blas_build_rate(s, sah=True)
     blas_ids = [gs.blas[m] for m in s.mesh_id]
     inst_host = [rg.pack_instances(M, blas_ids, s.material_id) for M in motions]
     inst_dev = [torch.from_numpy(x).cuda() for x in inst_host]
@@ -319,7 +332,7 @@ def run_medium(args, world, rank, local, embedded=False):
     torch.cuda.synchronize()
 
     # algorithmic work per closest-hit ray: one counting frame on a second scene
-    with rg.GpuScene(s, flags=rg.RG_SCENE_COUNT | path_flag(args)) as gc:
+    with rg.GpuScene(s, flags=rg.RG_SCENE_COUNT | path_flag(args), morton_flags=blas_flag(args)) as gc:
         rg.rg_tlas_build(gc.h, torch.from_numpy(inst_host[args.warmup]).cuda())
         rg.rg_reset_stats(gc.h)
         rg.rg_render(gc.h, cam, W, H, D)
@@ -554,7 +567,7 @@ def run_medium(args, world, rank, local, embedded=False):
                        "l2": "flushed before each frame (256 MiB write on the frame's stream, inside the timed region)",
                        "fxaa": {"ms": round(fxaa_ms, 4), "gbs": round(W * H * 32 / (fxaa_ms / 1e3) / 1e9, 1),
                                 "bytes_per_pixel": 32, "note": "k_fxaa_luma + k_fxaa on the frame, timed alone, not in the step"},
-                       "parallelism": f"replicas x{world}", "bvh": "compressed 8-wide" if args.compressed else "binary float32"},
+                       "parallelism": f"replicas x{world}", "bvh": bvh_label(args)},
             "roofline": roofline,
             "gpu_launches": int(stats_f[0]["kernel_launches"]),
         }
@@ -567,7 +580,8 @@ def run_medium(args, world, rank, local, embedded=False):
                                   "each image read back on a copy stream while later frames render; one timed "
                                   "region incl. L2 flushes"}
         if not embedded and world == 1 and not args.no_serving:
-            out["serving"] = run_serving(args.requests, pair=not args.no_pair, lanes=args.lanes)
+            out["serving"] = run_serving(args.requests, pair=not args.no_pair, lanes=args.lanes,
+                                         blas_flags=blas_flag(args))
         if not embedded and world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"], ref = cpu_baseline(s, motions[args.warmup:], args.cpu_seconds)
             # the GPU's render and camera-ray records of the oracle's first frame
@@ -578,7 +592,7 @@ def run_medium(args, world, rank, local, embedded=False):
             out["error_vs_oracle"] = {
                 "pixels": pixel_error_vs_oracle(img0.cpu().numpy(), ref["frame"]),
                 "rays": hit_error_vs_oracle(rg.split_hits(hits0), ref["ray_ref"]),
-                "bvh": "compressed 8-wide" if args.compressed else "binary float32",
+                "bvh": bvh_label(args),
                 "sample": f"the whole frame of the first timed motion, and {len(ref['rays']):,} seeded camera rays of "
                           "it traced as closest-hit queries (rg_trace_rays)"}
     for c in ctxs[1:]:
@@ -620,7 +634,7 @@ def ray_bytes(cst, node_b, any_hit):
 def large_counts(s, rg, torch, args, motion, d_c, d_a):
     """Node, triangle and instance counts per ray of the large query (a
     counting traversal on a second scene with the same motion)."""
-    with rg.GpuScene(s, flags=rg.RG_SCENE_COUNT | path_flag(args)) as gc:
+    with rg.GpuScene(s, flags=rg.RG_SCENE_COUNT | path_flag(args), morton_flags=blas_flag(args)) as gc:
         rg.rg_tlas_build(gc.h, torch.from_numpy(rg.pack_instances(motion, [gc.blas[m] for m in s.mesh_id],
                                                                   s.material_id)).cuda())
         rg.rg_reset_stats(gc.h)
@@ -747,7 +761,7 @@ def run_native_large(args, world, rank, local):
     closest, anyhit = g.large_rays(s, n)
     n_frames = args.warmup + args.steps
     motions = [g.motion(s.M, k) for k in range(min(n_frames, 8))]
-    gs = rg.GpuScene(s, flags=rg.RG_SCENE_TIMING | path_flag(args))
+    gs = rg.GpuScene(s, flags=rg.RG_SCENE_TIMING | path_flag(args), morton_flags=blas_flag(args))
     blas_ids = [gs.blas[m] for m in s.mesh_id]
     inst_host = [rg.pack_instances(M, blas_ids, s.material_id) for M in motions]
     inst_dev = [torch.from_numpy(x).cuda() for x in inst_host]
@@ -874,7 +888,7 @@ def run_native_large(args, world, rank, local):
                 "latency": "per step (TLAS rebuild + both queries), CUDA events on the stream",
                 "l2": "inputs larger than L2 (2 x 512 MiB of rays, about 400 MB of BVH and triangle records); "
                       "no flush",
-                "parallelism": f"replicas x{world}", "bvh": "compressed 8-wide" if args.compressed else "binary float32"},
+                "parallelism": f"replicas x{world}", "bvh": bvh_label(args)},
             "roofline": roofline,
             "gpu_launches": int(st["kernel_launches"]),
         }
@@ -907,7 +921,8 @@ def run_native_large(args, world, rank, local):
         if not args.no_medium:
             out["medium"] = medium_summary(run_medium(args_for_medium(args), 1, 0, local, embedded=True))
         if not args.no_serving:
-            out["serving"] = run_serving(args.requests, pair=not args.no_pair, lanes=args.lanes)
+            out["serving"] = run_serving(args.requests, pair=not args.no_pair, lanes=args.lanes,
+                                         blas_flags=blas_flag(args))
     else:
         gs.close()
     if rank == 0:
@@ -964,7 +979,7 @@ def pct(xs, q):
     return xs[min(len(xs) - 1, max(0, math.ceil(q * len(xs)) - 1))]
 
 
-def run_serving(n_requests, admit_rays=0, pair=True, lanes=0):
+def run_serving(n_requests, admit_rays=0, pair=True, lanes=0, blas_flags=0):
     """The request stream through the continuous-batching server in real time,
     then the same stream one request at a time (rg_tlas_refit + rg_render each,
     in arrival order, against the same arrival clock).  Latency = arrival to
@@ -974,7 +989,7 @@ def run_serving(n_requests, admit_rays=0, pair=True, lanes=0):
 
     scenes = g.serving_scenes()
     reqs = g.serving_requests(n_requests)
-    gss = [rg.GpuScene(sc, flags=0 if pair else rg.RG_SCENE_NO_PAIR) for sc in scenes]
+    gss = [rg.GpuScene(sc, flags=0 if pair else rg.RG_SCENE_NO_PAIR, morton_flags=blas_flags) for sc in scenes]
     trans = [g.motion(scenes[q["scene"]].M, q["motion_seed"]) for q in reqs]
     cams = [rg.make_camera(sc.camera) for sc in scenes]
     srv = rg.rg_server_create(admit_rays=admit_rays, flags=0 if pair else rg.RG_SERVER_NO_PAIR, lanes=lanes)
@@ -1088,10 +1103,11 @@ def gpu_index(local):
 
 # ---------------------------------------------------------------- oracle arms
 
-def blas_build_rate(scene, reps=3):
+def blas_build_rate(scene, reps=3, sah=False):
     """BLAS builds of the scene's meshes (LBVH: boxes, Morton codes, radix
-    sort, Karras hierarchy, refit, bounding sphere), inputs already on the
-    device, CUDA events around the builds; the median of `reps` builds."""
+    sort, Karras hierarchy, refit, bounding sphere; with sah the binned-SAH
+    build, one host round trip per tree level), inputs already on the device,
+    CUDA events around the builds; the median of `reps` builds."""
     import torch
     import paper_2001_09792_gb300 as rg
     meshes = [(torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda(),
@@ -1105,7 +1121,7 @@ def blas_build_rate(scene, reps=3):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         for tv, ti in meshes:
-            rg.rg_blas_build(h, tv, ti)
+            rg.rg_blas_build(h, tv, ti, rg.RG_BLAS_SAH if sah else rg.RG_MORTON30)
         e1.record()
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
@@ -1290,7 +1306,7 @@ def run_native_serve(args, world, rank, local):
     _build.build()
     if rank != 0:
         return
-    r = run_serving(args.requests, pair=not args.no_pair, lanes=args.lanes)
+    r = run_serving(args.requests, pair=not args.no_pair, lanes=args.lanes, blas_flags=blas_flag(args))
     out = {"metric": "served Mrays/s and p50/p99 request latency (continuous batching) vs one request at a time",
            "value": r["mrays_s"], "unit": "Mrays/s", "n_gpus": 1, "steps": r["steps"], "warmup": len(g.serving_scenes()),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

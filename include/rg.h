@@ -132,7 +132,7 @@ rg_status rg_scene_destroy(rg_scene* scene);
 
 /* ---- step 1 of the paper's model: the two-layered structure (Sec. 1) ---- */
 
-enum { RG_MORTON30 = 0u, RG_MORTON63 = 1u, RG_COMPRESSED = 2u };
+enum { RG_MORTON30 = 0u, RG_MORTON63 = 1u, RG_COMPRESSED = 2u, RG_BLAS_SAH = 4u };
 /* Largest number of triangles in one leaf slot of the wide BLAS (1..3;
  * default 2), as a flag of rg_blas_build.  (TLAS leaf slots hold one
  * instance each.) */
@@ -142,7 +142,12 @@ enum { RG_MORTON30 = 0u, RG_MORTON63 = 1u, RG_COMPRESSED = 2u };
  * d_vtx: nv x float3 (12 B each); d_idx: nt x uint3 vertex indices (CCW =
  * outward).  flags: RG_MORTON30 (10 bits/axis, u32 keys) or RG_MORTON63 (21
  * bits/axis, u64 keys), plus RG_COMPRESSED to also build the compressed
- * 8-wide BVH (always built in an RG_SCENE_COMPRESSED scene).  Writes the new
+ * 8-wide BVH (always built in an RG_SCENE_COMPRESSED scene), plus
+ * RG_BLAS_SAH to build for trace speed rather than build speed: every split
+ * is chosen by the binned surface-area heuristic (16 bins per axis; below 40
+ * levels the Karras hierarchy of the Morton codes takes over); same node
+ * layout, any query gives the same results, and the build takes one host
+ * round trip per tree level.  Writes the new
  * BLAS id to *blas_id.  nt >= 1;
  * indices must be < nv (checked on the device: RG_ERR_INVALID_ARG at
  * rg_sync).  The mesh is copied; d_vtx/d_idx may be freed after the call

@@ -50,6 +50,7 @@ def lib():
             L.orc_stable_sort.argtypes = [P, u32, P]
             L.orc_karras.argtypes = [P, u32, P, P, P]
             L.orc_range_boxes.argtypes = [P, u32, P, P, P]
+            L.orc_sah_build.argtypes = [P, u32, P, P, P, P]
             L.orc_instance_prep.argtypes = [P, u32, P, P, P, P]
             L.orc_bound_r2.argtypes = [P, u32, P]
             L.orc_bound_r2.restype = ctypes.c_float
@@ -157,6 +158,22 @@ def lbvh_reference(vtx, idx, bits=10):
     boxes = range_boxes(lohi[perm], first, last)
     return dict(lohi=lohi, codes=codes, cbounds=cb, perm=perm, sorted_codes=sk, first=first, last=last,
                 split=split, boxes=boxes)
+
+
+def sah_reference(vtx, idx, bits=10):
+    """The binned-SAH hierarchy of one mesh (the trace-speed BLAS build, see
+    orc_sah_build): dict with the triangle of each leaf (perm), the children of
+    each internal node (child, (n-1, 2) uint32, bit 31 a leaf) and the
+    triangle boxes (lohi, in triangle order)."""
+    lohi = tri_bounds(vtx, idx)
+    codes, _ = morton(lohi, bits)
+    perm = stable_sort(codes)
+    sk = _c(codes[perm], np.uint64)
+    n = lohi.shape[0]
+    perm_out = np.empty(n, np.uint32)
+    child = np.zeros((max(n - 1, 0), 2), np.uint32)
+    lib().orc_sah_build(_p(lohi), n, _p(sk), _p(_c(perm, np.uint32)), _p(perm_out), _p(child))
+    return dict(perm=perm_out, child=child, lohi=lohi)
 
 
 # ---------------------------------------------------------------- float64 scene

@@ -719,6 +719,133 @@ int orc_karras(const uint64_t* k, uint32_t n, int32_t* first, int32_t* last, int
     return 0;
 }
 
+// Binned surface-area-heuristic hierarchy (the BLAS build for trace speed;
+// the paper's framework leaves acceleration structures to the Vulkan driver,
+// so this build is a choice of the implementation, written out here in its
+// plain definition).  The leaves start in Morton order.  A range of c leaves
+// at depth `level` whose root is internal node d:
+//   * c <= 2 or level >= 40: the Karras hierarchy of the range's own keys
+//     (local indices), its node j numbered d + j, its leaf j numbered b + j;
+//   * otherwise, per axis, 16 bins of the centroids c = 0.5 (lo + hi) over the
+//     range's centroid bounds: bin = floor((c - cmin) * s), s = 16 / (cmax -
+//     cmin) (capped at 3e38; 0 for a point), clamped to 0..15 (NaN to 0); the
+//     boundary of least A(left) n(left) + A(right) n(right), A the half area
+//     dx dy + dy dz + dz dx of the union box, taken over axes 0, 1, 2 and
+//     boundaries 1..15 in that order, the first of equal costs kept; when
+//     every side split leaves one side empty, the range is halved by
+//     position.  The range is partitioned stably (left leaves first, each
+//     side in its previous order); node d's children are node d + 1 (or leaf
+//     b when one leaf) and node d + n(left) (or leaf b + n(left)).
+// Every operation is float32 as written (no contraction).  Outputs: perm_out,
+// the triangle of each leaf, and child, two per internal node (bit 31: leaf).
+int orc_sah_build(const float* lohi, uint32_t n, const uint64_t* sorted_keys, const uint32_t* perm_in,
+                  uint32_t* perm_out, uint32_t* child) {
+    const uint32_t kLeafBit = 0x80000000u;
+    std::vector<uint32_t> prim(perm_in, perm_in + n);
+    std::vector<uint64_t> key(sorted_keys, sorted_keys + n);
+    struct Range {
+        uint32_t b, c, d, level;
+    };
+    std::vector<Range> todo;
+    if (n >= 2) todo.push_back({0u, n, 0u, 0u});
+    auto centroid = [&](uint32_t t, int a) { return 0.5f * (lohi[6 * (size_t)t + a] + lohi[6 * (size_t)t + 3 + a]); };
+    auto half_area = [](const float* lo, const float* hi) {
+        const float dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+        return (dx * dy + dy * dz) + dz * dx;
+    };
+    while (!todo.empty()) {
+        const Range R = todo.back();
+        todo.pop_back();
+        if (R.c <= 2 || R.level >= 40) {
+            std::vector<int32_t> f(R.c - 1), l(R.c - 1), sp(R.c - 1);
+            orc_karras(key.data() + R.b, R.c, f.data(), l.data(), sp.data());
+            for (uint32_t j = 0; j + 1 < R.c; ++j) {
+                const uint32_t g = (uint32_t)sp[j];
+                child[2 * (size_t)(R.d + j)] = (uint32_t)f[j] == g ? (kLeafBit | (R.b + g)) : R.d + g;
+                child[2 * (size_t)(R.d + j) + 1] = (uint32_t)l[j] == g + 1 ? (kLeafBit | (R.b + g + 1)) : R.d + g + 1;
+            }
+            continue;
+        }
+        float cmin[3] = {INFINITY, INFINITY, INFINITY}, cmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (uint32_t p = R.b; p < R.b + R.c; ++p)
+            for (int a = 0; a < 3; ++a) {
+                cmin[a] = std::min(cmin[a], centroid(prim[p], a));
+                cmax[a] = std::max(cmax[a], centroid(prim[p], a));
+            }
+        float scale[3];
+        for (int a = 0; a < 3; ++a) {
+            const float ext = cmax[a] - cmin[a];
+            scale[a] = ext > 0.0f ? std::min(16.0f / ext, 3.0e38f) : 0.0f;
+        }
+        auto bin = [&](uint32_t t, int a) {
+            const float v = (centroid(t, a) - cmin[a]) * scale[a];
+            if (!(v >= 0.0f)) return 0;
+            return v < 16.0f ? (int)v : 15;
+        };
+        uint32_t cnt[3][16] = {};
+        float blo[3][16][3], bhi[3][16][3];
+        for (int a = 0; a < 3; ++a)
+            for (int k = 0; k < 16; ++k)
+                for (int q = 0; q < 3; ++q) {
+                    blo[a][k][q] = INFINITY;
+                    bhi[a][k][q] = -INFINITY;
+                }
+        for (uint32_t p = R.b; p < R.b + R.c; ++p)
+            for (int a = 0; a < 3; ++a) {
+                const int k = bin(prim[p], a);
+                ++cnt[a][k];
+                for (int q = 0; q < 3; ++q) {
+                    blo[a][k][q] = std::min(blo[a][k][q], lohi[6 * (size_t)prim[p] + q]);
+                    bhi[a][k][q] = std::max(bhi[a][k][q], lohi[6 * (size_t)prim[p] + 3 + q]);
+                }
+            }
+        float best = INFINITY;
+        int best_axis = -1, best_split = 0;
+        uint32_t nl = R.c / 2;
+        for (int a = 0; a < 3; ++a)
+            for (int s = 1; s < 16; ++s) {
+                float llo[3] = {INFINITY, INFINITY, INFINITY}, lhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+                float rlo[3] = {INFINITY, INFINITY, INFINITY}, rhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+                uint32_t cl = 0, cr = 0;
+                for (int k = 0; k < 16; ++k) {
+                    float* lo = k < s ? llo : rlo;
+                    float* hi = k < s ? lhi : rhi;
+                    (k < s ? cl : cr) += cnt[a][k];
+                    for (int q = 0; q < 3; ++q) {
+                        lo[q] = std::min(lo[q], blo[a][k][q]);
+                        hi[q] = std::max(hi[q], bhi[a][k][q]);
+                    }
+                }
+                if (cl == 0 || cr == 0) continue;
+                const float cost = half_area(llo, lhi) * (float)cl + half_area(rlo, rhi) * (float)cr;
+                if (cost < best) {
+                    best = cost;
+                    best_axis = a;
+                    best_split = s;
+                    nl = cl;
+                }
+            }
+        std::vector<uint32_t> lp, rp;
+        std::vector<uint64_t> lk, rk;
+        for (uint32_t p = R.b; p < R.b + R.c; ++p) {
+            const bool left = best_axis < 0 ? (p - R.b < nl) : (bin(prim[p], best_axis) < best_split);
+            (left ? lp : rp).push_back(prim[p]);
+            (left ? lk : rk).push_back(key[p]);
+        }
+        std::copy(lp.begin(), lp.end(), prim.begin() + R.b);
+        std::copy(rp.begin(), rp.end(), prim.begin() + R.b + nl);
+        std::copy(lk.begin(), lk.end(), key.begin() + R.b);
+        std::copy(rk.begin(), rk.end(), key.begin() + R.b + nl);
+        const uint32_t nr = R.c - nl;
+        child[2 * (size_t)R.d] = nl == 1 ? (kLeafBit | R.b) : R.d + 1;
+        child[2 * (size_t)R.d + 1] = nr == 1 ? (kLeafBit | (R.b + nl)) : R.d + nl;
+        if (nl >= 2) todo.push_back({R.b, nl, R.d + 1, R.level + 1});
+        if (nr >= 2) todo.push_back({R.b + nl, nr, R.d + nl, R.level + 1});
+    }
+    std::copy(prim.begin(), prim.end(), perm_out);
+    return 0;
+}
+
 // Box of every internal node = union of the (sorted) leaf boxes in its range.
 int orc_range_boxes(const float* lohi_sorted, uint32_t n, const int32_t* first, const int32_t* last, float* boxes) {
     for (uint32_t i = 0; i + 1 < n; ++i) {

@@ -30,6 +30,7 @@ RG_SCENE_COMPRESSED = 4
 RG_SCENE_NO_PAIR = 8
 RG_SCENE_FRUGAL = 16
 RG_COMPRESSED = 2
+RG_BLAS_SAH = 4
 RG_TLAS_ID = 0xFFFFFFFF
 RG_MAT_DIFFUSE, RG_MAT_MIRROR, RG_MAT_GLASS = 0, 1, 2
 MISS = 0xFFFFFFFF

@@ -17,7 +17,7 @@ OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librg.so")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 
-SOURCES = ["build.cu", "wide.cu", "trace.cu", "render.cu", "api.cu", "noalloc.cu", "serve.cu"]
+SOURCES = ["build.cu", "wide.cu", "sah.cu", "trace.cu", "render.cu", "api.cu", "noalloc.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", f"-I{INCLUDE}"]

@@ -309,11 +309,16 @@ __device__ __forceinline__ int delta(const K* __restrict__ k, int64_t n, int64_t
 
 // Internal node i of the Karras hierarchy over n sorted keys: its children
 // (bit 31 marks a leaf) into child_base[i * stride], its key range into
-// ranges (optional), its children's parent entries (optional).
+// ranges (optional), its children's parent entries (optional).  For a
+// segment of a larger tree (node_off > 0), node and leaf indices are offset by
+// node_off and leaf_off, parents are laid out for n_all leaves, and the
+// segment root's own parent entry is left alone.
 template <class K>
 __device__ __forceinline__ void karras_node(const K* __restrict__ keys, uint32_t n, int64_t i,
                                             uint32_t* __restrict__ child_base, int stride, uint32_t* __restrict__ parents,
-                                            uint32_t* __restrict__ ranges) {
+                                            uint32_t* __restrict__ ranges, uint32_t node_off = 0, uint32_t leaf_off = 0,
+                                            uint32_t n_all = 0) {
+    if (n_all == 0) n_all = n;
     const int64_t N = n;
     int d = (delta(keys, N, i, i + 1) - delta(keys, N, i, i - 1)) >= 0 ? 1 : -1;
     int dmin = delta(keys, N, i, i - d);
@@ -333,19 +338,41 @@ __device__ __forceinline__ void karras_node(const K* __restrict__ keys, uint32_t
     } while (t > 1);
     int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
     int64_t lo = i < j ? i : j, hi = i < j ? j : i;
-    uint32_t left = (lo == gamma) ? (kLeaf | (uint32_t)gamma) : (uint32_t)gamma;
-    uint32_t right = (hi == gamma + 1) ? (kLeaf | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
-    child_base[(size_t)i * stride] = left;
-    child_base[(size_t)i * stride + 1] = right;
+    uint32_t left = (lo == gamma) ? (kLeaf | (leaf_off + (uint32_t)gamma)) : node_off + (uint32_t)gamma;
+    uint32_t right = (hi == gamma + 1) ? (kLeaf | (leaf_off + (uint32_t)(gamma + 1))) : node_off + (uint32_t)(gamma + 1);
+    const size_t me = node_off + (size_t)i;
+    child_base[me * stride] = left;
+    child_base[me * stride + 1] = right;
     if (ranges) {
-        ranges[2 * (size_t)i] = (uint32_t)lo;
-        ranges[2 * (size_t)i + 1] = (uint32_t)hi;
+        ranges[2 * me] = leaf_off + (uint32_t)lo;
+        ranges[2 * me + 1] = leaf_off + (uint32_t)hi;
     }
     if (parents) {
-        parents[(left & kLeaf) ? (size_t)(n - 1) + (left & ~kLeaf) : left] = (uint32_t)i;
-        parents[(right & kLeaf) ? (size_t)(n - 1) + (right & ~kLeaf) : right] = (uint32_t)i;
-        if (i == 0) parents[0] = kNone;
+        parents[(left & kLeaf) ? (size_t)(n_all - 1) + (left & ~kLeaf) : left] = (uint32_t)me;
+        parents[(right & kLeaf) ? (size_t)(n_all - 1) + (right & ~kLeaf) : right] = (uint32_t)me;
+        if (i == 0 && node_off == 0) parents[0] = kNone;
     }
+}
+
+// One thread per internal node of all segments: the segment by binary search
+// over the segments' first thread numbers.
+template <class K>
+__global__ void k_karras_segments(const K* __restrict__ keys, const KarrasSeg* __restrict__ segs, uint32_t n_segs,
+                                  uint32_t n_threads, uint32_t n_leaves, uint32_t* __restrict__ child_base,
+                                  uint32_t* __restrict__ parents, uint32_t* __restrict__ ranges) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_threads) return;
+    uint32_t lo = 0, hi = n_segs - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) / 2;
+        if (segs[mid].first <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const KarrasSeg S = segs[lo];
+    karras_node(keys + S.begin, S.count, (int64_t)(g - S.first), child_base, 16, parents, ranges, S.node, S.begin,
+                n_leaves);
 }
 
 template <class K>
@@ -768,6 +795,21 @@ __global__ void k_invert_perm(const uint32_t* __restrict__ perm, uint32_t n, uin
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) inv[perm[j]] = j;
 }
 }  // namespace
+
+cudaError_t launch_karras_segments(const void* keys, int key_bits, const KarrasSeg* segs, uint32_t n_segs,
+                                   uint32_t n_threads, uint32_t n_leaves, float4* nodes, uint32_t* parents,
+                                   uint32_t* ranges, cudaStream_t s) {
+    if (n_segs == 0 || n_threads == 0) return cudaSuccess;
+    uint32_t* child_base = reinterpret_cast<uint32_t*>(nodes) + 12;
+    if (key_bits == 64)
+        k_karras_segments<uint64_t><<<grid_for(n_threads), kBlock, 0, s>>>(
+            static_cast<const uint64_t*>(keys), segs, n_segs, n_threads, n_leaves, child_base, parents, ranges);
+    else
+        k_karras_segments<uint32_t><<<grid_for(n_threads), kBlock, 0, s>>>(
+            static_cast<const uint32_t*>(keys), segs, n_segs, n_threads, n_leaves, child_base, parents, ranges);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_invert_perm(const uint32_t* perm, uint32_t n, uint32_t* inv, cudaStream_t s) {
     if (n == 0) return cudaSuccess;

@@ -205,6 +205,54 @@ cudaError_t launch_tlas_leaves_refit(const InstDev* tmp, const float* wbox, cons
                                      const uint32_t* parents, float4* nodes, uint32_t* flags, InstDev* inst_out,
                                      DevStatus* st, cudaStream_t s);
 
+// Karras hierarchies over segments of the sorted keys (the bottom of the SAH
+// build): segment k spans leaves begin .. begin + count - 1 and its internal
+// nodes are node .. node + count - 2 (its root is `node`, whose parent entry
+// the caller writes); `first` numbers its internal nodes in one flat range of
+// n_threads threads (ascending over the segments).
+struct KarrasSeg {
+    uint32_t begin, count, node, first;
+};
+cudaError_t launch_karras_segments(const void* keys, int key_bits, const KarrasSeg* segs, uint32_t n_segs,
+                                   uint32_t n_threads, uint32_t n_leaves, float4* nodes, uint32_t* parents,
+                                   uint32_t* ranges, cudaStream_t s);
+
+// sah.cu: binned-SAH topology, one level of segments per launch sequence.
+constexpr int kSahBins = 16;            // bins per axis
+constexpr uint32_t kSahChunk = 2048;    // triangles per block of a level's kernels
+constexpr uint32_t kSahSmall = 2;       // segments of at most this many triangles get the Karras hierarchy
+constexpr uint32_t kSahMaxLevels = 40;  // deeper segments get the Karras hierarchy whatever their size
+constexpr uint32_t kSahAccInts = 6 + 3 * kSahBins * 7;  // per task: centroid bounds, then 7 values per bin and axis
+struct SahTask {                        // one segment split at this level
+    uint32_t begin, count, node;        // leaves begin .. begin + count - 1, internal node `node`
+    uint32_t first_block, n_blocks;     // its blocks in the level's block list
+    uint32_t pad[3];
+};
+struct SahParam {                       // per task: binning frame and the chosen split
+    float cmin[3], scale[3];
+    int axis, split;                    // axis -1: halved by position
+    uint32_t nl;                        // triangles on the left
+    uint32_t pad[3];
+};
+struct SahLevel {
+    const float* lohi;                  // triangle boxes (lo xyz, hi xyz)
+    uint32_t n_leaves, m, n_blocks;     // triangles of the mesh, tasks, blocks
+    const SahTask* tasks;
+    const uint2* blk;                   // per block: task, first position of its chunk
+    int* acc;                           // per task: centroid bounds and bins (scratch)
+    SahParam* par;
+    uint32_t* prim_at;                  // triangle at each position (updated)
+    void* key_at;                       // its Morton code (updated)
+    uint32_t* prim_out;                 // scratch, n
+    void* key_out;                      // scratch, n
+    uint32_t *blk_left, *blk_off;       // scratch, per block
+    uint32_t* out_nl;                   // per task: triangles on the left
+    float4* nodes;
+    uint32_t* parents;
+    uint32_t* ranges;                   // may be null
+};
+cudaError_t launch_sah_level(const SahLevel& L, int key_bits, cudaStream_t s);
+
 // wide.cu
 // Collapse a binary LBVH (n leaves) into a compressed 8-wide BVH in one
 // single-block launch.  Items are triangles (tris2 -> tris8) or instances

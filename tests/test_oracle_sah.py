@@ -1,0 +1,140 @@
+"""Pins of the oracle's binned-SAH build (orc_sah_build) against closed forms
+and invariants: rows of equal boxes along each axis give the balanced tree
+the heuristic's cost 2 s^2 + 2 (16 - s)^2 (least at s = 8) implies; two distant
+clusters are separated at the root; identical centroids are halved by
+position; every tree is valid with contiguous leaf ranges; the surface-area
+cost is below the LBVH's.  (The hand-over to the Karras hierarchy below 40
+levels is not pinned: no input found reaches that depth, since the binned
+heuristic splits several boxes off a geometric series per level.)"""
+import numpy as np
+import pytest
+
+import oracle
+import scenegen as g
+
+LEAF = 0x80000000
+
+
+def tree_ranges(child, n):
+    """(first, last, depth) of every internal node; asserts each node and leaf
+    is reached once from the root and each subtree's leaves are contiguous."""
+    child = np.asarray(child, np.int64).reshape(-1, 2)
+    m = max(n - 1, 0)
+    seen = np.zeros(m, bool)
+    depth = np.zeros(m, np.int64)
+    order, stack = [], [0] if n > 1 else []
+    while stack:
+        k = stack.pop()
+        assert not seen[k], f"node {k} reached twice"
+        seen[k] = True
+        order.append(k)
+        for c in child[k]:
+            if not c & LEAF:
+                depth[c] = depth[k] + 1
+                stack.append(int(c))
+    assert len(order) == m
+    size = np.zeros(m, np.int64)
+    for k in reversed(order):
+        size[k] = sum(1 if c & LEAF else size[c] for c in child[k])
+    first = np.zeros(m, np.int64)
+    leaves = np.zeros(n, bool)
+    for k in order:
+        f = first[k]
+        for c in child[k]:
+            if c & LEAF:
+                assert (c & ~LEAF) == f, (k, c, f)
+                assert not leaves[f]
+                leaves[f] = True
+                f += 1
+            else:
+                first[c] = f
+                f += size[c]
+    assert n <= 1 or leaves.all()
+    return first, first + size - 1, depth
+
+
+def boxes_mesh(lo, hi):
+    """One triangle per box, spanning the box's lo and hi corners (its own
+    bounding box is the box)."""
+    lo, hi = np.asarray(lo, np.float32), np.asarray(hi, np.float32)
+    n = lo.shape[0]
+    v = np.empty((3 * n, 3), np.float32)
+    v[0::3] = lo
+    v[1::3] = hi
+    v[2::3] = np.c_[hi[:, 0], lo[:, 1], hi[:, 2]]
+    return v, np.arange(3 * n, dtype=np.uint32).reshape(n, 3)
+
+
+def sah_cost(lohi_leaves, first, last):
+    lo = np.array([lohi_leaves[f:l + 1, :3].min(0) for f, l in zip(first, last)], np.float64)
+    hi = np.array([lohi_leaves[f:l + 1, 3:].max(0) for f, l in zip(first, last)], np.float64)
+    d = hi - lo
+    a = d[:, 0] * d[:, 1] + d[:, 1] * d[:, 2] + d[:, 2] * d[:, 0]
+    return a.sum() / a[0]
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_row_of_equal_boxes_is_balanced(axis):
+    k = np.arange(16, dtype=np.float32)
+    lo = np.zeros((16, 3), np.float32)
+    hi = np.ones((16, 3), np.float32)
+    lo[:, axis] = k
+    hi[:, axis] = k + 0.5
+    v, i = boxes_mesh(lo, hi)
+    r = oracle.sah_reference(v, i)
+    first, last, _ = tree_ranges(r["child"], 16)
+    for f, l, c in zip(first, last, r["child"]):
+        n = l - f + 1
+        left = 1 if c[0] & LEAF else None
+        if left is None:
+            left_last = last[c[0]]
+            left = left_last - f + 1
+        assert left == n // 2, (f, l, left)
+    # leaves in spatial order along the axis
+    assert np.array_equal(r["perm"], np.arange(16))
+
+
+def test_distant_clusters_split_at_the_root():
+    rng = np.random.default_rng(3)
+    a = rng.uniform(0, 1, (40, 3)).astype(np.float32)
+    b = rng.uniform(0, 1, (25, 3)).astype(np.float32) + np.float32([100, 0, 0])
+    lo = np.r_[a, b]
+    v, i = boxes_mesh(lo, lo + np.float32(0.05))
+    r = oracle.sah_reference(v, i)
+    first, last, _ = tree_ranges(r["child"], 65)
+    c0 = int(r["child"][0][0])
+    left = set(r["perm"][first[0]:(last[c0] if not c0 & LEAF else 0) + 1].tolist())
+    assert left in (set(range(40)), set(range(40, 65)))
+
+
+def test_identical_centroids_are_halved():
+    v = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
+    i = np.zeros((37, 3), np.uint32) + [0, 1, 2]
+    r = oracle.sah_reference(v, i)
+    first, last, _ = tree_ranges(r["child"], 37)
+    for k, c in enumerate(r["child"]):
+        n = last[k] - first[k] + 1
+        if n <= 2:
+            continue
+        left = 1 if c[0] & LEAF else last[c[0]] - first[k] + 1
+        assert left == n // 2
+
+
+@pytest.mark.parametrize("mesh", ["ico4", "soup", "large1"])
+def test_valid_and_cheaper_than_lbvh(mesh):
+    if mesh == "ico4":
+        v, i = g.make_mesh("ico", 4)
+    elif mesh == "soup":
+        rng = np.random.default_rng(7)
+        v = rng.normal(size=(5000, 3)).astype(np.float32)
+        i = rng.integers(0, 5000, size=(7001, 3)).astype(np.uint32)
+    else:
+        v, i = g.large_scene().meshes[1]          # 25,600 triangles
+    n = i.shape[0]
+    r = oracle.sah_reference(v, i)
+    assert np.array_equal(np.sort(r["perm"]), np.arange(n))
+    first, last, depth = tree_ranges(r["child"], n)
+    ref = oracle.lbvh_reference(v, i)
+    cs = sah_cost(r["lohi"][r["perm"]], first, last)
+    cl = sah_cost(ref["lohi"][ref["perm"]], ref["first"], ref["last"])
+    assert cs < 0.97 * cl, (cs, cl)
