@@ -3,6 +3,7 @@
 // build, trace and render calls.  See include/rg.h for the contract.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstddef>
 #include <cstdio>
@@ -322,103 +323,9 @@ rg_status lbvh_topology(TempAlloc& tmp, const float* lohi, uint32_t n, const int
     return RG_OK;
 }
 
-// Binned-SAH topology (RG_BLAS_SAH, sah.cu): the LBVH's Morton sort, then
-// levels of SAH splits over the segments of more than kSahSmall triangles
-// (one host round trip per level for the left counts), then the Karras
-// hierarchy inside every remaining segment.  Same outputs as lbvh_topology.
-rg_status sah_topology(TempAlloc& tmp, const float* lohi, uint32_t n, const int* cb_ord, int bits, float4* nodes,
-                       uint32_t* perm, uint32_t* parents, cudaStream_t s, uint32_t* ranges = nullptr) {
-    const int key_bits = bits == 21 ? 64 : 32;
-    const size_t kb = key_bits / 8;
-    void *codes, *sorted, *vals, *scratch;
-    rg_status r;
-    if ((r = tmp.get(&codes, n * kb, "morton codes"))) return r;
-    if ((r = tmp.get(&sorted, n * kb, "sorted codes"))) return r;
-    if ((r = tmp.get(&vals, n * 4ull, "sort values"))) return r;
-    if ((r = tmp.get(&scratch, radix_sort_scratch_bytes(n, key_bits), "sort scratch"))) return r;
-    RG_CK(launch_morton(lohi, n, cb_ord, bits, codes, static_cast<uint32_t*>(vals), nullptr, s));
-    RG_CK(radix_sort_pairs(codes, static_cast<uint32_t*>(vals), n, key_bits, sorted, perm, scratch, s));
-    if (n <= kSahSmall) {
-        RG_CK(launch_karras(sorted, n, key_bits, reinterpret_cast<uint32_t*>(nodes) + 12, 16, parents, s, ranges));
-        return RG_OK;
-    }
-    const uint32_t max_tasks = n / (kSahSmall + 1) + 1;
-    const uint32_t max_blocks = n / kSahChunk + max_tasks;
-    void *prim_out, *key_out, *d_tasks, *d_blk, *acc, *par, *blk_left, *blk_off, *out_nl;
-    if ((r = tmp.get(&prim_out, n * 4ull, "SAH positions")) || (r = tmp.get(&key_out, n * kb, "SAH keys")) ||
-        (r = tmp.get(&d_tasks, (size_t)max_tasks * sizeof(SahTask), "SAH tasks")) ||
-        (r = tmp.get(&d_blk, (size_t)max_blocks * sizeof(uint2), "SAH blocks")) ||
-        (r = tmp.get(&acc, (size_t)max_tasks * kSahAccInts * 4, "SAH bins")) ||
-        (r = tmp.get(&par, (size_t)max_tasks * sizeof(SahParam), "SAH splits")) ||
-        (r = tmp.get(&blk_left, (size_t)max_blocks * 4, "SAH block counts")) ||
-        (r = tmp.get(&blk_off, (size_t)max_blocks * 4, "SAH block offsets")) ||
-        (r = tmp.get(&out_nl, (size_t)max_tasks * 4, "SAH left counts")))
-        return r;
-    std::vector<SahTask> tasks(1);
-    tasks[0] = SahTask{0u, n, 0u, 0u, 0u, {0u, 0u, 0u}};
-    std::vector<KarrasSeg> segs;
-    uint32_t seg_threads = 0;
-    std::vector<uint2> blk;
-    std::vector<uint32_t> nl;
-    for (uint32_t level = 0; !tasks.empty(); ++level) {
-        blk.clear();
-        for (uint32_t t = 0; t < (uint32_t)tasks.size(); ++t) {
-            tasks[t].first_block = (uint32_t)blk.size();
-            for (uint32_t p = tasks[t].begin; p < tasks[t].begin + tasks[t].count; p += kSahChunk)
-                blk.push_back(make_uint2(t, p));
-            tasks[t].n_blocks = (uint32_t)blk.size() - tasks[t].first_block;
-        }
-        const uint32_t m = (uint32_t)tasks.size();
-        RG_CK(cudaMemcpyAsync(d_tasks, tasks.data(), m * sizeof(SahTask), cudaMemcpyHostToDevice, s));
-        RG_CK(cudaMemcpyAsync(d_blk, blk.data(), blk.size() * sizeof(uint2), cudaMemcpyHostToDevice, s));
-        SahLevel L{};
-        L.lohi = lohi;
-        L.n_leaves = n;
-        L.m = m;
-        L.n_blocks = (uint32_t)blk.size();
-        L.tasks = static_cast<const SahTask*>(d_tasks);
-        L.blk = static_cast<const uint2*>(d_blk);
-        L.acc = static_cast<int*>(acc);
-        L.par = static_cast<SahParam*>(par);
-        L.prim_at = perm;
-        L.key_at = sorted;
-        L.prim_out = static_cast<uint32_t*>(prim_out);
-        L.key_out = key_out;
-        L.blk_left = static_cast<uint32_t*>(blk_left);
-        L.blk_off = static_cast<uint32_t*>(blk_off);
-        L.out_nl = static_cast<uint32_t*>(out_nl);
-        L.nodes = nodes;
-        L.parents = parents;
-        L.ranges = ranges;
-        RG_CK(launch_sah_level(L, key_bits, s));
-        nl.resize(m);
-        RG_CK(cudaMemcpyAsync(nl.data(), out_nl, m * 4ull, cudaMemcpyDeviceToHost, s));
-        RG_CK(cudaStreamSynchronize(s));
-        std::vector<SahTask> next;
-        auto child = [&](uint32_t b, uint32_t c, uint32_t node) {
-            if (c <= 1) return;
-            if (c <= kSahSmall || level + 1 >= kSahMaxLevels) {
-                segs.push_back(KarrasSeg{b, c, node, seg_threads});
-                seg_threads += c - 1;
-            } else {
-                next.push_back(SahTask{b, c, node, 0u, 0u, {0u, 0u, 0u}});
-            }
-        };
-        for (uint32_t t = 0; t < m; ++t) {
-            const SahTask& T = tasks[t];
-            child(T.begin, nl[t], T.node + 1);
-            child(T.begin + nl[t], T.count - nl[t], T.node + nl[t]);
-        }
-        tasks.swap(next);
-    }
-    if (!segs.empty()) {
-        void* d_segs;
-        if ((r = tmp.get(&d_segs, segs.size() * sizeof(KarrasSeg), "Karras segments"))) return r;
-        RG_CK(cudaMemcpyAsync(d_segs, segs.data(), segs.size() * sizeof(KarrasSeg), cudaMemcpyHostToDevice, s));
-        RG_CK(launch_karras_segments(sorted, key_bits, static_cast<const KarrasSeg*>(d_segs), (uint32_t)segs.size(),
-                                     seg_threads, n, nodes, parents, ranges, s));
-    }
-    return RG_OK;
+// The call's stream-ordered temporaries, for builders outside this file.
+rg_status temp_get(void* ctx, void** p, size_t bytes, const char* what) {
+    return static_cast<TempAlloc*>(ctx)->get(p, bytes, what);
 }
 
 }  // namespace
@@ -624,11 +531,15 @@ rg_status rg_blas_build(rg_scene* s, const float* d_vtx, uint32_t nv, const uint
              RG_CK(launch_init_bounds(static_cast<int*>(cb), st));
              RG_CK(launch_tri_bounds(d_vtx, nv, d_idx, nt, static_cast<float*>(lohi), static_cast<int*>(cb), s->st, st));
              if (nt > 1) {
-                 auto topology = (flags & RG_BLAS_SAH) ? sah_topology : lbvh_topology;
-                 if ((q = topology(tmp, static_cast<float*>(lohi), nt, static_cast<int*>(cb), bits, b.nodes,
-                                   static_cast<uint32_t*>(perm), static_cast<uint32_t*>(parents), st,
-                                   static_cast<uint32_t*>(ranges))))
-                     return q;
+                 if (flags & RG_BLAS_SAH)
+                     q = sah_topology(ScratchAlloc{temp_get, &tmp}, static_cast<float*>(lohi), nt,
+                                      static_cast<int*>(cb), bits, b.nodes, static_cast<uint32_t*>(perm),
+                                      static_cast<uint32_t*>(parents), st, static_cast<uint32_t*>(ranges));
+                 else
+                     q = lbvh_topology(tmp, static_cast<float*>(lohi), nt, static_cast<int*>(cb), bits, b.nodes,
+                                       static_cast<uint32_t*>(perm), static_cast<uint32_t*>(parents), st,
+                                       static_cast<uint32_t*>(ranges));
+                 if (q) return q;
                  RG_CK(cudaMemsetAsync(fl, 0, (size_t)(nt - 1) * 4, st));
              } else {
                  RG_CK(cudaMemsetAsync(perm, 0, 4, st));

@@ -222,6 +222,7 @@ constexpr int kSahBins = 16;            // bins per axis
 constexpr uint32_t kSahChunk = 2048;    // triangles per block of a level's kernels
 constexpr uint32_t kSahSmall = 2;       // segments of at most this many triangles get the Karras hierarchy
 constexpr uint32_t kSahMaxLevels = 40;  // deeper segments get the Karras hierarchy whatever their size
+constexpr uint32_t kSahSliceTasks = 65536;  // segments per launch sequence (bounds the scratch)
 constexpr uint32_t kSahAccInts = 6 + 3 * kSahBins * 7;  // per task: centroid bounds, then 7 values per bin and axis
 struct SahTask {                        // one segment split at this level
     uint32_t begin, count, node;        // leaves begin .. begin + count - 1, internal node `node`
@@ -252,6 +253,18 @@ struct SahLevel {
     uint32_t* ranges;                   // may be null
 };
 cudaError_t launch_sah_level(const SahLevel& L, int key_bits, cudaStream_t s);
+// Device temporaries of one library call (stream-ordered, freed when the call
+// returns); get() reports its own failures.
+struct ScratchAlloc {
+    rg_status (*get)(void* ctx, void** p, size_t bytes, const char* what);
+    void* ctx;
+};
+// The binned-SAH topology over n triangle boxes: Morton sort into perm, then
+// the SAH levels (one host round trip each) and the Karras hierarchy inside
+// the remaining segments; children, parents and (optional) leaf ranges as the
+// LBVH emits them.
+rg_status sah_topology(const ScratchAlloc& tmp, const float* lohi, uint32_t n, const int* cb_ord, int bits,
+                       float4* nodes, uint32_t* perm, uint32_t* parents, cudaStream_t s, uint32_t* ranges);
 
 // wide.cu
 // Collapse a binary LBVH (n leaves) into a compressed 8-wide BVH in one

@@ -15,6 +15,10 @@
 // the order of the atomics, and from one thread's fixed-order sweep, so the
 // build is deterministic.  The node boxes are computed afterwards by the
 // LBVH's bottom-up refit.
+#include <algorithm>
+#include <string>
+#include <vector>
+
 #include "rg_internal.cuh"
 
 namespace rg {
@@ -397,5 +401,125 @@ cudaError_t launch_sah_level(const SahLevel& L, int key_bits, cudaStream_t s) {
     if (L.m == 0) return cudaSuccess;
     return key_bits == 64 ? sah_level_t<uint64_t>(L, s) : sah_level_t<uint32_t>(L, s);
 }
+
+namespace {
+rg_status sah_cuda_fail(cudaError_t e, const char* what) {
+    cudaGetLastError();  // clear a sticky launch error
+    return report_error(e == cudaErrorMemoryAllocation ? RG_ERR_OOM : RG_ERR_CUDA,
+                        (std::string(what) + ": " + cudaGetErrorString(e)).c_str());
+}
+}  // namespace
+
+#define SAH_CK(call)                                             \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return sah_cuda_fail(e_, #call);  \
+    } while (0)
+
+// Binned-SAH topology (RG_BLAS_SAH): the LBVH's Morton sort, then
+// levels of SAH splits over the segments of more than kSahSmall triangles
+// (one host round trip per level for the left counts), then the Karras
+// hierarchy inside every remaining segment.  Same outputs as lbvh_topology.
+rg_status sah_topology(const ScratchAlloc& tmp, const float* lohi, uint32_t n, const int* cb_ord, int bits, float4* nodes,
+                       uint32_t* perm, uint32_t* parents, cudaStream_t s, uint32_t* ranges) {
+    const int key_bits = bits == 21 ? 64 : 32;
+    const size_t kb = key_bits / 8;
+    void *codes, *sorted, *vals, *scratch;
+    rg_status r;
+    if ((r = tmp.get(tmp.ctx, &codes, n * kb, "morton codes"))) return r;
+    if ((r = tmp.get(tmp.ctx, &sorted, n * kb, "sorted codes"))) return r;
+    if ((r = tmp.get(tmp.ctx, &vals, n * 4ull, "sort values"))) return r;
+    if ((r = tmp.get(tmp.ctx, &scratch, radix_sort_scratch_bytes(n, key_bits), "sort scratch"))) return r;
+    SAH_CK(launch_morton(lohi, n, cb_ord, bits, codes, static_cast<uint32_t*>(vals), nullptr, s));
+    SAH_CK(radix_sort_pairs(codes, static_cast<uint32_t*>(vals), n, key_bits, sorted, perm, scratch, s));
+    if (n <= kSahSmall) {
+        SAH_CK(launch_karras(sorted, n, key_bits, reinterpret_cast<uint32_t*>(nodes) + 12, 16, parents, s, ranges));
+        return RG_OK;
+    }
+    // a level's segments go through the kernels in slices of at most
+    // kSahSliceTasks, which bounds the bins' scratch (1,368 B per segment)
+    const uint32_t max_tasks = std::min(n / (kSahSmall + 1) + 1, kSahSliceTasks);
+    const uint32_t max_blocks = n / kSahChunk + max_tasks;
+    void *prim_out, *key_out, *d_tasks, *d_blk, *acc, *par, *blk_left, *blk_off, *out_nl;
+    if ((r = tmp.get(tmp.ctx, &prim_out, n * 4ull, "SAH positions")) || (r = tmp.get(tmp.ctx, &key_out, n * kb, "SAH keys")) ||
+        (r = tmp.get(tmp.ctx, &d_tasks, (size_t)max_tasks * sizeof(SahTask), "SAH tasks")) ||
+        (r = tmp.get(tmp.ctx, &d_blk, (size_t)max_blocks * sizeof(uint2), "SAH blocks")) ||
+        (r = tmp.get(tmp.ctx, &acc, (size_t)max_tasks * kSahAccInts * 4, "SAH bins")) ||
+        (r = tmp.get(tmp.ctx, &par, (size_t)max_tasks * sizeof(SahParam), "SAH splits")) ||
+        (r = tmp.get(tmp.ctx, &blk_left, (size_t)max_blocks * 4, "SAH block counts")) ||
+        (r = tmp.get(tmp.ctx, &blk_off, (size_t)max_blocks * 4, "SAH block offsets")) ||
+        (r = tmp.get(tmp.ctx, &out_nl, (size_t)max_tasks * 4, "SAH left counts")))
+        return r;
+    std::vector<SahTask> tasks(1);
+    tasks[0] = SahTask{0u, n, 0u, 0u, 0u, {0u, 0u, 0u}};
+    std::vector<KarrasSeg> segs;
+    uint32_t seg_threads = 0;
+    std::vector<uint2> blk;
+    std::vector<uint32_t> nl;
+    std::vector<SahTask> next;
+    for (uint32_t level = 0; !tasks.empty(); ++level) {
+        next.clear();
+        for (size_t t0 = 0; t0 < tasks.size(); t0 += kSahSliceTasks) {
+            const uint32_t m = (uint32_t)std::min(tasks.size() - t0, (size_t)kSahSliceTasks);
+            SahTask* slice = tasks.data() + t0;
+            blk.clear();
+            for (uint32_t t = 0; t < m; ++t) {
+                slice[t].first_block = (uint32_t)blk.size();
+                for (uint32_t p = slice[t].begin; p < slice[t].begin + slice[t].count; p += kSahChunk)
+                    blk.push_back(make_uint2(t, p));
+                slice[t].n_blocks = (uint32_t)blk.size() - slice[t].first_block;
+            }
+            SAH_CK(cudaMemcpyAsync(d_tasks, slice, m * sizeof(SahTask), cudaMemcpyHostToDevice, s));
+            SAH_CK(cudaMemcpyAsync(d_blk, blk.data(), blk.size() * sizeof(uint2), cudaMemcpyHostToDevice, s));
+            SahLevel L{};
+            L.lohi = lohi;
+            L.n_leaves = n;
+            L.m = m;
+            L.n_blocks = (uint32_t)blk.size();
+            L.tasks = static_cast<const SahTask*>(d_tasks);
+            L.blk = static_cast<const uint2*>(d_blk);
+            L.acc = static_cast<int*>(acc);
+            L.par = static_cast<SahParam*>(par);
+            L.prim_at = perm;
+            L.key_at = sorted;
+            L.prim_out = static_cast<uint32_t*>(prim_out);
+            L.key_out = key_out;
+            L.blk_left = static_cast<uint32_t*>(blk_left);
+            L.blk_off = static_cast<uint32_t*>(blk_off);
+            L.out_nl = static_cast<uint32_t*>(out_nl);
+            L.nodes = nodes;
+            L.parents = parents;
+            L.ranges = ranges;
+            SAH_CK(launch_sah_level(L, key_bits, s));
+            nl.resize(m);
+            SAH_CK(cudaMemcpyAsync(nl.data(), out_nl, m * 4ull, cudaMemcpyDeviceToHost, s));
+            SAH_CK(cudaStreamSynchronize(s));
+            auto child = [&](uint32_t b, uint32_t c, uint32_t node) {
+                if (c <= 1) return;
+                if (c <= kSahSmall || level + 1 >= kSahMaxLevels) {
+                    segs.push_back(KarrasSeg{b, c, node, seg_threads});
+                    seg_threads += c - 1;
+                } else {
+                    next.push_back(SahTask{b, c, node, 0u, 0u, {0u, 0u, 0u}});
+                }
+            };
+            for (uint32_t t = 0; t < m; ++t) {
+                const SahTask& T = slice[t];
+                child(T.begin, nl[t], T.node + 1);
+                child(T.begin + nl[t], T.count - nl[t], T.node + nl[t]);
+            }
+        }
+        tasks.swap(next);
+    }
+    if (!segs.empty()) {
+        void* d_segs;
+        if ((r = tmp.get(tmp.ctx, &d_segs, segs.size() * sizeof(KarrasSeg), "Karras segments"))) return r;
+        SAH_CK(cudaMemcpyAsync(d_segs, segs.data(), segs.size() * sizeof(KarrasSeg), cudaMemcpyHostToDevice, s));
+        SAH_CK(launch_karras_segments(sorted, key_bits, static_cast<const KarrasSeg*>(d_segs), (uint32_t)segs.size(),
+                                     seg_threads, n, nodes, parents, ranges, s));
+    }
+    return RG_OK;
+}
+
 
 }  // namespace rg

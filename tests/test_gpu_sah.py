@@ -79,7 +79,9 @@ def peeled_series(n=70):
     return boxes_mesh(lo, np.c_[s * np.float32(1.8), s, s].astype(np.float32))
 
 
-SAH_MESHES = dict(MESHES, peeled=peeled_series(), large1=g.large_scene().meshes[1])
+# large3 (409,600 triangles) has levels of more than 65,536 segments, which
+# the build runs in several slices
+SAH_MESHES = dict(MESHES, peeled=peeled_series(), large1=g.large_scene().meshes[1], large3=g.large_scene().meshes[3])
 
 
 @pytest.mark.parametrize("name", list(SAH_MESHES))
