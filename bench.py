@@ -648,8 +648,11 @@ def large_e2e(rg, torch, gs, inst_host, closest, anyhit, steps, first):
     closest-hit rays and the any-hit rays are copied from pinned host memory
     and the hit records copied back to it, in chunks of E2E_CHUNK rays (by
     default one per kind) pipelined over a copy-in stream, the tracing stream
-    and a copy-out stream (two device buffers, used by the kinds in turn).  One timed region over all steps.  Returns
-    (closest rays, seconds, H2D bytes per step, D2H bytes per step)."""
+    and a copy-out stream.  Each kind has a ring of device buffers two steps
+    deep, so a chunk's rays can be copied in while the previous step's chunk
+    of the same kind is traced (a whole step of time for each copy).  One
+    timed region over all steps.  Returns (closest rays, seconds, H2D bytes per
+    step, D2H bytes per step)."""
     n = closest.shape[0]
     pin_c = torch.from_numpy(closest).pin_memory()
     pin_a = torch.from_numpy(anyhit).pin_memory()
@@ -657,12 +660,14 @@ def large_e2e(rg, torch, gs, inst_host, closest, anyhit, steps, first):
     out_c = torch.empty((n, 5), dtype=torch.int32).pin_memory()
     out_a = torch.empty((n, 5), dtype=torch.int32).pin_memory()
     C = min(E2E_CHUNK, n)
-    d_rays = [torch.empty((C, 8), dtype=torch.float32, device="cuda") for _ in range(2)]
-    d_hits = [torch.empty((C, 5), dtype=torch.int32, device="cuda") for _ in range(2)]
+    chunks = (n + C - 1) // C
+    ring = 2 * chunks   # buffers per kind
+    d_rays = [[torch.empty((C, 8), dtype=torch.float32, device="cuda") for _ in range(ring)] for _ in range(2)]
+    d_hits = [[torch.empty((C, 5), dtype=torch.int32, device="cuda") for _ in range(ring)] for _ in range(2)]
     d_inst = torch.empty_like(torch.from_numpy(inst_host[0])).cuda()
     s_in, s_run, s_out = torch.cuda.Stream(), torch.cuda.current_stream(), torch.cuda.Stream()
-    traced = [None, None]   # buffer b's rays have been traced (its ray buffer may be refilled)
-    copied = [None, None]   # buffer b's hits have been copied out (its hit buffer may be rewritten)
+    traced = [[None] * ring for _ in range(2)]   # buffer's rays have been traced (it may be refilled)
+    copied = [[None] * ring for _ in range(2)]   # buffer's hits have been copied out (it may be rewritten)
     rg.rg_sync(gs.h)
     rg.rg_reset_stats(gs.h)
     torch.cuda.synchronize()
@@ -670,7 +675,6 @@ def large_e2e(rg, torch, gs, inst_host, closest, anyhit, steps, first):
     e0.record(s_run)
     s_in.wait_event(e0)
     s_out.wait_event(e0)
-    b = 0
     for k in range(first, first + steps):
         with torch.cuda.stream(s_in):
             d_inst.copy_(pin_inst[k % len(pin_inst)], non_blocking=True)
@@ -680,27 +684,27 @@ def large_e2e(rg, torch, gs, inst_host, closest, anyhit, steps, first):
         rg.rg_tlas_build(gs.h, d_inst, stream=s_run)
         inst_used = torch.cuda.Event()
         inst_used.record(s_run)
-        for host_in, host_out, flags in ((pin_c, out_c, rg.RG_CLOSEST), (pin_a, out_a, rg.RG_ANY)):
-            for c0 in range(0, n, C):
+        for kind, (host_in, host_out, flags) in enumerate(((pin_c, out_c, rg.RG_CLOSEST), (pin_a, out_a, rg.RG_ANY))):
+            for j, c0 in enumerate(range(0, n, C)):
                 m = min(C, n - c0)
+                b = ((k - first) * chunks + j) % ring
                 with torch.cuda.stream(s_in):
-                    if traced[b] is not None:
-                        s_in.wait_event(traced[b])
-                    d_rays[b][:m].copy_(host_in[c0:c0 + m], non_blocking=True)
+                    if traced[kind][b] is not None:
+                        s_in.wait_event(traced[kind][b])
+                    d_rays[kind][b][:m].copy_(host_in[c0:c0 + m], non_blocking=True)
                     loaded = torch.cuda.Event()
                     loaded.record(s_in)
                 s_run.wait_event(loaded)
-                if copied[b] is not None:
-                    s_run.wait_event(copied[b])
-                rg.rg_trace_rays(gs.h, d_rays[b][:m], flags, d_hits[b], stream=s_run)
-                traced[b] = torch.cuda.Event()
-                traced[b].record(s_run)
+                if copied[kind][b] is not None:
+                    s_run.wait_event(copied[kind][b])
+                rg.rg_trace_rays(gs.h, d_rays[kind][b][:m], flags, d_hits[kind][b], stream=s_run)
+                traced[kind][b] = torch.cuda.Event()
+                traced[kind][b].record(s_run)
                 with torch.cuda.stream(s_out):
-                    s_out.wait_event(traced[b])
-                    host_out[c0:c0 + m].copy_(d_hits[b][:m], non_blocking=True)
-                    copied[b] = torch.cuda.Event()
-                    copied[b].record(s_out)
-                b ^= 1
+                    s_out.wait_event(traced[kind][b])
+                    host_out[c0:c0 + m].copy_(d_hits[kind][b][:m], non_blocking=True)
+                    copied[kind][b] = torch.cuda.Event()
+                    copied[kind][b].record(s_out)
         s_in.wait_event(inst_used)  # the next step's transforms overwrite d_inst
     s_run.wait_stream(s_out)
     s_run.wait_stream(s_in)
