@@ -167,10 +167,14 @@ def test_tiny_any_hit(tiny):
     assert np.array_equal(occ, c["inst"] != MISS)
 
 
-def test_medium_rays_at_full_launch(medium):
+@pytest.mark.parametrize("blas", ["lbvh", "sah"])
+def test_medium_rays_at_full_launch(medium, blas):
     """Camera rays of the 1920x1080 view plus random rays in the scene box, all
-    traced in one launch; the oracle checks a seeded sample."""
+    traced in one launch, on LBVH and on binned-SAH BLAS (the benchmark's
+    build); the oracle checks a seeded sample."""
     s, gs, O = medium
+    if blas == "sah":
+        gs = rg.GpuScene(s, morton_flags=rg.RG_BLAS_SAH)
     all_cam = camera_rays(s)
     lo, hi = s.world_aabb()
     rnd = g.random_rays(1_000_000, lo, hi, seed=5)
@@ -179,7 +183,9 @@ def test_medium_rays_at_full_launch(medium):
     idx = np.random.default_rng(0).choice(len(rays), 100_000, replace=False)
     ref = O.trace(rays[idx], kappa=KAPPA, rel_t=REL_T)
     frac = compare_closest({k: v[idx] for k, v in h.items()}, ref, label="medium")
-    print(f"medium: differing (exempt) fraction {frac:.2e}, ambiguous {ref['ambiguous'].mean():.2e}")
+    if blas == "sah":
+        gs.close()
+    print(f"medium ({blas}): differing (exempt) fraction {frac:.2e}, ambiguous {ref['ambiguous'].mean():.2e}")
 
 
 def test_bvh_equals_brute_force_bit_exact():
