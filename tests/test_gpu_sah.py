@@ -148,8 +148,9 @@ def test_sah_scene_vs_oracle():
     compare_closest(h, ref, label="sah")
 
 
-def test_sah_scene_renders_like_lbvh():
-    s = g.tiny_scene()
+@pytest.mark.parametrize("scene", ["tiny", "medium"])
+def test_sah_scene_renders_like_lbvh(scene):
+    s = g.tiny_scene() if scene == "tiny" else g.medium_scene()
     imgs = []
     for flags in (rg.RG_MORTON30, rg.RG_BLAS_SAH):
         with rg.GpuScene(s, morton_flags=flags) as gs:
