@@ -76,6 +76,8 @@ def parse(argv=None):
     p.add_argument("--requests", type=int, default=400, help="serving: requests in the Poisson stream")
     p.add_argument("--lanes", type=int, default=0, help="serving: server lanes (0: the library's default)")
     p.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    p.add_argument("--tlas", default="sah", choices=["sah", "lbvh"],
+                   help="large workload: TLAS hierarchy, binned SAH in one block (RG_SCENE_SAH_TLAS) or LBVH")
     p.add_argument("--blas", default="sah", choices=["sah", "lbvh"],
                    help="BLAS build of every scene: binned SAH (RG_BLAS_SAH, for trace speed) or LBVH (for build speed)")
     p.add_argument("--no-medium", action="store_true", help="large: skip the medium render frame")
@@ -259,9 +261,15 @@ def blas_flag(args):
     return rg.RG_BLAS_SAH if getattr(args, "blas", "sah") == "sah" else rg.RG_MORTON30
 
 
-def bvh_label(args):
+def tlas_flag(args):
+    import paper_2001_09792_gb300 as rg
+    return rg.RG_SCENE_SAH_TLAS if getattr(args, "tlas", "sah") == "sah" else 0
+
+
+def bvh_label(args, tlas=False):
     return (("compressed 8-wide" if args.compressed else "binary float32") + ", BLAS "
-            + ("binned SAH" if getattr(args, "blas", "sah") == "sah" else "LBVH"))
+            + ("binned SAH" if getattr(args, "blas", "sah") == "sah" else "LBVH")
+            + ((", TLAS " + ("binned SAH" if getattr(args, "tlas", "sah") == "sah" else "LBVH")) if tlas else ""))
 
 
 def node_bytes(args):
@@ -634,7 +642,8 @@ def ray_bytes(cst, node_b, any_hit):
 def large_counts(s, rg, torch, args, motion, d_c, d_a):
     """Node, triangle and instance counts per ray of the large query (a
     counting traversal on a second scene with the same motion)."""
-    with rg.GpuScene(s, flags=rg.RG_SCENE_COUNT | path_flag(args), morton_flags=blas_flag(args)) as gc:
+    flags = rg.RG_SCENE_COUNT | path_flag(args) | tlas_flag(args)
+    with rg.GpuScene(s, flags=flags, morton_flags=blas_flag(args)) as gc:
         rg.rg_tlas_build(gc.h, torch.from_numpy(rg.pack_instances(motion, [gc.blas[m] for m in s.mesh_id],
                                                                   s.material_id)).cuda())
         rg.rg_reset_stats(gc.h)
@@ -765,7 +774,7 @@ def run_native_large(args, world, rank, local):
     closest, anyhit = g.large_rays(s, n)
     n_frames = args.warmup + args.steps
     motions = [g.motion(s.M, k) for k in range(min(n_frames, 8))]
-    gs = rg.GpuScene(s, flags=rg.RG_SCENE_TIMING | path_flag(args), morton_flags=blas_flag(args))
+    gs = rg.GpuScene(s, flags=rg.RG_SCENE_TIMING | path_flag(args) | tlas_flag(args), morton_flags=blas_flag(args))
     blas_ids = [gs.blas[m] for m in s.mesh_id]
     inst_host = [rg.pack_instances(M, blas_ids, s.material_id) for M in motions]
     inst_dev = [torch.from_numpy(x).cuda() for x in inst_host]
@@ -892,7 +901,7 @@ def run_native_large(args, world, rank, local):
                 "latency": "per step (TLAS rebuild + both queries), CUDA events on the stream",
                 "l2": "inputs larger than L2 (2 x 512 MiB of rays, about 400 MB of BVH and triangle records); "
                       "no flush",
-                "parallelism": f"replicas x{world}", "bvh": bvh_label(args)},
+                "parallelism": f"replicas x{world}", "bvh": bvh_label(args, tlas=True)},
             "roofline": roofline,
             "gpu_launches": int(st["kernel_launches"]),
         }

@@ -88,8 +88,19 @@ typedef struct { float pos[3]; float intensity[3]; } rg_light;
  * each depth level's shadow rays and the next level's closest-hit rays in one
  * launch (binary BVH); RG_SCENE_NO_PAIR makes them two launches.
  * RG_SCENE_FRUGAL sizes rg_render's queues from each depth level's ray count
- * (the host waits once per level) instead of the frame's worst case. */
-enum { RG_SCENE_TIMING = 1u, RG_SCENE_COUNT = 2u, RG_SCENE_COMPRESSED = 4u, RG_SCENE_NO_PAIR = 8u, RG_SCENE_FRUGAL = 16u };
+ * (the host waits once per level) instead of the frame's worst case.
+ * RG_SCENE_SAH_TLAS builds a TLAS of 2 to 4,096 instances for trace speed:
+ * the hierarchy of rg_blas_build's RG_BLAS_SAH, built in one single-block
+ * launch without host round trips (larger TLAS keep the LBVH); the same hit
+ * records, a slower build. */
+enum {
+    RG_SCENE_TIMING = 1u,
+    RG_SCENE_COUNT = 2u,
+    RG_SCENE_COMPRESSED = 4u,
+    RG_SCENE_NO_PAIR = 8u,
+    RG_SCENE_FRUGAL = 16u,
+    RG_SCENE_SAH_TLAS = 32u
+};
 typedef struct { float background[3]; float ambient; uint32_t flags; } rg_scene_desc;
 
 /* Counters since the last rg_reset_stats. */

@@ -165,7 +165,13 @@ def sah_reference(vtx, idx, bits=10):
     orc_sah_build): dict with the triangle of each leaf (perm), the children of
     each internal node (child, (n-1, 2) uint32, bit 31 a leaf) and the
     triangle boxes (lohi, in triangle order)."""
-    lohi = tri_bounds(vtx, idx)
+    return sah_boxes(tri_bounds(vtx, idx), bits)
+
+
+def sah_boxes(lohi, bits=10):
+    """The binned-SAH hierarchy over boxes (lo xyz, hi xyz per row; triangles
+    or a TLAS's instance world boxes), as sah_reference."""
+    lohi = _c(lohi, np.float32).reshape(-1, 6)
     codes, _ = morton(lohi, bits)
     perm = stable_sort(codes)
     sk = _c(codes[perm], np.uint64)

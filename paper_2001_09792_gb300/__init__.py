@@ -29,6 +29,7 @@ RG_SCENE_COUNT = 2
 RG_SCENE_COMPRESSED = 4
 RG_SCENE_NO_PAIR = 8
 RG_SCENE_FRUGAL = 16
+RG_SCENE_SAH_TLAS = 32
 RG_COMPRESSED = 2
 RG_BLAS_SAH = 4
 RG_TLAS_ID = 0xFFFFFFFF

@@ -571,7 +571,10 @@ rg_status rg_blas_build(rg_scene* s, const float* d_vtx, uint32_t nv, const uint
 static rg_status tlas_common(rg_scene* s, const rg_instance* d_inst, uint32_t n, cudaStream_t st, bool refit) {
     rg_status r;
     TempAlloc tmp(st);
-    if (n <= kTlasSmallMax) {
+    // the SAH hierarchy (one block) when asked for, else the LBVH; a one-launch
+    // build or refit of a small TLAS when its topology is the LBVH's or fixed
+    const bool sah = (s->desc.flags & RG_SCENE_SAH_TLAS) && n >= 2 && n <= kSahOneMax;
+    if (n <= kTlasSmallMax && !(sah && !refit)) {
         // one single-block launch for the whole build or refit
         void* ranges = nullptr;
         if (!refit && s->wide && n > 1 && (r = tmp.get(&ranges, (size_t)(n - 1) * 8, "ranges"))) return r;
@@ -595,19 +598,26 @@ static rg_status tlas_common(rg_scene* s, const rg_instance* d_inst, uint32_t n,
     RG_CK(launch_instance_prep(d_inst, n, s->B->d_blas.p, (uint32_t)s->B->blas.size(), s->inst_tmp.p, s->wbox.p,
                                refit ? nullptr : static_cast<int*>(cb), refit, s->st, st));
     void* ranges = nullptr;
+    void* boxes_done = nullptr;  // set by the SAH build when it wrote every node's boxes
     if (!refit) {
         if (n > 1) {
             if (s->wide && (r = tmp.get(&ranges, (size_t)(n - 1) * 8, "ranges"))) return r;
-            if ((r = lbvh_topology(tmp, s->wbox.p, n, static_cast<int*>(cb), 10, s->tlas_nodes.p, s->perm.p,
-                                   s->parents.p, st, static_cast<uint32_t*>(ranges))))
-                return r;
+            if (sah && (r = tmp.get(&boxes_done, 16, "box flag"))) return r;
+            if (sah)
+                r = sah_one_topology(ScratchAlloc{temp_get, &tmp}, s->wbox.p, n, static_cast<int*>(cb), 10,
+                                     s->tlas_nodes.p, s->perm.p, s->parents.p, st, static_cast<uint32_t*>(ranges),
+                                     static_cast<uint32_t*>(boxes_done));
+            else
+                r = lbvh_topology(tmp, s->wbox.p, n, static_cast<int*>(cb), 10, s->tlas_nodes.p, s->perm.p,
+                                  s->parents.p, st, static_cast<uint32_t*>(ranges));
+            if (r) return r;
         } else {
             RG_CK(cudaMemsetAsync(s->perm.p, 0, 4, st));
         }
     }
     if (n > 1) RG_CK(cudaMemsetAsync(s->flags.p, 0, (size_t)(n - 1) * 4, st));
     RG_CK(launch_tlas_leaves_refit(s->inst_tmp.p, s->wbox.p, s->perm.p, n, s->parents.p, s->tlas_nodes.p, s->flags.p,
-                                   s->inst.p, s->st, st));
+                                   s->inst.p, s->st, st, static_cast<const uint32_t*>(boxes_done)));
     if (s->wide) {
         WideOut out{s->tlas8.p, s->src8.p, s->item_src8.p, s->counts8.p, s->tasks8.p};
         if (refit)

@@ -10,6 +10,7 @@
 // Every float32 operation that decides a Morton code or a box is an explicit
 // round-to-nearest (or directed) intrinsic, so no FMA contraction can change
 // a result: codes, order, topology and boxes are reproducible bit for bit.
+#include "karras.cuh"
 #include "rg_internal.cuh"
 
 namespace rg {
@@ -291,68 +292,7 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const K* __restrict
 }
 
 // ---------------------------------------------------------------- Karras
-template <class K>
-__device__ __forceinline__ int clz_key(K x);
-template <>
-__device__ __forceinline__ int clz_key<uint32_t>(uint32_t x) { return __clz(x); }
-template <>
-__device__ __forceinline__ int clz_key<uint64_t>(uint64_t x) { return __clzll(x); }
-
-// augmented common-prefix length (Karras 2012, Sec. 4); -1 outside [0, n)
-template <class K>
-__device__ __forceinline__ int delta(const K* __restrict__ k, int64_t n, int64_t i, int64_t j) {
-    if (j < 0 || j >= n) return -1;
-    K a = k[i], b = k[j];
-    if (a != b) return clz_key<K>(a ^ b);
-    return (int)(8 * sizeof(K)) + __clz((uint32_t)i ^ (uint32_t)j);
-}
-
-// Internal node i of the Karras hierarchy over n sorted keys: its children
-// (bit 31 marks a leaf) into child_base[i * stride], its key range into
-// ranges (optional), its children's parent entries (optional).  For a
-// segment of a larger tree (node_off > 0), node and leaf indices are offset by
-// node_off and leaf_off, parents are laid out for n_all leaves, and the
-// segment root's own parent entry is left alone.
-template <class K>
-__device__ __forceinline__ void karras_node(const K* __restrict__ keys, uint32_t n, int64_t i,
-                                            uint32_t* __restrict__ child_base, int stride, uint32_t* __restrict__ parents,
-                                            uint32_t* __restrict__ ranges, uint32_t node_off = 0, uint32_t leaf_off = 0,
-                                            uint32_t n_all = 0) {
-    if (n_all == 0) n_all = n;
-    const int64_t N = n;
-    int d = (delta(keys, N, i, i + 1) - delta(keys, N, i, i - 1)) >= 0 ? 1 : -1;
-    int dmin = delta(keys, N, i, i - d);
-    int64_t lmax = 2;
-    while (delta(keys, N, i, i + lmax * d) > dmin) lmax <<= 1;
-    int64_t l = 0;
-    for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
-        if (delta(keys, N, i, i + (l + t) * d) > dmin) l += t;
-    int64_t j = i + l * d;
-    int dnode = delta(keys, N, i, j);
-    int64_t s = 0, t;
-    int64_t div = 2;
-    do {
-        t = (l + div - 1) / div;
-        if (delta(keys, N, i, i + (s + t) * d) > dnode) s += t;
-        div <<= 1;
-    } while (t > 1);
-    int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
-    int64_t lo = i < j ? i : j, hi = i < j ? j : i;
-    uint32_t left = (lo == gamma) ? (kLeaf | (leaf_off + (uint32_t)gamma)) : node_off + (uint32_t)gamma;
-    uint32_t right = (hi == gamma + 1) ? (kLeaf | (leaf_off + (uint32_t)(gamma + 1))) : node_off + (uint32_t)(gamma + 1);
-    const size_t me = node_off + (size_t)i;
-    child_base[me * stride] = left;
-    child_base[me * stride + 1] = right;
-    if (ranges) {
-        ranges[2 * me] = leaf_off + (uint32_t)lo;
-        ranges[2 * me + 1] = leaf_off + (uint32_t)hi;
-    }
-    if (parents) {
-        parents[(left & kLeaf) ? (size_t)(n_all - 1) + (left & ~kLeaf) : left] = (uint32_t)me;
-        parents[(right & kLeaf) ? (size_t)(n_all - 1) + (right & ~kLeaf) : right] = (uint32_t)me;
-        if (i == 0 && node_off == 0) parents[0] = kNone;
-    }
-}
+// (delta, karras_node: karras.cuh)
 
 // One thread per internal node of all segments: the segment by binary search
 // over the segments' first thread numbers.
@@ -592,11 +532,13 @@ __global__ void k_instance_prep(const rg_instance* __restrict__ in, uint32_t n, 
 
 __global__ void k_tlas_leaves_refit(const InstDev* __restrict__ tmp, const float* __restrict__ wbox,
                                     const uint32_t* __restrict__ perm, uint32_t n, const uint32_t* __restrict__ parents,
-                                    float4* nodes, uint32_t* flags, InstDev* __restrict__ inst_out, DevStatus* st) {
+                                    float4* nodes, uint32_t* flags, InstDev* __restrict__ inst_out, DevStatus* st,
+                                    const uint32_t* __restrict__ boxes_done) {
     uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     uint32_t k = perm[j];
     inst_out[j] = tmp[k];
+    if (boxes_done && *boxes_done) return;
     float box[6];
 #pragma unroll
     for (int a = 0; a < 6; ++a) box[a] = wbox[6 * (size_t)k + a];
@@ -845,8 +787,9 @@ cudaError_t launch_instance_prep(const rg_instance* in, uint32_t n, const BlasDe
 
 cudaError_t launch_tlas_leaves_refit(const InstDev* tmp, const float* wbox, const uint32_t* perm, uint32_t n,
                                      const uint32_t* parents, float4* nodes, uint32_t* flags, InstDev* inst_out,
-                                     DevStatus* st, cudaStream_t s) {
-    k_tlas_leaves_refit<<<grid_for(n), kBlock, 0, s>>>(tmp, wbox, perm, n, parents, nodes, flags, inst_out, st);
+                                     DevStatus* st, cudaStream_t s, const uint32_t* boxes_done) {
+    k_tlas_leaves_refit<<<grid_for(n), kBlock, 0, s>>>(tmp, wbox, perm, n, parents, nodes, flags, inst_out, st,
+                                                       boxes_done);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -201,9 +201,12 @@ constexpr uint32_t kTlasSmallMax = 1024;
 cudaError_t launch_tlas_small(const rg_instance* in, uint32_t n, const BlasDev* blas, uint32_t nblas, InstDev* tmp,
                               float* wbox, bool refit, float4* nodes, uint32_t* perm, uint32_t* parents,
                               uint32_t* flags, uint32_t* ranges, InstDev* inst_out, DevStatus* st, cudaStream_t s);
+// The instances in leaf order and the bottom-up refit of the node boxes; with
+// boxes_done set (device memory, may be null) the boxes are already in place
+// and only the instances are copied.
 cudaError_t launch_tlas_leaves_refit(const InstDev* tmp, const float* wbox, const uint32_t* perm, uint32_t n,
                                      const uint32_t* parents, float4* nodes, uint32_t* flags, InstDev* inst_out,
-                                     DevStatus* st, cudaStream_t s);
+                                     DevStatus* st, cudaStream_t s, const uint32_t* boxes_done = nullptr);
 
 // Karras hierarchies over segments of the sorted keys (the bottom of the SAH
 // build): segment k spans leaves begin .. begin + count - 1 and its internal
@@ -223,6 +226,7 @@ constexpr uint32_t kSahChunk = 2048;    // triangles per block of a level's kern
 constexpr uint32_t kSahSmall = 2;       // segments of at most this many triangles get the Karras hierarchy
 constexpr uint32_t kSahMaxLevels = 40;  // deeper segments get the Karras hierarchy whatever their size
 constexpr uint32_t kSahSliceTasks = 65536;  // segments per launch sequence (bounds the scratch)
+constexpr uint32_t kSahOneMax = 4096;       // items of the build without host round trips (launch_sah_small)
 constexpr uint32_t kSahAccInts = 6 + 3 * kSahBins * 7;  // per task: centroid bounds, then 7 values per bin and axis
 struct SahTask {                        // one segment split at this level
     uint32_t begin, count, node;        // leaves begin .. begin + count - 1, internal node `node`
@@ -253,6 +257,23 @@ struct SahLevel {
     uint32_t* ranges;                   // may be null
 };
 cudaError_t launch_sah_level(const SahLevel& L, int key_bits, cudaStream_t s);
+// The same binned-SAH hierarchy for 2 <= n <= kSahOneMax items from their
+// 30-bit Morton codes, in three launches without host round trips (the sort
+// and the top levels in one block, then the subtrees of at most 128 items in
+// a block each, then the leaf order): perm_out (the item of each leaf),
+// children, parents, (optional) leaf ranges, and the boxes of every node's
+// children where the splits give them; *boxes_done is 1 when every node's
+// boxes were written, 0 when the bottom-up refit must compute them.
+struct SahSmallScratch {
+    uint32_t* keys;       // n: the sorted codes
+    uint32_t* perm0;      // n: the Morton order
+    uint32_t* rank;       // n
+    void* pending;        // n / 3 + 1 entries of 16 B
+    uint32_t* n_pending;  // 1
+    uint32_t* boxes_done; // 1
+};
+cudaError_t launch_sah_small(const float* lohi, uint32_t n, const uint32_t* codes, uint32_t* perm_out, float4* nodes,
+                             uint32_t* parents, uint32_t* ranges, const SahSmallScratch& w, cudaStream_t s);
 // Device temporaries of one library call (stream-ordered, freed when the call
 // returns); get() reports its own failures.
 struct ScratchAlloc {
@@ -265,6 +286,12 @@ struct ScratchAlloc {
 // LBVH emits them.
 rg_status sah_topology(const ScratchAlloc& tmp, const float* lohi, uint32_t n, const int* cb_ord, int bits,
                        float4* nodes, uint32_t* perm, uint32_t* parents, cudaStream_t s, uint32_t* ranges);
+// The same, for 2 <= n <= kSahOneMax and bits 10, without host round trips
+// (launch_sah_small); it also writes the node boxes it can, and sets
+// *boxes_done (device memory) as launch_sah_small says.
+rg_status sah_one_topology(const ScratchAlloc& tmp, const float* lohi, uint32_t n, const int* cb_ord, int bits,
+                           float4* nodes, uint32_t* perm, uint32_t* parents, cudaStream_t s, uint32_t* ranges,
+                           uint32_t* boxes_done);
 
 // wide.cu
 // Collapse a binary LBVH (n leaves) into a compressed 8-wide BVH in one

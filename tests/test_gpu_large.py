@@ -1,7 +1,8 @@
 """Large incoherent ray queries at full size: 4,096 instances of 16 meshes
 (1,938,944 unique triangles, about 60M instanced), a full TLAS rebuild after
 seeded motion, then 16,777,216 closest-hit rays and 16,777,216 any-hit rays
-each traced in one launch, on binned-SAH BLAS as the benchmark builds them.
+each traced in one launch, on binned-SAH BLAS and TLAS as the benchmark
+builds them.
 The oracle checks a seeded sample of each set."""
 import numpy as np
 import pytest
@@ -22,7 +23,7 @@ def large():
     s = g.large_scene()
     assert sum(m[1].shape[0] for m in s.meshes) == 1_938_944
     assert s.n_instances == 4096
-    gs = rg.GpuScene(s, morton_flags=rg.RG_BLAS_SAH)   # the BLAS build the benchmark times
+    gs = rg.GpuScene(s, flags=rg.RG_SCENE_SAH_TLAS, morton_flags=rg.RG_BLAS_SAH)   # the builds the benchmark times
     M1 = g.motion(s.M, 1)
     host = gs.inst_host.copy()
     host[:, :12] = M1.reshape(-1, 12)

@@ -6,8 +6,9 @@ every internal node is reached once and every subtree's leaves are one range
 of the leaf order; every child box is
 the union of the oracle's triangle boxes below it, bit for bit; the tree's
 surface-area cost is lower than the LBVH's; two builds are identical; and
-every query answers exactly as on the LBVH build (closest-hit records and
-rendered images bit for bit, any-hit occlusion), which the oracle pins."""
+every query answers exactly as on the LBVH build (closest-hit records bit
+for bit, any-hit occlusion, rendered images to the rounding of their atomic
+sums), which the oracle pins."""
 import numpy as np
 import pytest
 import torch
@@ -157,7 +158,9 @@ def test_sah_scene_renders_like_lbvh(scene):
             img = rg.rg_render(gs.h, s.camera, s.width, s.height, s.max_depth)
             rg.rg_sync(gs.h)
             imgs.append(img.cpu().numpy())
-    assert np.array_equal(imgs[0].view(np.uint32), imgs[1].view(np.uint32))
+    # hit records are the same; a pixel's contributions are summed by float
+    # atomics in launch order, so the images agree to rounding, not bit for bit
+    assert np.abs(imgs[0].astype(np.float64) - imgs[1]).max() <= 1e-5
 
 
 def test_sah_compressed_matches_binary():
@@ -171,3 +174,74 @@ def test_sah_compressed_matches_binary():
         assert np.array_equal(a[k], b[k]), k
     for k in ("t", "u", "v"):
         assert np.array_equal(a[k].view(np.uint32), b[k].view(np.uint32)), k
+
+
+# ---------------------------------------------------------------- TLAS (one-block build)
+
+@pytest.mark.parametrize("n_inst", [2, 3, 17, 65, 66, 300, 1024, 1025, 4096, 4099])
+def test_sah_tlas_matches_oracle(n_inst):
+    from test_gpu_build import small_instanced_scene
+    check_sah_tlas(small_instanced_scene(n_inst, n_inst), n_inst)
+
+
+@pytest.mark.parametrize("n_inst,dup", [(300, (100, 200)), (129, (0, 129)), (1000, (0, 1000)), (4096, (7, 3000))])
+def test_sah_tlas_with_coincident_instances(n_inst, dup):
+    """Instances with one transform and mesh share their centroid: segments of
+    them are halved by position, and their nodes' boxes come from the refit."""
+    from test_gpu_build import small_instanced_scene
+    s = small_instanced_scene(n_inst + 5, n_inst)
+    a, b = dup
+    s.M[a:b] = s.M[a]
+    s.mesh_id[a:b] = s.mesh_id[a]
+    check_sah_tlas(s, n_inst)
+
+
+def check_sah_tlas(s, n_inst):
+    """The SAH TLAS of scene s against the oracle: instance boxes, leaf order,
+    children, and both child boxes of every node (unions of leaf boxes)."""
+    from test_gpu_build import object_bounds
+    with rg.GpuScene(s, flags=rg.RG_SCENE_SAH_TLAS) as gs:
+        ex = rg.rg_tlas_export(gs.h, n_inst)
+    obj_box, obj_r2 = object_bounds(s)
+    _, wbox, rc = oracle.instance_prep(s.M, obj_box, obj_r2)
+    assert rc == 0 and np.array_equal(ex["wbox"], wbox)
+    _, _, _, _, ch = node_fields(ex["nodes"])
+    if n_inst > 4096:     # beyond the one-block build: the LBVH
+        codes, _ = oracle.morton(wbox, 10)
+        assert np.array_equal(ex["order"], oracle.stable_sort(codes))
+        return
+    ref = oracle.sah_boxes(wbox)
+    assert np.array_equal(ex["order"], ref["perm"])
+    assert np.array_equal(ch, ref["child"])
+    first, last, _ = tree_ranges(ch, n_inst)
+    ws = wbox[ref["perm"]]
+    lo0, hi0, lo1, hi1, _ = node_fields(ex["nodes"])
+    for k in range(n_inst - 1):
+        c0 = int(ch[k][0])
+        split = (c0 & ~LEAF) if c0 & LEAF else last[c0]
+        assert np.array_equal(np.r_[lo0[k], hi0[k]], np.r_[ws[first[k]:split + 1, :3].min(0),
+                                                           ws[first[k]:split + 1, 3:].max(0)]), k
+        assert np.array_equal(np.r_[lo1[k], hi1[k]], np.r_[ws[split + 1:last[k] + 1, :3].min(0),
+                                                           ws[split + 1:last[k] + 1, 3:].max(0)]), k
+
+
+def test_sah_tlas_answers_like_lbvh_and_refits():
+    s = _random_scene(71, 1500)
+    lo, hi = s.world_aabb()
+    rays = g.random_rays(200_000, lo - 5, hi + 5, seed=72)
+    with rg.GpuScene(s) as gl, rg.GpuScene(s, flags=rg.RG_SCENE_SAH_TLAS) as gs:
+        a, b = trace(gl, rays), trace(gs, rays)
+        for k in ("inst", "prim"):
+            assert np.array_equal(a[k], b[k]), k
+        for k in ("t", "u", "v"):
+            assert np.array_equal(a[k].view(np.uint32), b[k].view(np.uint32)), k
+        assert (b["inst"] != MISS).mean() > 0.05
+        # a refit keeps the SAH topology and answers like a fresh SAH build
+        M2 = g.motion(s.M, 3)
+        inst = torch.from_numpy(rg.pack_instances(M2, [gs.blas[m] for m in s.mesh_id], s.material_id)).cuda()
+        rg.rg_tlas_refit(gs.h, inst)
+        c = trace(gs, rays)
+        rg.rg_tlas_build(gs.h, inst)
+        d = trace(gs, rays)
+        for k in ("inst", "prim", "t"):
+            assert np.array_equal(c[k].view(np.uint32) if k == "t" else c[k], d[k].view(np.uint32) if k == "t" else d[k])
