@@ -68,6 +68,9 @@ def parse(argv=None):
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU baseline budget (wall seconds)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--serial", action="store_true",
+                   help="large workload: trace the step's two queries one after the other on one stream (default: "
+                        "the any-hit query on a second stream, overlapping the closest-hit query)")
     p.add_argument("--compressed", action="store_true",
                    help="trace with the compressed 8-wide BVH (default: the float32 binary BVH, faster here)")
     p.add_argument("--workload", default="large", choices=["large", "medium", "serve"],
@@ -652,7 +655,7 @@ def large_counts(s, rg, torch, args, motion, d_c, d_a):
         return rg.rg_get_stats(gc.h)
 
 
-def large_e2e(rg, torch, gs, inst_host, closest, anyhit, steps, first):
+def large_e2e(rg, torch, gs, inst_host, closest, anyhit, steps, first, serial=False):
     """The large steps end to end: per step the instance transforms, the
     closest-hit rays and the any-hit rays are copied from pinned host memory
     and the hit records copied back to it, in chunks of E2E_CHUNK rays (by
@@ -660,8 +663,11 @@ def large_e2e(rg, torch, gs, inst_host, closest, anyhit, steps, first):
     and a copy-out stream.  Each kind has a ring of device buffers two steps
     deep, so a chunk's rays can be copied in while the previous step's chunk
     of the same kind is traced (a whole step of time for each copy).  One
-    timed region over all steps.  Returns (closest rays, seconds, H2D bytes per
-    step, D2H bytes per step)."""
+    timed region over all steps.  As in the device-side steps, the any-hit rays
+    are traced on a stream of their own during the closest-hit launch (unless
+    serial), and a step's TLAS rebuild waits for the previous step's any-hit
+    launch.  Returns (closest rays, seconds, H2D bytes per step, D2H bytes per
+    step)."""
     n = closest.shape[0]
     pin_c = torch.from_numpy(closest).pin_memory()
     pin_a = torch.from_numpy(anyhit).pin_memory()
@@ -675,6 +681,8 @@ def large_e2e(rg, torch, gs, inst_host, closest, anyhit, steps, first):
     d_hits = [[torch.empty((C, 5), dtype=torch.int32, device="cuda") for _ in range(ring)] for _ in range(2)]
     d_inst = torch.empty_like(torch.from_numpy(inst_host[0])).cuda()
     s_in, s_run, s_out = torch.cuda.Stream(), torch.cuda.current_stream(), torch.cuda.Stream()
+    s_run2 = s_run if serial else torch.cuda.Stream()  # the any-hit launches
+    any_done = None
     traced = [[None] * ring for _ in range(2)]   # buffer's rays have been traced (it may be refilled)
     copied = [[None] * ring for _ in range(2)]   # buffer's hits have been copied out (it may be rewritten)
     rg.rg_sync(gs.h)
@@ -684,16 +692,21 @@ def large_e2e(rg, torch, gs, inst_host, closest, anyhit, steps, first):
     e0.record(s_run)
     s_in.wait_event(e0)
     s_out.wait_event(e0)
+    s_run2.wait_event(e0)
     for k in range(first, first + steps):
         with torch.cuda.stream(s_in):
             d_inst.copy_(pin_inst[k % len(pin_inst)], non_blocking=True)
             ready = torch.cuda.Event()
             ready.record(s_in)
         s_run.wait_event(ready)
+        if any_done is not None:
+            s_run.wait_event(any_done)  # the previous any-hit launch reads the TLAS
         rg.rg_tlas_build(gs.h, d_inst, stream=s_run)
         inst_used = torch.cuda.Event()
         inst_used.record(s_run)
+        s_run2.wait_event(inst_used)
         for kind, (host_in, host_out, flags) in enumerate(((pin_c, out_c, rg.RG_CLOSEST), (pin_a, out_a, rg.RG_ANY))):
+            run = s_run if kind == 0 else s_run2
             for j, c0 in enumerate(range(0, n, C)):
                 m = min(C, n - c0)
                 b = ((k - first) * chunks + j) % ring
@@ -703,18 +716,22 @@ def large_e2e(rg, torch, gs, inst_host, closest, anyhit, steps, first):
                     d_rays[kind][b][:m].copy_(host_in[c0:c0 + m], non_blocking=True)
                     loaded = torch.cuda.Event()
                     loaded.record(s_in)
-                s_run.wait_event(loaded)
+                run.wait_event(loaded)
                 if copied[kind][b] is not None:
-                    s_run.wait_event(copied[kind][b])
-                rg.rg_trace_rays(gs.h, d_rays[kind][b][:m], flags, d_hits[kind][b], stream=s_run)
+                    run.wait_event(copied[kind][b])
+                rg.rg_trace_rays(gs.h, d_rays[kind][b][:m], flags, d_hits[kind][b], stream=run)
                 traced[kind][b] = torch.cuda.Event()
-                traced[kind][b].record(s_run)
+                traced[kind][b].record(run)
                 with torch.cuda.stream(s_out):
                     s_out.wait_event(traced[kind][b])
                     host_out[c0:c0 + m].copy_(d_hits[kind][b][:m], non_blocking=True)
                     copied[kind][b] = torch.cuda.Event()
                     copied[kind][b].record(s_out)
+        if not serial:
+            any_done = torch.cuda.Event()
+            any_done.record(s_run2)
         s_in.wait_event(inst_used)  # the next step's transforms overwrite d_inst
+    s_run.wait_stream(s_run2)
     s_run.wait_stream(s_out)
     s_run.wait_stream(s_in)
     e1.record(s_run)
@@ -783,10 +800,25 @@ def run_native_large(args, world, rank, local):
     h_a = torch.empty((n, 5), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step(k):
+    s_any = torch.cuda.Stream()
+
+    def step(k, serial=args.serial):
+        # the TLAS rebuild, then the closest-hit query (and its exact-attribute
+        # pass) and the any-hit query; by default the any-hit query runs on a
+        # second stream at the same time, and the step ends when both have
         rg.rg_tlas_build(gs.h, inst_dev[k % len(inst_dev)])
+        if serial:
+            rg.rg_trace_rays(gs.h, d_c, rg.RG_CLOSEST, h_c)
+            rg.rg_trace_rays(gs.h, d_a, rg.RG_ANY, h_a)
+            return
+        built = torch.cuda.Event()
+        built.record(stream)
+        s_any.wait_event(built)
         rg.rg_trace_rays(gs.h, d_c, rg.RG_CLOSEST, h_c)
-        rg.rg_trace_rays(gs.h, d_a, rg.RG_ANY, h_a)
+        rg.rg_trace_rays(gs.h, d_a, rg.RG_ANY, h_a, stream=s_any)
+        done = torch.cuda.Event()
+        done.record(s_any)
+        stream.wait_event(done)
 
     for k in range(args.warmup):
         step(k)
@@ -820,10 +852,25 @@ def run_native_large(args, world, rank, local):
     rg.rg_sync(gs.h)
     last_motion = (n_frames - 1) % len(motions)
     gpu_hits = rg.split_hits(h_c[: min(n, 1 << 20)]) if rank == 0 else None
+    st_serial = None
+    if not args.serial:
+        # each launch alone: a few steps with the queries one after the other
+        # (outside the timed region; context for the overlapped launch times)
+        rg.rg_reset_stats(gs.h)
+        torch.cuda.synchronize()
+        e_s0, e_s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_s0.record(stream)
+        for k in range(3):
+            step(n_frames + k, serial=True)
+        e_s1.record(stream)
+        torch.cuda.synchronize()
+        st_serial = rg.rg_get_stats(gs.h)
+        st_serial["step_ms"] = e_s0.elapsed_time(e_s1) / 3
+        rg.rg_sync(gs.h)
 
     e2e = None
     if not args.no_e2e:
-        e2e = large_e2e(rg, torch, gs, inst_host, closest, anyhit, args.steps, args.warmup)
+        e2e = large_e2e(rg, torch, gs, inst_host, closest, anyhit, args.steps, args.warmup, serial=args.serial)
     (wall_all, e2e_s_all), (closest_all, any_all, e2e_rays_all) = reduce_over_ranks(
         [wall, e2e[1] if e2e else 0.0], [float(st["closest_rays"]), float(st["shadow_rays"]),
                                          float(e2e[0]) if e2e else 0.0], "cuda")
@@ -840,6 +887,16 @@ def run_native_large(args, world, rank, local):
         r_ms = st["refine_ms"] / max(st["refine_launches"], 1)
         c_bytes = bpr * n
         counted_gbs = c_bytes / (c_ms / 1e3) / 1e9
+        alone = None  # each launch alone (the serialized steps after an overlapped timed region)
+        if st_serial is not None:
+            sc = st_serial["trace_ms"] / max(st_serial["trace_launches"], 1)
+            sa = st_serial["any_ms"] / max(st_serial["any_launches"], 1)
+            sr = st_serial["refine_ms"] / max(st_serial["refine_launches"], 1)
+            alone = {"closest_launch_ms": round(sc, 3), "refine_ms": round(sr, 3), "any_launch_ms": round(sa, 3),
+                     "tlas_rebuild_and_rest_ms": round(st_serial["step_ms"] - sc - sr - sa, 3),
+                     "step_ms": round(st_serial["step_ms"], 3),
+                     "note": "3 steps with the two queries one after the other, after the timed region"}
+        q_c, q_r, q_a = (sc, sr, sa) if alone else (c_ms, r_ms, a_ms)
         prof = "trace_large_compressed.md" if args.compressed else "trace_large.md"
         tr = traffic_record(prof, "dram_bytes_per_closest_launch")
         ipr = traffic_record(prof, "warp_inst_per_closest_ray")
@@ -854,6 +911,7 @@ def run_native_large(args, world, rank, local):
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         issue_peak = sms * 4 * sm_max_mhz() * 1e6 / 1e9
         achieved = None if ipr is None else ipr * n / (c_ms / 1e3) / 1e9
+        achieved_alone = None if (ipr is None or alone is None) else ipr * n / (sc / 1e3) / 1e9
         roofline = {
             "bound": "issue", "achieved": None if achieved is None else round(achieved, 1), "peak": round(issue_peak, 1),
             "unit": "G warp-instructions/s", "frac": None if achieved is None else round(achieved / issue_peak, 4),
@@ -879,6 +937,14 @@ def run_native_large(args, world, rank, local):
             "step_check": {"algorithmic_bytes_per_step": round(c_bytes + bpa * n),
                            "gbs_over_ms_per_step": round((c_bytes + bpa * n) / (step_ms / 1e3) / 1e9, 1)},
             "l2": profile_l2(prof)}
+        if alone:
+            roofline["per_launch"] += ("; the timed steps trace the any-hit query on a second stream during the "
+                                       "closest-hit launch, so avg_launch_ms includes the shared time")
+            roofline["alone"] = {"avg_launch_ms": round(sc, 4),
+                                 "achieved": None if achieved_alone is None else round(achieved_alone, 1),
+                                 "frac": None if achieved_alone is None else round(achieved_alone / issue_peak, 4),
+                                 "note": "the same launch with the GPU to itself (serialized steps after the timed "
+                                         "region)"}
         out = {
             "metric": METRIC,
             "value": round(closest_all / wall_all / 1e6, 2),
@@ -890,13 +956,17 @@ def run_native_large(args, world, rank, local):
             "config": {
                 "workload": LARGE_WORKLOAD, "instances": s.n_instances, "instanced_tris": s.instanced_tris(),
                 "closest_rays_per_step": n, "any_hit_rays_per_step": n,
-                "value_is": "closest-hit rays per step / ms_per_step (the step: TLAS rebuild + closest-hit launch "
-                            "+ exact-attribute pass + any-hit launch)",
+                "value_is": "closest-hit rays per step / ms_per_step (the step: TLAS rebuild, then the closest-hit "
+                            "launch + exact-attribute pass and the any-hit launch, "
+                            + ("one after the other)" if args.serial else "the any-hit launch on a second stream "
+                               "at the same time)"),
                 "closest_launch_ms": round(c_ms, 3), "refine_ms": round(r_ms, 3), "any_launch_ms": round(a_ms, 3),
-                "closest_query_mrays_s": round(n / ((c_ms + r_ms) / 1e3) / 1e6, 2),
-                "any_hit_mrays_s": round(n / (a_ms / 1e3) / 1e6, 2),
+                "closest_query_mrays_s": round(n / ((q_c + q_r) / 1e3) / 1e6, 2),
+                "any_hit_mrays_s": round(n / (q_a / 1e3) / 1e6, 2),
                 "all_rays_mrays_s": round((closest_all + any_all) / wall_all / 1e6, 2),
-                "tlas_rebuild_and_rest_ms": round(step_ms - c_ms - r_ms - a_ms, 3),
+                "tlas_rebuild_and_rest_ms": (alone["tlas_rebuild_and_rest_ms"] if alone
+                                             else round(step_ms - c_ms - r_ms - a_ms, 3)),
+                "launches_alone": alone,
                 "p50_ms": round(ms_sorted[len(ms) // 2], 3), "p99_ms": round(pct(ms, 0.99), 3),
                 "latency": "per step (TLAS rebuild + both queries), CUDA events on the stream",
                 "l2": "inputs larger than L2 (2 x 512 MiB of rays, about 400 MB of BVH and triangle records); "
@@ -911,8 +981,9 @@ def run_native_large(args, world, rank, local):
             out["e2e"] = {"value": round(e2e_rays_all / e2e_s_all / 1e6, 2), "unit": "Mrays/s",
                           "h2d_bytes_per_step": int(e2e[2]), "d2h_bytes_per_step": int(e2e[3]),
                           "note": "rays in pinned host memory, hit records back to pinned host memory, each kind's rays "
-                                  "copied in while the other kind traces and its hits copied out while the next kind "
-                                  "traces (copy-in, trace, copy-out streams), one timed region"}
+                                  "copied in during the previous step and its hits copied out while the next launches "
+                                  "trace (copy-in, trace, copy-out streams; the any-hit launches on a second trace "
+                                  "stream unless --serial), one timed region"}
     if world == 1 and rank == 0:
         if not args.no_cpu_baseline:
             import oracle

@@ -207,7 +207,10 @@ enum {
  * on their exact distances rounded to float32 (then instance, then prim), so
  * exact ties such as coplanar surfaces have one answer.  Any hit: only
  * occluded / not is defined; the record of some hit carries the float32 t,
- * u, v of the watertight test. */
+ * u, v of the watertight test.  Calls on one scene from one host thread may
+ * run at the same time on different streams (each takes a work counter of its
+ * own; at most 64 calls in flight), provided no rg_tlas_build or
+ * rg_tlas_refit of the scene runs meanwhile. */
 rg_status rg_trace_rays(rg_scene* scene, const rg_ray* d_rays, uint32_t n, uint32_t flags, rg_hit* d_hits,
                         void* stream);
 

@@ -170,6 +170,10 @@ struct EventPair {
 
 }  // namespace
 
+// rg_trace_rays calls that may be in flight at once (each takes a work
+// counter of its own, in turn)
+constexpr uint32_t kTraceSlots = 64;
+
 struct rg_scene {
     int device = 0;
     rg_scene_desc desc{};
@@ -204,6 +208,8 @@ struct rg_scene {
     DevBuf<uint32_t> seg_count;    // per shadow ray of a split launch: segments finished / occluded (kept zero)
     DevBuf<uint32_t> counters;     // [0] closest work, [1] next count, [2] shadow work, [3] unused,
                                    // [4 + l] shadow rays toward light l
+    DevBuf<uint32_t> trace_ctr;    // rg_trace_rays work counters: kTraceSlots slots, 128 B apart
+    uint32_t trace_slot = 0;       // the next call's slot
     uint32_t* h_counts = nullptr;  // pinned, 16 entries
     cudaEvent_t count_ev = nullptr;  // the next level's ray count has reached h_counts
     // statistics and timing
@@ -353,8 +359,10 @@ rg_status rg_scene_create(rg_scene** out, const rg_scene_desc* desc) {
         delete s;
         return r;
     }
-    if ((r = s->counters.ensure(4 + kMaxLights, "counters"))) {
+    if ((r = s->counters.ensure(4 + kMaxLights, "counters")) ||
+        (r = s->trace_ctr.ensure((size_t)kTraceSlots * 32, "trace counters"))) {
         cudaFree(s->st);
+        s->counters.release();
         delete s;
         return r;
     }
@@ -364,6 +372,7 @@ rg_status rg_scene_create(rg_scene** out, const rg_scene_desc* desc) {
     if (e != cudaSuccess) {
         cudaFree(s->st);
         s->counters.release();
+        s->trace_ctr.release();
         delete s;
         return cuda_fail(e, "scene setup");
     }
@@ -438,6 +447,7 @@ rg_status rg_scene_destroy(rg_scene* s) {
     s->hits.release();
     s->seg_count.release();
     s->counters.release();
+    s->trace_ctr.release();
     if (s->st) cudaFree(s->st);
     if (s->h_counts) cudaFreeHost(s->h_counts);
     if (s->count_ev) cudaEventDestroy(s->count_ev);
@@ -718,9 +728,11 @@ rg_status rg_trace_rays(rg_scene* s, const rg_ray* d_rays, uint32_t n, uint32_t 
     a.rays = reinterpret_cast<const float4*>(d_rays);
     a.n = n;
     a.hits_abi = d_hits;
-    a.work_counter = s->counters.p;
+    // a work counter of its own, so calls on other streams may run at the same time
+    uint32_t* ctr = s->trace_ctr.p + 32 * (size_t)(s->trace_slot++ % kTraceSlots);
+    a.work_counter = ctr;
     a.iter_cap = iter_cap_for(s, flags & RG_TRACE_BRUTE);
-    RG_CK(cudaMemsetAsync(s->counters.p, 0, 4, st));
+    RG_CK(cudaMemsetAsync(ctr, 0, 4, st));
     const bool any = flags & RG_ANY;
     EventPair* ev;
     if ((r = event_begin(s, any ? 1 : 0, st, &ev))) return r;

@@ -703,47 +703,77 @@ cudaError_t launch_mode(const TraceArgs& a0, cudaStream_t s, const TraceShape& s
 // float32 test enforced.  Both traversals (binary and wide) name candidates
 // by (instance, prim); the binary TLAS's instance records and the BLAS
 // triangle records locate them.
-__global__ void __launch_bounds__(256) k_refine_hits(const float4* __restrict__ rays, rg_hit* __restrict__ hits,
-                                                     uint32_t n, const InstDev* __restrict__ inst,
-                                                     const uint32_t* __restrict__ leaf_of_inst,
-                                                     const BlasDev* __restrict__ blas) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        uint32_t* rec = reinterpret_cast<uint32_t*>(hits + i);
-        uint32_t id = rec[0], prim = rec[1];
-        if (id == kMiss) continue;
-        const uint32_t id2 = rec[3], prim2 = rec[4];
-        const float t0 = __uint_as_float(rec[2]);
-        const float4 r0 = __ldg(rays + 2 * (size_t)i), r1 = __ldg(rays + 2 * (size_t)i + 1);
-        auto candidate = [&](uint32_t cid, uint32_t cprim) {
-            const InstDev* I = inst + __ldg(leaf_of_inst + cid);
-            const float4 m0 = __ldg(&I->m[0]), m1 = __ldg(&I->m[1]), m2 = __ldg(&I->m[2]);
-            const float4 meta0 = __ldg(reinterpret_cast<const float4*>(&I->nodes));  // nodes, tris
-            const uint32_t b = __ldg(&I->blas);
-            const float4* tris = reinterpret_cast<const float4*>(
-                ((unsigned long long)__float_as_uint(meta0.w) << 32) | __float_as_uint(meta0.z));
-            const uint32_t* lp = reinterpret_cast<const uint32_t*>(__ldg(reinterpret_cast<const unsigned long long*>(
-                &blas[b].leaf_of_prim)));
-            const float4* tp = tris + kTriStride * (size_t)__ldg(lp + cprim);  // axis order (x, y, z)
-            const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
-            Refined q = refine_hit(r0, r1, t0, m0, m1, m2, v0, v1, v2);
-            q.t = fminf(fmaxf(q.t, r0.w), r1.w);
-            return q;
-        };
-        Refined q = candidate(id, prim);
-        if (id2 != kMiss) {
-            const Refined q2 = candidate(id2, prim2);
-            if (hit_before(q2.t, id2, prim2, q.t, id, prim)) {
-                q = q2;
-                id = id2;
-                prim = prim2;
-            }
+// One closest hit's exact t, u, v and tie decision (record i is a hit).
+__device__ __forceinline__ void refine_one(const float4* __restrict__ rays, rg_hit* __restrict__ hits, uint32_t i,
+                                           const InstDev* __restrict__ inst, const uint32_t* __restrict__ leaf_of_inst,
+                                           const BlasDev* __restrict__ blas) {
+    uint32_t* rec = reinterpret_cast<uint32_t*>(hits + i);
+    uint32_t id = rec[0], prim = rec[1];
+    const uint32_t id2 = rec[3], prim2 = rec[4];
+    const float t0 = __uint_as_float(rec[2]);
+    const float4 r0 = __ldg(rays + 2 * (size_t)i), r1 = __ldg(rays + 2 * (size_t)i + 1);
+    auto candidate = [&](uint32_t cid, uint32_t cprim) {
+        const InstDev* I = inst + __ldg(leaf_of_inst + cid);
+        const float4 m0 = __ldg(&I->m[0]), m1 = __ldg(&I->m[1]), m2 = __ldg(&I->m[2]);
+        const float4 meta0 = __ldg(reinterpret_cast<const float4*>(&I->nodes));  // nodes, tris
+        const uint32_t b = __ldg(&I->blas);
+        const float4* tris = reinterpret_cast<const float4*>(
+            ((unsigned long long)__float_as_uint(meta0.w) << 32) | __float_as_uint(meta0.z));
+        const uint32_t* lp = reinterpret_cast<const uint32_t*>(__ldg(reinterpret_cast<const unsigned long long*>(
+            &blas[b].leaf_of_prim)));
+        const float4* tp = tris + kTriStride * (size_t)__ldg(lp + cprim);  // axis order (x, y, z)
+        const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+        Refined q = refine_hit(r0, r1, t0, m0, m1, m2, v0, v1, v2);
+        q.t = fminf(fmaxf(q.t, r0.w), r1.w);
+        return q;
+    };
+    Refined q = candidate(id, prim);
+    if (id2 != kMiss) {
+        const Refined q2 = candidate(id2, prim2);
+        if (hit_before(q2.t, id2, prim2, q.t, id, prim)) {
+            q = q2;
+            id = id2;
+            prim = prim2;
         }
-        rec[0] = id;
-        rec[1] = prim;
-        rec[2] = __float_as_uint(q.t);
-        rec[3] = __float_as_uint(q.u);
-        rec[4] = __float_as_uint(q.v);
     }
+    rec[0] = id;
+    rec[1] = prim;
+    rec[2] = __float_as_uint(q.t);
+    rec[3] = __float_as_uint(q.u);
+    rec[4] = __float_as_uint(q.v);
+}
+
+// The exact attributes of every closest hit.  Misses are already final.  A
+// warp walks tiles of 32 records and queues the hits' indices in shared
+// memory (ballots), then refines them 32 at a time, so the long float-float
+// path runs with full warps whatever the hit rate.
+constexpr int kRefineBlock = 256;
+__global__ void __launch_bounds__(kRefineBlock, 4) k_refine_hits(const float4* __restrict__ rays,
+                                                              rg_hit* __restrict__ hits, uint32_t n,
+                                                              const InstDev* __restrict__ inst,
+                                                              const uint32_t* __restrict__ leaf_of_inst,
+                                                              const BlasDev* __restrict__ blas) {
+    __shared__ uint32_t queue[kRefineBlock / 32][64];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t* q = queue[warp];
+    uint32_t qn = 0;  // queued hits (the same in every lane)
+    const size_t stride = (size_t)gridDim.x * kRefineBlock;
+    for (size_t tile = ((size_t)blockIdx.x * kRefineBlock + warp * 32u); tile < n; tile += stride) {
+        const size_t i = tile + lane;
+        const bool hit = i < n && reinterpret_cast<const uint32_t*>(hits + i)[0] != kMiss;
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, hit);
+        if (hit) q[qn + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)i;
+        qn += __popc(bal);
+        __syncwarp();
+        if (qn >= 32) {
+            refine_one(rays, hits, q[lane], inst, leaf_of_inst, blas);
+            __syncwarp();
+            if (lane + 32u < qn) q[lane] = q[lane + 32u];
+            qn -= 32;
+            __syncwarp();
+        }
+    }
+    if (lane < qn) refine_one(rays, hits, q[lane], inst, leaf_of_inst, blas);
 }
 
 }  // namespace
@@ -751,8 +781,8 @@ __global__ void __launch_bounds__(256) k_refine_hits(const float4* __restrict__ 
 cudaError_t launch_refine_hits(const float4* rays, rg_hit* hits, uint32_t n, const InstDev* inst,
                                const uint32_t* leaf_of_inst, const BlasDev* blas, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    const uint32_t blocks = min((n + 255u) / 256u, (uint32_t)device_sm_count() * 8u);
-    k_refine_hits<<<blocks, 256, 0, s>>>(rays, hits, n, inst, leaf_of_inst, blas);
+    const uint32_t blocks = min((n + kRefineBlock - 1u) / kRefineBlock, (uint32_t)device_sm_count() * 8u);
+    k_refine_hits<<<blocks, kRefineBlock, 0, s>>>(rays, hits, n, inst, leaf_of_inst, blas);
     count_launches(1);
     return cudaGetLastError();
 }
