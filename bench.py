@@ -937,6 +937,17 @@ def run_native_large(args, world, rank, local):
             "step_check": {"algorithmic_bytes_per_step": round(c_bytes + bpa * n),
                            "gbs_over_ms_per_step": round((c_bytes + bpa * n) / (step_ms / 1e3) / 1e9, 1)},
             "l2": profile_l2(prof)}
+        ipa = traffic_record(prof, "warp_inst_per_any_ray")
+        ipf = traffic_record(prof, "warp_inst_per_refine_launch")
+        if ipr is not None and ipa is not None and ipf is not None:
+            # every warp instruction of a step's two queries (the captured
+            # counts) over the step time: the issue rate of the whole step
+            step_inst = ipr * n + ipf + ipa * n
+            roofline["step"] = {"warp_instructions": round(step_inst),
+                                "achieved": round(step_inst / (step_ms / 1e3) / 1e9, 1),
+                                "frac": round(step_inst / (step_ms / 1e3) / 1e9 / issue_peak, 4),
+                                "note": "closest-hit, exact-attribute and any-hit launches' warp instructions (ncu) "
+                                        "over ms_per_step (TLAS rebuild included, its instructions not counted)"}
         if alone:
             roofline["per_launch"] += ("; the timed steps trace the any-hit query on a second stream during the "
                                        "closest-hit launch, so avg_launch_ms includes the shared time")
