@@ -675,13 +675,15 @@ cudaError_t launch_pair_t(const TraceArgs& sa, const TraceArgs& ca, int blocks_p
     return cudaGetLastError();
 }
 
-// Refill threshold when the shape leaves it open (0): per-lane refill (8 idle
-// lanes) for the closest-hit queries of rg_trace_rays, whose rays are often
-// incoherent; whole-warp refill elsewhere (faster on camera, secondary and
-// shadow rays and on incoherent any-hit queries, as measured on GB300).
+// Refill threshold when the shape leaves it open (0): per-lane refill for the
+// queries of rg_trace_rays, whose rays are often incoherent (8 idle lanes for
+// closest hits; 16 for any hits: 3.51 ms on the large any-hit query, 3.53 ms
+// with 8, against 3.66 ms for whole-warp refill once node runs cut the
+// per-lane kernel's votes); whole-warp refill elsewhere (faster on the
+// renderer's camera, secondary and shadow rays, as measured on GB300).
 template <int MODE>
 constexpr int default_refill() {
-    return MODE == kModeClosestAbi ? 8 : 32;
+    return MODE == kModeClosestAbi ? 8 : (MODE == kModeAnyAbi ? 16 : 32);
 }
 
 // Launch of one binary-traversal mode.  Shapes other than 128 threads are
