@@ -723,15 +723,14 @@ cudaError_t launch_mode(const TraceArgs& a0, cudaStream_t s, const TraceShape& s
     return launch_block_128<MODE, BRUTE, STATS, false>(a, shape, s);
 }
 
-// Completes the provisional ABI hit records of a traversal launch (emit):
-// t, u, v of the chosen triangle recomputed exactly (refine_hit), and, when the
-// traversal found a runner-up within the tie band, the two candidates decided
-// again on their exact distances rounded to float32, then instance, then
-// primitive (the tie rule).  t is kept within the ray's [tmin, tmax], which the
-// float32 test enforced.  Both traversals (binary and wide) name candidates
-// by (instance, prim); the binary TLAS's instance records and the BLAS
-// triangle records locate them.
-// One closest hit's exact t, u, v and tie decision (record i is a hit).
+// Completes one provisional ABI hit record of a traversal launch (emit;
+// record i is a hit): t, u, v of the chosen triangle recomputed exactly
+// (refine_hit), and, when the traversal found a runner-up within the tie band,
+// the two candidates decided again on their exact distances rounded to
+// float32, then instance, then primitive (the tie rule).  t is kept within the
+// ray's [tmin, tmax], which the float32 test enforced.  Both traversals (binary
+// and wide) name candidates by (instance, prim); the binary TLAS's instance
+// records and the BLAS triangle records locate them.
 __device__ __forceinline__ void refine_one(const float4* __restrict__ rays, rg_hit* __restrict__ hits, uint32_t i,
                                            const InstDev* __restrict__ inst, const uint32_t* __restrict__ leaf_of_inst,
                                            const BlasDev* __restrict__ blas) {
