@@ -1,10 +1,10 @@
 """The sort entry point that allocates no device memory, checked against the
 allocating one (rg_radix_sort_pairs) through the C ABI.
 
-Some callers cannot allocate device memory while they sort -- code inside a
-CUDA graph capture, code under a caching allocator that holds the free
-memory, frame loops that may not stall -- so librg offers a variant whose
-temporaries live in a fixed device array.  Integer work: results must be
+Some callers cannot allocate device memory while they sort -- code whose
+device memory belongs to a caching allocator that already holds what the
+GPU has free, frame loops that may not stall on an allocation -- so librg
+offers a variant whose temporaries live in a fixed device array.  Integer work: results must be
 identical.  Two calls in a row, with different data, show that whatever the
 first call leaves in the shared array does not leak into the second."""
 import numpy as np
