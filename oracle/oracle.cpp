@@ -28,9 +28,7 @@
 //        top-down recursion over the Morton order (orc_sah_build).  The paper
 //        leaves acceleration structures to the driver, so this hierarchy is a
 //        choice of the implementation; the oracle states it so that the
-//        product's build can be compared with it bit for bit.  Its hand-over
-//        to the Karras hierarchy below 40 levels is unpinned (no input found
-//        reaches that depth).
+//        product's build can be compared with it bit for bit.
 //  * Ray queries (paper Sec. 1: closest-hit, any-hit and miss per ray), in
 //    float64 on an independent object-median BVH (or brute force), using the
 //    watertight ray/triangle test of Woop, Benthin & Wald (JCGT 2013).  The

@@ -3,9 +3,10 @@ and invariants: rows of equal boxes along each axis give the balanced tree
 the heuristic's cost 2 s^2 + 2 (16 - s)^2 (least at s = 8) implies; two distant
 clusters are separated at the root; identical centroids are halved by
 position; every tree is valid with contiguous leaf ranges; the surface-area
-cost is below the LBVH's.  (The hand-over to the Karras hierarchy below 40
-levels is not pinned: no input found reaches that depth, since the binned
-heuristic splits several boxes off a geometric series per level.)"""
+cost is below the LBVH's; and the hand-over to the Karras hierarchy below 40
+levels: points 32x apart along one axis make the heuristic peel one point
+per level, and the range left at level 40 gets the radix tree that equal
+keys imply (split at the highest differing bit of the index range)."""
 import numpy as np
 import pytest
 
@@ -138,3 +139,61 @@ def test_valid_and_cheaper_than_lbvh(mesh):
     cs = sah_cost(r["lohi"][r["perm"]], first, last)
     cl = sah_cost(ref["lohi"][ref["perm"]], ref["first"], ref["last"])
     assert cs < 0.97 * cl, (cs, cl)
+
+
+def chain_to_level_40(k=42, m=9):
+    """Points on the x axis: k chain points at x = 2^(120 - 5j) and m tail
+    points at x = t 2^-100.  Each chain point lies 32x beyond the next, so in
+    any range the largest one is alone in bin 15 and all others share bin 0;
+    with zero y and z extents every split costs 0 and the first boundary of
+    axis 0 wins.  The heuristic therefore peels one chain point per level, and
+    the range left at level 40 (the last k - 40 chain points and the tail) is
+    handed to the Karras hierarchy of its keys, which are all 0 (they quantise
+    below the first Morton cell)."""
+    x = np.r_[np.float32(2.0) ** (120 - 5 * np.arange(k)), np.arange(m) * np.float32(2.0 ** -100)].astype(np.float32)
+    p = np.c_[x, np.zeros_like(x), np.zeros_like(x)]
+    return boxes_mesh(p, p)
+
+
+def karras_equal_keys(r, d, b):
+    """Children of the radix tree over r equal keys, internal node j numbered
+    d + j and leaf j numbered b + j.  With every key equal, a node over the
+    index range [f, l] splits after gamma, where the highest bit in which f
+    and l differ turns on; as in Karras 2012 the root is node 0, a left
+    child [f, gamma] is node gamma and a right child [gamma + 1, l] is node
+    gamma + 1."""
+    child = {}
+    todo = [(0, 0, r - 1)]
+    while todo:
+        node, f, l = todo.pop()
+        top = 1 << ((f ^ l).bit_length() - 1)
+        gamma = (l & ~(top - 1)) - 1
+        child[d + node] = (LEAF | (b + gamma) if gamma == f else d + gamma,
+                           LEAF | (b + gamma + 1) if gamma + 1 == l else d + gamma + 1)
+        if gamma != f:
+            todo.append((gamma, f, gamma))
+        if gamma + 1 != l:
+            todo.append((gamma + 1, gamma + 1, l))
+    return child
+
+
+@pytest.mark.parametrize("bits", [10, 21])
+def test_hand_over_to_karras_at_level_40(bits):
+    k, m = 42, 9
+    v, i = chain_to_level_40(k, m)
+    n = k + m
+    r = oracle.sah_reference(v, i, bits)
+    first, last, depth = tree_ranges(r["child"], n)
+    # levels 0..39: node L peels chain point L into leaf n - 1 - L
+    for lv in range(40):
+        assert tuple(int(c) for c in r["child"][lv]) == (lv + 1, LEAF | (n - 1 - lv)), lv
+    assert np.array_equal(r["perm"][n - 40:], np.arange(40)[::-1])
+    # level 40: the Karras tree of the remaining r = n - 40 points, in their
+    # Morton order (all keys 0, so index order: chain points 40, 41, the tail)
+    rest = n - 40
+    assert np.array_equal(r["perm"][:rest], np.arange(40, n))
+    want = karras_equal_keys(rest, 40, 0)
+    assert len(want) == rest - 1
+    for node, ch in want.items():
+        assert tuple(int(c) for c in r["child"][node]) == ch, node
+    assert depth.max() == 40 + (rest - 1).bit_length() - 1
