@@ -46,10 +46,10 @@ def plain_differ(h, ref):
     id_diff = (h["inst"] != ref["inst"]) | (h["prim"] != ref["prim"])
     hit = ~id_diff & (ref["inst"] != MISS)
     t_ref = ref["t"]
-    dt = np.abs(h["t"].astype(np.float64) - t_ref)
-    du = np.abs(h["u"].astype(np.float64) - ref["u"])
-    dv = np.abs(h["v"].astype(np.float64) - ref["v"])
-    with np.errstate(invalid="ignore"):
+    with np.errstate(invalid="ignore"):   # inf - inf where both records are misses; those rays are checked below
+        dt = np.abs(h["t"].astype(np.float64) - t_ref)
+        du = np.abs(h["u"].astype(np.float64) - ref["u"])
+        dv = np.abs(h["v"].astype(np.float64) - ref["v"])
         bad_t = hit & ~(dt <= REL_T * np.abs(t_ref))
         bad_u = hit & ~(du <= REL_B * np.maximum(np.abs(ref["u"]), B_FLOOR))
         bad_v = hit & ~(dv <= REL_B * np.maximum(np.abs(ref["v"]), B_FLOOR))
