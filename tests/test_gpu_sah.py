@@ -18,7 +18,7 @@ import paper_2001_09792_gb300 as rg
 import scenegen as g
 from test_gpu_build import LEAF, MESHES, cu, node_fields
 from test_gpu_trace import KAPPA, MISS, REL_T, compare_closest, trace, _random_scene
-from test_oracle_sah import boxes_mesh, tree_ranges
+from test_oracle_sah import boxes_mesh, chain_to_level_40, tree_ranges
 
 pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("librg")]
 
@@ -81,8 +81,10 @@ def peeled_series(n=70):
 
 
 # large3 (409,600 triangles) has levels of more than 65,536 segments, which
-# the build runs in several slices
-SAH_MESHES = dict(MESHES, peeled=peeled_series(), large1=g.large_scene().meshes[1], large3=g.large_scene().meshes[3])
+# the build runs in several slices; chain40 reaches the hand-over to the
+# Karras hierarchy at level 40
+SAH_MESHES = dict(MESHES, peeled=peeled_series(), chain40=chain_to_level_40(), large1=g.large_scene().meshes[1],
+                  large3=g.large_scene().meshes[3])
 
 
 @pytest.mark.parametrize("name", list(SAH_MESHES))
@@ -194,6 +196,25 @@ def test_sah_tlas_with_coincident_instances(n_inst, dup):
     s.M[a:b] = s.M[a]
     s.mesh_id[a:b] = s.mesh_id[a]
     check_sah_tlas(s, n_inst)
+
+
+def test_sah_tlas_hand_over_at_level_40():
+    """Instances of a one-point mesh placed at the points of
+    chain_to_level_40: their world boxes are those points, so the one-block
+    TLAS build peels one instance per level and hands the 11 left at level
+    40 to the Karras hierarchy, as the oracle does."""
+    from test_oracle_sah import chain_to_level_40
+    v, _ = chain_to_level_40()
+    n = v.shape[0] // 3
+    M = np.zeros((n, 3, 4), np.float32)
+    M[:, 0, 0] = M[:, 1, 1] = M[:, 2, 2] = 1.0
+    M[:, :, 3] = v[0::3]
+    point = (np.zeros((3, 3), np.float32), np.array([[0, 1, 2]], np.uint32))
+    s = g.Scene(meshes=[point], M=M, mesh_id=np.zeros(n, np.uint32), material_id=np.zeros(n, np.uint32),
+                mat_type=np.zeros(1, np.uint32), mat_albedo=np.full((1, 3), 0.5, np.float32),
+                mat_ior=np.ones(1, np.float32), light_pos=np.array([[0, 50, 0]], np.float32),
+                light_I=np.ones((1, 3), np.float32))
+    check_sah_tlas(s, n)
 
 
 def check_sah_tlas(s, n_inst):
