@@ -27,6 +27,10 @@
  *  - All device geometry is float32.  float64 is used on the device only to
  *    invert instance transforms.
  *  - Calls on one scene must not run concurrently from several host threads.
+ *  - A scene lives on the CUDA device that was current when it was created.
+ *    Every call on it makes that device current for the calling thread (and
+ *    leaves it current); the device buffers and the stream passed to it must
+ *    belong to that device.
  */
 #ifndef RG_H
 #define RG_H

@@ -184,10 +184,12 @@ def _torch():
     return torch
 
 
-def _stream(stream):
+def _stream(stream, device=None):
+    """The stream argument: `stream`, or the current stream of `device` (an
+    index; None: the current device)."""
     torch = _torch()
     if stream is None:
-        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
     if isinstance(stream, torch.cuda.Stream):
         return ctypes.c_void_p(stream.cuda_stream)
     return ctypes.c_void_p(int(stream))
@@ -208,10 +210,31 @@ def _dev(t, dtype, shape_tail=None, name="tensor"):
 
 # ---------------------------------------------------------------- scene
 
+# CUDA device index of each scene made here (a scene lives on the device that
+# was current when it was created, and its calls run there)
+_SCENE_DEVICE = {}
+
+
+def _scene_dev(scene):
+    """Device index of a scene made through this binding (None otherwise)."""
+    return _SCENE_DEVICE.get(scene.value if isinstance(scene, ctypes.c_void_p) else scene)
+
+
+def _same_device(dev, **tensors):
+    """Raise unless every given tensor is on CUDA device `dev` (None: no check):
+    the library would hand another GPU's addresses to the scene's kernels."""
+    if dev is None:
+        return
+    for name, t in tensors.items():
+        if t is not None and t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the scene on cuda:{dev}")
+
+
 def rg_scene_create(background=(0.2, 0.3, 0.5), ambient=0.1, flags=0):
     d = rg_scene_desc(f32x3(*background), float(ambient), int(flags))
     h = ctypes.c_void_p()
     _check(lib().rg_scene_create(ctypes.byref(h), ctypes.byref(d)))
+    _SCENE_DEVICE[h.value] = _torch().cuda.current_device()
     return h
 
 
@@ -219,11 +242,15 @@ def rg_scene_create_shared(src):
     """A scene sharing src's BLAS, with copies of its materials and lights."""
     h = ctypes.c_void_p()
     _check(lib().rg_scene_create_shared(ctypes.byref(h), src))
+    dev = _scene_dev(src)
+    if dev is not None:
+        _SCENE_DEVICE[h.value] = dev
     return h
 
 
 def rg_scene_destroy(scene):
     _check(lib().rg_scene_destroy(scene))
+    _SCENE_DEVICE.pop(scene.value if isinstance(scene, ctypes.c_void_p) else scene, None)
 
 
 def rg_blas_build(scene, vtx, idx, flags=RG_MORTON30, stream=None):
@@ -231,8 +258,11 @@ def rg_blas_build(scene, vtx, idx, flags=RG_MORTON30, stream=None):
     torch = _torch()
     pv = _dev(vtx, torch.float32, (3,), "vtx")
     pi = _dev(idx, torch.int32, (3,), "idx")
+    dev = _scene_dev(scene)
+    _same_device(dev, vtx=vtx, idx=idx)
     out = ctypes.c_uint32()
-    _check(lib().rg_blas_build(scene, pv, vtx.shape[0], pi, idx.shape[0], flags, ctypes.byref(out), _stream(stream)))
+    _check(lib().rg_blas_build(scene, pv, vtx.shape[0], pi, idx.shape[0], flags, ctypes.byref(out),
+                               _stream(stream, dev)))
     return out.value
 
 
@@ -252,12 +282,18 @@ def pack_instances(M, blas_ids, material_ids=None):
 def rg_tlas_build(scene, inst, stream=None):
     """inst: (n,16) float32 CUDA tensor of rg_instance records (see pack_instances)."""
     torch = _torch()
-    _check(lib().rg_tlas_build(scene, _dev(inst, torch.float32, (16,), "inst"), inst.shape[0], _stream(stream)))
+    p = _dev(inst, torch.float32, (16,), "inst")
+    dev = _scene_dev(scene)
+    _same_device(dev, inst=inst)
+    _check(lib().rg_tlas_build(scene, p, inst.shape[0], _stream(stream, dev)))
 
 
 def rg_tlas_refit(scene, inst, stream=None):
     torch = _torch()
-    _check(lib().rg_tlas_refit(scene, _dev(inst, torch.float32, (16,), "inst"), inst.shape[0], _stream(stream)))
+    p = _dev(inst, torch.float32, (16,), "inst")
+    dev = _scene_dev(scene)
+    _same_device(dev, inst=inst)
+    _check(lib().rg_tlas_refit(scene, p, inst.shape[0], _stream(stream, dev)))
 
 
 def rg_scene_set_materials(scene, types, albedo, ior):
@@ -292,7 +328,9 @@ def rg_trace_rays(scene, rays, flags=RG_CLOSEST, hits=None, stream=None):
     ph = _dev(hits, torch.int32, (5,), "hits")
     if hits.shape[0] < n:
         raise ValueError("hits buffer too small")
-    _check(lib().rg_trace_rays(scene, pr, n, flags, ph, _stream(stream)))
+    dev = _scene_dev(scene)
+    _same_device(dev, rays=rays, hits=hits)
+    _check(lib().rg_trace_rays(scene, pr, n, flags, ph, _stream(stream, dev)))
     return hits
 
 
@@ -312,13 +350,16 @@ def make_camera(camera):
 def rg_render(scene, camera, width, height, max_depth, out=None, stream=None):
     """Render into a (h, w, 4) float32 CUDA tensor (allocated if out is None)."""
     torch = _torch()
+    dev = _scene_dev(scene)
     if out is None:
-        out = torch.empty((height, width, 4), dtype=torch.float32, device="cuda")
+        out = torch.empty((height, width, 4), dtype=torch.float32,
+                          device="cuda" if dev is None else torch.device("cuda", dev))
     if out.numel() != width * height * 4 or out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous():
         raise ValueError("out must be a contiguous float32 CUDA tensor of w*h*4 elements")
+    _same_device(dev, out=out)
     cam = camera if isinstance(camera, rg_camera) else make_camera(camera)
     _check(lib().rg_render(scene, ctypes.byref(cam), width, height, max_depth, ctypes.c_void_p(out.data_ptr()),
-                           _stream(stream)))
+                           _stream(stream, dev)))
     return out
 
 
@@ -330,10 +371,13 @@ def rg_fxaa(image, out=None, stream=None):
         raise ValueError("image must be a contiguous (h, w, 4) float32 CUDA tensor")
     if out is None:
         out = torch.empty_like(image)
-    if out.shape != image.shape or out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous():
-        raise ValueError("out must match the image")
+    if out.shape != image.shape or out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous() \
+            or out.device != image.device:
+        raise ValueError("out must match the image (shape, type, device)")
     h, w = image.shape[0], image.shape[1]
-    _check(lib().rg_fxaa(ctypes.c_void_p(image.data_ptr()), w, h, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    with torch.cuda.device(image.device):
+        _check(lib().rg_fxaa(ctypes.c_void_p(image.data_ptr()), w, h, ctypes.c_void_p(out.data_ptr()),
+                             _stream(stream)))
     return out
 
 

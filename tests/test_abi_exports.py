@@ -146,3 +146,26 @@ def test_product_path_has_no_cpu_fallback():
     with pytest.raises(rg.RgError) as e:
         rg.rg_scene_create()
     assert e.value.status == rg.RG_ERR_CUDA
+
+
+def test_binding_checks_tensor_devices_against_the_scene():
+    """The binding knows the device of each scene it made and refuses tensors
+    on another device (their addresses would reach the scene's kernels);
+    scenes it did not make are not checked.  A stand-in object carries the
+    only attribute the check reads."""
+    import types
+
+    def on(idx):
+        return types.SimpleNamespace(device=types.SimpleNamespace(index=idx))
+
+    rg._same_device(None, rays=on(1))
+    rg._same_device(0, rays=on(0), hits=None)
+    with pytest.raises(ValueError, match="rays is on cuda:1, the scene on cuda:0"):
+        rg._same_device(0, rays=on(1))
+    h = ctypes.c_void_p(0x1234560)
+    assert rg._scene_dev(h) is None
+    rg._SCENE_DEVICE[h.value] = 2
+    try:
+        assert rg._scene_dev(h) == 2 and rg._scene_dev(h.value) == 2
+    finally:
+        del rg._SCENE_DEVICE[h.value]
