@@ -493,6 +493,19 @@ def test_snell_tir_schlick():
         else:
             T2, R2 = out
             assert abs(ior * math.sin(th) - math.hypot(T2[0], T2[2])) < 1e-12
+    # Schlick at 60 degrees from vacuum: 0.04 + 0.96 (1 - 1/2)^5 = 0.07
+    _, R = oracle.refract(np.array([math.sin(math.radians(60)), -0.5, 0.0]), n, True, ior)
+    assert abs(R - 0.07) < 1e-15
+    # the cosine is taken on the vacuum side, so a ray leaving the glass along
+    # the reversed refracted direction of an entering ray is weighted alike
+    for deg in (10.0, 35.0, 60.0, 85.0):
+        th = math.radians(deg)
+        d = np.array([math.sin(th), -math.cos(th), 0.0])
+        T, R_in = oracle.refract(d, n, True, ior)
+        back = np.array([-T[0], -T[1], -T[2]])          # inside, travelling up to the face
+        T_out, R_out = oracle.refract(back, -n, False, ior)
+        np.testing.assert_allclose(T_out, -d, atol=1e-14)
+        assert abs(R_in - R_out) < 1e-14, (deg, R_in, R_out)
     # a slab with parallel faces: the exit direction equals the entry direction
     d = np.array([0.6, -0.8, 0.0])
     T, _ = oracle.refract(d, n, True, ior)
@@ -524,6 +537,11 @@ def test_lambert_single_plane():
     want = a * AMB + a * 1.0 * cos
     np.testing.assert_allclose(r["rgba"][0], [want, want, want, 1.0], rtol=1e-12)
     assert r["closest_rays"] == 1 and r["shadow_rays"] == 1
+    # a light behind the lit side contributes nothing and casts no shadow ray
+    O = shading_scene([(v, i)], [g.affine(np.eye(3), [0, 0, 0])], [0], [(0, (a, a, a), 1.0)], (3.0, -4.0, 0.0))
+    r = O.render(cam, 1, 1, 1)
+    np.testing.assert_allclose(r["rgba"][0], [a * AMB, a * AMB, a * AMB, 1.0], rtol=1e-12)
+    assert r["closest_rays"] == 1 and r["shadow_rays"] == 0
 
 
 def test_shadow_and_miss():
@@ -600,6 +618,34 @@ def test_glass_slab_passes_straight_through_pixel():
     np.testing.assert_allclose(r["rgba"][0, :3], want, rtol=1e-7)
 
 
+def test_instanced_shading_equals_pretransformed_mesh():
+    """A mesh under a rotated, non-uniformly scaled and sheared instance
+    renders like the same mesh with its vertices moved to world space (and
+    an identity instance): the shading normal is the object normal carried by
+    the inverse transpose, the hit point and the reflected and refracted rays
+    follow from the world-space geometry."""
+    rng = np.random.default_rng(12)
+    A = g.random_rotation(rng) @ np.diag([2.0, 0.5, 1.25]) @ np.array([[1, 0.4, 0], [0, 1, 0], [0, 0.3, 1]])
+    M = np.zeros((3, 4))
+    M[:, :3] = A
+    M[:, 3] = [0.5, 1.0, -0.25]
+    M = M.astype(np.float32)
+    v, i = g.make_mesh("ico", 2)
+    floor_v, floor_i = g.quad_mesh(40.0, -4.0)
+    vw = (v.astype(np.float64) @ M[:, :3].astype(np.float64).T + M[:, 3]).astype(np.float32)
+    mats = [(0, (0.5, 0.5, 0.5), 1.0), (0, (0.75, 0.5, 0.25), 1.0), (1, (0.9, 0.9, 0.9), 1.0), (2, (1, 1, 1), 1.5)]
+    cam = dict(eye=(1.0, 6.0, 9.0), target=(0.5, 0.5, 0.0), up=(0, 1, 0), vfov=30.0)
+    for mat in (1, 2, 3):   # diffuse, mirror, glass
+        a = shading_scene([(v, i), (floor_v, floor_i)], [M, g.affine(np.eye(3), [0, 0, 0])], [0, 1],
+                          [mats[mat], mats[0]], (4.0, 8.0, 6.0))
+        b = shading_scene([(vw, i), (floor_v, floor_i)], [g.affine(np.eye(3), [0, 0, 0])] * 2, [0, 1],
+                          [mats[mat], mats[0]], (4.0, 8.0, 6.0))
+        ra, rb = a.render(cam, 24, 24, 4), b.render(cam, 24, 24, 4)
+        ok = ~(ra["ambiguous"] | rb["ambiguous"])
+        assert ok.mean() > 0.9 and ra["rgba"][ok, 3].mean() > 0.2
+        np.testing.assert_allclose(ra["rgba"][ok], rb["rgba"][ok], atol=2e-5, err_msg=f"material {mat}")
+
+
 # ----------------------------------------------------------- camera and tiny scene
 
 def test_camera_model():
@@ -617,6 +663,13 @@ def test_camera_model():
     assert abs(up_ang - want) < 1e-9
     # top row looks up more than the forward axis
     assert d[0] @ np.array([0, 1, 0]) > F @ np.array([0, 1, 0])
+    # horizontal angle between the end pixels of the centre row (odd height):
+    # 2 atan((1 - 1/w) (w/h) tan 30), the vertical field widened by the aspect ratio
+    h = 49
+    dd = oracle.camera_dirs(cam, w, h, np.array([24 * w, 24 * w + w - 1], np.uint32))
+    ang = math.degrees(math.acos(np.clip(dd[0] @ dd[1], -1, 1)))
+    want = 2 * math.degrees(math.atan((1 - 1 / w) * (w / h) * math.tan(math.radians(30))))
+    assert abs(ang - want) < 1e-9
 
 
 def test_tiny_scene_render_sanity():
