@@ -80,3 +80,16 @@ def test_any_hit_segment_ending_at_the_surface_is_ambiguous():
                                 (6.0, True, False)]:
         out = O.trace(down([(0.5, -0.5)], tmax=tmax), any_hit=True)
         assert out["occluded"][0] == occluded and out["ambiguous"][0] == amb, tmax
+
+
+def test_error_band_width_at_an_outer_edge():
+    """The band's width is the stated float32 error bound: for these rays
+    (identity instance, origin height 5, unit direction, vertices of
+    magnitude 1, hit distance 5) eta = 16 * 2^-24 * (5 + 5 * 1 + 1).  A ray
+    passing 0.95 eta outside the quad's edge is flagged, one passing 1.05 eta
+    outside is a clear miss."""
+    eta = 16 * 2.0 ** -24 * (5 + 5 + 1)
+    out = quads([0.0]).trace(down([(1 + 0.95 * eta, 0.2), (1 + 1.05 * eta, 0.2),
+                                   (0.2, -1 - 0.95 * eta), (0.2, -1 - 1.05 * eta)]))
+    assert (out["inst"] == MISS).all()
+    assert list(out["ambiguous"]) == [True, False, True, False]

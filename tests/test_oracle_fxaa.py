@@ -121,3 +121,48 @@ def test_tiny_sizes():
         img = np.random.default_rng(h * 10 + w).uniform(0, 1, (h, w, 4)).astype(np.float32)
         out = oracle.fxaa(img)
         assert out.shape == img.shape and np.all(np.isfinite(out))
+
+
+def straight_edge(left, right, h=6, w=12):
+    img = np.ones((h, w, 4), np.float32)
+    img[:, : w // 2, :3] = left
+    img[:, w // 2:, :3] = right
+    return img
+
+
+@pytest.mark.parametrize("left,right,why", [
+    # luma weights 0.299 / 0.587 / 0.114: lumas 0.547 | 0.698, range 0.151
+    # above 0.125 * 0.698; with red and green weights swapped the lumas would
+    # be 0.766 | 0.698 and the range (0.068) below 0.125 * 0.766
+    ((1.0, 0.0, 0.0), (0.55, 0.55, 0.0), "weights"),
+    # luma is the square root: 0.141 | 0.2, range 0.059 above 0.0312; the
+    # linear values (0.02 | 0.04) would stay below it
+    ((0.02, 0.02, 0.02), (0.04, 0.04, 0.04), "square root"),
+    # range 0.837 - 0.707 = 0.130 between 0.125 and 0.25 of the brighter luma
+    ((0.5, 0.5, 0.5), (0.7, 0.7, 0.7), "relative threshold"),
+])
+def test_edge_thresholds(left, right, why):
+    """A straight edge above the contrast threshold: both edge pixels move
+    by sub(1/3) toward each other (no edge end is found), whatever the two
+    colours, since the contrast is normalised by the range."""
+    img = straight_edge(left, right)
+    out = oracle.fxaa(img)
+    a, b = np.array(left, np.float64), np.array(right, np.float64)
+    np.testing.assert_allclose(out[3, 5, :3], a + sub(1 / 3) * (b - a), atol=2e-6, err_msg=why)
+    np.testing.assert_allclose(out[3, 6, :3], b + sub(1 / 3) * (a - b), atol=2e-6, err_msg=why)
+    assert np.array_equal(out[:, :4], img[:, :4])
+
+
+def test_edge_end_at_a_quarter_of_the_step():
+    """The black block of block_image on a grey floor (0.49, luma 0.7)
+    instead of a white one: searching along the top edge at y = 9.5 the
+    bilinear luma is 0.5 over the block and 0.85 beyond it, 0.35 from the
+    edge luma.  That is at least a quarter of the pixel's luma step (1), so
+    the ends are found at x = 19 and 28 as on the white floor, and the black
+    pixel (24, 10) blends by 0.5 - 4/9 = 1/18 again; a search that needed
+    half the step would run to the image border and leave sub(1/3)."""
+    img = block_image()
+    img[10:, :20, :3] = 0.49
+    img[10:, 28:, :3] = 0.49
+    out = oracle.fxaa(img)
+    np.testing.assert_allclose(out[10, 24, :3], 1 / 18, atol=2e-6)

@@ -113,12 +113,42 @@ def test_identical_centroids_are_halved():
     i = np.zeros((37, 3), np.uint32) + [0, 1, 2]
     r = oracle.sah_reference(v, i)
     first, last, _ = tree_ranges(r["child"], 37)
+    assert np.array_equal(np.sort(r["perm"]), np.arange(37))
     for k, c in enumerate(r["child"]):
         n = last[k] - first[k] + 1
         if n <= 2:
             continue
         left = 1 if c[0] & LEAF else last[c[0]] - first[k] + 1
         assert left == n // 2
+
+
+def test_large_box_is_split_off_alone():
+    """Fourteen small boxes in a row, one more small box at x = 23 and a
+    10-unit cube at x = 20..30.  Isolating the cube costs 23.75 * 15 + 300 =
+    656.25 (half areas times counts), pairing it with its small neighbour
+    13.75 * 14 + 240 * 2 = 672.5, so the root splits the cube off alone; the
+    small neighbour sits one bin below the cube (bins 14 and 15 of the 16),
+    so only a binning with all 16 bins can separate them."""
+    lo = np.zeros((16, 3), np.float32)
+    hi = np.zeros((16, 3), np.float32)
+    for k in range(14):
+        lo[k], hi[k] = [k, 0, 0], [k + 0.5, 0.5, 0.5]
+    lo[14], hi[14] = [23, 0, 0], [23.5, 0.5, 0.5]
+    lo[15], hi[15] = [20, -5, -5], [30, 5, 5]
+    v, i = boxes_mesh(lo, hi)
+    r = oracle.sah_reference(v, i)
+    assert int(r["child"][0][1]) == LEAF | 15 and r["perm"][15] == 15
+    tree_ranges(r["child"], 16)
+
+
+def test_equal_costs_keep_the_first_axis():
+    """Four equal boxes at the corners of a square in the xy plane: the x and
+    y splits cost the same (2 * 11 each side), and the first candidate in
+    the order of axes wins, so the root separates the two columns."""
+    lo = np.array([[0, 0, 0], [4, 0, 0], [0, 4, 0], [4, 4, 0]], np.float32)
+    v, i = boxes_mesh(lo, lo + np.float32(1))
+    r = oracle.sah_reference(v, i)
+    assert list(r["perm"]) == [0, 2, 1, 3]
 
 
 @pytest.mark.parametrize("mesh", ["ico4", "soup", "large1"])
