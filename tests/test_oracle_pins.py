@@ -544,6 +544,19 @@ def test_lambert_single_plane():
     assert r["closest_rays"] == 1 and r["shadow_rays"] == 0
 
 
+def test_lambert_colours_multiply_per_channel():
+    """A coloured light on a coloured plane: each channel is the albedo times
+    (ambient + intensity * cosine) of that channel."""
+    v, i = g.quad_mesh(20.0, 0.0)
+    alb, I = (0.75, 0.5, 0.25), (0.5, 1.0, 2.0)
+    O = shading_scene([(v, i)], [g.affine(np.eye(3), [0, 0, 0])], [0], [(0, alb, 1.0)], (3.0, 4.0, 0.0), I)
+    cam = dict(eye=(0, 10, 0), target=(0, 0, 0), up=(0, 0, -1), vfov=10.0)
+    r = O.render(cam, 1, 1, 1)
+    cos = (4 - 1e-4) / math.sqrt(9 + (4 - 1e-4) ** 2)
+    want = [a * AMB + a * li * cos for a, li in zip(alb, I)]
+    np.testing.assert_allclose(r["rgba"][0, :3], want, rtol=1e-12)
+
+
 def test_shadow_and_miss():
     v, i = g.quad_mesh(20.0, 0.0)
     cv, ci = g.cube_mesh(0.5)
@@ -581,6 +594,12 @@ def test_mirror_to_wall():
     # with max_depth 1 the mirror contributes nothing
     r = O.render(cam, 1, 1, 1)
     np.testing.assert_allclose(r["rgba"][0, :3], [0, 0, 0], atol=0)
+    # a coloured mirror tints each channel of what it reflects by its own factor
+    tints = (0.875, 0.5, 0.25)
+    O = shading_scene([(floor_v, floor_i), (wv, wi)], [g.affine(np.eye(3), [0, 0, 0])] * 2, [0, 1],
+                      [(1, tints, 1.0), (0, (a, a, a), 1.0)], (2.0, 2.0, 0.0))
+    r = O.render(cam, 1, 1, 2)
+    np.testing.assert_allclose(r["rgba"][0, :3], [tt * (a * AMB + a * 1.0 * cos) for tt in tints], rtol=1e-9)
 
 
 def test_glass_slab_passes_straight_through_pixel():
@@ -644,6 +663,24 @@ def test_instanced_shading_equals_pretransformed_mesh():
         ok = ~(ra["ambiguous"] | rb["ambiguous"])
         assert ok.mean() > 0.9 and ra["rgba"][ok, 3].mean() > 0.2
         np.testing.assert_allclose(ra["rgba"][ok], rb["rgba"][ok], atol=2e-5, err_msg=f"material {mat}")
+
+
+def test_total_internal_reflection_traps_the_ray():
+    """A camera inside a glass cube (half size 5) at (-4.5, 0, 0) looking along
+    (1, 0, -1): the ray meets the faces at 45 degrees, beyond the critical
+    angle 41.8, in the closed loop bottom (x = 0.5), right (z = -0.5), top
+    (x = -0.5), left (z = 0.5), each time far from the face's edges and its
+    diagonal.  Every bounce is a total internal reflection that stays inside,
+    so the path ends at the depth limit with nothing: black, alpha 1."""
+    cv, ci = g.cube_mesh(0.5)
+    O = shading_scene([(cv, ci)], [g.affine(np.eye(3) * 10.0, [0, 0, 0])], [0], [(2, (1, 1, 1), 1.5)],
+                      (0.0, 50.0, 0.0))
+    cam = dict(eye=(-4.5, 0, 0), target=(-3.5, 0, -1), up=(0, 1, 0), vfov=1.0)
+    for depth in (2, 5, 8):
+        r = O.render(cam, 1, 1, depth)
+        assert not r["ambiguous"][0]
+        np.testing.assert_array_equal(r["rgba"][0], [0, 0, 0, 1])
+        assert r["closest_rays"] == depth and r["shadow_rays"] == 0
 
 
 # ----------------------------------------------------------- camera and tiny scene
