@@ -42,7 +42,9 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
+            # RG_ORACLE_LIB: a copy of the oracle built elsewhere (the planted-slip
+            # check, plant_slips.py, points it at a copy with one change)
+            L = ctypes.CDLL(os.environ.get("RG_ORACLE_LIB") or build())
             P = ctypes.c_void_p
             u32, i64, i32, f64, f32 = ctypes.c_uint32, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_float
             L.orc_tri_bounds.argtypes = [P, u32, P, u32, P]
